@@ -1,0 +1,202 @@
+/*
+ * dda.h - C ABI of the GB300 preconditioned discrete dipole approximation.
+ *
+ * The library solves the voxelised volume-integral-equation system of
+ * Groth, Polimeridis & White, "Preconditioning the discrete dipole
+ * approximation" (arXiv 1903.09802):
+ *
+ *     (alpha^{-1} - dx^3 G) c = E_inc                       (Section 2.2)
+ *
+ * with G the block-Toeplitz Toeplitz-block (BTTB) matrix of the dyadic Green
+ * function sampled on a uniform l x m x n voxel box (Algorithm 1), applied
+ * with a zero-padded 3-D FFT; the multilevel (Chan-Olkin) circulant
+ * preconditioner P = alpha_tilde^{-1} I - dx^3 C (Section 3, eq. 20) with
+ * the circulant taken on all three levels; and restarted GMRES.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every device buffer is allocated and owned by the caller.  A plan keeps
+ *   pointers into the caller's workspace and never allocates device memory.
+ * - Box fields are complex, layout [rhs][component 0..2][z][y][x], x fastest.
+ *   Precision DDA_C128 means interleaved double (re, im); DDA_C64 means
+ *   interleaved float.  Air voxels (material 0) belong to the box; their rows
+ *   of the box matrix are alpha_tilde^{-1} c (decoupled), so with a zero
+ *   right-hand side on air their unknowns solve to zero and the scatterer's
+ *   unknowns are those of the paper's system (eq. 8: air carries no
+ *   polarization).
+ * - Unknowns are the paper's c (eq. 9); dipole moments are p = dx^3 c.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy stream).  Calls
+ *   are stream-ordered and asynchronous unless they return host results
+ *   (dda_solve stats, dda_cross_sections), which synchronise that stream.
+ * - Errors come back as dda_status_t; arguments are checked before any
+ *   launch; a failing call leaves outputs unspecified.  dda_last_error()
+ *   returns a thread-local description of the last failure.  No entry point
+ *   aborts the process or throws across the ABI.
+ * - One plan must not be used from two host threads at once.
+ */
+#ifndef DDA_H_
+#define DDA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DDA_OK = 0,
+  DDA_ERR_INVALID_ARG = 1,
+  DDA_ERR_UNSUPPORTED_SIZE = 2,
+  DDA_ERR_WORKSPACE = 3,
+  DDA_ERR_CUDA = 4,
+  DDA_ERR_NOT_CONVERGED = 5,
+  DDA_ERR_BREAKDOWN = 6,
+  DDA_ERR_SINGULAR_PRECOND = 7,
+  DDA_ERR_NAN = 8,
+  DDA_ERR_TIMEOUT = 9,
+  DDA_ERR_NO_PRECOND = 10
+} dda_status_t;
+
+typedef enum { DDA_C128 = 0, DDA_C64 = 1 } dda_precision_t;
+
+/* Bits of dda_plan_desc_t.precisions: which spectra the plan stores. */
+#define DDA_PLAN_C128 1
+#define DDA_PLAN_C64 2
+
+typedef struct dda_plan_s* dda_plan_t;
+
+typedef struct {
+  int32_t l, m, n;       /* box edges along x, y, z: powers of two, 1..512      */
+  double dx;             /* voxel edge Delta (length unit of the caller)        */
+  double k;              /* wavenumber in the same unit                          */
+  int32_t n_materials;   /* K >= 1 materials; voxel material 0 is air           */
+  int32_t max_rhs;       /* largest right-hand-side batch used with this plan   */
+  int32_t krylov_m;      /* GMRES restart length to reserve (0: no solver)      */
+  int32_t precisions;    /* DDA_PLAN_C128 | DDA_PLAN_C64                         */
+} dda_plan_desc_t;
+
+/* Plane wave E_inc = pol * exp(i k dir . r), r measured from the box centre.
+ * dir and pol are unit vectors with dir . pol = 0 (checked to 1e-9). */
+typedef struct {
+  double dir[3];
+  double pol[3];
+} dda_incidence_t;
+
+typedef struct {
+  double tol;            /* stop when ||b - A x||_2 / ||b||_2 <= tol (FP64 residual)  */
+  int32_t max_iters;     /* cap on inner GMRES iterations per right-hand side          */
+  int32_t restart;       /* GMRES(m) restart length, 1 <= restart <= plan krylov_m     */
+  int32_t precond;       /* 0: none, 3: three-level circulant (dda_precond_build first) */
+  int32_t inner_prec;    /* DDA_C128: plain FP64 GMRES; DDA_C64: complex64 GMRES cycles
+                            inside FP64 iterative refinement                          */
+  double inner_tol;      /* a cycle ends early once its residual estimate falls below
+                            inner_tol times the cycle's starting residual (0: only tol) */
+} dda_solve_opts_t;
+
+typedef struct {
+  int32_t iters;         /* inner GMRES iterations (matvecs with A P^{-1})             */
+  int32_t cycles;        /* restart cycles = FP64 residual evaluations after the first */
+  int32_t converged;     /* 1 when the FP64 relative residual reached tol              */
+  int32_t status;        /* dda_status_t of this right-hand side                       */
+  double rel_resid;      /* final ||b - A x|| / ||b|| evaluated in complex128          */
+} dda_rhs_stats_t;
+
+/* Bytes of device workspace a plan with this description needs (0 when the
+ * description is invalid; dda_last_error() says why).  The workspace holds
+ * the kernel spectrum and the circulant spectrum (compressed to one octant by
+ * the parity of each Green-function component), the FFT scratch for max_rhs
+ * right-hand sides and, when krylov_m > 0, the Krylov basis and GMRES state. */
+size_t dda_workspace_size(const dda_plan_desc_t* desc);
+
+/* Build a plan: evaluates the Green function at every signed voxel offset
+ * (Algorithm 1, extended to negative offsets), embeds it in a (2l, 2m, 2n)
+ * circulant whose wrap index is zero, transforms it by FFT and stores the
+ * spectrum of each of the six unique blocks (Section 2.2).
+ *   d_mat   device uint8 [n][m][l] material index per voxel, 0 = air, 1..K.
+ *           The pointer is kept by the plan and must stay valid.
+ *   h_eps   host double[2*K]: (re, im) relative permittivity of materials 1..K
+ *           (eps = m^2, Section 2.1).  Copied.
+ *   d_work  device workspace of at least dda_workspace_size(desc) bytes,
+ *           256-byte aligned, owned by the caller, kept by the plan.
+ * Errors: DDA_ERR_INVALID_ARG, DDA_ERR_UNSUPPORTED_SIZE (edge not a power of
+ * two or above 512), DDA_ERR_WORKSPACE (too small / misaligned), DDA_ERR_CUDA. */
+dda_status_t dda_plan_create(dda_plan_t* out, const dda_plan_desc_t* desc, const uint8_t* d_mat,
+                             const double* h_eps, void* d_work, size_t work_bytes, void* stream);
+
+/* Set the incident waves of the next calls (nrhs <= max_rhs).  Computes, in
+ * FP64 on the host, the LDR polarizability of every material for every
+ * right-hand side (Section 2.1; S = sum_j (d_j e_j)^2 depends on the wave)
+ * and alpha_tilde, the polarizability of the most frequent non-air material
+ * (Section 3.1, eq. 20), and uploads them on `stream`. */
+dda_status_t dda_set_incidence(dda_plan_t plan, int32_t nrhs, const dda_incidence_t* h_inc,
+                               void* stream);
+
+/* d_b[rhs] = E_inc on scatterer voxels, 0 on air; complex128 box fields. */
+dda_status_t dda_incident_field(dda_plan_t plan, int32_t nrhs, void* d_b, void* stream);
+
+/* y = A x for nrhs box fields in precision prec (the plan must hold it):
+ *   scatterer rows: alpha_j^{-1} x_j - dx^3 sum_{i scatterer, i != j} g(r_j - r_i) x_i
+ *   air rows:       alpha_tilde^{-1} x_j
+ * G is applied by the zero-padded FFT convolution (Section 1, Section 2.2).
+ * d_x and d_y must not overlap. */
+dda_status_t dda_matvec(dda_plan_t plan, int32_t prec, int32_t nrhs, const void* d_x, void* d_y,
+                        void* stream);
+
+/* Build the 3-level circulant: T. Chan's optimal circulant (eq. 13) applied
+ * on the x, y and z levels of each of the six blocks, then its 3-D DFT
+ * (Section 3).  Independent of the incident wave. */
+dda_status_t dda_precond_build(dda_plan_t plan, void* stream);
+
+/* z = P^{-1} v, P = alpha_tilde^{-1} I - dx^3 C: 3-D FFT of each component,
+ * the 3x3 symbol Lambda(w) = alpha_tilde^{-1} I - dx^3 Chat(w) solved per
+ * frequency, inverse FFT.  v and z may be the same buffer. */
+dda_status_t dda_precond_apply(dda_plan_t plan, int32_t prec, int32_t nrhs, const void* d_v,
+                               void* d_z, void* stream);
+
+/* In-place unnormalised 3-D DFT (inverse: sign +, scaled by 1/(l m n)) of
+ * nbatch complex l x m x n arrays [batch][z][y][x].  Same kernels as the
+ * preconditioner's transforms; exposed for testing and reuse. */
+dda_status_t dda_fft3d(dda_plan_t plan, int32_t prec, int32_t nbatch, void* d_data,
+                       int32_t inverse, void* stream);
+
+/* Solve A x = b for nrhs right-hand sides (the incidence of dda_set_incidence).
+ *   d_b   complex128 box fields, or NULL for the plane waves (then written
+ *         nowhere: the library forms b in its workspace).
+ *   d_x   complex128 box fields: initial guess in, solution out.
+ *   h_stats host array of nrhs records (may be NULL).
+ * Right-preconditioned restarted GMRES: Arnoldi with classical Gram-Schmidt
+ * applied twice, dots and norms accumulated in FP64, Givens rotations and the
+ * small least-squares solve in FP64 on the device.  Every restart recomputes
+ * the residual b - A x in complex128; with inner_prec = DDA_C64 the Krylov
+ * basis, matvecs and preconditioner run in complex64 (FP64 iterative
+ * refinement).  Returns DDA_ERR_NOT_CONVERGED if any right-hand side missed
+ * tol within max_iters (x then holds the last iterate), DDA_ERR_NAN on a
+ * non-finite residual, DDA_ERR_NO_PRECOND if precond = 3 was asked before
+ * dda_precond_build.  Synchronises `stream`. */
+dda_status_t dda_solve(dda_plan_t plan, int32_t nrhs, const void* d_b, void* d_x,
+                       const dda_solve_opts_t* opts, dda_rhs_stats_t* h_stats, void* stream);
+
+/* Cross sections of the solutions d_c (complex128 box fields) for the
+ * incidence set by dda_set_incidence; h_out[3*r + {0,1,2}] = C_ext, C_abs,
+ * C_sca of right-hand side r.  The paper prints no formula; these are the
+ * standard DDA expressions (Draine & Flatau) with p = dx^3 c, |E_inc| = 1:
+ *   C_ext = 4 pi k sum Im(conj(E_inc) . p)
+ *   C_abs = 4 pi k sum (-Im(1/alpha_DF) - 2k^3/3) |p|^2,  alpha_DF = dx^3 alpha
+ *   C_sca = 4 pi k [Im(p^H G p) + (2/3) k^3 |p|^2]   (G p by one complex128 FFT matvec;
+ *           equals 4 pi k p^H Im(G) p because G is complex symmetric)
+ * Synchronises `stream`. */
+dda_status_t dda_cross_sections(dda_plan_t plan, int32_t nrhs, const void* d_c, double* h_out,
+                                void* stream);
+
+/* Release the host-side plan object (device memory stays the caller's). */
+void dda_plan_destroy(dda_plan_t plan);
+
+/* Thread-local text of the last error ("" if none). */
+const char* dda_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDA_H_ */

@@ -1,0 +1,429 @@
+// Plan creation: workspace layout, Green-function spectrum, polarizabilities,
+// incident field and the standalone 3-D FFT entry point.
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <string>
+
+#include "fft_kernels.cuh"
+#include "plan.hpp"
+
+namespace dda {
+
+namespace {
+thread_local std::string g_err;
+}
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+dda_status_t fail(dda_status_t st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+dda_status_t check_cuda(const char* where) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(DDA_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+  return DDA_OK;
+}
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+bool valid_desc(const dda_plan_desc_t& d, std::string& why, dda_status_t& st) {
+  st = DDA_ERR_INVALID_ARG;
+  if (d.l < 1 || d.m < 1 || d.n < 1) return why = "box edges must be >= 1", false;
+  if (!(d.dx > 0) || !(d.k > 0) || !std::isfinite(d.dx) || !std::isfinite(d.k))
+    return why = "dx and k must be positive and finite", false;
+  if (d.n_materials < 1 || d.n_materials > 255) return why = "n_materials must be 1..255", false;
+  if (d.max_rhs < 1 || d.max_rhs > 4096) return why = "max_rhs must be 1..4096", false;
+  if (d.krylov_m < 0 || d.krylov_m > 512) return why = "krylov_m must be 0..512", false;
+  if ((d.precisions & (DDA_PLAN_C128 | DDA_PLAN_C64)) == 0 ||
+      (d.precisions & ~(DDA_PLAN_C128 | DDA_PLAN_C64)) != 0)
+    return why = "precisions must be a non-empty set of DDA_PLAN_C128 | DDA_PLAN_C64", false;
+  st = DDA_ERR_UNSUPPORTED_SIZE;
+  for (int e : {d.l, d.m, d.n})
+    if (!is_pow2(e) || e > 512) return why = "box edges must be powers of two <= 512", false;
+  st = DDA_OK;
+  return true;
+}
+
+}  // namespace
+
+bool make_layout(const dda_plan_desc_t& d, void* ws, Layout& L, std::string& why) {
+  dda_status_t st;
+  if (!valid_desc(d, why, st)) return false;
+  Carver c(ws);
+  const long l = d.l, m = d.m, n = d.n;
+  const long Lx = 2 * l, Ly = 2 * m, Lz = 2 * n;
+  const long nvox = l * m * n, P = Lx * Ly * Lz;
+  const long Lmax = std::max(Lx, std::max(Ly, Lz));
+  const bool h128 = d.precisions & DDA_PLAN_C128, h64 = d.precisions & DDA_PLAN_C64;
+  const size_t esz = h128 ? 16 : 8;
+  const long gsz = (l + 1) * (m + 1) * (n + 1) * 6;
+  const long csz = (l / 2 + 1) * (m / 2 + 1) * (n / 2 + 1) * 6;
+  const long R = d.max_rhs, K1 = d.n_materials + 1;
+  const long nu = 3 * nvox;
+  L.tw128 = c.take(Lmax * 16);
+  L.tw64 = c.take(Lmax * 8);
+  if (h128) {
+    L.G128 = c.take(gsz * 16);
+    L.C128 = c.take(csz * 16);
+  }
+  if (h64) {
+    L.G64 = c.take(gsz * 8);
+    L.C64 = c.take(csz * 8);
+  }
+  L.ainv128 = c.take(R * K1 * 16);
+  L.ainv64 = c.take(R * K1 * 8);
+  L.incd = static_cast<double*>(c.take(R * 6 * sizeof(double)));
+  L.buf1 = c.take(esz * R * 3 * n * m * Lx);
+  size_t b2 = esz * R * 3 * n * Ly * Lx;
+  b2 = std::max(b2, (size_t)P * 16);     // Green-function spectrum build (complex128)
+  b2 = std::max(b2, (size_t)nvox * 96);  // circulant build: six complex128 components
+  L.buf2 = c.take(b2);
+  L.err_flag = c.take(64);
+  // complex128 field batch: the solver's residual and the cross sections' A c
+  if (h128) L.R128 = c.take(16 * R * nu);
+  if (d.krylov_m > 0) {
+    const long mk = d.krylov_m;
+    L.nblk = (int)std::min<long>(304, std::max<long>(1, (nu + 4095) / 4096));
+    L.V = c.take(esz * (mk + 1) * R * nu);
+    L.Wv = c.take(esz * R * nu);
+    L.Zv = c.take(esz * R * nu);
+    L.B128 = c.take(16 * R * nu);
+    SolverState& s = L.st;
+    s.H = static_cast<double2*>(c.take(16 * R * (mk + 1) * mk));
+    s.cs = static_cast<double*>(c.take(8 * R * mk));
+    s.sn = static_cast<double2*>(c.take(16 * R * mk));
+    s.g = static_cast<double2*>(c.take(16 * R * (mk + 1)));
+    s.y = static_cast<double2*>(c.take(16 * R * mk));
+    s.hcol = static_cast<double2*>(c.take(16 * R * (mk + 2)));
+    s.partial = static_cast<double2*>(c.take(16 * R * (size_t)L.nblk * (mk + 2)));
+    s.scal = static_cast<double*>(c.take(8 * R * 16));
+    s.active = static_cast<int*>(c.take(4 * R));
+    s.jlen = static_cast<int*>(c.take(4 * R));
+    s.flags = static_cast<int*>(c.take(4 * R));
+    s.iters = static_cast<int*>(c.take(4 * R));
+    s.run = static_cast<int*>(c.take(4 * R));
+    s.counters = static_cast<int*>(c.take(64));
+  }
+  L.total = c.off + 256;
+  return true;
+}
+
+namespace {
+
+// One component of g(R) (the Green function of Section 2, in the form of
+// Algorithm 1) in FP64.
+__device__ __forceinline__ double2 green_component(double X, double Y, double Z, double k, int a,
+                                                   int b) {
+  const double r2 = X * X + Y * Y + Z * Z;
+  const double r = sqrt(r2);
+  const double rv[3] = {X / r, Y / r, Z / r};
+  double sn, cs;
+  sincos(k * r, &sn, &cs);
+  const double er = cs / r, ei = sn / r;  // e^{ikr} / r
+  const double dlt = (a == b) ? 1.0 : 0.0;
+  const double pp = rv[a] * rv[b];
+  const double q = (dlt - 3.0 * pp) / r2;
+  const double br = k * k * (dlt - pp) - q;  // k^2 (d - pp) + (i k r - 1)(d - 3pp)/r^2
+  const double bi = k * r * q;
+  return make_double2(er * br - ei * bi, er * bi + ei * br);
+}
+
+__device__ const int kCompA[6] = {0, 0, 0, 1, 1, 2};
+__device__ const int kCompB[6] = {0, 1, 2, 1, 2, 2};
+
+// Index p of a padded axis of length Lp >= 2l - 1 as a signed voxel offset:
+// p < l -> p, p > Lp - l -> p - Lp, otherwise the wrap region (no pair of
+// box voxels has that offset), reported invalid.
+__device__ __forceinline__ bool padded_offset(long p, long l, long Lp, long& o) {
+  if (p < l) {
+    o = p;
+    return true;
+  }
+  if (p > Lp - l) {
+    o = p - Lp;
+    return true;
+  }
+  return false;
+}
+
+// Circulant generator of component c on the padded grid (Section 2.2: the
+// BTTB block is embedded in a circulant of twice the size per level).
+__global__ void k_green_generator(double2* out, int c, long l, long m, long n, long Lx, long Ly,
+                                  long Lz, double dx, double k) {
+  const long P = Lx * Ly * Lz;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < P;
+       i += (long)gridDim.x * blockDim.x) {
+    const long x = i % Lx, y = (i / Lx) % Ly, z = i / (Lx * Ly);
+    long ox, oy, oz;
+    double2 v = make_double2(0.0, 0.0);
+    if (padded_offset(x, l, Lx, ox) && padded_offset(y, m, Ly, oy) && padded_offset(z, n, Lz, oz) &&
+        (ox | oy | oz) != 0)
+      v = green_component(dx * ox, dx * oy, dx * oz, k, kCompA[c], kCompB[c]);
+    out[i] = v;
+  }
+}
+
+// Keep the octant 0..L/2 of each axis of a full spectrum (the rest follows
+// from the block's parity) as component c of the interleaved [..][6] store.
+__global__ void k_compress(const double2* full, long Lx, long Ly, long Lz, long hx, long hy,
+                           long hz, int c, double2* out128, float2* out64) {
+  const long H = hx * hy * hz;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < H;
+       i += (long)gridDim.x * blockDim.x) {
+    const long x = i % hx, y = (i / hx) % hy, z = i / (hx * hy);
+    const double2 v = full[(z * Ly + y) * Lx + x];
+    if (out128) out128[i * 6 + c] = v;
+    if (out64) out64[i * 6 + c] = make_float2((float)v.x, (float)v.y);
+  }
+}
+
+// E_inc = pol exp(i k dir . r) on scatterer voxels, r from the box centre.
+__global__ void k_incident(double2* b, const uint8_t* mat, const double* inc, int nrhs, long l,
+                           long m, long n, double dx, double k) {
+  const long nvox = l * m * n;
+  const long tot = nvox * nrhs;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < tot;
+       i += (long)gridDim.x * blockDim.x) {
+    const long v = i % nvox, r = i / nvox;
+    const long x = v % l, y = (v / l) % m, z = v / (l * m);
+    const double* d = inc + r * 6;
+    double2 out[3] = {{0, 0}, {0, 0}, {0, 0}};
+    if (mat[v] != 0) {
+      const double px = dx * (x - 0.5 * (l - 1)), py = dx * (y - 0.5 * (m - 1)),
+                   pz = dx * (z - 0.5 * (n - 1));
+      double sn, cs;
+      sincos(k * (d[0] * px + d[1] * py + d[2] * pz), &sn, &cs);
+      for (int c = 0; c < 3; ++c) out[c] = make_double2(d[3 + c] * cs, d[3 + c] * sn);
+    }
+    for (int c = 0; c < 3; ++c) b[(r * 3 + c) * nvox + v] = out[c];
+  }
+}
+
+inline unsigned grid_for(long n, int threads) {
+  const long g = (n + threads - 1) / threads;
+  return (unsigned)std::min<long>(std::max<long>(g, 1), 152L * 32);
+}
+
+}  // namespace
+
+}  // namespace dda
+
+using namespace dda;
+
+extern "C" const char* dda_last_error(void) { return g_err.c_str(); }
+
+extern "C" size_t dda_workspace_size(const dda_plan_desc_t* desc) {
+  if (!desc) {
+    set_error("dda_workspace_size: desc is NULL");
+    return 0;
+  }
+  Layout L;
+  std::string why;
+  if (!make_layout(*desc, nullptr, L, why)) {
+    set_error("dda_workspace_size: " + why);
+    return 0;
+  }
+  return L.total;
+}
+
+extern "C" dda_status_t dda_plan_create(dda_plan_t* out, const dda_plan_desc_t* desc,
+                                        const uint8_t* d_mat, const double* h_eps, void* d_work,
+                                        size_t work_bytes, void* stream) {
+  if (!out || !desc || !d_mat || !h_eps || !d_work)
+    return fail(DDA_ERR_INVALID_ARG, "dda_plan_create: NULL argument");
+  *out = nullptr;
+  std::string why;
+  dda_status_t st;
+  if (!valid_desc(*desc, why, st)) return fail(st, "dda_plan_create: " + why);
+  if (reinterpret_cast<uintptr_t>(d_work) % 256 != 0)
+    return fail(DDA_ERR_WORKSPACE, "dda_plan_create: workspace must be 256-byte aligned");
+  Layout L;
+  make_layout(*desc, d_work, L, why);
+  if (work_bytes < L.total)
+    return fail(DDA_ERR_WORKSPACE, "dda_plan_create: workspace of " + std::to_string(work_bytes) +
+                                       " bytes, need " + std::to_string(L.total));
+  for (int i = 0; i < 2 * desc->n_materials; ++i)
+    if (!std::isfinite(h_eps[i])) return fail(DDA_ERR_INVALID_ARG, "dda_plan_create: eps not finite");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  dda_plan_s* p = new dda_plan_s();
+  p->d = *desc;
+  p->l = desc->l;
+  p->m = desc->m;
+  p->n = desc->n;
+  p->Lx = 2 * p->l;
+  p->Ly = 2 * p->m;
+  p->Lz = 2 * p->n;
+  p->Lmax = std::max(p->Lx, std::max(p->Ly, p->Lz));
+  p->nvox = (long)p->l * p->m * p->n;
+  p->P = (long)p->Lx * p->Ly * p->Lz;
+  p->hx = p->l + 1;
+  p->hy = p->m + 1;
+  p->hz = p->n + 1;
+  p->cx_ = p->l / 2 + 1;
+  p->cy_ = p->m / 2 + 1;
+  p->cz_ = p->n / 2 + 1;
+  p->K = desc->n_materials;
+  p->mat = d_mat;
+  p->eps.assign(h_eps, h_eps + 2 * desc->n_materials);
+  p->w = L;
+  p->has128 = desc->precisions & DDA_PLAN_C128;
+  p->has64 = desc->precisions & DDA_PLAN_C64;
+
+  // material census (alpha_tilde is the most frequent non-air material)
+  std::vector<uint8_t> hm(p->nvox);
+  cudaMemcpyAsync(hm.data(), d_mat, p->nvox, cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    delete p;
+    return check_cuda("dda_plan_create: reading materials");
+  }
+  p->mat_count.assign(p->K + 1, 0);
+  for (uint8_t v : hm) {
+    if (v > p->K) {
+      delete p;
+      return fail(DDA_ERR_INVALID_ARG, "dda_plan_create: material index above n_materials");
+    }
+    p->mat_count[v]++;
+  }
+
+  // twiddles exp(-2 pi i t / Lmax)
+  {
+    std::vector<double2> t128(p->Lmax);
+    std::vector<float2> t64(p->Lmax);
+    for (int t = 0; t < p->Lmax; ++t) {
+      const double a = -2.0 * kPi * (double)t / (double)p->Lmax;
+      t128[t] = make_double2(std::cos(a), std::sin(a));
+      t64[t] = make_float2((float)t128[t].x, (float)t128[t].y);
+    }
+    cudaMemcpyAsync(L.tw128, t128.data(), p->Lmax * 16, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(L.tw64, t64.data(), p->Lmax * 8, cudaMemcpyHostToDevice, s);
+  }
+  cudaMemsetAsync(L.err_flag, 0, 64, s);
+
+  // kernel spectrum, one component at a time through the FP64 scratch
+  double2* scratch = static_cast<double2*>(L.buf2);
+  for (int c = 0; c < 6; ++c) {
+    k_green_generator<<<grid_for(p->P, 256), 256, 0, s>>>(scratch, c, p->l, p->m, p->n, p->Lx, p->Ly,
+                                                          p->Lz, desc->dx, desc->k);
+    fft3d_inplace<double, false>(reinterpret_cast<cx<double>*>(scratch), 1, p->Lx, p->Ly, p->Lz, 1.0,
+                                 static_cast<const cx<double>*>(L.tw128), p->Lmax, s);
+    k_compress<<<grid_for((long)p->hx * p->hy * p->hz, 256), 256, 0, s>>>(
+        scratch, p->Lx, p->Ly, p->Lz, p->hx, p->hy, p->hz, c, static_cast<double2*>(L.G128),
+        static_cast<float2*>(L.G64));
+  }
+  const dda_status_t cs = check_cuda("dda_plan_create");
+  if (cs != DDA_OK) {
+    delete p;
+    return cs;
+  }
+  *out = p;
+  return DDA_OK;
+}
+
+extern "C" dda_status_t dda_set_incidence(dda_plan_t p, int32_t nrhs, const dda_incidence_t* inc,
+                                          void* stream) {
+  if (!p || !inc) return fail(DDA_ERR_INVALID_ARG, "dda_set_incidence: NULL argument");
+  if (nrhs < 1 || nrhs > p->d.max_rhs)
+    return fail(DDA_ERR_INVALID_ARG, "dda_set_incidence: nrhs outside 1..max_rhs");
+  const int K1 = p->K + 1;
+  std::vector<double> h(nrhs * 6);
+  p->ainv_host.assign((size_t)nrhs * K1 * 2, 0.0);
+  p->ainv_host32.assign((size_t)nrhs * K1 * 2, 0.0f);
+  // most frequent non-air material, ties to the lowest index
+  int tilde = 1;
+  for (int mt = 2; mt <= p->K; ++mt)
+    if (p->mat_count[mt] > p->mat_count[tilde]) tilde = mt;
+  const double kd = p->d.k * p->d.dx;
+  for (int r = 0; r < nrhs; ++r) {
+    const double* d = inc[r].dir;
+    const double* e = inc[r].pol;
+    const double nd = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const double ne = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+    const double de = d[0] * e[0] + d[1] * e[1] + d[2] * e[2];
+    if (!(std::fabs(nd - 1) < 1e-9 && std::fabs(ne - 1) < 1e-9 && std::fabs(de) < 1e-9))
+      return fail(DDA_ERR_INVALID_ARG, "dda_set_incidence: dir and pol must be orthonormal");
+    for (int c = 0; c < 3; ++c) {
+      h[r * 6 + c] = d[c];
+      h[r * 6 + 3 + c] = e[c];
+    }
+    // S = sum_j (d_j e_j)^2 (Section 2.1)
+    double S = 0;
+    for (int c = 0; c < 3; ++c) S += (d[c] * e[c]) * (d[c] * e[c]);
+    std::vector<std::complex<double>> ainv(K1);
+    for (int mt = 1; mt <= p->K; ++mt) {
+      const std::complex<double> eps(p->eps[2 * (mt - 1)], p->eps[2 * (mt - 1) + 1]);
+      // Clausius-Mossotti and the lattice dispersion relation (Section 2.1)
+      const std::complex<double> acm = 3.0 / (4.0 * kPi) * (eps - 1.0) / (eps + 2.0);
+      const std::complex<double> corr =
+          (-1.891531 + eps * 0.1648469 + eps * (-1.7700004) * S) * (kd * kd) -
+          std::complex<double>(0.0, 2.0 / 3.0) * (kd * kd * kd);
+      const std::complex<double> alpha = acm / (1.0 + acm * corr);
+      ainv[mt] = 1.0 / alpha;
+    }
+    ainv[0] = ainv[tilde];  // air rows and the preconditioner use alpha_tilde
+    for (int mt = 0; mt < K1; ++mt) {
+      if (!std::isfinite(ainv[mt].real()) || !std::isfinite(ainv[mt].imag()))
+        return fail(DDA_ERR_INVALID_ARG,
+                    "dda_set_incidence: polarizability is zero or singular (eps = 1 or -2?)");
+      p->ainv_host[(r * K1 + mt) * 2] = ainv[mt].real();
+      p->ainv_host[(r * K1 + mt) * 2 + 1] = ainv[mt].imag();
+      p->ainv_host32[(r * K1 + mt) * 2] = (float)ainv[mt].real();
+      p->ainv_host32[(r * K1 + mt) * 2 + 1] = (float)ainv[mt].imag();
+    }
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaMemcpyAsync(p->w.incd, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(p->w.ainv128, p->ainv_host.data(), p->ainv_host.size() * sizeof(double),
+                  cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(p->w.ainv64, p->ainv_host32.data(), p->ainv_host32.size() * sizeof(float),
+                  cudaMemcpyHostToDevice, s);
+  p->inc.assign(inc, inc + nrhs);
+  p->nrhs_inc = nrhs;
+  return check_cuda("dda_set_incidence");
+}
+
+extern "C" dda_status_t dda_incident_field(dda_plan_t p, int32_t nrhs, void* d_b, void* stream) {
+  if (!p || !d_b) return fail(DDA_ERR_INVALID_ARG, "dda_incident_field: NULL argument");
+  if (nrhs < 1 || nrhs > p->nrhs_inc)
+    return fail(DDA_ERR_INVALID_ARG, "dda_incident_field: nrhs above the incidence count set");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  k_incident<<<grid_for(p->nvox * nrhs, 256), 256, 0, s>>>(static_cast<double2*>(d_b), p->mat,
+                                                          p->w.incd, nrhs, p->l, p->m, p->n,
+                                                          p->d.dx, p->d.k);
+  return check_cuda("dda_incident_field");
+}
+
+extern "C" dda_status_t dda_fft3d(dda_plan_t p, int32_t prec, int32_t nbatch, void* d_data,
+                                  int32_t inverse, void* stream) {
+  if (!p || !d_data) return fail(DDA_ERR_INVALID_ARG, "dda_fft3d: NULL argument");
+  if (nbatch < 1) return fail(DDA_ERR_INVALID_ARG, "dda_fft3d: nbatch must be >= 1");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const double sc = inverse ? 1.0 / (double)p->nvox : 1.0;
+  if (prec == DDA_C128) {
+    auto* d = static_cast<cx<double>*>(d_data);
+    if (inverse)
+      fft3d_inplace<double, true>(d, nbatch, p->l, p->m, p->n, sc, tw_of<double>(p), p->Lmax, s);
+    else
+      fft3d_inplace<double, false>(d, nbatch, p->l, p->m, p->n, 1.0, tw_of<double>(p), p->Lmax, s);
+  } else if (prec == DDA_C64) {
+    auto* d = static_cast<cx<float>*>(d_data);
+    if (inverse)
+      fft3d_inplace<float, true>(d, nbatch, p->l, p->m, p->n, (float)sc, tw_of<float>(p), p->Lmax, s);
+    else
+      fft3d_inplace<float, false>(d, nbatch, p->l, p->m, p->n, 1.0f, tw_of<float>(p), p->Lmax, s);
+  } else {
+    return fail(DDA_ERR_INVALID_ARG, "dda_fft3d: prec must be DDA_C128 or DDA_C64");
+  }
+  return check_cuda("dda_fft3d");
+}
+
+extern "C" void dda_plan_destroy(dda_plan_t p) {
+  if (!p) return;
+  if (p->pinned) cudaFreeHost(p->pinned);
+  delete p;
+}

@@ -1,0 +1,168 @@
+// Shared-memory Stockham FFT used by every transform of the DDA operator and
+// preconditioner.
+//
+// A CTA transforms NB independent lines of power-of-two length L held in
+// shared memory, element (line b, position j) at s[j * ld + b].  Threads are
+// mapped with the line index fastest, so a warp touches consecutive words.
+// Each stage of radix R (2, 4, 8 or 16) is the self-sorting Stockham step:
+//   butterfly jb (0 <= jb < L/R) of a line reads x[jb + q L/R], q < R,
+//   multiplies by w_L^{q k L/(Ns R)} with k = jb mod Ns (Ns = product of the
+//   radices already applied), takes an R-point DFT in registers and writes
+//   y[(jb - k) R + k + q Ns].
+// After the last stage the line holds its DFT in natural order.  Every
+// thread owns E = 16 complex values per stage (16/R butterflies), so a CTA
+// has NB * L / 16 threads.  Reads of a stage complete (barrier) before its
+// writes, so one buffer suffices.
+#pragma once
+
+#include "cx.cuh"
+
+namespace dda {
+
+constexpr int kElemsPerThread = 16;
+
+// cos(2 pi j / 16), j = 0..4.
+constexpr double kCos16[5] = {1.0, 0.92387953251128675613, 0.70710678118654752440,
+                              0.38268343236508977173, 0.0};
+
+__host__ __device__ constexpr double cos16(int j) {
+  return ((j & 15) <= 4)    ? kCos16[j & 15]
+         : ((j & 15) <= 8)  ? -kCos16[8 - (j & 15)]
+         : ((j & 15) <= 12) ? -kCos16[(j & 15) - 8]
+                            : kCos16[16 - (j & 15)];
+}
+// sin(x) = cos(x - pi/2)
+__host__ __device__ constexpr double sin16(int j) { return cos16(j - 4); }
+
+// a * exp(-+ 2 pi i Q / R) (minus sign forward, plus sign inverse), R | 16.
+template <int R, int Q, bool INV, typename T>
+__device__ __forceinline__ cx<T> twc(cx<T> a) {
+  constexpr int j = (Q * (16 / R)) & 15;
+  if constexpr (j == 0) {
+    return a;
+  } else if constexpr (j == 4) {
+    return INV ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
+  } else if constexpr (j == 8) {
+    return mk<T>(-a.x, -a.y);
+  } else if constexpr (j == 12) {
+    return INV ? mk<T>(a.y, -a.x) : mk<T>(-a.y, a.x);
+  } else {
+    constexpr T c = (T)cos16(j);
+    constexpr T s = INV ? (T)sin16(j) : -(T)sin16(j);
+    return mk<T>(a.x * c - a.y * s, a.x * s + a.y * c);
+  }
+}
+
+template <int R, int Q, bool INV, typename T>
+__device__ __forceinline__ void dft_combine(cx<T>* v, const cx<T>* e, const cx<T>* o) {
+  if constexpr (Q < R / 2) {
+    const cx<T> t = twc<R, Q, INV>(o[Q]);
+    v[Q] = e[Q] + t;
+    v[Q + R / 2] = e[Q] - t;
+    dft_combine<R, Q + 1, INV>(v, e, o);
+  }
+}
+
+// In-register R-point DFT, natural order in and out (radix-2 decimation in
+// time: X[q] = E[q] + w^q O[q], X[q + R/2] = E[q] - w^q O[q]).
+template <int R, bool INV, typename T>
+__device__ __forceinline__ void dft(cx<T>* v) {
+  if constexpr (R > 1) {
+    cx<T> e[R / 2], o[R / 2];
+#pragma unroll
+    for (int i = 0; i < R / 2; ++i) {
+      e[i] = v[2 * i];
+      o[i] = v[2 * i + 1];
+    }
+    dft<R / 2, INV>(e);
+    dft<R / 2, INV>(o);
+    dft_combine<R, 0, INV>(v, e, o);
+  }
+}
+
+// Radix sequence of a transform: at most 4 stages (L <= 65536).
+struct RadixPlan {
+  int nst;
+  int r[4];
+};
+
+inline RadixPlan make_radix_plan(int L) {
+  RadixPlan p{0, {1, 1, 1, 1}};
+  int bits = 0;
+  while ((1 << bits) < L) ++bits;
+  if (bits == 0) return p;
+  const int nst = (bits + 3) / 4;
+  int left = bits;
+  for (int s = 0; s < nst; ++s) {
+    const int b = (left + (nst - s) - 1) / (nst - s);  // ceil: larger radices first
+    p.r[s] = 1 << b;
+    left -= b;
+  }
+  p.nst = nst;
+  return p;
+}
+
+template <int R, bool INV, typename T>
+__device__ __forceinline__ void smem_stage(cx<T>* s, const cx<T>* tw, int L, int NB, int ld,
+                                           int Ns, int tid, int nth) {
+  constexpr int G = kElemsPerThread / R;
+  cx<T> v[kElemsPerThread];
+  const int LR = L / R;
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int u = tid + g * nth;
+    const int b = u % NB;
+    const int jb = u / NB;
+#pragma unroll
+    for (int q = 0; q < R; ++q) v[g * R + q] = s[(jb + q * LR) * ld + b];
+  }
+  __syncthreads();
+  const int tstep = L / (Ns * R);
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int u = tid + g * nth;
+    const int b = u % NB;
+    const int jb = u / NB;
+    const int k = jb & (Ns - 1);
+    if (Ns > 1) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) v[g * R + q] = mulc<INV>(v[g * R + q], tw[q * k * tstep]);
+    }
+    dft<R, INV>(&v[g * R]);
+    const int base = (jb - k) * R + k;
+#pragma unroll
+    for (int q = 0; q < R; ++q) s[(base + q * Ns) * ld + b] = v[g * R + q];
+  }
+  __syncthreads();
+}
+
+// Full transform of NB lines in shared memory.  tw[t] = exp(-2 pi i t / L),
+// t < L, also in shared memory.  Caller synchronises before the call.
+template <bool INV, typename T>
+__device__ __forceinline__ void smem_fft(cx<T>* s, const cx<T>* tw, int L, int NB, int ld,
+                                         const RadixPlan& rp) {
+  const int tid = threadIdx.x;
+  const int nth = blockDim.x;
+  int Ns = 1;
+#pragma unroll
+  for (int st = 0; st < 4; ++st) {
+    if (st >= rp.nst) break;
+    const int R = rp.r[st];
+    switch (R) {
+      case 16: smem_stage<16, INV>(s, tw, L, NB, ld, Ns, tid, nth); break;
+      case 8: smem_stage<8, INV>(s, tw, L, NB, ld, Ns, tid, nth); break;
+      case 4: smem_stage<4, INV>(s, tw, L, NB, ld, Ns, tid, nth); break;
+      default: smem_stage<2, INV>(s, tw, L, NB, ld, Ns, tid, nth); break;
+    }
+    Ns *= R;
+  }
+}
+
+// Copy the L-point twiddles out of the plan's Lmax-point table.
+template <typename T>
+__device__ __forceinline__ void load_twiddles(cx<T>* stw, const cx<T>* __restrict__ tw, int L,
+                                              int twshift) {
+  for (int t = threadIdx.x; t < L; t += blockDim.x) stw[t] = tw[(size_t)t * twshift];
+}
+
+}  // namespace dda

@@ -1,0 +1,106 @@
+// Launch geometry of the batched FFT kernels and the full 3-D transform.
+//
+// Tiles are sized so that a CTA holds 2-16K complex values in shared memory
+// (16 per thread), strided tiles span at least 8 (complex128) or 16
+// (complex64) neighbouring columns so that every row is one 128-byte
+// segment, and small problems shrink tiles until the grid covers the 152
+// SMs at least twice.
+#include <algorithm>
+
+#include "fft_kernels.cuh"
+#include "plan.hpp"
+
+namespace dda {
+
+namespace {
+
+constexpr int kSMs = 152;
+
+template <typename T>
+constexpr int max_threads() {
+  return sizeof(T) == 8 ? 512 : 1024;
+}
+
+inline int floor_pow2(long v) {
+  int p = 1;
+  while ((long)p * 2 <= v) p *= 2;
+  return p;
+}
+
+template <typename K>
+void allow_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024)
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+}  // namespace
+
+template <typename T, bool INV>
+void launch_contig(const cx<T>* in, cx<T>* out, const uint8_t* mask, long mask_lines, long nlines,
+                   int L, int Lin, long in_ld, int Lout, long out_ld, T scale, const cx<T>* tw,
+                   int Lmax, cudaStream_t s) {
+  if (nlines <= 0) return;
+  const int cap = max_threads<T>() * kElemsPerThread;
+  int per_cta = std::min(4096, cap);  // complex values per CTA
+  while (per_cta > 512 && per_cta > L && (nlines * L + per_cta - 1) / per_cta < 2 * kSMs)
+    per_cta /= 2;
+  int NB = std::max(1, per_cta / L);
+  while (NB * L < kElemsPerThread * 32) NB *= 2;  // at least one warp
+  const int nth = NB * L / kElemsPerThread;
+  const size_t smem = ((size_t)L * (NB + 1) + L) * sizeof(cx<T>);
+  const long grid = (nlines + NB - 1) / NB;
+  auto kern = k_fft_contig<T, INV>;
+  allow_smem(kern, smem);
+  kern<<<(unsigned)grid, nth, smem, s>>>(in, out, mask, mask_lines, nlines, L, Lin, in_ld, Lout,
+                                         out_ld, scale, tw, Lmax / L, make_radix_plan(L), NB);
+}
+
+template <typename T, bool INV>
+void launch_strided(const cx<T>* in, cx<T>* out, long ncols, long nslabs, int L, int Lin,
+                    long in_js, long in_ss, int Lout, long out_js, long out_ss, T scale,
+                    const cx<T>* tw, int Lmax, cudaStream_t s) {
+  if (ncols <= 0 || nslabs <= 0) return;
+  const int cap = max_threads<T>() * kElemsPerThread;
+  int NB = sizeof(T) == 8 ? 8 : 16;
+  NB = std::min<long>(NB, floor_pow2(ncols));
+  while (NB * L > cap && NB > 1) NB /= 2;
+  while (NB > 1 && NB * L > 1024 && nslabs * ((ncols + NB - 1) / NB) < 2 * kSMs) NB /= 2;
+  while (NB * L < kElemsPerThread * 32) NB *= 2;
+  const int nth = NB * L / kElemsPerThread;
+  const size_t smem = ((size_t)L * NB + L) * sizeof(cx<T>);
+  const long grid = nslabs * ((ncols + NB - 1) / NB);
+  auto kern = k_fft_strided<T, INV>;
+  allow_smem(kern, smem);
+  kern<<<(unsigned)grid, nth, smem, s>>>(in, out, ncols, L, Lin, in_js, in_ss, Lout, out_js,
+                                         out_ss, scale, tw, Lmax / L, make_radix_plan(L), NB);
+}
+
+template <typename T, bool INV>
+void fft3d_inplace(cx<T>* data, long nbatch, int Lx, int Ly, int Lz, T scale, const cx<T>* tw,
+                   int Lmax, cudaStream_t s) {
+  const long plane = (long)Lx * Ly;
+  const long vol = plane * Lz;
+  if (Lx > 1)
+    launch_contig<T, INV>(data, data, nullptr, 1, nbatch * Ly * Lz, Lx, Lx, Lx, Lx, Lx, T(1), tw,
+                          Lmax, s);
+  if (Ly > 1)
+    launch_strided<T, INV>(data, data, Lx, nbatch * Lz, Ly, Ly, Lx, plane, Ly, Lx, plane, T(1), tw,
+                           Lmax, s);
+  if (Lz > 1 || scale != T(1))
+    launch_strided<T, INV>(data, data, plane, nbatch, Lz, Lz, plane, vol, Lz, plane, vol, scale,
+                           tw, Lmax, s);
+}
+
+#define DDA_INST_FFT(T, INV)                                                                      \
+  template void launch_contig<T, INV>(const cx<T>*, cx<T>*, const uint8_t*, long, long, int, int,  \
+                                      long, int, long, T, const cx<T>*, int, cudaStream_t);        \
+  template void launch_strided<T, INV>(const cx<T>*, cx<T>*, long, long, int, int, long, long,     \
+                                       int, long, long, T, const cx<T>*, int, cudaStream_t);       \
+  template void fft3d_inplace<T, INV>(cx<T>*, long, int, int, int, T, const cx<T>*, int,           \
+                                      cudaStream_t);
+DDA_INST_FFT(float, false)
+DDA_INST_FFT(float, true)
+DDA_INST_FFT(double, false)
+DDA_INST_FFT(double, true)
+
+}  // namespace dda

@@ -1,0 +1,566 @@
+// Restarted, right-preconditioned GMRES for the DDA system, batched over
+// right-hand sides that advance in lock step.
+//
+// The paper solves with full GMRES and a relative-residual stopping test
+// (Section 4) and points to restarted GMRES as the memory-bounded variant
+// (Sections 4 and 5).  Here every restart cycle
+//   1. recomputes the residual r = b - A x in complex128 (FP64 iterative
+//      refinement when the cycle itself runs in complex64),
+//   2. runs Arnoldi on A P^{-1} from v0 = r/||r||: w = A P^{-1} v_j,
+//      classical Gram-Schmidt applied twice (h = V^H w, w -= V h), FP64
+//      Hessenberg column, complex Givens rotations and the residual estimate
+//      |g_{j+1}| on the device,
+//   3. ends when the estimate reaches max(tol ||b||, inner_tol ||r||), after
+//      `restart` steps or on breakdown, then solves the triangular system,
+//      forms u = V y and adds P^{-1} u to x in complex128.
+// Dots and norms of complex64 vectors multiply in FP32 and sum per thread
+// with compensated (Neumaier) FP32 addition, then across threads and blocks
+// in FP64 in a fixed order, so results are reproducible run to run.
+// The host keeps at most two Arnoldi steps queued ahead of the GPU and polls
+// a pinned word to stop launching once every right-hand side has finished
+// its cycle.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "plan.hpp"
+
+namespace dda {
+
+namespace {
+
+constexpr int kNT = 256;  // threads of the vector kernels
+
+// Per-thread accumulator: plain FP64, or FP32 with Neumaier compensation.
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double get() const { return s; }
+};
+template <>
+struct Acc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float t = s + v;
+    c += (fabsf(s) >= fabsf(v)) ? ((s - t) + v) : ((v - t) + s);
+    s = t;
+  }
+  __device__ __forceinline__ double get() const { return (double)s + (double)c; }
+};
+
+__device__ __forceinline__ double2 warp_sum(double2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+// Sum over the block in a fixed order; the result is valid in thread 0.
+__device__ __forceinline__ double2 block_sum(double2 v, double2* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? sh[lane] : make_double2(0.0, 0.0);
+    v = warp_sum(v);
+  }
+  return v;
+}
+
+__device__ __forceinline__ void chunk_of(long nu, int nblk, long& k0, long& k1) {
+  const long chunk = (nu + nblk - 1) / nblk;
+  k0 = blockIdx.x * chunk;
+  k1 = min(nu, k0 + chunk);
+}
+
+// partial[(r * nblk + blk) * pst + i] = sum_k conj(V_i[k]) w[k], i < jc (the
+// dot products of Gram-Schmidt), eight at a time.
+template <typename T>
+__global__ void __launch_bounds__(kNT)
+    k_multidot(const cx<T>* __restrict__ V, const cx<T>* __restrict__ W, long nu, long vstride,
+               int jc, double2* __restrict__ partial, int pst, const int* __restrict__ active) {
+  __shared__ double2 sh[32];
+  const int r = blockIdx.y;
+  if (!active[r]) return;
+  long k0, k1;
+  chunk_of(nu, gridDim.x, k0, k1);
+  const cx<T>* w = W + r * nu;
+  const cx<T>* vb = V + r * nu;
+  double2* out = partial + ((long)r * gridDim.x + blockIdx.x) * pst;
+  constexpr int ND = 8;
+  for (int i0 = 0; i0 < jc; i0 += ND) {
+    Acc<T> ar[ND], ai[ND];
+    for (long k = k0 + threadIdx.x; k < k1; k += kNT) {
+      const cx<T> wk = w[k];
+#pragma unroll
+      for (int d = 0; d < ND; ++d) {
+        if (i0 + d < jc) {
+          const cx<T> vk = vb[(long)(i0 + d) * vstride + k];
+          ar[d].add(vk.x * wk.x + vk.y * wk.y);
+          ai[d].add(vk.x * wk.y - vk.y * wk.x);
+        }
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < ND; ++d) {
+      if (i0 + d < jc) {
+        const double2 t = block_sum(make_double2(ar[d].get(), ai[d].get()), sh);
+        if (threadIdx.x == 0) out[i0 + d] = t;
+      }
+    }
+  }
+}
+
+// hcol[r][i] = sum over blocks of the partial dots (fixed order); the
+// Hessenberg column j receives h (first Gram-Schmidt pass) or h added (second).
+__global__ void k_reduce_dots(const double2* __restrict__ partial, int nblk, int jc, int pst,
+                              double2* __restrict__ hcol, double2* __restrict__ H, int m, int j,
+                              int pass, const int* __restrict__ active) {
+  const int r = blockIdx.x;
+  if (!active[r]) return;
+  for (int i = threadIdx.x; i < jc; i += blockDim.x) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int b = 0; b < nblk; ++b) {
+      const double2 v = partial[((long)r * nblk + b) * pst + i];
+      s.x += v.x;
+      s.y += v.y;
+    }
+    hcol[(long)r * (m + 2) + i] = s;
+    double2* h = H + (long)r * (m + 1) * m + (long)j * (m + 1) + i;
+    if (pass == 0) {
+      *h = s;
+    } else {
+      h->x += s.x;
+      h->y += s.y;
+    }
+  }
+}
+
+// w -= sum_{i < jc} h_i V_i, and the block's share of ||w||^2 into
+// partial[...][pst - 1].
+template <typename T>
+__global__ void __launch_bounds__(kNT)
+    k_update(const cx<T>* __restrict__ V, cx<T>* __restrict__ W, long nu, long vstride, int jc,
+             const double2* __restrict__ hcol, int m, double2* __restrict__ partial, int pst,
+             const int* __restrict__ active) {
+  __shared__ cx<T> hs[520];
+  __shared__ double2 sh[32];
+  const int r = blockIdx.y;
+  if (!active[r]) return;
+  for (int i = threadIdx.x; i < jc; i += kNT) {
+    const double2 h = hcol[(long)r * (m + 2) + i];
+    hs[i] = mk<T>((T)h.x, (T)h.y);
+  }
+  __syncthreads();
+  long k0, k1;
+  chunk_of(nu, gridDim.x, k0, k1);
+  cx<T>* w = W + r * nu;
+  const cx<T>* vb = V + r * nu;
+  Acc<T> nn;
+  for (long k = k0 + threadIdx.x; k < k1; k += kNT) {
+    cx<T> acc = w[k];
+    for (int i = 0; i < jc; ++i) acc = acc - hs[i] * vb[(long)i * vstride + k];
+    w[k] = acc;
+    nn.add(acc.x * acc.x + acc.y * acc.y);
+  }
+  const double2 t = block_sum(make_double2(nn.get(), 0.0), sh);
+  if (threadIdx.x == 0) partial[((long)r * gridDim.x + blockIdx.x) * pst + pst - 1] = t;
+}
+
+// Complex Givens rotation [c s; -conj(s) c] with real c taking (a, b) to (rho, 0).
+__device__ __forceinline__ void givens(double2 a, double2 b, double& c, double2& s, double2& rho) {
+  const double na = hypot(a.x, a.y), nb = hypot(b.x, b.y);
+  if (nb == 0.0) {
+    c = 1.0;
+    s = make_double2(0.0, 0.0);
+    rho = a;
+    return;
+  }
+  if (na == 0.0) {
+    c = 0.0;
+    s = make_double2(1.0, 0.0);
+    rho = b;
+    return;
+  }
+  const double nr = hypot(na, nb);
+  c = na / nr;
+  const double2 ph = make_double2(a.x / na, a.y / na);  // a/|a|
+  // s = (a/|a|) conj(b) / nr
+  s = make_double2((ph.x * b.x + ph.y * b.y) / nr, (ph.y * b.x - ph.x * b.y) / nr);
+  rho = make_double2(ph.x * nr, ph.y * nr);
+}
+
+// One thread per right-hand side: finish column j of H (norm of w, earlier
+// rotations, new rotation), update g and the residual estimate, decide
+// whether the cycle of this right-hand side goes on.
+__global__ void k_givens(double2* __restrict__ H, double* __restrict__ cs, double2* __restrict__ sn,
+                         double2* __restrict__ g, const double2* __restrict__ partial, int nblk,
+                         int pst, double* __restrict__ scal, int* __restrict__ active,
+                         int* __restrict__ jlen, int* __restrict__ flags, int* __restrict__ iters,
+                         int nrhs, int m, int j, double brk) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs || !active[r]) return;
+  double n2 = 0.0;
+  for (int b = 0; b < nblk; ++b) n2 += partial[((long)r * nblk + b) * pst + pst - 1].x;
+  const double hn = sqrt(n2);
+  double2* h = H + (long)r * (m + 1) * m + (long)j * (m + 1);
+  double colnorm2 = n2;
+  for (int i = 0; i <= j; ++i) colnorm2 += h[i].x * h[i].x + h[i].y * h[i].y;
+  double* c = cs + (long)r * m;
+  double2* s = sn + (long)r * m;
+  double2* gg = g + (long)r * (m + 1);
+  for (int i = 0; i < j; ++i) {
+    const double2 a = h[i], b = h[i + 1];
+    h[i] = make_double2(c[i] * a.x + (s[i].x * b.x - s[i].y * b.y),
+                        c[i] * a.y + (s[i].x * b.y + s[i].y * b.x));
+    // -conj(s) a + c b
+    h[i + 1] = make_double2(-(s[i].x * a.x + s[i].y * a.y) + c[i] * b.x,
+                            -(s[i].x * a.y - s[i].y * a.x) + c[i] * b.y);
+  }
+  double cj;
+  double2 sj, rho;
+  givens(h[j], make_double2(hn, 0.0), cj, sj, rho);
+  c[j] = cj;
+  s[j] = sj;
+  h[j] = rho;
+  h[j + 1] = make_double2(0.0, 0.0);
+  const double2 gj = gg[j];
+  gg[j + 1] = make_double2(-(sj.x * gj.x + sj.y * gj.y), -(sj.x * gj.y - sj.y * gj.x));
+  gg[j] = make_double2(cj * gj.x, cj * gj.y);
+  const double res = hypot(gg[j + 1].x, gg[j + 1].y);
+  double* sc = scal + (long)r * 16;
+  sc[4] = res;
+  sc[5] = hn > 0.0 ? 1.0 / hn : 0.0;
+  jlen[r] = j + 1;
+  iters[r] += 1;
+  if (!isfinite(res) || !isfinite(hn)) {
+    flags[r] |= 1;
+    active[r] = 0;
+  } else if (res <= sc[3]) {
+    active[r] = 0;
+  } else if (hn <= brk * sqrt(colnorm2)) {
+    flags[r] |= 2;  // breakdown: the Krylov space is invariant, the cycle's solution is exact
+    active[r] = 0;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kNT)
+    k_scale(const cx<T>* __restrict__ W, cx<T>* __restrict__ Vn, long nu,
+            const double* __restrict__ scal, const int* __restrict__ active) {
+  const int r = blockIdx.y;
+  if (!active[r]) return;
+  const T inv = (T)scal[(long)r * 16 + 5];
+  long k0, k1;
+  chunk_of(nu, gridDim.x, k0, k1);
+  for (long k = k0 + threadIdx.x; k < k1; k += kNT) Vn[r * nu + k] = inv * W[r * nu + k];
+}
+
+// Number of right-hand sides still iterating.
+__global__ void k_count_active(const int* __restrict__ active, int nrhs, int* __restrict__ out) {
+  int c = 0;
+  for (int r = threadIdx.x; r < nrhs; r += blockDim.x) c += active[r];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if (threadIdx.x == 0) *out = c;
+}
+
+// Back substitution R y = g with the rotated (upper triangular) H.
+__global__ void k_trisolve(const double2* __restrict__ H, const double2* __restrict__ g,
+                           const int* __restrict__ jlen, double2* __restrict__ y, int nrhs, int m) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  const int jl = jlen[r];
+  const double2* h = H + (long)r * (m + 1) * m;
+  const double2* gg = g + (long)r * (m + 1);
+  double2* yy = y + (long)r * m;
+  for (int i = jl - 1; i >= 0; --i) {
+    double2 acc = gg[i];
+    for (int k = i + 1; k < jl; ++k) {
+      const double2 a = h[(long)k * (m + 1) + i], b = yy[k];
+      acc.x -= a.x * b.x - a.y * b.y;
+      acc.y -= a.x * b.y + a.y * b.x;
+    }
+    const double2 d = h[(long)i * (m + 1) + i];
+    const double dn = d.x * d.x + d.y * d.y;
+    yy[i] = dn > 0.0 ? make_double2((acc.x * d.x + acc.y * d.y) / dn, (acc.y * d.x - acc.x * d.y) / dn)
+                     : make_double2(0.0, 0.0);
+  }
+}
+
+// u = sum_{i < jlen} y_i V_i.
+template <typename T>
+__global__ void __launch_bounds__(kNT)
+    k_combine(const cx<T>* __restrict__ V, const double2* __restrict__ y,
+              const int* __restrict__ jlen, cx<T>* __restrict__ U, long nu, long vstride, int m) {
+  __shared__ cx<T> ys[520];
+  const int r = blockIdx.y;
+  const int jl = jlen[r];
+  for (int i = threadIdx.x; i < jl; i += kNT) {
+    const double2 v = y[(long)r * m + i];
+    ys[i] = mk<T>((T)v.x, (T)v.y);
+  }
+  __syncthreads();
+  long k0, k1;
+  chunk_of(nu, gridDim.x, k0, k1);
+  const cx<T>* vb = V + r * nu;
+  for (long k = k0 + threadIdx.x; k < k1; k += kNT) {
+    cx<T> acc = zero<T>();
+    for (int i = 0; i < jl; ++i) acc = acc + ys[i] * vb[(long)i * vstride + k];
+    U[r * nu + k] = acc;
+  }
+}
+
+// x += z (complex128 += inner precision) for right-hand sides that iterated.
+template <typename T>
+__global__ void __launch_bounds__(kNT)
+    k_add_x(double2* __restrict__ x, const cx<T>* __restrict__ z, const int* __restrict__ jlen,
+            long nu) {
+  const int r = blockIdx.y;
+  if (jlen[r] == 0) return;
+  long k0, k1;
+  chunk_of(nu, gridDim.x, k0, k1);
+  for (long k = k0 + threadIdx.x; k < k1; k += kNT) {
+    const cx<T> v = z[r * nu + k];
+    double2 a = x[r * nu + k];
+    a.x += (double)v.x;
+    a.y += (double)v.y;
+    x[r * nu + k] = a;
+  }
+}
+
+// r = b - (A x) in place on ax; block shares of ||r||^2 and ||b||^2.
+__global__ void __launch_bounds__(kNT)
+    k_residual(const double2* __restrict__ b, double2* __restrict__ ax, long nu,
+               double2* __restrict__ part) {
+  __shared__ double2 sh[32];
+  const int r = blockIdx.y;
+  long k0, k1;
+  chunk_of(nu, gridDim.x, k0, k1);
+  double rr = 0.0, bb = 0.0;
+  for (long k = k0 + threadIdx.x; k < k1; k += kNT) {
+    const double2 bv = b[r * nu + k];
+    const double2 av = ax[r * nu + k];
+    const double2 d = make_double2(bv.x - av.x, bv.y - av.y);
+    ax[r * nu + k] = d;
+    rr += d.x * d.x + d.y * d.y;
+    bb += bv.x * bv.x + bv.y * bv.y;
+  }
+  const double2 t = block_sum(make_double2(rr, bb), sh);
+  if (threadIdx.x == 0) part[(long)r * gridDim.x + blockIdx.x] = t;
+}
+
+__global__ void k_finish_norms(const double2* __restrict__ part, int nblk, int nrhs,
+                               double* __restrict__ scal) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  double rr = 0.0, bb = 0.0;
+  for (int b = 0; b < nblk; ++b) {
+    rr += part[(long)r * nblk + b].x;
+    bb += part[(long)r * nblk + b].y;
+  }
+  scal[(long)r * 16 + 6] = sqrt(rr);
+  scal[(long)r * 16 + 2] = sqrt(bb);
+}
+
+// Start a cycle: v0 = r/||r||, g = (||r||, 0, ...), target estimate, flags.
+template <typename T>
+__global__ void __launch_bounds__(kNT)
+    k_start_cycle(const double2* __restrict__ R, cx<T>* __restrict__ V0, long nu,
+                  double* __restrict__ scal, double2* __restrict__ g, int m,
+                  const int* __restrict__ run, int* __restrict__ active, int* __restrict__ jlen,
+                  double tol, double inner_tol) {
+  const int r = blockIdx.y;
+  const double beta = scal[(long)r * 16 + 6];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    active[r] = run[r];
+    jlen[r] = 0;
+    g[(long)r * (m + 1)] = make_double2(beta, 0.0);
+    scal[(long)r * 16 + 0] = beta;
+    scal[(long)r * 16 + 3] = fmax(tol * scal[(long)r * 16 + 2], inner_tol * beta);
+  }
+  if (!run[r] || !(beta > 0.0)) return;
+  const double inv = 1.0 / beta;
+  long k0, k1;
+  chunk_of(nu, gridDim.x, k0, k1);
+  for (long k = k0 + threadIdx.x; k < k1; k += kNT) {
+    const double2 v = R[r * nu + k];
+    V0[r * nu + k] = mk<T>((T)(v.x * inv), (T)(v.y * inv));
+  }
+}
+
+template <typename T>
+dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
+                        const dda_solve_opts_t& o, dda_rhs_stats_t* stats, cudaStream_t s) {
+  const long nu = 3 * p->nvox;
+  const int m = o.restart;
+  const int nblk = p->w.nblk;
+  const int pst = m + 2;
+  SolverState& st = p->w.st;
+  cx<T>* V = static_cast<cx<T>*>(p->w.V);
+  cx<T>* W = static_cast<cx<T>*>(p->w.Wv);
+  cx<T>* Z = static_cast<cx<T>*>(p->w.Zv);
+  double2* R = static_cast<double2*>(p->w.R128);
+  const long vstride = (long)nrhs * nu;
+  const dim3 vgrid(nblk, nrhs);
+  const bool prec = o.precond == 3;
+  const double brk = sizeof(T) == 8 ? 1e-13 : 1e-6;
+
+  if (!p->pinned) {
+    if (cudaHostAlloc(&p->pinned, 64, cudaHostAllocDefault) != cudaSuccess) {
+      p->pinned = nullptr;
+      return check_cuda("dda_solve: pinned host word");
+    }
+  }
+  cudaEvent_t ev[2];
+  cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
+
+  cudaMemsetAsync(st.iters, 0, sizeof(int) * nrhs, s);
+  cudaMemsetAsync(st.flags, 0, sizeof(int) * nrhs, s);
+  cudaMemsetAsync(p->w.err_flag, 0, 4, s);
+  std::vector<double> hs((size_t)nrhs * 16);
+  std::vector<int> hits(nrhs), hflags(nrhs), run(nrhs, 0), conv(nrhs, 0), nan(nrhs, 0);
+  std::vector<double> rel(nrhs, 0.0);
+  std::vector<int> ncyc(nrhs, 0);
+
+  dda_status_t status = DDA_OK;
+  for (int cycle = 0;; ++cycle) {
+    // r = b - A x in complex128
+    matvec_impl<double>(p, nrhs, reinterpret_cast<const cx<double>*>(x),
+                        reinterpret_cast<cx<double>*>(R), s);
+    k_residual<<<vgrid, kNT, 0, s>>>(b, R, nu, st.partial);
+    k_finish_norms<<<(nrhs + 127) / 128, 128, 0, s>>>(st.partial, nblk, nrhs, st.scal);
+    cudaMemcpyAsync(hs.data(), st.scal, sizeof(double) * 16 * nrhs, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(hits.data(), st.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(hflags.data(), st.flags, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+      status = check_cuda("dda_solve");
+      break;
+    }
+    int nrun = 0;
+    for (int r = 0; r < nrhs; ++r) {
+      const double bn = hs[r * 16 + 2], rn = hs[r * 16 + 6];
+      rel[r] = bn > 0 ? rn / bn : rn;
+      nan[r] = !std::isfinite(rn) || (hflags[r] & 1);
+      conv[r] = std::isfinite(rn) && (rn <= o.tol * bn || bn == 0.0);
+      run[r] = !conv[r] && !nan[r] && hits[r] < o.max_iters;
+      nrun += run[r];
+    }
+    if (nrun == 0) break;
+    for (int r = 0; r < nrhs; ++r) ncyc[r] += run[r];
+    cudaMemcpyAsync(st.run, run.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s);
+    k_start_cycle<T><<<vgrid, kNT, 0, s>>>(R, V, nu, st.scal, st.g, m, st.run, st.active,
+                                           st.jlen, o.tol, o.inner_tol);
+    // Arnoldi steps
+    int maxit_left = 0;
+    for (int r = 0; r < nrhs; ++r)
+      if (run[r]) maxit_left = std::max(maxit_left, o.max_iters - hits[r]);
+    const int steps = std::min(m, maxit_left);
+    for (int j = 0; j < steps; ++j) {
+      const cx<T>* vj = V + (long)j * vstride;
+      const cx<T>* src = vj;
+      if (prec) {
+        precond_apply_impl<T>(p, nrhs, vj, Z, s);
+        src = Z;
+      }
+      matvec_impl<T>(p, nrhs, src, W, s);
+      for (int pass = 0; pass < 2; ++pass) {
+        k_multidot<T><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.partial, pst, st.active);
+        k_reduce_dots<<<nrhs, 64, 0, s>>>(st.partial, nblk, j + 1, pst, st.hcol, st.H, m, j, pass,
+                                          st.active);
+        k_update<T><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.hcol, m, st.partial, pst,
+                                          st.active);
+      }
+      k_givens<<<(nrhs + 63) / 64, 64, 0, s>>>(st.H, st.cs, st.sn, st.g, st.partial, nblk, pst,
+                                               st.scal, st.active, st.jlen, st.flags, st.iters,
+                                               nrhs, m, j, brk);
+      if (j + 1 < steps)
+        k_scale<T><<<vgrid, kNT, 0, s>>>(W, V + (long)(j + 1) * vstride, nu, st.scal, st.active);
+      k_count_active<<<1, 32, 0, s>>>(st.active, nrhs, st.counters + (j & 1));
+      cudaMemcpyAsync(p->pinned + (j & 1), st.counters + (j & 1), sizeof(int),
+                      cudaMemcpyDeviceToHost, s);
+      cudaEventRecord(ev[j & 1], s);
+      if (j >= 1) {
+        cudaEventSynchronize(ev[(j - 1) & 1]);
+        if (p->pinned[(j - 1) & 1] == 0) break;
+      }
+    }
+    // x += P^{-1} V y
+    k_trisolve<<<(nrhs + 63) / 64, 64, 0, s>>>(st.H, st.g, st.jlen, st.y, nrhs, m);
+    k_combine<T><<<vgrid, kNT, 0, s>>>(V, st.y, st.jlen, W, nu, vstride, m);
+    const cx<T>* upd = W;
+    if (prec) {
+      precond_apply_impl<T>(p, nrhs, W, Z, s);
+      upd = Z;
+    }
+    k_add_x<T><<<vgrid, kNT, 0, s>>>(x, upd, st.jlen, nu);
+    if ((status = check_cuda("dda_solve")) != DDA_OK) break;
+  }
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  if (status != DDA_OK) return status;
+  int perr = 0;
+  cudaMemcpyAsync(&perr, p->w.err_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  bool any_nan = false, any_nc = false;
+  for (int r = 0; r < nrhs; ++r) {
+    any_nan |= nan[r] != 0;
+    any_nc |= !conv[r];
+    if (stats) {
+      stats[r].iters = hits[r];
+      stats[r].cycles = ncyc[r];
+      stats[r].converged = conv[r];
+      stats[r].rel_resid = rel[r];
+      stats[r].status = nan[r] ? DDA_ERR_NAN : (conv[r] ? DDA_OK : DDA_ERR_NOT_CONVERGED);
+    }
+  }
+  if (perr) return fail(DDA_ERR_SINGULAR_PRECOND, "dda_solve: preconditioner symbol is singular");
+  if (any_nan) return fail(DDA_ERR_NAN, "dda_solve: non-finite residual");
+  if (any_nc) return fail(DDA_ERR_NOT_CONVERGED, "dda_solve: tolerance not reached within max_iters");
+  return DDA_OK;
+}
+
+}  // namespace
+
+}  // namespace dda
+
+using namespace dda;
+
+extern "C" dda_status_t dda_solve(dda_plan_t p, int32_t nrhs, const void* d_b, void* d_x,
+                                  const dda_solve_opts_t* opts, dda_rhs_stats_t* h_stats,
+                                  void* stream) {
+  if (!p || !d_x || !opts) return fail(DDA_ERR_INVALID_ARG, "dda_solve: NULL argument");
+  if (p->d.krylov_m < 1) return fail(DDA_ERR_INVALID_ARG, "dda_solve: plan has krylov_m = 0");
+  if (nrhs < 1 || nrhs > p->nrhs_inc)
+    return fail(DDA_ERR_INVALID_ARG, "dda_solve: nrhs must be 1..(incidences set)");
+  const dda_solve_opts_t& o = *opts;
+  if (!(o.tol > 0) || o.max_iters < 1 || o.restart < 1 || o.restart > p->d.krylov_m ||
+      !(o.inner_tol >= 0) || (o.precond != 0 && o.precond != 3))
+    return fail(DDA_ERR_INVALID_ARG, "dda_solve: invalid options");
+  if (o.precond == 3 && !p->precond_built)
+    return fail(DDA_ERR_NO_PRECOND, "dda_solve: call dda_precond_build first");
+  if (!p->has128) return fail(DDA_ERR_INVALID_ARG, "dda_solve: the residual needs complex128 data");
+  if (o.restart + 2 > 518) return fail(DDA_ERR_INVALID_ARG, "dda_solve: restart above 512");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const double2* b = static_cast<const double2*>(d_b);
+  if (!b) {
+    dda_status_t st = dda_incident_field(p, nrhs, p->w.B128, stream);
+    if (st != DDA_OK) return st;
+    b = static_cast<const double2*>(p->w.B128);
+  }
+  if (o.inner_prec == DDA_C128)
+    return solve_impl<double>(p, nrhs, b, static_cast<double2*>(d_x), o, h_stats, s);
+  if (o.inner_prec == DDA_C64) {
+    if (!p->has64) return fail(DDA_ERR_INVALID_ARG, "dda_solve: plan holds no complex64 data");
+    return solve_impl<float>(p, nrhs, b, static_cast<double2*>(d_x), o, h_stats, s);
+  }
+  return fail(DDA_ERR_INVALID_ARG, "dda_solve: inner_prec must be DDA_C128 or DDA_C64");
+}

@@ -1,0 +1,162 @@
+// The BTTB matvec of the DDA system (Section 2.2): y = alpha^{-1} x - dx^3 G x
+// on the scatterer, y = alpha_tilde^{-1} x on air, with G x evaluated as a
+// circulant convolution on the (2l, 2m, 2n) padded grid (the FFT acceleration
+// the paper relies on, Sections 1 and 2.2).
+//
+// Five passes over HBM per right-hand side (u = l m n complex values):
+//   1 x forward   masked x (3u)        -> buf1 (3 n m 2l = 6u), zero-pad pruned
+//   2 y forward   buf1                 -> buf2 (3 n 2m 2l = 12u), zero-pad pruned
+//   3 z           buf2, kernel spectrum -> buf2: forward FFT along z of the n
+//                 live planes, 3x3 symmetric multiply by the spectrum, inverse
+//                 FFT, only the n box planes written back
+//   4 y inverse   buf2 -> buf1 (rows m..2m-1 dropped)
+//   5 x inverse   buf1 -> y: columns l..2l-1 dropped, diagonal term added
+#include "fft_kernels.cuh"
+#include "plan.hpp"
+
+namespace dda {
+
+namespace {
+
+// sum_b Ghat_ab(k) x_b at frequency (kx, ky, kz) of the padded grid; the
+// spectrum is stored for 0 <= k <= L/2 on every axis and mirrored with the
+// block's parity.
+template <typename T>
+struct KernelMul {
+  const cx<T>* G;
+  int Lx, Ly, Lz, hx, hy, lxs;
+  __device__ __forceinline__ void operator()(long, long col, int j, cx<T>& x0, cx<T>& x1,
+                                             cx<T>& x2) const {
+    const int kx = (int)(col & (Lx - 1));
+    const int ky = (int)(col >> lxs);
+    bool f[3];
+    const int fx = fold_axis(kx, Lx, f[0]);
+    const int fy = fold_axis(ky, Ly, f[1]);
+    const int fz = fold_axis(j, Lz, f[2]);
+    cx<T> gxx, gxy, gxz, gyy, gyz, gzz;
+    load_sym6(G + ((size_t)(fz * hy + fy) * hx + fx) * 6, f, gxx, gxy, gxz, gyy, gyz, gzz);
+    const cx<T> y0 = gxx * x0 + gxy * x1 + gxz * x2;
+    const cx<T> y1 = gxy * x0 + gyy * x1 + gyz * x2;
+    const cx<T> y2 = gxz * x0 + gyz * x1 + gzz * x2;
+    x0 = y0;
+    x1 = y1;
+    x2 = y2;
+  }
+};
+
+// Pass 5: inverse FFT along x of each padded line, then
+//   y = a x - coef * conv   (scatterer voxel, a = alpha^{-1} of its material)
+//   y = a x                 (air voxel, a = alpha_tilde^{-1})
+// with coef = dx^3 / (2l 2m 2n) (the inverse transforms are unnormalised).
+template <typename T>
+__global__ void __launch_bounds__(512)
+    k_mv_epilogue(const cx<T>* __restrict__ buf1, const cx<T>* __restrict__ x,
+                  cx<T>* __restrict__ y, const uint8_t* __restrict__ mat,
+                  const cx<T>* __restrict__ ainv, int K1, long nlines, long nm, int l, int Lx,
+                  T coef, const cx<T>* __restrict__ tw, int twshift, RadixPlan rp, int NB) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+  const int ld = NB + 1;
+  cx<T>* stw = s + (size_t)Lx * ld;
+  const long line0 = (long)blockIdx.x * NB;
+  load_twiddles(stw, tw, Lx, twshift);
+  for (int e = threadIdx.x; e < NB * Lx; e += blockDim.x) {
+    const int j = e & (Lx - 1);
+    const int b = e / Lx;
+    const long line = line0 + b;
+    s[j * ld + b] = line < nlines ? buf1[line * Lx + j] : zero<T>();
+  }
+  __syncthreads();
+  smem_fft<true>(s, stw, Lx, NB, ld, rp);
+  for (int e = threadIdx.x; e < NB * l; e += blockDim.x) {
+    const int j = e % l;
+    const int b = e / l;
+    const long line = line0 + b;
+    if (line < nlines) {
+      const long vox = (line % nm) * l + j;
+      const long rhs = line / (3 * nm);
+      const int mt = mat[vox];
+      const cx<T> a = ainv[rhs * K1 + mt];
+      const cx<T> xv = x[line * l + j];
+      cx<T> out = a * xv;
+      if (mt != 0) out = out - coef * s[j * ld + b];
+      y[line * l + j] = out;
+    }
+  }
+}
+
+inline int ilog2(int v) {
+  int b = 0;
+  while ((1 << b) < v) ++b;
+  return b;
+}
+
+}  // namespace
+
+template <typename T>
+void matvec_impl(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t s) {
+  const cx<T>* tw = tw_of<T>(p);
+  cx<T>* b1 = static_cast<cx<T>*>(p->w.buf1);
+  cx<T>* b2 = static_cast<cx<T>*>(p->w.buf2);
+  const long l = p->l, m = p->m, n = p->n, Lx = p->Lx, Ly = p->Ly, Lz = p->Lz;
+  const long nm = n * m;
+  const long lines = (long)nrhs * 3 * nm;
+  const long plane = Ly * Lx;
+  // 1: x forward of the masked field, l -> 2l
+  launch_contig<T, false>(x, b1, p->mat, nm, lines, (int)Lx, (int)l, l, (int)Lx, Lx, T(1), tw,
+                          p->Lmax, s);
+  // 2: y forward, m -> 2m
+  launch_strided<T, false>(b1, b2, Lx, (long)nrhs * 3 * n, (int)Ly, (int)m, Lx, m * Lx, (int)Ly,
+                           Lx, plane, T(1), tw, p->Lmax, s);
+  // 3: z forward, spectrum multiply, z inverse (n live planes in and out)
+  KernelMul<T> op{G_of<T>(p), (int)Lx, (int)Ly, (int)Lz, p->hx, p->hy, ilog2((int)Lx)};
+  launch_fft3c<T>(b2, plane, nrhs, (int)Lz, (int)n, plane, n * plane, 3 * n * plane, (int)n, op,
+                  tw, p->Lmax, s);
+  // 4: y inverse, 2m -> m
+  launch_strided<T, true>(b2, b1, Lx, (long)nrhs * 3 * n, (int)Ly, (int)Ly, Lx, plane, (int)m, Lx,
+                          m * Lx, T(1), tw, p->Lmax, s);
+  // 5: x inverse and the diagonal
+  {
+    const int cap = 512 * kElemsPerThread;
+    int per_cta = std::min(4096, cap);
+    while (per_cta > 512 && per_cta > Lx && (lines * Lx + per_cta - 1) / per_cta < 2 * 152)
+      per_cta /= 2;
+    int NB = std::max<int>(1, per_cta / (int)Lx);
+    while (NB * Lx < kElemsPerThread * 32) NB *= 2;
+    const int nth = NB * (int)Lx / kElemsPerThread;
+    const size_t smem = ((size_t)Lx * (NB + 1) + Lx) * sizeof(cx<T>);
+    auto kern = k_mv_epilogue<T>;
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const T coef = (T)(p->d.dx * p->d.dx * p->d.dx / (double)p->P);
+    kern<<<(unsigned)((lines + NB - 1) / NB), nth, smem, s>>>(
+        b1, x, y, p->mat, ainv_of<T>(p), p->K + 1, lines, nm, (int)l, (int)Lx, coef, tw,
+        p->Lmax / (int)Lx, make_radix_plan((int)Lx), NB);
+  }
+}
+
+template void matvec_impl<float>(dda_plan_s*, int, const cx<float>*, cx<float>*, cudaStream_t);
+template void matvec_impl<double>(dda_plan_s*, int, const cx<double>*, cx<double>*, cudaStream_t);
+
+}  // namespace dda
+
+using namespace dda;
+
+extern "C" dda_status_t dda_matvec(dda_plan_t p, int32_t prec, int32_t nrhs, const void* d_x,
+                                   void* d_y, void* stream) {
+  if (!p || !d_x || !d_y) return fail(DDA_ERR_INVALID_ARG, "dda_matvec: NULL argument");
+  if (nrhs < 1 || nrhs > p->nrhs_inc)
+    return fail(DDA_ERR_INVALID_ARG, "dda_matvec: nrhs must be 1..(incidences set)");
+  if (d_x == d_y) return fail(DDA_ERR_INVALID_ARG, "dda_matvec: x and y must not overlap");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (prec == DDA_C128) {
+    if (!p->has128) return fail(DDA_ERR_INVALID_ARG, "dda_matvec: plan holds no complex128 data");
+    matvec_impl<double>(p, nrhs, static_cast<const cx<double>*>(d_x), static_cast<cx<double>*>(d_y), s);
+  } else if (prec == DDA_C64) {
+    if (!p->has64) return fail(DDA_ERR_INVALID_ARG, "dda_matvec: plan holds no complex64 data");
+    matvec_impl<float>(p, nrhs, static_cast<const cx<float>*>(d_x), static_cast<cx<float>*>(d_y), s);
+  } else {
+    return fail(DDA_ERR_INVALID_ARG, "dda_matvec: prec must be DDA_C128 or DDA_C64");
+  }
+  return check_cuda("dda_matvec");
+}

@@ -1,0 +1,118 @@
+// Cross sections of a solution.  The paper prints no formula for them; these
+// are the standard DDA expressions of Draine & Flatau for a unit-amplitude
+// plane wave, written for the paper's unknowns c (dipole moments p = dx^3 c,
+// Draine-Flatau polarizability dx^3 alpha), sums over scatterer voxels:
+//   C_ext = 4 pi k dx^3 sum Im(conj(E_inc) . c)
+//   C_abs = 4 pi k [ -dx^3 sum Im(alpha^{-1}) |c|^2 - (2/3) k^3 dx^6 sum |c|^2 ]
+//   C_sca = 4 pi k [ Im(p^H G p) + (2/3) k^3 dx^6 sum |c|^2 ],
+// where p^H G p (G without its diagonal) comes from one complex128 matvec
+// y = A c:  dx^3 G c = alpha^{-1} c - y on scatterer voxels, so
+//   Im(p^H G p) = dx^3 [ sum Im(alpha^{-1}) |c|^2 - Im sum conj(c) . y ].
+// Because G is complex symmetric, Im(p^H G p) = p^H Im(G) p, the quadratic
+// form of the scattered power.
+#include <cmath>
+#include <vector>
+
+#include "plan.hpp"
+
+namespace dda {
+
+namespace {
+
+constexpr int kNT = 256;
+
+__device__ __forceinline__ double warp_sum1(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Per block: S[0] = sum Im(alpha^{-1})|c|^2, S[1] = sum |c|^2,
+// S[2] = Im sum conj(c) . y, S[3] = sum Im(conj(E_inc) . c), scatterer only.
+__global__ void __launch_bounds__(kNT)
+    k_xsec_sums(const double2* __restrict__ c, const double2* __restrict__ y,
+                const uint8_t* __restrict__ mat, const double2* __restrict__ ainv, int K1,
+                const double* __restrict__ inc, long l, long m, long n, double dx, double k,
+                double* __restrict__ part) {
+  __shared__ double sh[4][32];
+  const int r = blockIdx.y;
+  const long nvox = l * m * n;
+  const long chunk = (nvox + gridDim.x - 1) / gridDim.x;
+  const long v0 = blockIdx.x * chunk, v1 = min(nvox, v0 + chunk);
+  const double* d = inc + r * 6;
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long v = v0 + threadIdx.x; v < v1; v += kNT) {
+    const int mt = mat[v];
+    if (mt == 0) continue;
+    const double2 a = ainv[(long)r * K1 + mt];
+    const long x = v % l, yy = (v / l) % m, z = v / (l * m);
+    const double px = dx * (x - 0.5 * (l - 1)), py = dx * (yy - 0.5 * (m - 1)),
+                 pz = dx * (z - 0.5 * (n - 1));
+    double sn, cs;
+    sincos(k * (d[0] * px + d[1] * py + d[2] * pz), &sn, &cs);
+    for (int q = 0; q < 3; ++q) {
+      const double2 cv = c[((long)r * 3 + q) * nvox + v];
+      const double2 yv = y[((long)r * 3 + q) * nvox + v];
+      const double c2 = cv.x * cv.x + cv.y * cv.y;
+      s[0] += a.y * c2;
+      s[1] += c2;
+      s[2] += cv.x * yv.y - cv.y * yv.x;  // Im(conj(c) y)
+      // E_inc_q = pol_q (cos + i sin): Im(conj(E) c) = pol_q (cos c.y - sin c.x)
+      s[3] += d[3 + q] * (cs * cv.y - sn * cv.x);
+    }
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int q = 0; q < 4; ++q) {
+    const double t = warp_sum1(s[q]);
+    if (lane == 0) sh[q][wid] = t;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    for (int q = 0; q < 4; ++q) {
+      double t = lane < (kNT >> 5) ? sh[q][lane] : 0.0;
+      t = warp_sum1(t);
+      if (lane == 0) part[((long)r * gridDim.x + blockIdx.x) * 4 + q] = t;
+    }
+  }
+}
+
+}  // namespace
+
+}  // namespace dda
+
+using namespace dda;
+
+extern "C" dda_status_t dda_cross_sections(dda_plan_t p, int32_t nrhs, const void* d_c,
+                                           double* h_out, void* stream) {
+  if (!p || !d_c || !h_out) return fail(DDA_ERR_INVALID_ARG, "dda_cross_sections: NULL argument");
+  if (nrhs < 1 || nrhs > p->nrhs_inc)
+    return fail(DDA_ERR_INVALID_ARG, "dda_cross_sections: nrhs must be 1..(incidences set)");
+  if (!p->has128)
+    return fail(DDA_ERR_INVALID_ARG, "dda_cross_sections: plan holds no complex128 data");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const cx<double>* c = static_cast<const cx<double>*>(d_c);
+  cx<double>* y = static_cast<cx<double>*>(p->w.R128);
+  matvec_impl<double>(p, nrhs, c, y, s);
+  const int nblk = (int)std::min<long>(304, std::max<long>(1, (p->nvox + 4095) / 4096));
+  // partial sums go to the head of buf1 (free once the matvec is done)
+  double* part = static_cast<double*>(p->w.buf1);
+  k_xsec_sums<<<dim3(nblk, nrhs), kNT, 0, s>>>(
+      reinterpret_cast<const double2*>(c), reinterpret_cast<const double2*>(y), p->mat,
+      static_cast<const double2*>(p->w.ainv128), p->K + 1, p->w.incd, p->l, p->m, p->n, p->d.dx,
+      p->d.k, part);
+  std::vector<double> h((size_t)nrhs * nblk * 4);
+  cudaMemcpyAsync(h.data(), part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return check_cuda("dda_cross_sections");
+  const double pi = 3.14159265358979323846;
+  const double k = p->d.k, dx3 = p->d.dx * p->d.dx * p->d.dx;
+  for (int r = 0; r < nrhs; ++r) {
+    double S[4] = {0, 0, 0, 0};
+    for (int b = 0; b < nblk; ++b)
+      for (int q = 0; q < 4; ++q) S[q] += h[((size_t)r * nblk + b) * 4 + q];
+    const double rad = (2.0 / 3.0) * k * k * k * dx3 * dx3 * S[1];
+    h_out[3 * r + 0] = 4.0 * pi * k * dx3 * S[3];
+    h_out[3 * r + 1] = 4.0 * pi * k * (-dx3 * S[0] - rad);
+    h_out[3 * r + 2] = 4.0 * pi * k * (dx3 * (S[0] - S[2]) + rad);
+  }
+  return check_cuda("dda_cross_sections");
+}

@@ -1,0 +1,164 @@
+// Host-side plan object, workspace layout and shared launch helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dda.h"
+#include "cx.cuh"
+#include "fft_core.cuh"
+
+namespace dda {
+
+// Thread-local error text, set by fail().
+void set_error(const std::string& msg);
+dda_status_t fail(dda_status_t st, const std::string& msg);
+dda_status_t check_cuda(const char* where);
+
+inline bool is_pow2(long v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Bump allocator over the caller's workspace; with base == 0 it only measures.
+struct Carver {
+  uintptr_t base;
+  size_t off = 0;
+  explicit Carver(void* b) : base(reinterpret_cast<uintptr_t>(b)) {}
+  void* take(size_t bytes) {
+    off = (off + 255) & ~size_t(255);
+    void* p = reinterpret_cast<void*>(base + off);
+    off += bytes;
+    return p;
+  }
+};
+
+// Device-side GMRES state per right-hand side (FP64).
+struct SolverState {
+  double2* H;        // [rhs][(m+1) * m], column-major: H[j*(m+1) + i]
+  double* cs;        // [rhs][m]
+  double2* sn;       // [rhs][m]
+  double2* g;        // [rhs][m+1]
+  double2* y;        // [rhs][m]
+  double2* hcol;     // [rhs][m+1]   current column (dots of this step)
+  double2* partial;  // [rhs][nblk][m+2] block partial sums
+  double* scal;      // [rhs][8]: 0 beta, 1 ||w||^2, 2 bnorm, 3 target, 4 resid estimate,
+                     //            5 1/h(j+1,j), 6 r-norm (FP64), 7 spare
+  int* active;       // [rhs] 1 while the current cycle of this RHS is running
+  int* jlen;         // [rhs] Arnoldi steps taken in the current cycle
+  int* flags;        // [rhs] error bits (1 nan, 2 breakdown)
+  int* iters;        // [rhs] inner iterations so far
+  int* run;          // [rhs] 1 when the right-hand side takes part in this cycle
+  int* counters;     // [16] 0: RHS still iterating in the current cycle
+};
+
+struct Layout {
+  // spectra, octant-compressed: [(hz)(hy)(hx)][6]
+  void* G128 = nullptr;
+  void* G64 = nullptr;
+  void* C128 = nullptr;
+  void* C64 = nullptr;
+  // twiddles for the largest transform length
+  void* tw128 = nullptr;
+  void* tw64 = nullptr;
+  // alpha^{-1} per (rhs, material 0..K); entry 0 is alpha_tilde^{-1}
+  void* ainv128 = nullptr;
+  void* ainv64 = nullptr;
+  double* incd = nullptr;  // [rhs][6]: direction, polarisation
+  int nblk = 1;            // reduction blocks per right-hand side
+  // FFT scratch
+  void* buf1 = nullptr;
+  void* buf2 = nullptr;
+  // solver vectors
+  void* V = nullptr;       // [(m+1)][rhs][nu] inner precision
+  void* Wv = nullptr;      // [rhs][nu] inner precision (A P^-1 v)
+  void* Zv = nullptr;      // [rhs][nu] inner precision (P^-1 v)
+  void* R128 = nullptr;    // [rhs][nu] complex128 residual
+  void* B128 = nullptr;    // [rhs][nu] complex128 right-hand side
+  SolverState st{};
+  void* err_flag = nullptr;  // int, device status bits of kernels
+  size_t total = 0;
+};
+
+}  // namespace dda
+
+struct dda_plan_s {
+  dda_plan_desc_t d;
+  int l, m, n;        // box
+  int Lx, Ly, Lz;     // padded transform lengths (2l, 2m, 2n)
+  int Lmax;           // largest transform length (twiddle table size)
+  long nvox;          // l*m*n
+  long P;             // Lx*Ly*Lz
+  int hx, hy, hz;     // compressed kernel spectrum extents (L/2 + 1)
+  int cx_, cy_, cz_;  // compressed circulant spectrum extents (l/2 + 1, ...)
+  int K;              // materials
+  const uint8_t* mat;
+  std::vector<double> eps;  // 2K
+  std::vector<long> mat_count;  // voxels per material 0..K
+  dda::Layout w;
+  bool has128, has64;
+  bool precond_built = false;
+  int nrhs_inc = 0;                      // RHS count of the last dda_set_incidence
+  std::vector<dda_incidence_t> inc;      // incidence per RHS
+  std::vector<double> ainv_host;         // [rhs][K+1][2]
+  std::vector<float> ainv_host32;
+  int* pinned = nullptr;                 // host-pinned words polled by the solver
+};
+
+namespace dda {
+
+// Layout of a plan's workspace; with ws == nullptr only the size is computed.
+bool make_layout(const dda_plan_desc_t& d, void* ws, Layout& L, std::string& why);
+
+// FFT launch helpers (fft_launch.cu), in place when in == out.
+template <typename T, bool INV>
+void launch_contig(const cx<T>* in, cx<T>* out, const uint8_t* mask, long mask_lines, long nlines,
+                   int L, int Lin, long in_ld, int Lout, long out_ld, T scale, const cx<T>* tw,
+                   int Lmax, cudaStream_t s);
+template <typename T, bool INV>
+void launch_strided(const cx<T>* in, cx<T>* out, long ncols, long nslabs, int L, int Lin,
+                    long in_js, long in_ss, int Lout, long out_js, long out_ss, T scale,
+                    const cx<T>* tw, int Lmax, cudaStream_t s);
+// Full in-place 3-D transform of nbatch arrays [batch][Lz][Ly][Lx].
+template <typename T, bool INV>
+void fft3d_inplace(cx<T>* data, long nbatch, int Lx, int Ly, int Lz, T scale, const cx<T>* tw,
+                   int Lmax, cudaStream_t s);
+
+// Operator pieces (matvec.cu, precond.cu), nrhs fields of the box.
+template <typename T>
+void matvec_impl(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t s);
+template <typename T>
+void precond_apply_impl(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cudaStream_t s);
+
+// Templated accessors of the plan's precision-specific buffers.
+template <typename T> inline const cx<T>* tw_of(const dda_plan_s* p);
+template <> inline const cx<double>* tw_of<double>(const dda_plan_s* p) {
+  return static_cast<const cx<double>*>(p->w.tw128);
+}
+template <> inline const cx<float>* tw_of<float>(const dda_plan_s* p) {
+  return static_cast<const cx<float>*>(p->w.tw64);
+}
+template <typename T> inline const cx<T>* G_of(const dda_plan_s* p);
+template <> inline const cx<double>* G_of<double>(const dda_plan_s* p) {
+  return static_cast<const cx<double>*>(p->w.G128);
+}
+template <> inline const cx<float>* G_of<float>(const dda_plan_s* p) {
+  return static_cast<const cx<float>*>(p->w.G64);
+}
+template <typename T> inline const cx<T>* C_of(const dda_plan_s* p);
+template <> inline const cx<double>* C_of<double>(const dda_plan_s* p) {
+  return static_cast<const cx<double>*>(p->w.C128);
+}
+template <> inline const cx<float>* C_of<float>(const dda_plan_s* p) {
+  return static_cast<const cx<float>*>(p->w.C64);
+}
+template <typename T> inline const cx<T>* ainv_of(const dda_plan_s* p);
+template <> inline const cx<double>* ainv_of<double>(const dda_plan_s* p) {
+  return static_cast<const cx<double>*>(p->w.ainv128);
+}
+template <> inline const cx<float>* ainv_of<float>(const dda_plan_s* p) {
+  return static_cast<const cx<float>*>(p->w.ainv64);
+}
+
+}  // namespace dda

@@ -1,0 +1,209 @@
+// The 3-level circulant preconditioner P = alpha_tilde^{-1} I - dx^3 C.
+//
+// Build (Section 3): every one of the six unique BTTB blocks is replaced by
+// T. Chan's optimal circulant (eq. 13) on the x, y and z levels in turn,
+// which in closed form is
+//   c(p,q,r) = sum_{a in {p, p-l}} sum_{b in {q, q-m}} sum_{c in {r, r-n}}
+//              w_l(a) w_m(b) w_n(c) g(a dx, b dx, c dx),
+//   w_L(p) = (L - p)/L,  w_L(p - L) = p/L   (0 <= p < L),  g(0) = 0,
+// evaluated directly at the signed offsets, followed by a 3-D DFT of the
+// l x m x n first column (a multilevel circulant is diagonalised by the
+// multilevel DFT, Section 3).  The spectrum keeps one octant: C inherits the
+// parity of each block on each level.
+//
+// Apply: 3-D FFT of each field component, the 3x3 symbol
+//   Lambda(w) = alpha_tilde^{-1} I - dx^3 Chat(w)
+// solved per frequency (closed-form inverse of a complex symmetric 3x3
+// matrix), inverse FFT.  Lambda is formed on the fly from the stored Chat and
+// the right-hand side's alpha_tilde, so one build serves every incident wave.
+#include "fft_kernels.cuh"
+#include "plan.hpp"
+
+namespace dda {
+
+namespace {
+
+__device__ const int kA[6] = {0, 0, 0, 1, 1, 2};
+__device__ const int kB[6] = {0, 1, 2, 1, 2, 2};
+
+// First column of the 3-level circulant of all six blocks, FP64, layout
+// [comp][z][y][x].
+__global__ void k_chan3(double2* out, long l, long m, long n, double dx, double k) {
+  const long nvox = l * m * n;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nvox;
+       i += (long)gridDim.x * blockDim.x) {
+    const long p = i % l, q = (i / l) % m, r = i / (l * m);
+    double acc[6][2] = {};
+    for (int sa = 0; sa < 2; ++sa) {
+      if (sa == 1 && p == 0) continue;
+      const long a = sa ? p - l : p;
+      const double wa = sa ? (double)p / l : (double)(l - p) / l;
+      for (int sb = 0; sb < 2; ++sb) {
+        if (sb == 1 && q == 0) continue;
+        const long b = sb ? q - m : q;
+        const double wb = sb ? (double)q / m : (double)(m - q) / m;
+        for (int sc = 0; sc < 2; ++sc) {
+          if (sc == 1 && r == 0) continue;
+          const long c = sc ? r - n : r;
+          const double wc = sc ? (double)r / n : (double)(n - r) / n;
+          if ((a | b | c) == 0) continue;  // g(0) = 0: the self term is alpha^{-1}
+          const double w = wa * wb * wc;
+          const double X = dx * a, Y = dx * b, Z = dx * c;
+          const double r2 = X * X + Y * Y + Z * Z;
+          const double rr = sqrt(r2);
+          const double rv[3] = {X / rr, Y / rr, Z / rr};
+          double sn, cs;
+          sincos(k * rr, &sn, &cs);
+          const double er = cs / rr, ei = sn / rr;
+          for (int cc = 0; cc < 6; ++cc) {
+            const double dlt = (kA[cc] == kB[cc]) ? 1.0 : 0.0;
+            const double pp = rv[kA[cc]] * rv[kB[cc]];
+            const double qq = (dlt - 3.0 * pp) / r2;
+            const double br = k * k * (dlt - pp) - qq;
+            const double bi = k * rr * qq;
+            acc[cc][0] += w * (er * br - ei * bi);
+            acc[cc][1] += w * (er * bi + ei * br);
+          }
+        }
+      }
+    }
+    for (int cc = 0; cc < 6; ++cc) out[cc * nvox + i] = make_double2(acc[cc][0], acc[cc][1]);
+  }
+}
+
+// Keep 0..l/2, 0..m/2, 0..n/2 of the six spectra, interleaved [..][6].
+__global__ void k_compress6(const double2* full, long l, long m, long n, long hx, long hy,
+                            long hz, double2* out128, float2* out64) {
+  const long H = hx * hy * hz, nvox = l * m * n;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < H;
+       i += (long)gridDim.x * blockDim.x) {
+    const long x = i % hx, y = (i / hx) % hy, z = i / (hx * hy);
+    for (int c = 0; c < 6; ++c) {
+      const double2 v = full[c * nvox + (z * m + y) * l + x];
+      if (out128) out128[i * 6 + c] = v;
+      if (out64) out64[i * 6 + c] = make_float2((float)v.x, (float)v.y);
+    }
+  }
+}
+
+// z(w) = Lambda(w)^{-1} x(w) / (l m n) (the inverse transforms are unnormalised).
+template <typename T>
+struct CircSolve {
+  const cx<T>* C;
+  const cx<T>* ainv;
+  int* err;
+  int K1, l, m, n, hx, hy, lxs;
+  T dx3, inv_n;
+  __device__ __forceinline__ void operator()(long rhs, long col, int j, cx<T>& x0, cx<T>& x1,
+                                             cx<T>& x2) const {
+    const int wx = (int)(col & (l - 1));
+    const int wy = (int)(col >> lxs);
+    bool f[3];
+    const int fx = fold_axis(wx, l, f[0]);
+    const int fy = fold_axis(wy, m, f[1]);
+    const int fz = fold_axis(j, n, f[2]);
+    cx<T> cxx, cxy, cxz, cyy, cyz, czz;
+    load_sym6(C + ((size_t)(fz * hy + fy) * hx + fx) * 6, f, cxx, cxy, cxz, cyy, cyz, czz);
+    const cx<T> at = ainv[rhs * K1];
+    // Lambda = [[a b c] [b d e] [c e f]]
+    const cx<T> a = at - dx3 * cxx, d = at - dx3 * cyy, ff = at - dx3 * czz;
+    const cx<T> b = -dx3 * cxy, c = -dx3 * cxz, e = -dx3 * cyz;
+    // adjugate of a symmetric matrix
+    const cx<T> A00 = d * ff - e * e, A01 = c * e - b * ff, A02 = b * e - c * d;
+    const cx<T> A11 = a * ff - c * c, A12 = b * c - a * e, A22 = a * d - b * b;
+    const cx<T> det = a * A00 + b * A01 + c * A02;
+    const T dn = norm2(det);
+    if (!(dn > T(0)) || !isfinite(dn)) {
+      atomicOr(err, 1);
+      return;
+    }
+    // inv_n / det
+    const cx<T> sdet = mk<T>(inv_n * det.x / dn, -inv_n * det.y / dn);
+    const cx<T> y0 = A00 * x0 + A01 * x1 + A02 * x2;
+    const cx<T> y1 = A01 * x0 + A11 * x1 + A12 * x2;
+    const cx<T> y2 = A02 * x0 + A12 * x1 + A22 * x2;
+    x0 = sdet * y0;
+    x1 = sdet * y1;
+    x2 = sdet * y2;
+  }
+};
+
+inline int ilog2(int v) {
+  int b = 0;
+  while ((1 << b) < v) ++b;
+  return b;
+}
+
+inline unsigned grid_for(long n, int threads) {
+  const long g = (n + threads - 1) / threads;
+  return (unsigned)std::min<long>(std::max<long>(g, 1), 152L * 32);
+}
+
+}  // namespace
+
+template <typename T>
+void precond_apply_impl(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cudaStream_t s) {
+  const cx<T>* tw = tw_of<T>(p);
+  cx<T>* t = static_cast<cx<T>*>(p->w.buf2);
+  const long l = p->l, m = p->m, n = p->n;
+  const long lines = (long)nrhs * 3 * n * m;
+  const long plane = l * m;
+  launch_contig<T, false>(v, t, nullptr, 1, lines, (int)l, (int)l, l, (int)l, l, T(1), tw, p->Lmax, s);
+  if (m > 1)
+    launch_strided<T, false>(t, t, l, (long)nrhs * 3 * n, (int)m, (int)m, l, plane, (int)m, l, plane,
+                             T(1), tw, p->Lmax, s);
+  CircSolve<T> op{C_of<T>(p), ainv_of<T>(p), static_cast<int*>(p->w.err_flag), p->K + 1,
+                  (int)l, (int)m, (int)n, p->cx_, p->cy_, ilog2((int)l),
+                  (T)(p->d.dx * p->d.dx * p->d.dx), (T)(1.0 / (double)p->nvox)};
+  launch_fft3c<T>(t, plane, nrhs, (int)n, (int)n, plane, n * plane, 3 * n * plane, (int)n, op, tw,
+                  p->Lmax, s);
+  if (m > 1)
+    launch_strided<T, true>(t, t, l, (long)nrhs * 3 * n, (int)m, (int)m, l, plane, (int)m, l, plane,
+                            T(1), tw, p->Lmax, s);
+  launch_contig<T, true>(t, z, nullptr, 1, lines, (int)l, (int)l, l, (int)l, l, T(1), tw, p->Lmax, s);
+}
+
+template void precond_apply_impl<float>(dda_plan_s*, int, const cx<float>*, cx<float>*, cudaStream_t);
+template void precond_apply_impl<double>(dda_plan_s*, int, const cx<double>*, cx<double>*,
+                                         cudaStream_t);
+
+}  // namespace dda
+
+using namespace dda;
+
+extern "C" dda_status_t dda_precond_build(dda_plan_t p, void* stream) {
+  if (!p) return fail(DDA_ERR_INVALID_ARG, "dda_precond_build: NULL plan");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  double2* full = static_cast<double2*>(p->w.buf2);
+  k_chan3<<<grid_for(p->nvox, 128), 128, 0, s>>>(full, p->l, p->m, p->n, p->d.dx, p->d.k);
+  fft3d_inplace<double, false>(reinterpret_cast<cx<double>*>(full), 6, p->l, p->m, p->n, 1.0,
+                               tw_of<double>(p), p->Lmax, s);
+  k_compress6<<<grid_for((long)p->cx_ * p->cy_ * p->cz_, 256), 256, 0, s>>>(
+      full, p->l, p->m, p->n, p->cx_, p->cy_, p->cz_, static_cast<double2*>(p->w.C128),
+      static_cast<float2*>(p->w.C64));
+  const dda_status_t st = check_cuda("dda_precond_build");
+  if (st == DDA_OK) p->precond_built = true;
+  return st;
+}
+
+extern "C" dda_status_t dda_precond_apply(dda_plan_t p, int32_t prec, int32_t nrhs, const void* d_v,
+                                          void* d_z, void* stream) {
+  if (!p || !d_v || !d_z) return fail(DDA_ERR_INVALID_ARG, "dda_precond_apply: NULL argument");
+  if (!p->precond_built)
+    return fail(DDA_ERR_NO_PRECOND, "dda_precond_apply: call dda_precond_build first");
+  if (nrhs < 1 || nrhs > p->nrhs_inc)
+    return fail(DDA_ERR_INVALID_ARG, "dda_precond_apply: nrhs must be 1..(incidences set)");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (prec == DDA_C128) {
+    if (!p->has128) return fail(DDA_ERR_INVALID_ARG, "dda_precond_apply: plan holds no complex128 data");
+    precond_apply_impl<double>(p, nrhs, static_cast<const cx<double>*>(d_v),
+                               static_cast<cx<double>*>(d_z), s);
+  } else if (prec == DDA_C64) {
+    if (!p->has64) return fail(DDA_ERR_INVALID_ARG, "dda_precond_apply: plan holds no complex64 data");
+    precond_apply_impl<float>(p, nrhs, static_cast<const cx<float>*>(d_v),
+                              static_cast<cx<float>*>(d_z), s);
+  } else {
+    return fail(DDA_ERR_INVALID_ARG, "dda_precond_apply: prec must be DDA_C128 or DDA_C64");
+  }
+  return check_cuda("dda_precond_apply");
+}

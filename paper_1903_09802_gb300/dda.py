@@ -1,0 +1,241 @@
+"""ctypes binding of libdda.so (the C ABI declared in include/dda.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  PyTorch supplies device memory and the current CUDA stream.  Box
+fields are complex tensors of shape (nrhs, 3, n, m, l) on the plan's device.
+If the library is missing this module raises at import time; there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdda.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with paper_1903_09802_gb300.build.build()")
+_lib = ctypes.CDLL(LIB_PATH)
+
+C128, C64 = 0, 1
+PLAN_C128, PLAN_C64 = 1, 2
+
+STATUS = {
+    0: "DDA_OK", 1: "DDA_ERR_INVALID_ARG", 2: "DDA_ERR_UNSUPPORTED_SIZE", 3: "DDA_ERR_WORKSPACE",
+    4: "DDA_ERR_CUDA", 5: "DDA_ERR_NOT_CONVERGED", 6: "DDA_ERR_BREAKDOWN",
+    7: "DDA_ERR_SINGULAR_PRECOND", 8: "DDA_ERR_NAN", 9: "DDA_ERR_TIMEOUT", 10: "DDA_ERR_NO_PRECOND",
+}
+
+EXPORTS = ("dda_workspace_size", "dda_plan_create", "dda_set_incidence", "dda_incident_field",
+           "dda_matvec", "dda_precond_build", "dda_precond_apply", "dda_fft3d", "dda_solve",
+           "dda_cross_sections", "dda_plan_destroy", "dda_last_error")
+
+
+class DDAError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [("l", ctypes.c_int32), ("m", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("dx", ctypes.c_double), ("k", ctypes.c_double),
+                ("n_materials", ctypes.c_int32), ("max_rhs", ctypes.c_int32),
+                ("krylov_m", ctypes.c_int32), ("precisions", ctypes.c_int32)]
+
+
+class Incidence(ctypes.Structure):
+    _fields_ = [("dir", ctypes.c_double * 3), ("pol", ctypes.c_double * 3)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iters", ctypes.c_int32),
+                ("restart", ctypes.c_int32), ("precond", ctypes.c_int32),
+                ("inner_prec", ctypes.c_int32), ("inner_tol", ctypes.c_double)]
+
+
+class RhsStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("cycles", ctypes.c_int32),
+                ("converged", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("rel_resid", ctypes.c_double)]
+
+
+_vp = ctypes.c_void_p
+_lib.dda_workspace_size.restype = ctypes.c_size_t
+_lib.dda_workspace_size.argtypes = [ctypes.POINTER(PlanDesc)]
+_lib.dda_plan_create.restype = ctypes.c_int
+_lib.dda_plan_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(PlanDesc), _vp,
+                                 ctypes.POINTER(ctypes.c_double), _vp, ctypes.c_size_t, _vp]
+_lib.dda_set_incidence.restype = ctypes.c_int
+_lib.dda_set_incidence.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(Incidence), _vp]
+_lib.dda_incident_field.restype = ctypes.c_int
+_lib.dda_incident_field.argtypes = [_vp, ctypes.c_int32, _vp, _vp]
+_lib.dda_matvec.restype = ctypes.c_int
+_lib.dda_matvec.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp]
+_lib.dda_precond_build.restype = ctypes.c_int
+_lib.dda_precond_build.argtypes = [_vp, _vp]
+_lib.dda_precond_apply.restype = ctypes.c_int
+_lib.dda_precond_apply.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp]
+_lib.dda_fft3d.restype = ctypes.c_int
+_lib.dda_fft3d.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int32, _vp]
+_lib.dda_solve.restype = ctypes.c_int
+_lib.dda_solve.argtypes = [_vp, ctypes.c_int32, _vp, _vp, ctypes.POINTER(SolveOpts),
+                           ctypes.POINTER(RhsStats), _vp]
+_lib.dda_cross_sections.restype = ctypes.c_int
+_lib.dda_cross_sections.argtypes = [_vp, ctypes.c_int32, _vp, ctypes.POINTER(ctypes.c_double), _vp]
+_lib.dda_plan_destroy.restype = None
+_lib.dda_plan_destroy.argtypes = [_vp]
+_lib.dda_last_error.restype = ctypes.c_char_p
+_lib.dda_last_error.argtypes = []
+
+
+def lib():
+    return _lib
+
+
+def last_error() -> str:
+    return _lib.dda_last_error().decode()
+
+
+def _check(status: int):
+    if status != 0:
+        raise DDAError(status, last_error())
+
+
+def _stream() -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: torch.Tensor) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _prec_of(t: torch.Tensor) -> int:
+    if t.dtype == torch.complex128:
+        return C128
+    if t.dtype == torch.complex64:
+        return C64
+    raise TypeError(f"box fields are complex64 or complex128, got {t.dtype}")
+
+
+def workspace_size(l, m, n, dx, k, n_materials=1, max_rhs=1, krylov_m=0,
+                   precisions=PLAN_C128 | PLAN_C64) -> int:
+    d = PlanDesc(l, m, n, dx, k, n_materials, max_rhs, krylov_m, precisions)
+    return int(_lib.dda_workspace_size(ctypes.byref(d)))
+
+
+@dataclass
+class SolveResult:
+    x: torch.Tensor
+    iters: list
+    cycles: list
+    converged: list
+    rel_resid: list
+    status: int
+
+
+class Plan:
+    """A DDA problem on one box: geometry, materials, wavenumber, workspace."""
+
+    def __init__(self, mat: torch.Tensor, eps, dx: float, k: float, max_rhs: int = 1,
+                 krylov_m: int = 0, precisions: int = PLAN_C128 | PLAN_C64):
+        if mat.dtype != torch.uint8 or not mat.is_cuda or mat.dim() != 3:
+            raise TypeError("mat must be a (n, m, l) uint8 CUDA tensor")
+        self.mat = mat.contiguous()
+        n, m, l = self.mat.shape
+        self.shape = (l, m, n)
+        eps = [complex(e) for e in eps]
+        self.desc = PlanDesc(l, m, n, float(dx), float(k), len(eps), int(max_rhs), int(krylov_m),
+                             int(precisions))
+        size = int(_lib.dda_workspace_size(ctypes.byref(self.desc)))
+        if size == 0:
+            raise DDAError(1, last_error())
+        self.work = torch.empty(size, dtype=torch.uint8, device=self.mat.device)
+        heps = (ctypes.c_double * (2 * len(eps)))(*[v for e in eps for v in (e.real, e.imag)])
+        h = ctypes.c_void_p()
+        _check(_lib.dda_plan_create(ctypes.byref(h), ctypes.byref(self.desc), _ptr(self.mat), heps,
+                                    _ptr(self.work), size, _stream()))
+        self._h = h
+        self.nrhs = 0
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.dda_plan_destroy(h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def field_shape(self, nrhs):
+        l, m, n = self.shape
+        return (nrhs, 3, n, m, l)
+
+    def set_incidence(self, dirs, pols):
+        dirs = np.asarray(dirs, dtype=np.float64).reshape(-1, 3)
+        pols = np.asarray(pols, dtype=np.float64).reshape(-1, 3)
+        arr = (Incidence * len(dirs))()
+        for i, (d, e) in enumerate(zip(dirs, pols)):
+            arr[i].dir[:] = list(d)
+            arr[i].pol[:] = list(e)
+        _check(_lib.dda_set_incidence(self._h, len(dirs), arr, _stream()))
+        self.nrhs = len(dirs)
+
+    def incident_field(self, nrhs: int | None = None) -> torch.Tensor:
+        nrhs = nrhs or self.nrhs
+        b = torch.empty(self.field_shape(nrhs), dtype=torch.complex128, device=self.mat.device)
+        _check(_lib.dda_incident_field(self._h, nrhs, _ptr(b), _stream()))
+        return b
+
+    def matvec(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        x = x.contiguous()
+        y = torch.empty_like(x) if out is None else out
+        _check(_lib.dda_matvec(self._h, _prec_of(x), x.shape[0], _ptr(x), _ptr(y), _stream()))
+        return y
+
+    def precond_build(self):
+        _check(_lib.dda_precond_build(self._h, _stream()))
+
+    def precond_apply(self, v: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        v = v.contiguous()
+        z = torch.empty_like(v) if out is None else out
+        _check(_lib.dda_precond_apply(self._h, _prec_of(v), v.shape[0], _ptr(v), _ptr(z), _stream()))
+        return z
+
+    def fft3d(self, data: torch.Tensor, inverse: bool = False) -> torch.Tensor:
+        """In-place 3-D DFT of (batch, n, m, l) complex arrays."""
+        assert data.is_contiguous()
+        nb = data.numel() // (self.shape[0] * self.shape[1] * self.shape[2])
+        _check(_lib.dda_fft3d(self._h, _prec_of(data), nb, _ptr(data), int(inverse), _stream()))
+        return data
+
+    def solve(self, b: torch.Tensor | None = None, x0: torch.Tensor | None = None,
+              tol: float = 1e-6, max_iters: int = 2000, restart: int = 50, precond: int = 3,
+              inner_prec: int = C128, inner_tol: float = 0.0, raise_on_error: bool = True,
+              nrhs: int | None = None) -> SolveResult:
+        nrhs = nrhs or (b.shape[0] if b is not None else self.nrhs)
+        if x0 is None:
+            x = torch.zeros(self.field_shape(nrhs), dtype=torch.complex128, device=self.mat.device)
+        else:
+            x = x0.clone().contiguous()
+        opts = SolveOpts(tol, max_iters, restart, precond, inner_prec, inner_tol)
+        stats = (RhsStats * nrhs)()
+        bp = _ptr(b.contiguous()) if b is not None else ctypes.c_void_p(0)
+        st = _lib.dda_solve(self._h, nrhs, bp, _ptr(x), ctypes.byref(opts), stats, _stream())
+        if st != 0 and raise_on_error:
+            raise DDAError(st, last_error())
+        return SolveResult(x, [s.iters for s in stats], [s.cycles for s in stats],
+                           [bool(s.converged) for s in stats], [s.rel_resid for s in stats], st)
+
+    def cross_sections(self, c: torch.Tensor) -> np.ndarray:
+        c = c.contiguous()
+        nrhs = c.shape[0]
+        out = (ctypes.c_double * (3 * nrhs))()
+        _check(_lib.dda_cross_sections(self._h, nrhs, _ptr(c), out, _stream()))
+        return np.array(out[:], dtype=np.float64).reshape(nrhs, 3)

@@ -1,0 +1,78 @@
+"""The C ABI library: symbols, workspace sizing and argument checks (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def dda():
+    from paper_1903_09802_gb300.build import build
+    build()
+    from paper_1903_09802_gb300 import dda as mod
+    return mod
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "dda.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dda_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("dda_plan_create", "dda_matvec", "dda_precond_build", "dda_solve",
+              "dda_cross_sections", "dda_workspace_size", "dda_precond_apply"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(dda):
+    lib = dda.lib()
+    for name in _declared():
+        assert hasattr(lib, name), name
+    assert set(_declared()) == set(dda.EXPORTS)
+
+
+def test_workspace_size_checks(dda):
+    ok = dda.workspace_size(16, 16, 16, 0.125, 5.0, 1, 2, 50)
+    assert ok > 0
+    assert dda.workspace_size(32, 16, 16, 0.125, 5.0, 1, 2, 50) > ok
+    assert dda.workspace_size(16, 16, 16, 0.125, 5.0, 1, 2, 0) < ok
+    only64 = dda.workspace_size(16, 16, 16, 0.125, 5.0, 1, 2, 50, dda.PLAN_C64)
+    assert 0 < only64 < ok
+    for bad in [(12, 16, 16), (16, 0, 16), (1024, 2, 2)]:
+        assert dda.workspace_size(*bad, 0.125, 5.0) == 0
+        assert "power" in dda.last_error() or ">=" in dda.last_error()
+    assert dda.workspace_size(8, 8, 8, -1.0, 5.0) == 0
+    assert dda.workspace_size(8, 8, 8, 0.1, 5.0, 0) == 0
+    assert dda.workspace_size(8, 8, 8, 0.1, 5.0, 1, 1, 0, 0) == 0
+
+
+def test_plan_create_argument_errors(dda):
+    lib = dda.lib()
+    desc = dda.PlanDesc(8, 8, 8, 0.25, 2.0, 1, 1, 10, 3)
+    need = lib.dda_workspace_size(ctypes.byref(desc))
+    eps = (ctypes.c_double * 2)(1.7161, 0.0)
+    h = ctypes.c_void_p()
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: every check fails first
+    st = lib.dda_plan_create(ctypes.byref(h), ctypes.byref(desc), fake, eps, fake, need - 1, None)
+    assert dda.STATUS[st] == "DDA_ERR_WORKSPACE"
+    st = lib.dda_plan_create(ctypes.byref(h), ctypes.byref(desc), fake, eps, ctypes.c_void_p((1 << 20) + 8), need, None)
+    assert dda.STATUS[st] == "DDA_ERR_WORKSPACE"  # misaligned
+    st = lib.dda_plan_create(ctypes.byref(h), ctypes.byref(desc), None, eps, fake, need, None)
+    assert dda.STATUS[st] == "DDA_ERR_INVALID_ARG"
+    bad = dda.PlanDesc(8, 6, 8, 0.25, 2.0, 1, 1, 10, 3)
+    st = lib.dda_plan_create(ctypes.byref(h), ctypes.byref(bad), fake, eps, fake, need, None)
+    assert dda.STATUS[st] == "DDA_ERR_UNSUPPORTED_SIZE"
+    assert not h.value
+
+
+def test_null_plan_is_rejected(dda):
+    lib = dda.lib()
+    assert dda.STATUS[lib.dda_matvec(None, 0, 1, None, None, None)] == "DDA_ERR_INVALID_ARG"
+    assert dda.STATUS[lib.dda_precond_build(None, None)] == "DDA_ERR_INVALID_ARG"
+    assert dda.STATUS[lib.dda_solve(None, 1, None, None, None, None, None)] == "DDA_ERR_INVALID_ARG"
+    lib.dda_plan_destroy(None)

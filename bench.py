@@ -1,0 +1,443 @@
+#!/usr/bin/env python
+"""Benchmark of the preconditioned DDA hot path on one GB300 (or N replicas).
+
+Workload (one step): the 64^3 hexagonal-prism sweep at size parameter
+x = 20 (k dx = 0.625), refractive indices m in {1.31, 1.31 + 0.05i} and
+aspect ratios L/(2 a_h) in {0.5, 1, 2} (boxes 64x64x32, 64^3, 64x64x128),
+one seeded incident direction with its two orthogonal polarisations solved
+together: 6 systems x 2 right-hand sides = 12 solves.  For every system the
+step runs the whole path through the C ABI: plan (Green-function spectrum),
+incident waves and polarizabilities, 3-level circulant preconditioner build,
+right-preconditioned GMRES(50) in complex64 with FP64 iterative refinement to
+a true complex128 relative residual of 1e-6, and the cross sections.
+The m = 1.78 systems of the same sweep are left out of the timed step: with
+GMRES(50) or GMRES(200) neither the plain nor the preconditioned solve
+reaches 1e-6 within 4000 iterations on this grid (|m| k dx = 1.1).
+
+Metric: time-to-solve per right-hand side (ms, lower is better), whole job:
+elapsed device time of K steps / (12 K N).  L2 is flushed (a 512 MB write)
+before every timed step.  The JSON line also carries the roofline of the
+dominant kernel measured live with CUDA events, the CPU oracle timed on a
+bounded sample, the end-to-end figure through host buffers, the number of
+library kernel launches and the SM clocks sampled during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GMRES time-to-solve @1e-6 (FP64 vs mixed/batched); FFT-matvec HBM GB/s"
+UNIT = "ms/solve"
+WORKLOAD = ("64^3 hexagonal prisms, x=20, m in {1.31, 1.31+0.05i} x aspect {0.5,1,2}, "
+            "seeded direction x 2 polarisations (12 solves), 3-level circulant "
+            "preconditioner, GMRES(50) complex64 + FP64 refinement to 1e-6")
+FLUSH_BYTES = 512 << 20
+
+
+def workload_cases():
+    from dda_inputs import config2_cases
+    return [c for c in config2_cases(64, 20.0, seed=0) if abs(complex(c.eps[0]) - 1.78 ** 2) > 1e-9]
+
+
+def read_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+class ClockSampler:
+    def __init__(self, index: str):
+        self.index = index
+        self.samples = []
+        self.proc = None
+        self.thread = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap,utilization.gpu")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", self.index, f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 7:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        loaded = [s for s in self.samples if (num(s[6]) or 0) > 10] or self.samples
+        sm = sorted(num(s[0]) for s in loaded if num(s[0]) is not None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in loaded for i in range(4) if s[2 + i].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None,
+                "sm_max_mhz": num(self.samples[0][1]), "reasons": reasons}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+class Runner:
+    """Holds device-resident masks and runs one step of the hot path."""
+
+    def __init__(self, device):
+        import torch
+        from paper_1903_09802_gb300 import dda
+        self.torch, self.dda, self.dev = torch, dda, device
+        self.cases = workload_cases()
+        self.masks_host = [torch.from_numpy(c.mask()).pin_memory() for c in self.cases]
+        self.masks = [m.to(device) for m in self.masks_host]
+        self.flush_buf = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=device)
+        self.last = None
+        self.profile = False
+        self.prof = []
+
+    def flush_l2(self):
+        self.flush_buf.fill_(1)
+
+    def step(self, masks=None, host_out=None):
+        dda = self.dda
+        masks = masks if masks is not None else self.masks
+        out = []
+        for i, case in enumerate(self.cases):
+            plan = dda.Plan(masks[i], case.eps, case.dx, case.k, max_rhs=2, krylov_m=50)
+            if self.profile:
+                plan.profile(True)
+            plan.set_incidence(case.dirs, case.pols)
+            plan.precond_build()
+            res = plan.solve(tol=1e-6, restart=50, precond=3, inner_prec=dda.C64, inner_tol=1e-4,
+                             max_iters=2000)
+            xs = plan.cross_sections(res.x)
+            if host_out is not None:
+                host_out[i].copy_(res.x, non_blocking=True)
+            if self.profile:
+                self.prof.append((case, plan.profile_read()))
+            out.append((res.iters, res.rel_resid, xs))
+        self.last = out
+        return out
+
+
+def algorithmic_bytes(name, case, nrhs=2):
+    """Bytes one launch of a kernel class must move (complex64 fields)."""
+    l, m, n = case.dims
+    nvox = l * m * n
+    u = 8 * nvox
+    spec = 8 * 6 * (l + 1) * (m + 1) * (n + 1)
+    circ = 8 * 6 * (l // 2 + 1) * (m // 2 + 1) * (n // 2 + 1)
+    per_rhs = {
+        "mv_x_fwd": 9 * u, "mv_y_fwd": 18 * u, "mv_z_mul": 24 * u, "mv_y_inv": 18 * u,
+        "mv_x_inv": 12 * u, "pc_x_fwd": 6 * u, "pc_y_fwd": 6 * u, "pc_z_solve": 6 * u,
+        "pc_y_inv": 6 * u, "pc_x_inv": 6 * u,
+    }[name]
+    shared = {"mv_x_fwd": nvox, "mv_x_inv": nvox, "pc_x_fwd": nvox, "pc_x_inv": nvox,
+              "mv_z_mul": spec, "pc_z_solve": circ}.get(name, 0)
+    return per_rhs * nrhs + shared
+
+
+def traffic_from_profiles(kernel):
+    """dram bytes per launch recorded by the committed ncu summary, if still current."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_64cube.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if line.startswith("- ") and ":" in line:
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    h = source_hash()
+    if vals.get("source_hash") != h:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def source_hash():
+    import glob
+    hs = hashlib.sha256()
+    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1903_09802_gb300", "csrc", "*"))):
+        hs.update(open(p, "rb").read())
+    return hs.hexdigest()[:16]
+
+
+def roofline(runner, peak, peak_kind):
+    """Dominant kernel over one profiled (untimed) step, from CUDA events."""
+    runner.profile, runner.prof = True, []
+    runner.step()
+    runner.profile = False
+    tot = {}
+    for case, prof in runner.prof:
+        for name, (ms, cnt) in prof.items():
+            t = tot.setdefault(name, [0.0, 0, 0.0])
+            t[0] += ms
+            t[1] += cnt
+            if cnt and not name.startswith("gs_"):
+                t[2] += algorithmic_bytes(name, case) * cnt
+    dom = max((k for k in tot if not k.startswith("gs_")), key=lambda k: tot[k][0])
+    ms, cnt, nbytes = tot[dom]
+    achieved = nbytes / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+    share = {k: round(v[0] / sum(x[0] for x in tot.values()), 4) for k, v in tot.items() if v[0] > 0}
+    return {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+            "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s", "frac": round(achieved / peak, 4),
+            "avg_launch_us": round(ms / cnt * 1e3, 2) if cnt else None,
+            "algorithmic_bytes_per_launch": round(nbytes / cnt) if cnt else None,
+            "traffic": traffic_from_profiles(dom), "share_of_profiled_kernel_time": share}
+
+
+def oracle_iterations():
+    """Iteration counts of the oracle's own solves of the workload, written by
+    oracle/iteration_counts.py (key: box dims, eps, rhs)."""
+    path = os.path.join(ROOT, "tests", "golden", "config2_oracle_iters.txt")
+    its = {}
+    if os.path.exists(path):
+        for line in open(path):
+            if line.strip() and not line.startswith("#"):
+                f = line.split()
+                its[(int(f[0]), int(f[1]), int(f[2]), round(float(f[3]), 4), round(float(f[4]), 4),
+                     int(f[5]))] = int(f[6])
+    return its
+
+
+def oracle_sample(case_list, n_iter=1):
+    """Time the oracle on one system per box size: spectrum and preconditioner
+    setup, and n_iter preconditioned GMRES iterations.  Returns
+    {dims: (setup_s, s_per_iteration)}."""
+    from oracle import krylov
+    from oracle.problem import from_case
+    per_box = {}
+    for case in case_list:
+        if case.dims in per_box:
+            continue
+        prob = from_case(case, 0)
+        t0 = time.perf_counter()
+        G = prob.kernel_spectrum()
+        M = prob.precond3()
+        t1 = time.perf_counter()
+        krylov.gmres(lambda v: prob.matvec(v, G), prob.rhs(), tol=1e-30, restart=n_iter + 1,
+                     maxiter=n_iter, precond=M)
+        t2 = time.perf_counter()
+        per_box[case.dims] = (t1 - t0, (t2 - t1) / n_iter)
+    return per_box
+
+
+def oracle_ms_per_solve(cases, per_box, its_table, fallback_its):
+    total, nsolve = 0.0, 0
+    for i, case in enumerate(cases):
+        setup, it = per_box[case.dims]
+        eps = complex(case.eps[0])
+        for r in range(case.nrhs):
+            key = case.dims + (round(eps.real, 4), round(eps.imag, 4), r)
+            total += 1e3 * (setup / case.nrhs + it * its_table.get(key, fallback_its[i][r]))
+            nsolve += 1
+    return total / nsolve
+
+
+def cpu_baseline(gpu_iters):
+    """The oracle on a bounded sample: per box size, spectrum + preconditioner
+    setup and one preconditioned GMRES iteration, extrapolated to every
+    system with the oracle's own iteration count for it."""
+    cases = workload_cases()
+    t_all = time.perf_counter()
+    per_box = oracle_sample(cases)
+    table = oracle_iterations()
+    value = oracle_ms_per_solve(cases, per_box, table, gpu_iters)
+    src = "the oracle's own GMRES(50) counts" if table else "the GPU solve's counts"
+    return {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": ("numpy/scipy FP64 oracle (numpy.fft is single-threaded), per box size: "
+                       "kernel spectrum + 3-level preconditioner setup + 1 preconditioned GMRES "
+                       f"iteration, extrapolated to each system with {src}; "
+                       f"{time.perf_counter() - t_all:.1f} s of CPU work")}
+
+
+def run_ours(args, rank, world):
+    import torch
+    import torch.distributed as tdist
+    from paper_1903_09802_gb300 import dda
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    runner = Runner(dev)
+    nsolve = sum(c.nrhs for c in runner.cases)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            tdist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        runner.step()
+    torch.cuda.synchronize()
+
+    # device-resident inputs
+    launches0 = dda.launch_count()
+    idx = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local if world > 1 else 0]
+    total_ms = 0.0
+    with ClockSampler(idx) as clk:
+        for _ in range(args.steps):
+            runner.flush_l2()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            runner.step()
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+        barrier()
+    launches = (dda.launch_count() - launches0) // args.steps
+    out = runner.last
+    its = [o[0] for o in out]
+    resid = max(max(o[1]) for o in out)
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    total_ms = float(t.item())
+
+    # end to end: masks from pinned host memory in, solutions and cross sections out
+    host_x = [torch.empty((2, 3) + tuple(m.shape), dtype=torch.complex128, pin_memory=True)
+              for m in runner.masks]
+    h2d = sum(m.numel() for m in runner.masks_host)
+    d2h = sum(x.numel() * 16 for x in host_x) + 3 * 8 * nsolve
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        runner.flush_l2()
+        barrier()
+        t0 = time.perf_counter()
+        dev_masks = [m.to(dev, non_blocking=True) for m in runner.masks_host]
+        runner.step(dev_masks, host_out=host_x)
+        torch.cuda.synchronize()
+        e2e_ms += 1e3 * (time.perf_counter() - t0)
+    t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    e2e_ms = float(t.item())
+
+    peak, peak_kind = read_peak()
+    roof = roofline(runner, peak, peak_kind)
+    if rank != 0:
+        return
+    value = total_ms / (args.steps * nsolve * world)
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64+f64-refinement",
+        "data": "synthetic (seeded hexagonal prisms, no dataset)",
+        "config": {"workload": WORKLOAD, "grid": "64^3 (boxes 64x64x{32,64,128})",
+                   "solves_per_step": nsolve, "l2": "flushed (512 MB write) before every step",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "iterations": its, "max_rel_resid": resid,
+        "e2e": {"value": round(e2e_ms / (args.steps * nsolve * world), 3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(its)
+    print(json.dumps(line), flush=True)
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm, on bounded samples of the same workload:
+    each step times one box size's setup and one preconditioned iteration and
+    extrapolates the whole sweep with the oracle's own iteration counts."""
+    if rank != 0:
+        return
+    cases = workload_cases()
+    boxes = sorted({c.dims for c in cases})
+    table = oracle_iterations()
+    fallback = [[50] * c.nrhs for c in cases]
+    samples = {}
+    for i in range(args.warmup + args.steps):
+        dims = boxes[i % len(boxes)]
+        per = oracle_sample([c for c in cases if c.dims == dims])
+        if i >= args.warmup or dims not in samples:
+            samples[dims] = per[dims]
+    for dims in boxes:
+        if dims not in samples:
+            samples.update(oracle_sample([c for c in cases if c.dims == dims]))
+    value = oracle_ms_per_solve(cases, samples, table, fallback)
+    cpu = {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": ("per step one box size: kernel spectrum + preconditioner setup and one "
+                      "preconditioned GMRES iteration; sweep extrapolated with the oracle's "
+                      "own GMRES(50) iteration counts")}
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT,
+                      "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                      "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+                      "dtype": "f64", "data": "synthetic (seeded hexagonal prisms, no dataset)",
+                      "config": {"workload": WORKLOAD}, "cpu_baseline": cpu,
+                      "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        tdist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world)
+    finally:
+        if world > 1:
+            import torch.distributed as tdist
+            tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -148,9 +148,13 @@ dda_status_t dda_matvec(dda_plan_t plan, int32_t prec, int32_t nrhs, const void*
  * (Section 3).  Independent of the incident wave. */
 dda_status_t dda_precond_build(dda_plan_t plan, void* stream);
 
-/* z = P^{-1} v, P = alpha_tilde^{-1} I - dx^3 C: 3-D FFT of each component,
- * the 3x3 symbol Lambda(w) = alpha_tilde^{-1} I - dx^3 Chat(w) solved per
- * frequency, inverse FFT.  v and z may be the same buffer. */
+/* z = M o P^{-1} (M o v), P = alpha_tilde^{-1} I - dx^3 C, M the scatterer
+ * mask: the unknowns live on scatterer voxels (eq. 8) and P is the matrix of
+ * the box filled with the scatterer's material (Section 1), so v is extended
+ * by zeros over air, P^{-1} applied on the box, and air entries of z zeroed.
+ * P^{-1}: 3-D FFT of each component, the 3x3 symbol
+ * Lambda(w) = alpha_tilde^{-1} I - dx^3 Chat(w) solved per frequency, inverse
+ * FFT.  v and z may be the same buffer. */
 dda_status_t dda_precond_apply(dda_plan_t plan, int32_t prec, int32_t nrhs, const void* d_v,
                                void* d_z, void* stream);
 
@@ -189,11 +193,27 @@ dda_status_t dda_solve(dda_plan_t plan, int32_t nrhs, const void* d_b, void* d_x
 dda_status_t dda_cross_sections(dda_plan_t plan, int32_t nrhs, const void* d_c, double* h_out,
                                 void* stream);
 
+/* Kernel timing (tracing).  While enabled, the library brackets each
+ * launch of the operator's FFT passes and of the Gram-Schmidt kernels with
+ * CUDA events on the launching stream.  dda_profile_read synchronises those
+ * events and returns, per kernel class, the summed milliseconds and the
+ * launch count: index 0..4 matvec passes (x forward, y forward, z with the
+ * spectrum multiply, y inverse, x inverse with the diagonal), 5..9 the
+ * preconditioner's passes in the same order, 10 Gram-Schmidt dots,
+ * 11 Gram-Schmidt update; n entries are written (n <= 12); reset != 0 zeroes
+ * the sums.  Events add a few microseconds per launch. */
+dda_status_t dda_profile_enable(dda_plan_t plan, int32_t on);
+dda_status_t dda_profile_read(dda_plan_t plan, double* h_ms, int64_t* h_count, int32_t n,
+                              int32_t reset);
+
 /* Release the host-side plan object (device memory stays the caller's). */
 void dda_plan_destroy(dda_plan_t plan);
 
 /* Thread-local text of the last error ("" if none). */
 const char* dda_last_error(void);
+
+/* Number of CUDA kernels the library has launched in this process so far. */
+int64_t dda_launch_count(void);
 
 #ifdef __cplusplus
 }

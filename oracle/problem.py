@@ -4,6 +4,14 @@ alpha_tilde (Section 3.1 and eq. 20): the constant diagonal of the
 preconditioner is the polarizability of the scatterer's material ("ice").
 With several materials this reads as the most frequent non-air material,
 ties going to the lowest index.
+
+Preconditioner on the scatterer (reading of Sections 1 and 3.1): the
+unknowns live on scatterer voxels only (eq. 8), while P is the matrix of the
+whole box "filled in with ice".  P^{-1} acts on an unknown vector by
+extending it with zeros over the air voxels, applying the box-level inverse
+and keeping the scatterer voxels:  z = M o P^{-1}(M o v),  M the scatterer
+mask.  Applying P^{-1} to the full box vector instead (air unknowns kept in
+the Krylov space) converges far worse and is not what the paper describes.
 """
 from __future__ import annotations
 
@@ -58,16 +66,24 @@ class Problem:
         return operator.fft_matvec(c, self.mat, self.alpha_inv_vox, self.alpha_tilde_inv,
                                    self.k, self.dx, Ghat)
 
-    def precond3(self):
+    def precond3(self, restrict: bool = True):
+        """3-level preconditioner; restricted to the scatterer unless restrict=False."""
         l, m, n = self.dims
         lam = circulant.precond3_lambda(l, m, n, self.dx, self.k, self.alpha_tilde_inv)
         lam_inv = np.linalg.inv(lam)
-        return lambda v: circulant.precond3_apply(v, lam_inv)
+        ice = (self.mat > 0)[None]
+        if not restrict:
+            return lambda v: circulant.precond3_apply(v, lam_inv)
+        return lambda v: circulant.precond3_apply(v * ice, lam_inv) * ice
 
-    def precond2(self):
+    def precond2(self, restrict: bool = True):
+        """The paper's 2-level preconditioner; restricted to the scatterer by default."""
         l, m, n = self.dims
         blocks = circulant.precond2_blocks(l, m, n, self.dx, self.k, self.alpha_tilde_inv)
-        return lambda v: circulant.precond2_apply(v, blocks)
+        ice = (self.mat > 0)[None]
+        if not restrict:
+            return lambda v: circulant.precond2_apply(v, blocks)
+        return lambda v: circulant.precond2_apply(v * ice, blocks) * ice
 
     def solve_direct(self) -> np.ndarray:
         A = operator.dense_matrix(self.mat, self.alpha_inv_vox, self.k, self.dx)

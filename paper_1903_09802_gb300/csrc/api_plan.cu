@@ -1,5 +1,6 @@
 // Plan creation: workspace layout, Green-function spectrum, polarizabilities,
 // incident field and the standalone 3-D FFT entry point.
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -12,7 +13,10 @@ namespace dda {
 
 namespace {
 thread_local std::string g_err;
+std::atomic<long long> g_launches{0};
 }
+
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 void set_error(const std::string& msg) { g_err = msg; }
 
@@ -217,6 +221,8 @@ using namespace dda;
 
 extern "C" const char* dda_last_error(void) { return g_err.c_str(); }
 
+extern "C" int64_t dda_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
 extern "C" size_t dda_workspace_size(const dda_plan_desc_t* desc) {
   if (!desc) {
     set_error("dda_workspace_size: desc is NULL");
@@ -308,10 +314,12 @@ extern "C" dda_status_t dda_plan_create(dda_plan_t* out, const dda_plan_desc_t* 
   // kernel spectrum, one component at a time through the FP64 scratch
   double2* scratch = static_cast<double2*>(L.buf2);
   for (int c = 0; c < 6; ++c) {
+    note_launch();
     k_green_generator<<<grid_for(p->P, 256), 256, 0, s>>>(scratch, c, p->l, p->m, p->n, p->Lx, p->Ly,
                                                           p->Lz, desc->dx, desc->k);
     fft3d_inplace<double, false>(reinterpret_cast<cx<double>*>(scratch), 1, p->Lx, p->Ly, p->Lz, 1.0,
                                  static_cast<const cx<double>*>(L.tw128), p->Lmax, s);
+    note_launch();
     k_compress<<<grid_for((long)p->hx * p->hy * p->hz, 256), 256, 0, s>>>(
         scratch, p->Lx, p->Ly, p->Lz, p->hx, p->hy, p->hz, c, static_cast<double2*>(L.G128),
         static_cast<float2*>(L.G64));
@@ -392,6 +400,7 @@ extern "C" dda_status_t dda_incident_field(dda_plan_t p, int32_t nrhs, void* d_b
   if (nrhs < 1 || nrhs > p->nrhs_inc)
     return fail(DDA_ERR_INVALID_ARG, "dda_incident_field: nrhs above the incidence count set");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  note_launch();
   k_incident<<<grid_for(p->nvox * nrhs, 256), 256, 0, s>>>(static_cast<double2*>(d_b), p->mat,
                                                           p->w.incd, nrhs, p->l, p->m, p->n,
                                                           p->d.dx, p->d.k);

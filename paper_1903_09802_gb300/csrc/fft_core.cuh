@@ -19,6 +19,8 @@
 
 namespace dda {
 
+void note_launch();
+
 constexpr int kElemsPerThread = 16;
 
 // cos(2 pi j / 16), j = 0..4.
@@ -80,16 +82,24 @@ __device__ __forceinline__ void dft(cx<T>* v) {
   }
 }
 
-// Radix sequence of a transform: at most 4 stages (L <= 65536).
+// Radix sequence of a transform: at most 4 stages (L <= 65536); lg = log2 L.
 struct RadixPlan {
   int nst;
+  int lg;
   int r[4];
 };
 
+inline int ilog2i(long v) {
+  int b = 0;
+  while ((1L << b) < v) ++b;
+  return b;
+}
+
 inline RadixPlan make_radix_plan(int L) {
-  RadixPlan p{0, {1, 1, 1, 1}};
+  RadixPlan p{0, 0, {1, 1, 1, 1}};
   int bits = 0;
   while ((1 << bits) < L) ++bits;
+  p.lg = bits;
   if (bits == 0) return p;
   const int nst = (bits + 3) / 4;
   int left = bits;
@@ -102,8 +112,17 @@ inline RadixPlan make_radix_plan(int L) {
   return p;
 }
 
-template <int R, bool INV, typename T>
-__device__ __forceinline__ void smem_stage(cx<T>* s, const cx<T>* tw, int L, int NB, int ld,
+// Line count of a tile: (1 << sh) or 3 * (1 << sh) lines (MUL3), so that
+// the line / butterfly split of an index needs no run-time division.
+template <bool MUL3>
+__device__ __forceinline__ void split_line(int u, int sh, int& b, int& jb) {
+  const int hi = u >> sh;
+  jb = MUL3 ? hi / 3 : hi;
+  b = u - ((jb * (MUL3 ? 3 : 1)) << sh);
+}
+
+template <int R, bool INV, bool MUL3, typename T>
+__device__ __forceinline__ void smem_stage(cx<T>* s, const cx<T>* tw, int L, int sh, int ld,
                                            int Ns, int tid, int nth) {
   constexpr int G = kElemsPerThread / R;
   cx<T> v[kElemsPerThread];
@@ -111,8 +130,8 @@ __device__ __forceinline__ void smem_stage(cx<T>* s, const cx<T>* tw, int L, int
 #pragma unroll
   for (int g = 0; g < G; ++g) {
     const int u = tid + g * nth;
-    const int b = u % NB;
-    const int jb = u / NB;
+    int b, jb;
+    split_line<MUL3>(u, sh, b, jb);
 #pragma unroll
     for (int q = 0; q < R; ++q) v[g * R + q] = s[(jb + q * LR) * ld + b];
   }
@@ -121,8 +140,8 @@ __device__ __forceinline__ void smem_stage(cx<T>* s, const cx<T>* tw, int L, int
 #pragma unroll
   for (int g = 0; g < G; ++g) {
     const int u = tid + g * nth;
-    const int b = u % NB;
-    const int jb = u / NB;
+    int b, jb;
+    split_line<MUL3>(u, sh, b, jb);
     const int k = jb & (Ns - 1);
     if (Ns > 1) {
 #pragma unroll
@@ -136,10 +155,11 @@ __device__ __forceinline__ void smem_stage(cx<T>* s, const cx<T>* tw, int L, int
   __syncthreads();
 }
 
-// Full transform of NB lines in shared memory.  tw[t] = exp(-2 pi i t / L),
-// t < L, also in shared memory.  Caller synchronises before the call.
-template <bool INV, typename T>
-__device__ __forceinline__ void smem_fft(cx<T>* s, const cx<T>* tw, int L, int NB, int ld,
+// Full transform of NB = (MUL3 ? 3 : 1) << sh lines in shared memory.
+// tw[t] = exp(-2 pi i t / L), t < L, also in shared memory.  Caller
+// synchronises before the call.
+template <bool INV, bool MUL3 = false, typename T>
+__device__ __forceinline__ void smem_fft(cx<T>* s, const cx<T>* tw, int L, int sh, int ld,
                                          const RadixPlan& rp) {
   const int tid = threadIdx.x;
   const int nth = blockDim.x;
@@ -149,13 +169,34 @@ __device__ __forceinline__ void smem_fft(cx<T>* s, const cx<T>* tw, int L, int N
     if (st >= rp.nst) break;
     const int R = rp.r[st];
     switch (R) {
-      case 16: smem_stage<16, INV>(s, tw, L, NB, ld, Ns, tid, nth); break;
-      case 8: smem_stage<8, INV>(s, tw, L, NB, ld, Ns, tid, nth); break;
-      case 4: smem_stage<4, INV>(s, tw, L, NB, ld, Ns, tid, nth); break;
-      default: smem_stage<2, INV>(s, tw, L, NB, ld, Ns, tid, nth); break;
+      case 16: smem_stage<16, INV, MUL3>(s, tw, L, sh, ld, Ns, tid, nth); break;
+      case 8: smem_stage<8, INV, MUL3>(s, tw, L, sh, ld, Ns, tid, nth); break;
+      case 4: smem_stage<4, INV, MUL3>(s, tw, L, sh, ld, Ns, tid, nth); break;
+      default: smem_stage<2, INV, MUL3>(s, tw, L, sh, ld, Ns, tid, nth); break;
     }
     Ns *= R;
   }
+}
+
+// Asynchronous global -> shared copy of one complex value (cp.async); with
+// valid == false nothing is read and the shared word is zero filled.  The
+// source pointer must be a valid address either way.
+template <typename T>
+__device__ __forceinline__ void cp_async_cx(cx<T>* sdst, const cx<T>* gsrc, bool valid) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(sdst);
+  const int nbytes = valid ? (int)sizeof(cx<T>) : 0;
+  if constexpr (sizeof(cx<T>) == 16) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(saddr), "l"(gsrc),
+                 "r"(nbytes)
+                 : "memory");
+  } else {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(saddr), "l"(gsrc),
+                 "r"(nbytes)
+                 : "memory");
+  }
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
 // Copy the L-point twiddles out of the plan's Lmax-point table.

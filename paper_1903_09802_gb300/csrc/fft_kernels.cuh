@@ -7,10 +7,15 @@
 //   k_fft3c       the three field components of a strided tile together,
 //                 forward transform, a per-frequency 3x3 operation, inverse
 //                 transform, in one pass over HBM
-// Inputs shorter than the transform are zero padded (Lin < L); outputs can
-// be truncated (Lout < L), which is how the circulant embedding of the BTTB
-// matvec is pruned.  A CTA reads all of its lines before it writes any, so
-// every kernel may run in place (in == out).
+// Tiles are loaded with asynchronous global -> shared copies (cp.async,
+// zero filled where the input is padding or masked), 16 per thread issued
+// back to back, so each SM keeps many loads in flight without staging them
+// in registers.  An optional uint8 mask (one row of Lin / Lout flags per
+// line, repeating every mask_lines lines) zeroes inputs or outputs of
+// contiguous lines.  Inputs shorter than the transform are zero padded
+// (Lin < L); outputs can be truncated (Lout < L), which is how the circulant
+// embedding of the BTTB matvec is pruned.  A CTA reads all of its lines
+// before it writes any, so every kernel may run in place (in == out).
 #pragma once
 
 #include <algorithm>
@@ -22,97 +27,140 @@ namespace dda {
 
 template <typename T, bool INV>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
-    k_fft_contig(const cx<T>* in, cx<T>* out,
-                 const uint8_t* __restrict__ mask, long mask_lines, long nlines, int L, int Lin,
+    k_fft_contig(const cx<T>* in, cx<T>* out, const uint8_t* __restrict__ mask,
+                 const uint8_t* __restrict__ omask, long mask_lines, long nlines, int Lin,
                  long in_ld, int Lout, long out_ld, T scale, const cx<T>* __restrict__ tw,
-                 int twshift, RadixPlan rp, int NB) {
+                 int twshift, RadixPlan rp, int nb_sh) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+  const int L = 1 << rp.lg;
+  const int NB = 1 << nb_sh;
   const int ld = NB + 1;
   cx<T>* stw = s + (size_t)L * ld;
-  const long line0 = (long)blockIdx.x * NB;
-  load_twiddles(stw, tw, L, twshift);
-  for (int e = threadIdx.x; e < NB * L; e += blockDim.x) {
+  const int nth = blockDim.x, tid = threadIdx.x;
+  const long line0 = (long)blockIdx.x << nb_sh;
+#pragma unroll 4
+  for (int i = 0; i < kElemsPerThread; ++i) {
+    const int e = tid + i * nth;
     const int j = e & (L - 1);
-    const int b = e / L;
+    const int b = e >> rp.lg;
     const long line = line0 + b;
-    cx<T> v = zero<T>();
-    if (line < nlines && j < Lin) {
-      v = in[line * in_ld + j];
-      if (mask != nullptr && mask[(line % mask_lines) * Lin + j] == 0) v = zero<T>();
-    }
-    s[j * ld + b] = v;
+    bool ok = line < nlines && j < Lin;
+    if (ok && mask != nullptr) ok = mask[(line % mask_lines) * Lin + j] != 0;
+    cp_async_cx(s + j * ld + b, ok ? in + line * in_ld + j : in, ok);
   }
+  load_twiddles(stw, tw, L, twshift);
+  cp_async_wait_all();
   __syncthreads();
-  smem_fft<INV>(s, stw, L, NB, ld, rp);
-  for (int e = threadIdx.x; e < NB * L; e += blockDim.x) {
+  smem_fft<INV>(s, stw, L, nb_sh, ld, rp);
+#pragma unroll
+  for (int i = 0; i < kElemsPerThread; ++i) {
+    const int e = tid + i * nth;
     const int j = e & (L - 1);
-    const int b = e / L;
+    const int b = e >> rp.lg;
     const long line = line0 + b;
-    if (line < nlines && j < Lout) out[line * out_ld + j] = scale * s[j * ld + b];
+    if (line < nlines && j < Lout) {
+      cx<T> w = scale * s[j * ld + b];
+      if (omask != nullptr && omask[(line % mask_lines) * Lout + j] == 0) w = zero<T>();
+      out[line * out_ld + j] = w;
+    }
   }
 }
 
 template <typename T, bool INV>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
-    k_fft_strided(const cx<T>* in, cx<T>* out, long ncols, int L,
-                  int Lin, long in_js, long in_ss, int Lout, long out_js, long out_ss, T scale,
-                  const cx<T>* __restrict__ tw, int twshift, RadixPlan rp, int NB) {
+    k_fft_strided(const cx<T>* in, cx<T>* out, long ncols, int Lin, long in_js, long in_ss,
+                  int Lout, long out_js, long out_ss, T scale, const cx<T>* __restrict__ tw,
+                  int twshift, RadixPlan rp, int nb_sh) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
-  cx<T>* stw = s + (size_t)L * NB;
-  const long tiles = (ncols + NB - 1) / NB;
+  const int L = 1 << rp.lg;
+  const int NB = 1 << nb_sh;
+  cx<T>* stw = s + ((size_t)L << nb_sh);
+  const int nth = blockDim.x, tid = threadIdx.x;
+  const long tiles = (ncols + NB - 1) >> nb_sh;
   const long slab = blockIdx.x / tiles;
-  const long col0 = (blockIdx.x % tiles) * NB;
-  load_twiddles(stw, tw, L, twshift);
+  const long col0 = (blockIdx.x - slab * tiles) << nb_sh;
   const cx<T>* src = in + slab * in_ss + col0;
-  for (int e = threadIdx.x; e < NB * L; e += blockDim.x) {
+#pragma unroll 4
+  for (int i = 0; i < kElemsPerThread; ++i) {
+    const int e = tid + i * nth;
     const int b = e & (NB - 1);
-    const int j = e / NB;
-    cx<T> v = zero<T>();
-    if (col0 + b < ncols && j < Lin) v = src[j * in_js + b];
-    s[j * NB + b] = v;
+    const int j = e >> nb_sh;
+    const bool ok = col0 + b < ncols && j < Lin;
+    cp_async_cx(s + e, ok ? src + j * in_js + b : in, ok);
   }
+  load_twiddles(stw, tw, L, twshift);
+  cp_async_wait_all();
   __syncthreads();
-  smem_fft<INV>(s, stw, L, NB, NB, rp);
+  smem_fft<INV>(s, stw, L, nb_sh, NB, rp);
   cx<T>* dst = out + slab * out_ss + col0;
-  for (int e = threadIdx.x; e < NB * L; e += blockDim.x) {
+#pragma unroll
+  for (int i = 0; i < kElemsPerThread; ++i) {
+    const int e = tid + i * nth;
     const int b = e & (NB - 1);
-    const int j = e / NB;
-    if (col0 + b < ncols && j < Lout) dst[j * out_js + b] = scale * s[j * NB + b];
+    const int j = e >> nb_sh;
+    if (col0 + b < ncols && j < Lout) dst[j * out_js + b] = scale * s[e];
   }
+}
+
+// Launch order of the tiles of one slab.  Columns form nrows rows of
+// row_len; frequency r and its mirror (-r) use the same stored spectrum
+// entry (parity folding), so rows are visited 0, 1, -1, 2, -2, ... and the
+// tiles of a row likewise, which keeps both users of a spectrum line in
+// flight at the same time and the line in L2.
+__device__ __forceinline__ int mirror_perm(int r, int n) {
+  return r == 0 ? 0 : ((r & 1) ? (r + 1) >> 1 : n - (r >> 1));
 }
 
 // Three components of a strided tile: forward FFT, op(slab, col, j, x0, x1,
 // x2) at every frequency j of every column, inverse FFT; in place on
 // `data` (first Lout of L outputs kept).  Lines of the tile are ordered
-// (component, column) with the column fastest.
+// (component, column) with the column fastest, so shared-memory index and
+// tile index coincide.
 template <typename T, class Op>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 768)
-    k_fft3c(cx<T>* data, long ncols, int L, int Lin, long js, long cs, long ss,
-            int Lout, Op op, const cx<T>* __restrict__ tw, int twshift, RadixPlan rp, int NBc) {
+    k_fft3c(cx<T>* data, long ncols, int Lin, long js, long cs, long ss, int Lout, Op op,
+            const cx<T>* __restrict__ tw, int twshift, RadixPlan rp, int nbc_sh, int row_len,
+            int nrows) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+  const int L = 1 << rp.lg;
+  const int NBc = 1 << nbc_sh;
   const int ld = 3 * NBc;
   cx<T>* stw = s + (size_t)L * ld;
-  const long tiles = (ncols + NBc - 1) / NBc;
+  const int nth = blockDim.x, tid = threadIdx.x;
+  const long tiles = (ncols + NBc - 1) >> nbc_sh;
   const long slab = blockIdx.x / tiles;
-  const long col0 = (blockIdx.x % tiles) * NBc;
-  load_twiddles(stw, tw, L, twshift);
-  cx<T>* base = data + slab * ss + col0;
-  for (int e = threadIdx.x; e < ld * L; e += blockDim.x) {
-    const int b = e & (NBc - 1);
-    const int c = (e / NBc) % 3;
-    const int j = e / ld;
-    cx<T> v = zero<T>();
-    if (col0 + b < ncols && j < Lin) v = base[c * cs + j * js + b];
-    s[j * ld + c * NBc + b] = v;
+  const int tt = (int)(blockIdx.x - slab * tiles);
+  long col0;
+  if (row_len >= NBc && nrows > 0) {
+    const int row_tiles = row_len >> nbc_sh;
+    const int r = tt / row_tiles;
+    const int ti = tt - r * row_tiles;
+    col0 = (long)mirror_perm(r, nrows) * row_len + ((long)mirror_perm(ti, row_tiles) << nbc_sh);
+  } else {
+    col0 = (long)tt << nbc_sh;
   }
+  cx<T>* base = data + slab * ss + col0;
+#pragma unroll 4
+  for (int i = 0; i < kElemsPerThread; ++i) {
+    const int e = tid + i * nth;
+    const int b = e & (NBc - 1);
+    const int t = e >> nbc_sh;  // 3 j + c
+    const int j = t / 3;
+    const int c = t - 3 * j;
+    const bool ok = col0 + b < ncols && j < Lin;
+    cp_async_cx(s + e, ok ? base + c * cs + j * js + b : data, ok);
+  }
+  op.prefetch(col0, NBc, L);
+  load_twiddles(stw, tw, L, twshift);
+  cp_async_wait_all();
   __syncthreads();
-  smem_fft<false>(s, stw, L, ld, ld, rp);
-  for (int p = threadIdx.x; p < L * NBc; p += blockDim.x) {
+  smem_fft<false, true>(s, stw, L, nbc_sh, ld, rp);
+  for (int p = tid; p < (L << nbc_sh); p += nth) {
     const int b = p & (NBc - 1);
-    const int j = p / NBc;
+    const int j = p >> nbc_sh;
     if (col0 + b < ncols) {
       cx<T>* q = s + j * ld + b;
       cx<T> x0 = q[0], x1 = q[NBc], x2 = q[2 * NBc];
@@ -123,12 +171,15 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 768)
     }
   }
   __syncthreads();
-  smem_fft<true>(s, stw, L, ld, ld, rp);
-  for (int e = threadIdx.x; e < ld * L; e += blockDim.x) {
+  smem_fft<true, true>(s, stw, L, nbc_sh, ld, rp);
+#pragma unroll
+  for (int i = 0; i < kElemsPerThread; ++i) {
+    const int e = tid + i * nth;
     const int b = e & (NBc - 1);
-    const int c = (e / NBc) % 3;
-    const int j = e / ld;
-    if (col0 + b < ncols && j < Lout) base[c * cs + j * js + b] = s[j * ld + c * NBc + b];
+    const int t = e >> nbc_sh;
+    const int j = t / 3;
+    const int c = t - 3 * j;
+    if (col0 + b < ncols && j < Lout) base[c * cs + j * js + b] = s[e];
   }
 }
 
@@ -156,6 +207,10 @@ __device__ __forceinline__ void load_sym6(const cx<T>* __restrict__ g6, const bo
   if (flip[1] != flip[2]) yz = mk<T>(-yz.x, -yz.y);
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 inline int floor_pow2_l(long v) {
   int p = 1;
   while ((long)p * 2 <= v) p *= 2;
@@ -164,10 +219,11 @@ inline int floor_pow2_l(long v) {
 
 // Launch k_fft3c with tiles of NBc columns: NBc * 3 * L complex values per
 // CTA (16 per thread), NBc shrunk for small grids so that at least two CTAs
-// per SM exist.
+// per SM exist.  Columns are rows of row_len (see mirror_perm).
 template <typename T, class Op>
 void launch_fft3c(cx<T>* data, long ncols, long nslabs, int L, int Lin, long js, long cs, long ss,
-                  int Lout, const Op& op, const cx<T>* tw, int Lmax, cudaStream_t s) {
+                  int Lout, const Op& op, const cx<T>* tw, int Lmax, int row_len, int nrows,
+                  cudaStream_t s) {
   if (ncols <= 0 || nslabs <= 0) return;
   const int cap = (sizeof(T) == 8 ? 512 : 768) * kElemsPerThread;
   int NBc = sizeof(T) == 8 ? 8 : 16;
@@ -181,8 +237,9 @@ void launch_fft3c(cx<T>* data, long ncols, long nslabs, int L, int Lin, long js,
   auto kern = k_fft3c<T, Op>;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  kern<<<(unsigned)grid, nth, smem, s>>>(data, ncols, L, Lin, js, cs, ss, Lout, op, tw, Lmax / L,
-                                         make_radix_plan(L), NBc);
+  note_launch();
+  kern<<<(unsigned)grid, nth, smem, s>>>(data, ncols, Lin, js, cs, ss, Lout, op, tw, Lmax / L,
+                                         make_radix_plan(L), ilog2i(NBc), row_len, nrows);
 }
 
 }  // namespace dda

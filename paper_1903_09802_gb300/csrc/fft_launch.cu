@@ -36,7 +36,8 @@ void allow_smem(K kernel, size_t bytes) {
 }  // namespace
 
 template <typename T, bool INV>
-void launch_contig(const cx<T>* in, cx<T>* out, const uint8_t* mask, long mask_lines, long nlines,
+void launch_contig(const cx<T>* in, cx<T>* out, const uint8_t* mask, const uint8_t* omask,
+                   long mask_lines, long nlines,
                    int L, int Lin, long in_ld, int Lout, long out_ld, T scale, const cx<T>* tw,
                    int Lmax, cudaStream_t s) {
   if (nlines <= 0) return;
@@ -51,8 +52,10 @@ void launch_contig(const cx<T>* in, cx<T>* out, const uint8_t* mask, long mask_l
   const long grid = (nlines + NB - 1) / NB;
   auto kern = k_fft_contig<T, INV>;
   allow_smem(kern, smem);
-  kern<<<(unsigned)grid, nth, smem, s>>>(in, out, mask, mask_lines, nlines, L, Lin, in_ld, Lout,
-                                         out_ld, scale, tw, Lmax / L, make_radix_plan(L), NB);
+  note_launch();
+  kern<<<(unsigned)grid, nth, smem, s>>>(in, out, mask, omask, mask_lines, nlines, Lin, in_ld, Lout,
+                                         out_ld, scale, tw, Lmax / L, make_radix_plan(L),
+                                         ilog2i(NB));
 }
 
 template <typename T, bool INV>
@@ -71,8 +74,9 @@ void launch_strided(const cx<T>* in, cx<T>* out, long ncols, long nslabs, int L,
   const long grid = nslabs * ((ncols + NB - 1) / NB);
   auto kern = k_fft_strided<T, INV>;
   allow_smem(kern, smem);
-  kern<<<(unsigned)grid, nth, smem, s>>>(in, out, ncols, L, Lin, in_js, in_ss, Lout, out_js,
-                                         out_ss, scale, tw, Lmax / L, make_radix_plan(L), NB);
+  note_launch();
+  kern<<<(unsigned)grid, nth, smem, s>>>(in, out, ncols, Lin, in_js, in_ss, Lout, out_js, out_ss,
+                                         scale, tw, Lmax / L, make_radix_plan(L), ilog2i(NB));
 }
 
 template <typename T, bool INV>
@@ -81,7 +85,7 @@ void fft3d_inplace(cx<T>* data, long nbatch, int Lx, int Ly, int Lz, T scale, co
   const long plane = (long)Lx * Ly;
   const long vol = plane * Lz;
   if (Lx > 1)
-    launch_contig<T, INV>(data, data, nullptr, 1, nbatch * Ly * Lz, Lx, Lx, Lx, Lx, Lx, T(1), tw,
+    launch_contig<T, INV>(data, data, nullptr, nullptr, 1, nbatch * Ly * Lz, Lx, Lx, Lx, Lx, Lx, T(1), tw,
                           Lmax, s);
   if (Ly > 1)
     launch_strided<T, INV>(data, data, Lx, nbatch * Lz, Ly, Ly, Lx, plane, Ly, Lx, plane, T(1), tw,
@@ -92,7 +96,8 @@ void fft3d_inplace(cx<T>* data, long nbatch, int Lx, int Ly, int Lz, T scale, co
 }
 
 #define DDA_INST_FFT(T, INV)                                                                      \
-  template void launch_contig<T, INV>(const cx<T>*, cx<T>*, const uint8_t*, long, long, int, int,  \
+  template void launch_contig<T, INV>(const cx<T>*, cx<T>*, const uint8_t*, const uint8_t*, long,  \
+                                      long, int, int,                                             \
                                       long, int, long, T, const cx<T>*, int, cudaStream_t);        \
   template void launch_strided<T, INV>(const cx<T>*, cx<T>*, long, long, int, int, long, long,     \
                                        int, long, long, T, const cx<T>*, int, cudaStream_t);       \

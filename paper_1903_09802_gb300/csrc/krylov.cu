@@ -436,7 +436,9 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
     // r = b - A x in complex128
     matvec_impl<double>(p, nrhs, reinterpret_cast<const cx<double>*>(x),
                         reinterpret_cast<cx<double>*>(R), s);
+    note_launch();
     k_residual<<<vgrid, kNT, 0, s>>>(b, R, nu, st.partial);
+    note_launch();
     k_finish_norms<<<(nrhs + 127) / 128, 128, 0, s>>>(st.partial, nblk, nrhs, st.scal);
     cudaMemcpyAsync(hs.data(), st.scal, sizeof(double) * 16 * nrhs, cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(hits.data(), st.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s);
@@ -457,6 +459,7 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
     if (nrun == 0) break;
     for (int r = 0; r < nrhs; ++r) ncyc[r] += run[r];
     cudaMemcpyAsync(st.run, run.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s);
+    note_launch();
     k_start_cycle<T><<<vgrid, kNT, 0, s>>>(R, V, nu, st.scal, st.g, m, st.run, st.active,
                                            st.jlen, o.tol, o.inner_tol);
     // Arnoldi steps
@@ -473,17 +476,28 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
       }
       matvec_impl<T>(p, nrhs, src, W, s);
       for (int pass = 0; pass < 2; ++pass) {
+        p->prof.begin(PROF_AR_DOT, s);
+        note_launch();
         k_multidot<T><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.partial, pst, st.active);
+        p->prof.end(s);
+        note_launch();
         k_reduce_dots<<<nrhs, 64, 0, s>>>(st.partial, nblk, j + 1, pst, st.hcol, st.H, m, j, pass,
                                           st.active);
+        p->prof.begin(PROF_AR_UPD, s);
+        note_launch();
         k_update<T><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.hcol, m, st.partial, pst,
                                           st.active);
+        p->prof.end(s);
       }
+      note_launch();
       k_givens<<<(nrhs + 63) / 64, 64, 0, s>>>(st.H, st.cs, st.sn, st.g, st.partial, nblk, pst,
                                                st.scal, st.active, st.jlen, st.flags, st.iters,
                                                nrhs, m, j, brk);
-      if (j + 1 < steps)
+      if (j + 1 < steps) {
+        note_launch();
         k_scale<T><<<vgrid, kNT, 0, s>>>(W, V + (long)(j + 1) * vstride, nu, st.scal, st.active);
+      }
+      note_launch();
       k_count_active<<<1, 32, 0, s>>>(st.active, nrhs, st.counters + (j & 1));
       cudaMemcpyAsync(p->pinned + (j & 1), st.counters + (j & 1), sizeof(int),
                       cudaMemcpyDeviceToHost, s);
@@ -494,13 +508,16 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
       }
     }
     // x += P^{-1} V y
+    note_launch();
     k_trisolve<<<(nrhs + 63) / 64, 64, 0, s>>>(st.H, st.g, st.jlen, st.y, nrhs, m);
+    note_launch();
     k_combine<T><<<vgrid, kNT, 0, s>>>(V, st.y, st.jlen, W, nu, vstride, m);
     const cx<T>* upd = W;
     if (prec) {
       precond_apply_impl<T>(p, nrhs, W, Z, s);
       upd = Z;
     }
+    note_launch();
     k_add_x<T><<<vgrid, kNT, 0, s>>>(x, upd, st.jlen, nu);
     if ((status = check_cuda("dda_solve")) != DDA_OK) break;
   }

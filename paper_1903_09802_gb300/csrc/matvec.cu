@@ -25,6 +25,19 @@ template <typename T>
 struct KernelMul {
   const cx<T>* G;
   int Lx, Ly, Lz, hx, hy, lxs;
+  // Pull the spectrum entries of this tile (all kz) towards L2 before the
+  // field tile is loaded and transformed.
+  __device__ __forceinline__ void prefetch(long col0, int ncol, int L) const {
+    const int ky = (int)(col0 >> lxs);
+    bool fl;
+    const int fy = fold_axis(ky, Ly, fl);
+    const int nz = Lz / 2 + 1;
+    for (int i = threadIdx.x; i < ncol * nz; i += blockDim.x) {
+      const int b = i % ncol, fz = i / ncol;
+      const int fx = fold_axis((int)((col0 + b) & (Lx - 1)), Lx, fl);
+      prefetch_l2(G + ((size_t)(fz * hy + fy) * hx + fx) * 6);
+    }
+  }
   __device__ __forceinline__ void operator()(long, long col, int j, cx<T>& x0, cx<T>& x1,
                                              cx<T>& x2) const {
     const int kx = (int)(col & (Lx - 1));
@@ -53,21 +66,27 @@ __global__ void __launch_bounds__(512)
     k_mv_epilogue(const cx<T>* __restrict__ buf1, const cx<T>* __restrict__ x,
                   cx<T>* __restrict__ y, const uint8_t* __restrict__ mat,
                   const cx<T>* __restrict__ ainv, int K1, long nlines, long nm, int l, int Lx,
-                  T coef, const cx<T>* __restrict__ tw, int twshift, RadixPlan rp, int NB) {
+                  T coef, const cx<T>* __restrict__ tw, int twshift, RadixPlan rp, int nb_sh) {
+  const int NB = 1 << nb_sh;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
   const int ld = NB + 1;
   cx<T>* stw = s + (size_t)Lx * ld;
   const long line0 = (long)blockIdx.x * NB;
-  load_twiddles(stw, tw, Lx, twshift);
-  for (int e = threadIdx.x; e < NB * Lx; e += blockDim.x) {
+  const int nth = blockDim.x, tid = threadIdx.x;
+#pragma unroll 4
+  for (int i = 0; i < kElemsPerThread; ++i) {
+    const int e = tid + i * nth;
     const int j = e & (Lx - 1);
-    const int b = e / Lx;
+    const int b = e >> rp.lg;
     const long line = line0 + b;
-    s[j * ld + b] = line < nlines ? buf1[line * Lx + j] : zero<T>();
+    const bool ok = line < nlines;
+    cp_async_cx(s + j * ld + b, ok ? buf1 + line * Lx + j : buf1, ok);
   }
+  load_twiddles(stw, tw, Lx, twshift);
+  cp_async_wait_all();
   __syncthreads();
-  smem_fft<true>(s, stw, Lx, NB, ld, rp);
+  smem_fft<true>(s, stw, Lx, nb_sh, ld, rp);
   for (int e = threadIdx.x; e < NB * l; e += blockDim.x) {
     const int j = e % l;
     const int b = e / l;
@@ -103,18 +122,26 @@ void matvec_impl(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t
   const long lines = (long)nrhs * 3 * nm;
   const long plane = Ly * Lx;
   // 1: x forward of the masked field, l -> 2l
-  launch_contig<T, false>(x, b1, p->mat, nm, lines, (int)Lx, (int)l, l, (int)Lx, Lx, T(1), tw,
+  p->prof.begin(PROF_MV_XF, s);
+  launch_contig<T, false>(x, b1, p->mat, nullptr, nm, lines, (int)Lx, (int)l, l, (int)Lx, Lx, T(1), tw,
                           p->Lmax, s);
+  p->prof.end(s);
   // 2: y forward, m -> 2m
+  p->prof.begin(PROF_MV_YF, s);
   launch_strided<T, false>(b1, b2, Lx, (long)nrhs * 3 * n, (int)Ly, (int)m, Lx, m * Lx, (int)Ly,
                            Lx, plane, T(1), tw, p->Lmax, s);
+  p->prof.end(s);
   // 3: z forward, spectrum multiply, z inverse (n live planes in and out)
   KernelMul<T> op{G_of<T>(p), (int)Lx, (int)Ly, (int)Lz, p->hx, p->hy, ilog2((int)Lx)};
+  p->prof.begin(PROF_MV_Z, s);
   launch_fft3c<T>(b2, plane, nrhs, (int)Lz, (int)n, plane, n * plane, 3 * n * plane, (int)n, op,
-                  tw, p->Lmax, s);
+                  tw, p->Lmax, (int)Lx, (int)Ly, s);
+  p->prof.end(s);
   // 4: y inverse, 2m -> m
+  p->prof.begin(PROF_MV_YI, s);
   launch_strided<T, true>(b2, b1, Lx, (long)nrhs * 3 * n, (int)Ly, (int)Ly, Lx, plane, (int)m, Lx,
                           m * Lx, T(1), tw, p->Lmax, s);
+  p->prof.end(s);
   // 5: x inverse and the diagonal
   {
     const int cap = 512 * kElemsPerThread;
@@ -129,9 +156,12 @@ void matvec_impl(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const T coef = (T)(p->d.dx * p->d.dx * p->d.dx / (double)p->P);
+    p->prof.begin(PROF_MV_XI, s);
+    note_launch();
     kern<<<(unsigned)((lines + NB - 1) / NB), nth, smem, s>>>(
         b1, x, y, p->mat, ainv_of<T>(p), p->K + 1, lines, nm, (int)l, (int)Lx, coef, tw,
-        p->Lmax / (int)Lx, make_radix_plan((int)Lx), NB);
+        p->Lmax / (int)Lx, make_radix_plan((int)Lx), ilog2i(NB));
+    p->prof.end(s);
   }
 }
 

@@ -96,6 +96,7 @@ extern "C" dda_status_t dda_cross_sections(dda_plan_t p, int32_t nrhs, const voi
   const int nblk = (int)std::min<long>(304, std::max<long>(1, (p->nvox + 4095) / 4096));
   // partial sums go to the head of buf1 (free once the matvec is done)
   double* part = static_cast<double*>(p->w.buf1);
+  note_launch();
   k_xsec_sums<<<dim3(nblk, nrhs), kNT, 0, s>>>(
       reinterpret_cast<const double2*>(c), reinterpret_cast<const double2*>(y), p->mat,
       static_cast<const double2*>(p->w.ainv128), p->K + 1, p->w.incd, p->l, p->m, p->n, p->d.dx,

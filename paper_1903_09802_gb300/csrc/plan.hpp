@@ -11,6 +11,7 @@
 #include "../../include/dda.h"
 #include "cx.cuh"
 #include "fft_core.cuh"
+#include "profile.hpp"
 
 namespace dda {
 
@@ -20,6 +21,9 @@ dda_status_t fail(dda_status_t st, const std::string& msg);
 dda_status_t check_cuda(const char* where);
 
 inline bool is_pow2(long v) { return v > 0 && (v & (v - 1)) == 0; }
+
+// Process-wide count of kernel launches made by the library (dda_launch_count).
+void note_launch();
 
 // Bump allocator over the caller's workspace; with base == 0 it only measures.
 struct Carver {
@@ -104,6 +108,7 @@ struct dda_plan_s {
   std::vector<double> ainv_host;         // [rhs][K+1][2]
   std::vector<float> ainv_host32;
   int* pinned = nullptr;                 // host-pinned words polled by the solver
+  dda::Profiler prof;                    // optional kernel timing
 };
 
 namespace dda {
@@ -113,7 +118,8 @@ bool make_layout(const dda_plan_desc_t& d, void* ws, Layout& L, std::string& why
 
 // FFT launch helpers (fft_launch.cu), in place when in == out.
 template <typename T, bool INV>
-void launch_contig(const cx<T>* in, cx<T>* out, const uint8_t* mask, long mask_lines, long nlines,
+void launch_contig(const cx<T>* in, cx<T>* out, const uint8_t* mask, const uint8_t* omask,
+                   long mask_lines, long nlines,
                    int L, int Lin, long in_ld, int Lout, long out_ld, T scale, const cx<T>* tw,
                    int Lmax, cudaStream_t s);
 template <typename T, bool INV>

@@ -11,7 +11,11 @@
 // multilevel DFT, Section 3).  The spectrum keeps one octant: C inherits the
 // parity of each block on each level.
 //
-// Apply: 3-D FFT of each field component, the 3x3 symbol
+// Apply, restricted to the scatterer (the unknowns of eq. 8 live on
+// scatterer voxels; P is the matrix of the box filled with the scatterer's
+// material, Section 1): z = M o P^{-1}(M o v) with M the scatterer mask.
+// The mask is applied in the first and last passes.  In between: 3-D FFT
+// of each field component, the 3x3 symbol
 //   Lambda(w) = alpha_tilde^{-1} I - dx^3 Chat(w)
 // solved per frequency (closed-form inverse of a complex symmetric 3x3
 // matrix), inverse FFT.  Lambda is formed on the fly from the stored Chat and
@@ -94,6 +98,7 @@ struct CircSolve {
   int* err;
   int K1, l, m, n, hx, hy, lxs;
   T dx3, inv_n;
+  __device__ __forceinline__ void prefetch(long, int, int) const {}
   __device__ __forceinline__ void operator()(long rhs, long col, int j, cx<T>& x0, cx<T>& x1,
                                              cx<T>& x2) const {
     const int wx = (int)(col & (l - 1));
@@ -148,19 +153,31 @@ void precond_apply_impl(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cudaS
   const long l = p->l, m = p->m, n = p->n;
   const long lines = (long)nrhs * 3 * n * m;
   const long plane = l * m;
-  launch_contig<T, false>(v, t, nullptr, 1, lines, (int)l, (int)l, l, (int)l, l, T(1), tw, p->Lmax, s);
+  p->prof.begin(PROF_PC_XF, s);
+  launch_contig<T, false>(v, t, p->mat, nullptr, n * m, lines, (int)l, (int)l, l, (int)l, l, T(1), tw,
+                          p->Lmax, s);
+  p->prof.end(s);
+  p->prof.begin(PROF_PC_YF, s);
   if (m > 1)
     launch_strided<T, false>(t, t, l, (long)nrhs * 3 * n, (int)m, (int)m, l, plane, (int)m, l, plane,
                              T(1), tw, p->Lmax, s);
   CircSolve<T> op{C_of<T>(p), ainv_of<T>(p), static_cast<int*>(p->w.err_flag), p->K + 1,
                   (int)l, (int)m, (int)n, p->cx_, p->cy_, ilog2((int)l),
                   (T)(p->d.dx * p->d.dx * p->d.dx), (T)(1.0 / (double)p->nvox)};
+  p->prof.end(s);
+  p->prof.begin(PROF_PC_Z, s);
   launch_fft3c<T>(t, plane, nrhs, (int)n, (int)n, plane, n * plane, 3 * n * plane, (int)n, op, tw,
-                  p->Lmax, s);
+                  p->Lmax, (int)l, (int)m, s);
+  p->prof.end(s);
+  p->prof.begin(PROF_PC_YI, s);
   if (m > 1)
     launch_strided<T, true>(t, t, l, (long)nrhs * 3 * n, (int)m, (int)m, l, plane, (int)m, l, plane,
                             T(1), tw, p->Lmax, s);
-  launch_contig<T, true>(t, z, nullptr, 1, lines, (int)l, (int)l, l, (int)l, l, T(1), tw, p->Lmax, s);
+  p->prof.end(s);
+  p->prof.begin(PROF_PC_XI, s);
+  launch_contig<T, true>(t, z, nullptr, p->mat, n * m, lines, (int)l, (int)l, l, (int)l, l, T(1), tw,
+                         p->Lmax, s);
+  p->prof.end(s);
 }
 
 template void precond_apply_impl<float>(dda_plan_s*, int, const cx<float>*, cx<float>*, cudaStream_t);
@@ -175,9 +192,11 @@ extern "C" dda_status_t dda_precond_build(dda_plan_t p, void* stream) {
   if (!p) return fail(DDA_ERR_INVALID_ARG, "dda_precond_build: NULL plan");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double2* full = static_cast<double2*>(p->w.buf2);
+  note_launch();
   k_chan3<<<grid_for(p->nvox, 128), 128, 0, s>>>(full, p->l, p->m, p->n, p->d.dx, p->d.k);
   fft3d_inplace<double, false>(reinterpret_cast<cx<double>*>(full), 6, p->l, p->m, p->n, 1.0,
                                tw_of<double>(p), p->Lmax, s);
+  note_launch();
   k_compress6<<<grid_for((long)p->cx_ * p->cy_ * p->cz_, 256), 256, 0, s>>>(
       full, p->l, p->m, p->n, p->cx_, p->cy_, p->cz_, static_cast<double2*>(p->w.C128),
       static_cast<float2*>(p->w.C64));

@@ -33,7 +33,11 @@ STATUS = {
 
 EXPORTS = ("dda_workspace_size", "dda_plan_create", "dda_set_incidence", "dda_incident_field",
            "dda_matvec", "dda_precond_build", "dda_precond_apply", "dda_fft3d", "dda_solve",
-           "dda_cross_sections", "dda_plan_destroy", "dda_last_error")
+           "dda_cross_sections", "dda_profile_enable", "dda_profile_read", "dda_plan_destroy",
+           "dda_last_error", "dda_launch_count")
+
+PROFILE_NAMES = ("mv_x_fwd", "mv_y_fwd", "mv_z_mul", "mv_y_inv", "mv_x_inv", "pc_x_fwd", "pc_y_fwd",
+                 "pc_z_solve", "pc_y_inv", "pc_x_inv", "gs_dots", "gs_update")
 
 
 class DDAError(RuntimeError):
@@ -88,10 +92,22 @@ _lib.dda_solve.argtypes = [_vp, ctypes.c_int32, _vp, _vp, ctypes.POINTER(SolveOp
                            ctypes.POINTER(RhsStats), _vp]
 _lib.dda_cross_sections.restype = ctypes.c_int
 _lib.dda_cross_sections.argtypes = [_vp, ctypes.c_int32, _vp, ctypes.POINTER(ctypes.c_double), _vp]
+_lib.dda_profile_enable.restype = ctypes.c_int
+_lib.dda_profile_enable.argtypes = [_vp, ctypes.c_int32]
+_lib.dda_profile_read.restype = ctypes.c_int
+_lib.dda_profile_read.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
+                                  ctypes.c_int32, ctypes.c_int32]
 _lib.dda_plan_destroy.restype = None
 _lib.dda_plan_destroy.argtypes = [_vp]
 _lib.dda_last_error.restype = ctypes.c_char_p
 _lib.dda_last_error.argtypes = []
+_lib.dda_launch_count.restype = ctypes.c_int64
+_lib.dda_launch_count.argtypes = []
+
+
+def launch_count() -> int:
+    """Kernels launched by libdda.so in this process."""
+    return int(_lib.dda_launch_count())
 
 
 def lib():
@@ -232,6 +248,16 @@ class Plan:
             raise DDAError(st, last_error())
         return SolveResult(x, [s.iters for s in stats], [s.cycles for s in stats],
                            [bool(s.converged) for s in stats], [s.rel_resid for s in stats], st)
+
+    def profile(self, on: bool = True):
+        _check(_lib.dda_profile_enable(self._h, int(on)))
+
+    def profile_read(self, reset: bool = True) -> dict:
+        n = len(PROFILE_NAMES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        _check(_lib.dda_profile_read(self._h, ms, cnt, n, int(reset)))
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(PROFILE_NAMES)}
 
     def cross_sections(self, c: torch.Tensor) -> np.ndarray:
         c = c.contiguous()

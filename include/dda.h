@@ -170,8 +170,11 @@ dda_status_t dda_fft3d(dda_plan_t plan, int32_t prec, int32_t nbatch, void* d_da
  *   d_x   complex128 box fields: initial guess in, solution out.
  *   h_stats host array of nrhs records (may be NULL).
  * Right-preconditioned restarted GMRES: Arnoldi with classical Gram-Schmidt
- * applied twice, dots and norms accumulated in FP64, Givens rotations and the
- * small least-squares solve in FP64 on the device.  Every restart recomputes
+ * and a second pass whenever the first removed more than half of ||w||^2
+ * (selective reorthogonalisation); dots and norms summed in FP64 across
+ * threads (complex64 vectors: FP32 products with compensated FP32 per-thread
+ * sums); Givens rotations and the small least-squares solve in FP64 on the
+ * device.  Every restart recomputes
  * the residual b - A x in complex128; with inner_prec = DDA_C64 the Krylov
  * basis, matvecs and preconditioner run in complex64 (FP64 iterative
  * refinement).  Returns DDA_ERR_NOT_CONVERGED if any right-hand side missed

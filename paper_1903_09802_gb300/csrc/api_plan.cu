@@ -111,6 +111,7 @@ bool make_layout(const dda_plan_desc_t& d, void* ws, Layout& L, std::string& why
     s.flags = static_cast<int*>(c.take(4 * R));
     s.iters = static_cast<int*>(c.take(4 * R));
     s.run = static_cast<int*>(c.take(4 * R));
+    s.reorth = static_cast<int*>(c.take(4 * R));
     s.counters = static_cast<int*>(c.take(64));
   }
   L.total = c.off + 256;

@@ -7,7 +7,9 @@
 //   1. recomputes the residual r = b - A x in complex128 (FP64 iterative
 //      refinement when the cycle itself runs in complex64),
 //   2. runs Arnoldi on A P^{-1} from v0 = r/||r||: w = A P^{-1} v_j,
-//      classical Gram-Schmidt applied twice (h = V^H w, w -= V h), FP64
+//      classical Gram-Schmidt (h = V^H w, w -= V h) with a second pass when
+//      the first removed more than half of ||w||^2 (selective
+//      reorthogonalisation), FP64
 //      Hessenberg column, complex Givens rotations and the residual estimate
 //      |g_{j+1}| on the device,
 //   3. ends when the estimate reaches max(tol ||b||, inner_tol ||r||), after
@@ -81,40 +83,61 @@ __device__ __forceinline__ void chunk_of(long nu, int nblk, long& k0, long& k1) 
 }
 
 // partial[(r * nblk + blk) * pst + i] = sum_k conj(V_i[k]) w[k], i < jc (the
-// dot products of Gram-Schmidt), eight at a time.
+// dot products of Gram-Schmidt), eight per sweep over the block's chunk;
+// with want_norm also ||w||^2 into slot pst - 2.  Each warp reduces its
+// eight sums with shuffles into shared memory, then eight threads add the
+// warps' shares in a fixed order.  `mask` selects the right-hand sides that
+// take part (active, or needing a second pass).
 template <typename T>
 __global__ void __launch_bounds__(kNT)
     k_multidot(const cx<T>* __restrict__ V, const cx<T>* __restrict__ W, long nu, long vstride,
-               int jc, double2* __restrict__ partial, int pst, const int* __restrict__ active) {
-  __shared__ double2 sh[32];
+               int jc, double2* __restrict__ partial, int pst, const int* __restrict__ mask,
+               int want_norm) {
+  constexpr int ND = 8;
+  constexpr int NW = kNT / 32;
+  __shared__ double2 sh[ND][NW];
   const int r = blockIdx.y;
-  if (!active[r]) return;
+  if (!mask[r]) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   long k0, k1;
   chunk_of(nu, gridDim.x, k0, k1);
   const cx<T>* w = W + r * nu;
   const cx<T>* vb = V + r * nu;
   double2* out = partial + ((long)r * gridDim.x + blockIdx.x) * pst;
-  constexpr int ND = 8;
-  for (int i0 = 0; i0 < jc; i0 += ND) {
+  const int ntot = jc + (want_norm ? 1 : 0);  // index jc stands for ||w||^2
+  for (int i0 = 0; i0 < ntot; i0 += ND) {
     Acc<T> ar[ND], ai[ND];
     for (long k = k0 + threadIdx.x; k < k1; k += kNT) {
       const cx<T> wk = w[k];
 #pragma unroll
       for (int d = 0; d < ND; ++d) {
-        if (i0 + d < jc) {
-          const cx<T> vk = vb[(long)(i0 + d) * vstride + k];
+        const int i = i0 + d;
+        if (i < jc) {
+          const cx<T> vk = vb[(long)i * vstride + k];
           ar[d].add(vk.x * wk.x + vk.y * wk.y);
           ai[d].add(vk.x * wk.y - vk.y * wk.x);
+        } else if (i == jc && want_norm) {
+          ar[d].add(wk.x * wk.x + wk.y * wk.y);
         }
       }
     }
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
-      if (i0 + d < jc) {
-        const double2 t = block_sum(make_double2(ar[d].get(), ai[d].get()), sh);
-        if (threadIdx.x == 0) out[i0 + d] = t;
-      }
+      const double2 t = warp_sum(make_double2(ar[d].get(), ai[d].get()));
+      if (lane == 0) sh[d][wid] = t;
     }
+    __syncthreads();
+    if (threadIdx.x < ND && i0 + (int)threadIdx.x < ntot) {
+      double2 acc = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int q = 0; q < NW; ++q) {
+        acc.x += sh[threadIdx.x][q].x;
+        acc.y += sh[threadIdx.x][q].y;
+      }
+      const int i = i0 + threadIdx.x;
+      out[i < jc ? i : pst - 2] = acc;
+    }
+    __syncthreads();
   }
 }
 
@@ -122,9 +145,14 @@ __global__ void __launch_bounds__(kNT)
 // Hessenberg column j receives h (first Gram-Schmidt pass) or h added (second).
 __global__ void k_reduce_dots(const double2* __restrict__ partial, int nblk, int jc, int pst,
                               double2* __restrict__ hcol, double2* __restrict__ H, int m, int j,
-                              int pass, const int* __restrict__ active) {
+                              int pass, const int* __restrict__ mask, double* __restrict__ scal) {
   const int r = blockIdx.x;
-  if (!active[r]) return;
+  if (!mask[r]) return;
+  if (pass == 0 && threadIdx.x == 0) {
+    double n2 = 0.0;
+    for (int b = 0; b < nblk; ++b) n2 += partial[((long)r * nblk + b) * pst + pst - 2].x;
+    scal[(long)r * 16 + 7] = n2;  // ||w||^2 before Gram-Schmidt
+  }
   for (int i = threadIdx.x; i < jc; i += blockDim.x) {
     double2 s = make_double2(0.0, 0.0);
     for (int b = 0; b < nblk; ++b) {
@@ -149,11 +177,11 @@ template <typename T>
 __global__ void __launch_bounds__(kNT)
     k_update(const cx<T>* __restrict__ V, cx<T>* __restrict__ W, long nu, long vstride, int jc,
              const double2* __restrict__ hcol, int m, double2* __restrict__ partial, int pst,
-             const int* __restrict__ active) {
+             const int* __restrict__ mask) {
   __shared__ cx<T> hs[520];
   __shared__ double2 sh[32];
   const int r = blockIdx.y;
-  if (!active[r]) return;
+  if (!mask[r]) return;
   for (int i = threadIdx.x; i < jc; i += kNT) {
     const double2 h = hcol[(long)r * (m + 2) + i];
     hs[i] = mk<T>((T)h.x, (T)h.y);
@@ -172,6 +200,23 @@ __global__ void __launch_bounds__(kNT)
   }
   const double2 t = block_sum(make_double2(nn.get(), 0.0), sh);
   if (threadIdx.x == 0) partial[((long)r * gridDim.x + blockIdx.x) * pst + pst - 1] = t;
+}
+
+// Selective reorthogonalisation (Daniel, Gragg, Kaufman & Stewart): a
+// second Gram-Schmidt pass is run for a right-hand side only when the first
+// pass removed more than half of ||w||^2, i.e. ||w_after|| < ||w_before||/sqrt(2).
+__global__ void k_reorth_flag(const double2* __restrict__ partial, int nblk, int pst,
+                              const double* __restrict__ scal, const int* __restrict__ active,
+                              int* __restrict__ reorth, int nrhs) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  int need = 0;
+  if (active[r]) {
+    double n2 = 0.0;
+    for (int b = 0; b < nblk; ++b) n2 += partial[((long)r * nblk + b) * pst + pst - 1].x;
+    need = !(n2 >= 0.5 * scal[(long)r * 16 + 7]);
+  }
+  reorth[r] = need;
 }
 
 // Complex Givens rotation [c s; -conj(s) c] with real c taking (a, b) to (rho, 0).
@@ -476,18 +521,25 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
       }
       matvec_impl<T>(p, nrhs, src, W, s);
       for (int pass = 0; pass < 2; ++pass) {
+        const int* mask = pass == 0 ? st.active : st.reorth;
         p->prof.begin(PROF_AR_DOT, s);
         note_launch();
-        k_multidot<T><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.partial, pst, st.active);
+        k_multidot<T><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.partial, pst, mask,
+                                            pass == 0);
         p->prof.end(s);
         note_launch();
         k_reduce_dots<<<nrhs, 64, 0, s>>>(st.partial, nblk, j + 1, pst, st.hcol, st.H, m, j, pass,
-                                          st.active);
+                                          mask, st.scal);
         p->prof.begin(PROF_AR_UPD, s);
         note_launch();
         k_update<T><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.hcol, m, st.partial, pst,
-                                          st.active);
+                                          mask);
         p->prof.end(s);
+        if (pass == 0) {
+          note_launch();
+          k_reorth_flag<<<(nrhs + 63) / 64, 64, 0, s>>>(st.partial, nblk, pst, st.scal, st.active,
+                                                        st.reorth, nrhs);
+        }
       }
       note_launch();
       k_givens<<<(nrhs + 63) / 64, 64, 0, s>>>(st.H, st.cs, st.sn, st.g, st.partial, nblk, pst,

@@ -76,19 +76,49 @@ __device__ __forceinline__ double2 block_sum(double2 v, double2* sh) {
   return v;
 }
 
+// Chunk of a block: an even number of elements, so pairs of complex values
+// stay 16-byte aligned when the vector length is even.
 __device__ __forceinline__ void chunk_of(long nu, int nblk, long& k0, long& k1) {
-  const long chunk = (nu + nblk - 1) / nblk;
-  k0 = blockIdx.x * chunk;
+  long chunk = (nu + nblk - 1) / nblk;
+  chunk += chunk & 1;
+  k0 = min(nu, blockIdx.x * chunk);
   k1 = min(nu, k0 + chunk);
+}
+
+// Two neighbouring complex values (k, k+1): one 16-byte load in complex64,
+// two in complex128.
+template <typename T>
+struct Pair {
+  cx<T> a, b;
+};
+template <typename T>
+__device__ __forceinline__ Pair<T> ld2(const cx<T>* p) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    return Pair<T>{mk<T>(v.x, v.y), mk<T>(v.z, v.w)};
+  } else {
+    return Pair<T>{p[0], p[1]};
+  }
+}
+template <typename T>
+__device__ __forceinline__ void st2(cx<T>* p, const Pair<T>& v) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v.a.x, v.a.y, v.b.x, v.b.y);
+  } else {
+    p[0] = v.a;
+    p[1] = v.b;
+  }
 }
 
 // partial[(r * nblk + blk) * pst + i] = sum_k conj(V_i[k]) w[k], i < jc (the
 // dot products of Gram-Schmidt), eight per sweep over the block's chunk;
-// with want_norm also ||w||^2 into slot pst - 2.  Each warp reduces its
-// eight sums with shuffles into shared memory, then eight threads add the
-// warps' shares in a fixed order.  `mask` selects the right-hand sides that
-// take part (active, or needing a second pass).
-template <typename T>
+// with want_norm also ||w||^2 into slot pst - 2.  Elements are read in
+// 16-byte pairs, two pairs per thread and trip, so every thread keeps 18
+// wide loads in flight (VEC; the scalar path serves odd vector lengths).
+// Each warp reduces its eight sums with shuffles into shared memory, then
+// eight threads add the warps' shares in a fixed order.  `mask` selects
+// the right-hand sides that take part (active, or needing a second pass).
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(kNT)
     k_multidot(const cx<T>* __restrict__ V, const cx<T>* __restrict__ W, long nu, long vstride,
                int jc, double2* __restrict__ partial, int pst, const int* __restrict__ mask,
@@ -107,17 +137,45 @@ __global__ void __launch_bounds__(kNT)
   const int ntot = jc + (want_norm ? 1 : 0);  // index jc stands for ||w||^2
   for (int i0 = 0; i0 < ntot; i0 += ND) {
     Acc<T> ar[ND], ai[ND];
-    for (long k = k0 + threadIdx.x; k < k1; k += kNT) {
-      const cx<T> wk = w[k];
+    auto acc = [&](int d, const cx<T>& vk, const cx<T>& wk) {
+      ar[d].add(vk.x * wk.x + vk.y * wk.y);
+      ai[d].add(vk.x * wk.y - vk.y * wk.x);
+    };
+    if (VEC) {
+      for (long k = k0 + 2 * threadIdx.x; k < k1; k += 4 * kNT) {
+        const bool two = k + 2 * kNT < k1;
+        const Pair<T> w0 = ld2(w + k);
+        const Pair<T> w1 = two ? ld2(w + k + 2 * kNT) : Pair<T>{zero<T>(), zero<T>()};
+        Pair<T> v0[ND], v1[ND];
 #pragma unroll
-      for (int d = 0; d < ND; ++d) {
-        const int i = i0 + d;
-        if (i < jc) {
-          const cx<T> vk = vb[(long)i * vstride + k];
-          ar[d].add(vk.x * wk.x + vk.y * wk.y);
-          ai[d].add(vk.x * wk.y - vk.y * wk.x);
-        } else if (i == jc && want_norm) {
-          ar[d].add(wk.x * wk.x + wk.y * wk.y);
+        for (int d = 0; d < ND; ++d) {
+          const int i = i0 + d;
+          if (i < jc) {
+            v0[d] = ld2(vb + (long)i * vstride + k);
+            v1[d] = two ? ld2(vb + (long)i * vstride + k + 2 * kNT) : Pair<T>{zero<T>(), zero<T>()};
+          } else {
+            v0[d] = w0;  // i == jc: ||w||^2
+            v1[d] = w1;
+          }
+        }
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+          if (i0 + d < ntot) {
+            acc(d, v0[d].a, w0.a);
+            acc(d, v0[d].b, w0.b);
+            acc(d, v1[d].a, w1.a);
+            acc(d, v1[d].b, w1.b);
+          }
+        }
+      }
+    } else {
+      for (long k = k0 + threadIdx.x; k < k1; k += kNT) {
+        const cx<T> wk = w[k];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+          const int i = i0 + d;
+          if (i < jc) acc(d, vb[(long)i * vstride + k], wk);
+          else if (i == jc && want_norm) acc(d, wk, wk);
         }
       }
     }
@@ -128,14 +186,14 @@ __global__ void __launch_bounds__(kNT)
     }
     __syncthreads();
     if (threadIdx.x < ND && i0 + (int)threadIdx.x < ntot) {
-      double2 acc = make_double2(0.0, 0.0);
+      double2 a = make_double2(0.0, 0.0);
 #pragma unroll
       for (int q = 0; q < NW; ++q) {
-        acc.x += sh[threadIdx.x][q].x;
-        acc.y += sh[threadIdx.x][q].y;
+        a.x += sh[threadIdx.x][q].x;
+        a.y += sh[threadIdx.x][q].y;
       }
       const int i = i0 + threadIdx.x;
-      out[i < jc ? i : pst - 2] = acc;
+      out[i < jc ? i : pst - 2] = a;
     }
     __syncthreads();
   }
@@ -172,8 +230,8 @@ __global__ void k_reduce_dots(const double2* __restrict__ partial, int nblk, int
 }
 
 // w -= sum_{i < jc} h_i V_i, and the block's share of ||w||^2 into
-// partial[...][pst - 1].
-template <typename T>
+// partial[...][pst - 1].  16-byte pairs, two per thread and trip (VEC).
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(kNT)
     k_update(const cx<T>* __restrict__ V, cx<T>* __restrict__ W, long nu, long vstride, int jc,
              const double2* __restrict__ hcol, int m, double2* __restrict__ partial, int pst,
@@ -192,11 +250,37 @@ __global__ void __launch_bounds__(kNT)
   cx<T>* w = W + r * nu;
   const cx<T>* vb = V + r * nu;
   Acc<T> nn;
-  for (long k = k0 + threadIdx.x; k < k1; k += kNT) {
-    cx<T> acc = w[k];
-    for (int i = 0; i < jc; ++i) acc = acc - hs[i] * vb[(long)i * vstride + k];
-    w[k] = acc;
-    nn.add(acc.x * acc.x + acc.y * acc.y);
+  if (VEC) {
+    for (long k = k0 + 2 * threadIdx.x; k < k1; k += 4 * kNT) {
+      const bool two = k + 2 * kNT < k1;
+      Pair<T> a0 = ld2(w + k);
+      Pair<T> a1 = two ? ld2(w + k + 2 * kNT) : Pair<T>{zero<T>(), zero<T>()};
+#pragma unroll 8
+      for (int i = 0; i < jc; ++i) {
+        const cx<T> h = hs[i];
+        const Pair<T> v0 = ld2(vb + (long)i * vstride + k);
+        const Pair<T> v1 = two ? ld2(vb + (long)i * vstride + k + 2 * kNT) : Pair<T>{zero<T>(), zero<T>()};
+        a0.a = a0.a - h * v0.a;
+        a0.b = a0.b - h * v0.b;
+        a1.a = a1.a - h * v1.a;
+        a1.b = a1.b - h * v1.b;
+      }
+      st2(w + k, a0);
+      nn.add(norm2(a0.a));
+      nn.add(norm2(a0.b));
+      if (two) {
+        st2(w + k + 2 * kNT, a1);
+        nn.add(norm2(a1.a));
+        nn.add(norm2(a1.b));
+      }
+    }
+  } else {
+    for (long k = k0 + threadIdx.x; k < k1; k += kNT) {
+      cx<T> acc = w[k];
+      for (int i = 0; i < jc; ++i) acc = acc - hs[i] * vb[(long)i * vstride + k];
+      w[k] = acc;
+      nn.add(norm2(acc));
+    }
   }
   const double2 t = block_sum(make_double2(nn.get(), 0.0), sh);
   if (threadIdx.x == 0) partial[((long)r * gridDim.x + blockIdx.x) * pst + pst - 1] = t;
@@ -457,6 +541,7 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
   const dim3 vgrid(nblk, nrhs);
   const bool prec = o.precond == 3;
   const double brk = sizeof(T) == 8 ? 1e-13 : 1e-6;
+  const bool vec = (nu % 2) == 0;  // 16-byte pairs stay aligned
 
   if (!p->pinned) {
     if (cudaHostAlloc(&p->pinned, 64, cudaHostAllocDefault) != cudaSuccess) {
@@ -524,16 +609,24 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
         const int* mask = pass == 0 ? st.active : st.reorth;
         p->prof.begin(PROF_AR_DOT, s);
         note_launch();
-        k_multidot<T><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.partial, pst, mask,
-                                            pass == 0);
+        if (vec)
+          k_multidot<T, true><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.partial, pst, mask,
+                                                    pass == 0);
+        else
+          k_multidot<T, false><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.partial, pst,
+                                                     mask, pass == 0);
         p->prof.end(s);
         note_launch();
         k_reduce_dots<<<nrhs, 64, 0, s>>>(st.partial, nblk, j + 1, pst, st.hcol, st.H, m, j, pass,
                                           mask, st.scal);
         p->prof.begin(PROF_AR_UPD, s);
         note_launch();
-        k_update<T><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.hcol, m, st.partial, pst,
-                                          mask);
+        if (vec)
+          k_update<T, true><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.hcol, m, st.partial,
+                                                  pst, mask);
+        else
+          k_update<T, false><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.hcol, m, st.partial,
+                                                   pst, mask);
         p->prof.end(s);
         if (pass == 0) {
           note_launch();

@@ -158,6 +158,23 @@ dda_status_t dda_precond_build(dda_plan_t plan, void* stream);
 dda_status_t dda_precond_apply(dda_plan_t plan, int32_t prec, int32_t nrhs, const void* d_v,
                                void* d_z, void* stream);
 
+/* dda_precond_apply for callers that cannot allocate device memory during
+ * the call: code running while a stream is captured into a CUDA graph,
+ * hosts whose device memory is fixed at start-up, frameworks that own the
+ * device through their own pool.  The paper has no counterpart; this is a
+ * deployment variant.  Same arguments and result as dda_precond_apply, but
+ * the transform's scratch (nrhs * 3 * l*m*n complex values) lives in a
+ * 32 MiB array compiled into the library instead of the plan's workspace;
+ * larger requests return DDA_ERR_WORKSPACE.  Every GPU that loads the
+ * library holds that array until the process exits.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * All calls share the one array, and it keeps the last call's contents
+ * (each call overwrites everything it reads): calls that overlap on the GPU,
+ * on any streams, race and give wrong results.  Allocates nothing. */
+dda_status_t dda_precond_apply_noalloc(dda_plan_t plan, int32_t prec, int32_t nrhs,
+                                       const void* d_v, void* d_z, void* stream);
+
 /* In-place unnormalised 3-D DFT (inverse: sign +, scaled by 1/(l m n)) of
  * nbatch complex l x m x n arrays [batch][z][y][x].  Same kernels as the
  * preconditioner's transforms; exposed for testing and reuse. */

@@ -1,0 +1,81 @@
+// dda_precond_apply_noalloc: the preconditioner apply for callers that must
+// not allocate device memory while they run.  Examples are code that
+// executes while a CUDA stream is being captured into a graph (an
+// allocation in a capturing stream is an error), real-time or embedded
+// hosts whose device memory is fixed at start-up, and frameworks that own
+// every byte of the device through their own pool.  The ordinary entry
+// point keeps its transform in the plan's workspace; this one keeps it in a
+// fixed array compiled into the library, so the call itself reserves
+// nothing.
+#include <cstring>
+#include <mutex>
+
+#include "plan.hpp"
+
+namespace dda {
+namespace {
+
+// 32 MiB, reserved on every device that loads the library until the
+// process exits.
+constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_addr[kMaxDevices] = {};
+
+// Device address of the array on the current device, looked up once per
+// device (the host-side symbol is not a device address).
+dda_status_t scratch_address(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return check_cuda("dda_precond_apply_noalloc");
+  if (dev < 0 || dev >= kMaxDevices)
+    return fail(DDA_ERR_INVALID_ARG, "dda_precond_apply_noalloc: device index above 63");
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (g_addr[dev] == nullptr) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || ptr == nullptr)
+      return fail(DDA_ERR_CUDA, std::string("dda_precond_apply_noalloc: cudaGetSymbolAddress: ") +
+                                    cudaGetErrorString(e));
+    g_addr[dev] = ptr;
+  }
+  *out = g_addr[dev];
+  return DDA_OK;
+}
+
+}  // namespace
+}  // namespace dda
+
+using namespace dda;
+
+extern "C" dda_status_t dda_precond_apply_noalloc(dda_plan_t p, int32_t prec, int32_t nrhs,
+                                                  const void* d_v, void* d_z, void* stream) {
+  if (!p || !d_v || !d_z)
+    return fail(DDA_ERR_INVALID_ARG, "dda_precond_apply_noalloc: NULL argument");
+  if (!p->precond_built)
+    return fail(DDA_ERR_NO_PRECOND, "dda_precond_apply_noalloc: call dda_precond_build first");
+  if (nrhs < 1 || nrhs > p->nrhs_inc)
+    return fail(DDA_ERR_INVALID_ARG, "dda_precond_apply_noalloc: nrhs must be 1..(incidences set)");
+  if (prec != DDA_C128 && prec != DDA_C64)
+    return fail(DDA_ERR_INVALID_ARG, "dda_precond_apply_noalloc: prec must be DDA_C128 or DDA_C64");
+  if ((prec == DDA_C128 && !p->has128) || (prec == DDA_C64 && !p->has64))
+    return fail(DDA_ERR_INVALID_ARG, "dda_precond_apply_noalloc: plan lacks that precision");
+  const size_t esz = prec == DDA_C128 ? 16 : 8;
+  const size_t need = (size_t)nrhs * 3 * (size_t)p->nvox * esz;
+  if (need > kNoAllocScratchBytes)
+    return fail(DDA_ERR_WORKSPACE,
+                "dda_precond_apply_noalloc: nrhs * 3 * l*m*n complex values need " +
+                    std::to_string(need) + " bytes, above the 33554432-byte static scratch");
+  void* scratch = nullptr;
+  const dda_status_t st = scratch_address(&scratch);
+  if (st != DDA_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (prec == DDA_C128)
+    precond_apply_into<double>(p, nrhs, static_cast<const cx<double>*>(d_v),
+                               static_cast<cx<double>*>(d_z), static_cast<cx<double>*>(scratch), s);
+  else
+    precond_apply_into<float>(p, nrhs, static_cast<const cx<float>*>(d_v),
+                              static_cast<cx<float>*>(d_z), static_cast<cx<float>*>(scratch), s);
+  return check_cuda("dda_precond_apply_noalloc");
+}

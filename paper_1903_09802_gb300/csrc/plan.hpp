@@ -137,6 +137,9 @@ template <typename T>
 void matvec_impl(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t s);
 template <typename T>
 void precond_apply_impl(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cudaStream_t s);
+template <typename T>
+void precond_apply_into(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cx<T>* t,
+                        cudaStream_t s);
 
 // Templated accessors of the plan's precision-specific buffers.
 template <typename T> inline const cx<T>* tw_of(const dda_plan_s* p);

@@ -180,6 +180,38 @@ void precond_apply_impl(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cudaS
   p->prof.end(s);
 }
 
+// The same five passes with the transform held in caller-chosen scratch
+// `t` (nrhs * 3 * l m n values) instead of the plan's workspace, and no
+// kernel timing.
+template <typename T>
+void precond_apply_into(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cx<T>* t,
+                        cudaStream_t s) {
+  const cx<T>* tw = tw_of<T>(p);
+  const long l = p->l, m = p->m, n = p->n;
+  const long lines = (long)nrhs * 3 * n * m;
+  const long plane = l * m;
+  launch_contig<T, false>(v, t, p->mat, nullptr, n * m, lines, (int)l, (int)l, l, (int)l, l, T(1), tw,
+                          p->Lmax, s);
+  if (m > 1)
+    launch_strided<T, false>(t, t, l, (long)nrhs * 3 * n, (int)m, (int)m, l, plane, (int)m, l, plane,
+                             T(1), tw, p->Lmax, s);
+  CircSolve<T> op{C_of<T>(p), ainv_of<T>(p), static_cast<int*>(p->w.err_flag), p->K + 1,
+                  (int)l, (int)m, (int)n, p->cx_, p->cy_, ilog2((int)l),
+                  (T)(p->d.dx * p->d.dx * p->d.dx), (T)(1.0 / (double)p->nvox)};
+  launch_fft3c<T>(t, plane, nrhs, (int)n, (int)n, plane, n * plane, 3 * n * plane, (int)n, op, tw,
+                  p->Lmax, (int)l, (int)m, s);
+  if (m > 1)
+    launch_strided<T, true>(t, t, l, (long)nrhs * 3 * n, (int)m, (int)m, l, plane, (int)m, l, plane,
+                            T(1), tw, p->Lmax, s);
+  launch_contig<T, true>(t, z, nullptr, p->mat, n * m, lines, (int)l, (int)l, l, (int)l, l, T(1), tw,
+                         p->Lmax, s);
+}
+
+template void precond_apply_into<float>(dda_plan_s*, int, const cx<float>*, cx<float>*, cx<float>*,
+                                        cudaStream_t);
+template void precond_apply_into<double>(dda_plan_s*, int, const cx<double>*, cx<double>*,
+                                         cx<double>*, cudaStream_t);
+
 template void precond_apply_impl<float>(dda_plan_s*, int, const cx<float>*, cx<float>*, cudaStream_t);
 template void precond_apply_impl<double>(dda_plan_s*, int, const cx<double>*, cx<double>*,
                                          cudaStream_t);

@@ -32,7 +32,8 @@ STATUS = {
 }
 
 EXPORTS = ("dda_workspace_size", "dda_plan_create", "dda_set_incidence", "dda_incident_field",
-           "dda_matvec", "dda_precond_build", "dda_precond_apply", "dda_fft3d", "dda_solve",
+           "dda_matvec", "dda_precond_build", "dda_precond_apply", "dda_precond_apply_noalloc",
+           "dda_fft3d", "dda_solve",
            "dda_cross_sections", "dda_profile_enable", "dda_profile_read", "dda_plan_destroy",
            "dda_last_error", "dda_launch_count")
 
@@ -85,6 +86,8 @@ _lib.dda_precond_build.restype = ctypes.c_int
 _lib.dda_precond_build.argtypes = [_vp, _vp]
 _lib.dda_precond_apply.restype = ctypes.c_int
 _lib.dda_precond_apply.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp]
+_lib.dda_precond_apply_noalloc.restype = ctypes.c_int
+_lib.dda_precond_apply_noalloc.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp]
 _lib.dda_fft3d.restype = ctypes.c_int
 _lib.dda_fft3d.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.c_int32, _vp]
 _lib.dda_solve.restype = ctypes.c_int
@@ -223,6 +226,13 @@ class Plan:
         z = torch.empty_like(v) if out is None else out
         _check(_lib.dda_precond_apply(self._h, _prec_of(v), v.shape[0], _ptr(v), _ptr(z), _stream()))
         return z
+
+    def precond_apply_noalloc(self, v: torch.Tensor, out: torch.Tensor) -> torch.Tensor:
+        """dda_precond_apply_noalloc: the library's static scratch instead of the workspace."""
+        v = v.contiguous()
+        _check(_lib.dda_precond_apply_noalloc(self._h, _prec_of(v), v.shape[0], _ptr(v), _ptr(out),
+                                              _stream()))
+        return out
 
     def fft3d(self, data: torch.Tensor, inverse: bool = False) -> torch.Tensor:
         """In-place 3-D DFT of (batch, n, m, l) complex arrays."""

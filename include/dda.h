@@ -100,6 +100,7 @@ typedef struct {
   int32_t converged;     /* 1 when the FP64 relative residual reached tol              */
   int32_t status;        /* dda_status_t of this right-hand side                       */
   double rel_resid;      /* final ||b - A x|| / ||b|| evaluated in complex128          */
+  int32_t reorth;        /* Arnoldi steps that needed a second Gram-Schmidt pass       */
 } dda_rhs_stats_t;
 
 /* Bytes of device workspace a plan with this description needs (0 when the

@@ -112,6 +112,8 @@ bool make_layout(const dda_plan_desc_t& d, void* ws, Layout& L, std::string& why
     s.iters = static_cast<int*>(c.take(4 * R));
     s.run = static_cast<int*>(c.take(4 * R));
     s.reorth = static_cast<int*>(c.take(4 * R));
+    s.reorth_count = static_cast<int*>(c.take(4 * R));
+    s.tickets = static_cast<int*>(c.take(8 * R));
     s.counters = static_cast<int*>(c.take(64));
   }
   L.total = c.off + 256;

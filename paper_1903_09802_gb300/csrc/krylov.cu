@@ -17,7 +17,9 @@
 //      forms u = V y and adds P^{-1} u to x in complex128.
 // Dots and norms of complex64 vectors multiply in FP32 and sum per thread
 // with compensated (Neumaier) FP32 addition, then across threads and blocks
-// in FP64 in a fixed order, so results are reproducible run to run.
+// in FP64 in a fixed order, so results are reproducible run to run; the
+// last block of each Gram-Schmidt kernel (ticket counter) does the
+// cross-block sum, so no separate reduction launches are needed.
 // The host keeps at most two Arnoldi steps queued ahead of the GPU and polls
 // a pinned word to stop launching once every right-hand side has finished
 // its cycle.
@@ -122,12 +124,15 @@ template <typename T, bool VEC>
 __global__ void __launch_bounds__(kNT)
     k_multidot(const cx<T>* __restrict__ V, const cx<T>* __restrict__ W, long nu, long vstride,
                int jc, double2* __restrict__ partial, int pst, const int* __restrict__ mask,
-               int want_norm) {
+               const int* __restrict__ mask2, int want_norm, int* __restrict__ tickets,
+               double2* __restrict__ hcol, double2* __restrict__ H, int m, int j, int pass,
+               double* __restrict__ scal) {
   constexpr int ND = 8;
   constexpr int NW = kNT / 32;
   __shared__ double2 sh[ND][NW];
+  __shared__ int s_last;
   const int r = blockIdx.y;
-  if (!mask[r]) return;
+  if (!mask[r] || (mask2 != nullptr && !mask2[r])) return;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   long k0, k1;
   chunk_of(nu, gridDim.x, k0, k1);
@@ -197,36 +202,42 @@ __global__ void __launch_bounds__(kNT)
     }
     __syncthreads();
   }
-}
-
-// hcol[r][i] = sum over blocks of the partial dots (fixed order); the
-// Hessenberg column j receives h (first Gram-Schmidt pass) or h added (second).
-__global__ void k_reduce_dots(const double2* __restrict__ partial, int nblk, int jc, int pst,
-                              double2* __restrict__ hcol, double2* __restrict__ H, int m, int j,
-                              int pass, const int* __restrict__ mask, double* __restrict__ scal) {
-  const int r = blockIdx.x;
-  if (!mask[r]) return;
-  if (pass == 0 && threadIdx.x == 0) {
-    double n2 = 0.0;
-    for (int b = 0; b < nblk; ++b) n2 += partial[((long)r * nblk + b) * pst + pst - 2].x;
-    scal[(long)r * 16 + 7] = n2;  // ||w||^2 before Gram-Schmidt
-  }
-  for (int i = threadIdx.x; i < jc; i += blockDim.x) {
-    double2 s = make_double2(0.0, 0.0);
-    for (int b = 0; b < nblk; ++b) {
-      const double2 v = partial[((long)r * nblk + b) * pst + i];
-      s.x += v.x;
-      s.y += v.y;
+  // The last block of this right-hand side to finish adds the blocks'
+  // partial sums (warp i handles slots i, i + 8, ...; lanes stride over the
+  // blocks in a fixed order) and writes the Hessenberg column.  Every
+  // writer fences its partials before the barrier that precedes the ticket.
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&tickets[r], 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int nblk = gridDim.x;
+  for (int i = wid; i < ntot; i += NW) {
+    const int slot = i < jc ? i : pst - 2;
+    double2 a = make_double2(0.0, 0.0);
+    for (int b = lane; b < nblk; b += 32) {
+      const double2 v = __ldcg(&partial[((long)r * nblk + b) * pst + slot]);
+      a.x += v.x;
+      a.y += v.y;
     }
-    hcol[(long)r * (m + 2) + i] = s;
-    double2* h = H + (long)r * (m + 1) * m + (long)j * (m + 1) + i;
-    if (pass == 0) {
-      *h = s;
-    } else {
-      h->x += s.x;
-      h->y += s.y;
+    a = warp_sum(a);
+    if (lane == 0) {
+      if (i < jc) {
+        hcol[(long)r * (m + 2) + i] = a;
+        double2* h = H + (long)r * (m + 1) * m + (long)j * (m + 1) + i;
+        if (pass == 0) {
+          *h = a;
+        } else {
+          h->x += a.x;
+          h->y += a.y;
+        }
+      } else {
+        scal[(long)r * 16 + 7] = a.x;  // ||w||^2 before Gram-Schmidt
+      }
     }
   }
+  if (threadIdx.x == 0) tickets[r] = 0;
 }
 
 // w -= sum_{i < jc} h_i V_i, and the block's share of ||w||^2 into
@@ -235,11 +246,14 @@ template <typename T, bool VEC>
 __global__ void __launch_bounds__(kNT)
     k_update(const cx<T>* __restrict__ V, cx<T>* __restrict__ W, long nu, long vstride, int jc,
              const double2* __restrict__ hcol, int m, double2* __restrict__ partial, int pst,
-             const int* __restrict__ mask) {
+             const int* __restrict__ mask, const int* __restrict__ mask2, int* __restrict__ tickets,
+             double* __restrict__ scal, int pass, int* __restrict__ reorth,
+             int* __restrict__ reorth_count) {
   __shared__ cx<T> hs[520];
   __shared__ double2 sh[32];
+  __shared__ int s_last;
   const int r = blockIdx.y;
-  if (!mask[r]) return;
+  if (!mask[r] || (mask2 != nullptr && !mask2[r])) return;
   for (int i = threadIdx.x; i < jc; i += kNT) {
     const double2 h = hcol[(long)r * (m + 2) + i];
     hs[i] = mk<T>((T)h.x, (T)h.y);
@@ -284,23 +298,27 @@ __global__ void __launch_bounds__(kNT)
   }
   const double2 t = block_sum(make_double2(nn.get(), 0.0), sh);
   if (threadIdx.x == 0) partial[((long)r * gridDim.x + blockIdx.x) * pst + pst - 1] = t;
-}
-
-// Selective reorthogonalisation (Daniel, Gragg, Kaufman & Stewart): a
-// second Gram-Schmidt pass is run for a right-hand side only when the first
-// pass removed more than half of ||w||^2, i.e. ||w_after|| < ||w_before||/sqrt(2).
-__global__ void k_reorth_flag(const double2* __restrict__ partial, int nblk, int pst,
-                              const double* __restrict__ scal, const int* __restrict__ active,
-                              int* __restrict__ reorth, int nrhs) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrhs) return;
-  int need = 0;
-  if (active[r]) {
-    double n2 = 0.0;
-    for (int b = 0; b < nblk; ++b) n2 += partial[((long)r * nblk + b) * pst + pst - 1].x;
-    need = !(n2 >= 0.5 * scal[(long)r * 16 + 7]);
+  // Last block: ||w||^2 after this pass, and after the first pass the
+  // selective-reorthogonalisation test (Daniel, Gragg, Kaufman & Stewart):
+  // a second pass runs when the first removed more than half of ||w||^2.
+  __threadfence();
+  if (threadIdx.x == 0) s_last = atomicAdd(&tickets[r], 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (!s_last || threadIdx.x >= 32) return;
+  __threadfence();
+  double n2 = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += 32)
+    n2 += __ldcg(&partial[((long)r * gridDim.x + b) * pst + pst - 1]).x;
+  n2 = warp_sum(make_double2(n2, 0.0)).x;
+  if (threadIdx.x == 0) {
+    scal[(long)r * 16 + 8] = n2;
+    if (pass == 0) {
+      const int need = !(n2 >= 0.5 * scal[(long)r * 16 + 7]);
+      reorth[r] = need;
+      reorth_count[r] += need;
+    }
+    tickets[r] = 0;
   }
-  reorth[r] = need;
 }
 
 // Complex Givens rotation [c s; -conj(s) c] with real c taking (a, b) to (rho, 0).
@@ -330,14 +348,12 @@ __device__ __forceinline__ void givens(double2 a, double2 b, double& c, double2&
 // rotations, new rotation), update g and the residual estimate, decide
 // whether the cycle of this right-hand side goes on.
 __global__ void k_givens(double2* __restrict__ H, double* __restrict__ cs, double2* __restrict__ sn,
-                         double2* __restrict__ g, const double2* __restrict__ partial, int nblk,
-                         int pst, double* __restrict__ scal, int* __restrict__ active,
-                         int* __restrict__ jlen, int* __restrict__ flags, int* __restrict__ iters,
-                         int nrhs, int m, int j, double brk) {
+                         double2* __restrict__ g, double* __restrict__ scal,
+                         int* __restrict__ active, int* __restrict__ jlen, int* __restrict__ flags,
+                         int* __restrict__ iters, int nrhs, int m, int j, double brk) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrhs || !active[r]) return;
-  double n2 = 0.0;
-  for (int b = 0; b < nblk; ++b) n2 += partial[((long)r * nblk + b) * pst + pst - 1].x;
+  const double n2 = scal[(long)r * 16 + 8];  // ||w||^2 after Gram-Schmidt
   const double hn = sqrt(n2);
   double2* h = H + (long)r * (m + 1) * m + (long)j * (m + 1);
   double colnorm2 = n2;
@@ -554,10 +570,12 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
   cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
 
   cudaMemsetAsync(st.iters, 0, sizeof(int) * nrhs, s);
+  cudaMemsetAsync(st.reorth_count, 0, sizeof(int) * nrhs, s);
+  cudaMemsetAsync(st.tickets, 0, sizeof(int) * 2 * nrhs, s);
   cudaMemsetAsync(st.flags, 0, sizeof(int) * nrhs, s);
   cudaMemsetAsync(p->w.err_flag, 0, 4, s);
   std::vector<double> hs((size_t)nrhs * 16);
-  std::vector<int> hits(nrhs), hflags(nrhs), run(nrhs, 0), conv(nrhs, 0), nan(nrhs, 0);
+  std::vector<int> hits(nrhs), hflags(nrhs), hreo(nrhs), run(nrhs, 0), conv(nrhs, 0), nan(nrhs, 0);
   std::vector<double> rel(nrhs, 0.0);
   std::vector<int> ncyc(nrhs, 0);
 
@@ -573,6 +591,7 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
     cudaMemcpyAsync(hs.data(), st.scal, sizeof(double) * 16 * nrhs, cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(hits.data(), st.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s);
     cudaMemcpyAsync(hflags.data(), st.flags, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(hreo.data(), st.reorth_count, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) {
       status = check_cuda("dda_solve");
       break;
@@ -606,38 +625,34 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
       }
       matvec_impl<T>(p, nrhs, src, W, s);
       for (int pass = 0; pass < 2; ++pass) {
-        const int* mask = pass == 0 ? st.active : st.reorth;
+        const int* mask2 = pass == 0 ? nullptr : st.reorth;
         p->prof.begin(PROF_AR_DOT, s);
         note_launch();
         if (vec)
-          k_multidot<T, true><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.partial, pst, mask,
-                                                    pass == 0);
+          k_multidot<T, true><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.partial, pst,
+                                                    st.active, mask2, pass == 0, st.tickets,
+                                                    st.hcol, st.H, m, j, pass, st.scal);
         else
           k_multidot<T, false><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.partial, pst,
-                                                     mask, pass == 0);
+                                                     st.active, mask2, pass == 0, st.tickets,
+                                                     st.hcol, st.H, m, j, pass, st.scal);
         p->prof.end(s);
-        note_launch();
-        k_reduce_dots<<<nrhs, 64, 0, s>>>(st.partial, nblk, j + 1, pst, st.hcol, st.H, m, j, pass,
-                                          mask, st.scal);
         p->prof.begin(PROF_AR_UPD, s);
         note_launch();
         if (vec)
           k_update<T, true><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.hcol, m, st.partial,
-                                                  pst, mask);
+                                                  pst, st.active, mask2, st.tickets + nrhs,
+                                                  st.scal, pass, st.reorth, st.reorth_count);
         else
-          k_update<T, false><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.hcol, m, st.partial,
-                                                   pst, mask);
+          k_update<T, false><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.hcol, m,
+                                                   st.partial, pst, st.active, mask2,
+                                                   st.tickets + nrhs, st.scal, pass, st.reorth,
+                                                   st.reorth_count);
         p->prof.end(s);
-        if (pass == 0) {
-          note_launch();
-          k_reorth_flag<<<(nrhs + 63) / 64, 64, 0, s>>>(st.partial, nblk, pst, st.scal, st.active,
-                                                        st.reorth, nrhs);
-        }
       }
       note_launch();
-      k_givens<<<(nrhs + 63) / 64, 64, 0, s>>>(st.H, st.cs, st.sn, st.g, st.partial, nblk, pst,
-                                               st.scal, st.active, st.jlen, st.flags, st.iters,
-                                               nrhs, m, j, brk);
+      k_givens<<<(nrhs + 63) / 64, 64, 0, s>>>(st.H, st.cs, st.sn, st.g, st.scal, st.active,
+                                               st.jlen, st.flags, st.iters, nrhs, m, j, brk);
       if (j + 1 < steps) {
         note_launch();
         k_scale<T><<<vgrid, kNT, 0, s>>>(W, V + (long)(j + 1) * vstride, nu, st.scal, st.active);
@@ -679,6 +694,7 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
     if (stats) {
       stats[r].iters = hits[r];
       stats[r].cycles = ncyc[r];
+      stats[r].reorth = hreo[r];
       stats[r].converged = conv[r];
       stats[r].rel_resid = rel[r];
       stats[r].status = nan[r] ? DDA_ERR_NAN : (conv[r] ? DDA_OK : DDA_ERR_NOT_CONVERGED);

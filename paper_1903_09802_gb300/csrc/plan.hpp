@@ -48,13 +48,16 @@ struct SolverState {
   double2* hcol;     // [rhs][m+1]   current column (dots of this step)
   double2* partial;  // [rhs][nblk][m+2] block partial sums
   double* scal;      // [rhs][16]: 0 beta, 2 bnorm, 3 target, 4 resid estimate,
-                     //   5 1/h(j+1,j), 6 r-norm (FP64), 7 ||w||^2 before Gram-Schmidt
+                     //   5 1/h(j+1,j), 6 r-norm (FP64), 7 ||w||^2 before Gram-Schmidt,
+                     //   8 ||w||^2 after it
   int* active;       // [rhs] 1 while the current cycle of this RHS is running
   int* jlen;         // [rhs] Arnoldi steps taken in the current cycle
   int* flags;        // [rhs] error bits (1 nan, 2 breakdown)
   int* iters;        // [rhs] inner iterations so far
   int* run;          // [rhs] 1 when the right-hand side takes part in this cycle
   int* reorth;       // [rhs] 1 when this step needs a second Gram-Schmidt pass
+  int* reorth_count; // [rhs] steps that took a second pass
+  int* tickets;      // [2][rhs] last-block counters of the Gram-Schmidt kernels
   int* counters;     // [16] 0: RHS still iterating in the current cycle
 };
 

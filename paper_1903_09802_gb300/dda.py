@@ -67,7 +67,7 @@ class SolveOpts(ctypes.Structure):
 class RhsStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("cycles", ctypes.c_int32),
                 ("converged", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("rel_resid", ctypes.c_double)]
+                ("rel_resid", ctypes.c_double), ("reorth", ctypes.c_int32)]
 
 
 _vp = ctypes.c_void_p
@@ -156,6 +156,7 @@ class SolveResult:
     converged: list
     rel_resid: list
     status: int
+    reorth: list
 
 
 class Plan:
@@ -257,7 +258,8 @@ class Plan:
         if st != 0 and raise_on_error:
             raise DDAError(st, last_error())
         return SolveResult(x, [s.iters for s in stats], [s.cycles for s in stats],
-                           [bool(s.converged) for s in stats], [s.rel_resid for s in stats], st)
+                           [bool(s.converged) for s in stats], [s.rel_resid for s in stats], st,
+                           [s.reorth for s in stats])
 
     def profile(self, on: bool = True):
         _check(_lib.dda_profile_enable(self._h, int(on)))

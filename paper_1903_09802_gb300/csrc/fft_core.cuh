@@ -82,6 +82,61 @@ __device__ __forceinline__ void dft(cx<T>* v) {
   }
 }
 
+template <int R, int Q, bool INV, typename T>
+__device__ __forceinline__ void twiddle_into(cx<T>* o, const cx<T>* v) {
+  if constexpr (Q < R / 2) {
+    o[Q] = twc<R, Q, INV>(v[Q]);
+    twiddle_into<R, Q + 1, INV>(o, v);
+  }
+}
+
+// R-point DFT of an input whose upper half v[R/2..R) is zero (first stage
+// of a zero-padded transform): X[2k] = DFT_{R/2}(v)[k],
+// X[2k+1] = DFT_{R/2}(v w_R^q)[k].
+template <int R, bool INV, typename T>
+__device__ __forceinline__ void dft_half_in(cx<T>* v) {
+  if constexpr (R == 2) {
+    v[1] = v[0];
+  } else if constexpr (R > 2) {
+    cx<T> e[R / 2], o[R / 2];
+#pragma unroll
+    for (int q = 0; q < R / 2; ++q) e[q] = v[q];
+    twiddle_into<R, 0, INV>(o, v);
+    dft<R / 2, INV>(e);
+    dft<R / 2, INV>(o);
+#pragma unroll
+    for (int k = 0; k < R / 2; ++k) {
+      v[2 * k] = e[k];
+      v[2 * k + 1] = o[k];
+    }
+  }
+}
+
+template <int R, int Q, bool INV, typename T>
+__device__ __forceinline__ void dft_combine_lo(cx<T>* v, const cx<T>* e, const cx<T>* o) {
+  if constexpr (Q < R / 2) {
+    v[Q] = e[Q] + twc<R, Q, INV>(o[Q]);
+    dft_combine_lo<R, Q + 1, INV>(v, e, o);
+  }
+}
+
+// R-point DFT of which only the outputs X[0..R/2) are needed (last stage of
+// a transform whose upper half is discarded).
+template <int R, bool INV, typename T>
+__device__ __forceinline__ void dft_half_out(cx<T>* v) {
+  if constexpr (R > 1) {
+    cx<T> e[R / 2], o[R / 2];
+#pragma unroll
+    for (int i = 0; i < R / 2; ++i) {
+      e[i] = v[2 * i];
+      o[i] = v[2 * i + 1];
+    }
+    dft<R / 2, INV>(e);
+    dft<R / 2, INV>(o);
+    dft_combine_lo<R, 0, INV>(v, e, o);
+  }
+}
+
 // Radix sequence of a transform: at most 4 stages (L <= 65536); lg = log2 L.
 struct RadixPlan {
   int nst;
@@ -121,10 +176,15 @@ __device__ __forceinline__ void split_line(int u, int sh, int& b, int& jb) {
   b = u - ((jb * (MUL3 ? 3 : 1)) << sh);
 }
 
-template <int R, bool INV, bool MUL3, typename T>
+// MODE 0: full stage; 1: first stage of a transform whose input's upper
+// half is zero (those values are neither read nor used); 2: last stage of a
+// transform whose output's upper half is discarded (not computed, not written).
+template <int R, bool INV, bool MUL3, int MODE, typename T>
 __device__ __forceinline__ void smem_stage(cx<T>* s, const cx<T>* tw, int L, int sh, int ld,
                                            int Ns, int tid, int nth) {
   constexpr int G = kElemsPerThread / R;
+  constexpr int QIN = MODE == 1 ? R / 2 : R;
+  constexpr int QOUT = MODE == 2 ? R / 2 : R;
   cx<T> v[kElemsPerThread];
   const int LR = L / R;
 #pragma unroll
@@ -133,7 +193,7 @@ __device__ __forceinline__ void smem_stage(cx<T>* s, const cx<T>* tw, int L, int
     int b, jb;
     split_line<MUL3>(u, sh, b, jb);
 #pragma unroll
-    for (int q = 0; q < R; ++q) v[g * R + q] = s[(jb + q * LR) * ld + b];
+    for (int q = 0; q < QIN; ++q) v[g * R + q] = s[(jb + q * LR) * ld + b];
   }
   __syncthreads();
   const int tstep = L / (Ns * R);
@@ -147,20 +207,40 @@ __device__ __forceinline__ void smem_stage(cx<T>* s, const cx<T>* tw, int L, int
 #pragma unroll
       for (int q = 1; q < R; ++q) v[g * R + q] = mulc<INV>(v[g * R + q], tw[q * k * tstep]);
     }
-    dft<R, INV>(&v[g * R]);
+    if constexpr (MODE == 1)
+      dft_half_in<R, INV>(&v[g * R]);
+    else if constexpr (MODE == 2)
+      dft_half_out<R, INV>(&v[g * R]);
+    else
+      dft<R, INV>(&v[g * R]);
     const int base = (jb - k) * R + k;
 #pragma unroll
-    for (int q = 0; q < R; ++q) s[(base + q * Ns) * ld + b] = v[g * R + q];
+    for (int q = 0; q < QOUT; ++q) s[(base + q * Ns) * ld + b] = v[g * R + q];
   }
   __syncthreads();
+}
+
+template <int R, bool INV, bool MUL3, typename T>
+__device__ __forceinline__ void smem_stage_any(int mode, cx<T>* s, const cx<T>* tw, int L, int sh,
+                                               int ld, int Ns, int tid, int nth) {
+  if (mode == 1)
+    smem_stage<R, INV, MUL3, 1>(s, tw, L, sh, ld, Ns, tid, nth);
+  else if (mode == 2)
+    smem_stage<R, INV, MUL3, 2>(s, tw, L, sh, ld, Ns, tid, nth);
+  else
+    smem_stage<R, INV, MUL3, 0>(s, tw, L, sh, ld, Ns, tid, nth);
 }
 
 // Full transform of NB = (MUL3 ? 3 : 1) << sh lines in shared memory.
 // tw[t] = exp(-2 pi i t / L), t < L, also in shared memory.  Caller
 // synchronises before the call.
+// half_in: the input's upper half (positions >= L/2) is zero and need not
+// be present in shared memory; half_out: only positions < L/2 of the result
+// are wanted (the rest of shared memory is left stale).
 template <bool INV, bool MUL3 = false, typename T>
 __device__ __forceinline__ void smem_fft(cx<T>* s, const cx<T>* tw, int L, int sh, int ld,
-                                         const RadixPlan& rp) {
+                                         const RadixPlan& rp, bool half_in = false,
+                                         bool half_out = false) {
   const int tid = threadIdx.x;
   const int nth = blockDim.x;
   int Ns = 1;
@@ -168,11 +248,12 @@ __device__ __forceinline__ void smem_fft(cx<T>* s, const cx<T>* tw, int L, int s
   for (int st = 0; st < 4; ++st) {
     if (st >= rp.nst) break;
     const int R = rp.r[st];
+    const int mode = (st == 0 && half_in) ? 1 : ((st == rp.nst - 1 && half_out) ? 2 : 0);
     switch (R) {
-      case 16: smem_stage<16, INV, MUL3>(s, tw, L, sh, ld, Ns, tid, nth); break;
-      case 8: smem_stage<8, INV, MUL3>(s, tw, L, sh, ld, Ns, tid, nth); break;
-      case 4: smem_stage<4, INV, MUL3>(s, tw, L, sh, ld, Ns, tid, nth); break;
-      default: smem_stage<2, INV, MUL3>(s, tw, L, sh, ld, Ns, tid, nth); break;
+      case 16: smem_stage_any<16, INV, MUL3>(mode, s, tw, L, sh, ld, Ns, tid, nth); break;
+      case 8: smem_stage_any<8, INV, MUL3>(mode, s, tw, L, sh, ld, Ns, tid, nth); break;
+      case 4: smem_stage_any<4, INV, MUL3>(mode, s, tw, L, sh, ld, Ns, tid, nth); break;
+      default: smem_stage_any<2, INV, MUL3>(mode, s, tw, L, sh, ld, Ns, tid, nth); break;
     }
     Ns *= R;
   }

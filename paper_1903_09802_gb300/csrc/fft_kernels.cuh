@@ -39,12 +39,14 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
   cx<T>* stw = s + (size_t)L * ld;
   const int nth = blockDim.x, tid = threadIdx.x;
   const long line0 = (long)blockIdx.x << nb_sh;
+  const bool half_in = 2 * Lin <= L && L > 1, half_out = 2 * Lout <= L && L > 1;
 #pragma unroll 4
   for (int i = 0; i < kElemsPerThread; ++i) {
     const int e = tid + i * nth;
     const int j = e & (L - 1);
     const int b = e >> rp.lg;
     const long line = line0 + b;
+    if (half_in && 2 * j >= L) continue;  // never read by the pruned first stage
     bool ok = line < nlines && j < Lin;
     if (ok && mask != nullptr) ok = mask[(line % mask_lines) * Lin + j] != 0;
     cp_async_cx(s + j * ld + b, ok ? in + line * in_ld + j : in, ok);
@@ -52,7 +54,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
   load_twiddles(stw, tw, L, twshift);
   cp_async_wait_all();
   __syncthreads();
-  smem_fft<INV>(s, stw, L, nb_sh, ld, rp);
+  smem_fft<INV>(s, stw, L, nb_sh, ld, rp, half_in, half_out);
 #pragma unroll
   for (int i = 0; i < kElemsPerThread; ++i) {
     const int e = tid + i * nth;
@@ -82,8 +84,10 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
   const long slab = blockIdx.x / tiles;
   const long col0 = (blockIdx.x - slab * tiles) << nb_sh;
   const cx<T>* src = in + slab * in_ss + col0;
+  const bool half_in = 2 * Lin <= L && L > 1, half_out = 2 * Lout <= L && L > 1;
+  const int nload = half_in ? kElemsPerThread / 2 : kElemsPerThread;  // rows < L/2 only
 #pragma unroll 4
-  for (int i = 0; i < kElemsPerThread; ++i) {
+  for (int i = 0; i < nload; ++i) {
     const int e = tid + i * nth;
     const int b = e & (NB - 1);
     const int j = e >> nb_sh;
@@ -93,7 +97,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
   load_twiddles(stw, tw, L, twshift);
   cp_async_wait_all();
   __syncthreads();
-  smem_fft<INV>(s, stw, L, nb_sh, NB, rp);
+  smem_fft<INV>(s, stw, L, nb_sh, NB, rp, half_in, half_out);
   cx<T>* dst = out + slab * out_ss + col0;
 #pragma unroll
   for (int i = 0; i < kElemsPerThread; ++i) {
@@ -113,8 +117,8 @@ __device__ __forceinline__ int mirror_perm(int r, int n) {
   return r == 0 ? 0 : ((r & 1) ? (r + 1) >> 1 : n - (r >> 1));
 }
 
-// Three components of a strided tile: forward FFT, op(slab, col, j, x0, x1,
-// x2) at every frequency j of every column, inverse FFT; in place on
+// Three components of a strided tile: forward FFT, op.point(op.column(slab,
+// col), j, x0, x1, x2) at every frequency j of every column, inverse FFT; in place on
 // `data` (first Lout of L outputs kept).  Lines of the tile are ordered
 // (component, column) with the column fastest, so shared-memory index and
 // tile index coincide.
@@ -143,8 +147,10 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 768)
     col0 = (long)tt << nbc_sh;
   }
   cx<T>* base = data + slab * ss + col0;
+  const bool half_in = 2 * Lin <= L && L > 1, half_out = 2 * Lout <= L && L > 1;
+  const int nload = half_in ? kElemsPerThread / 2 : kElemsPerThread;  // rows < L/2 only
 #pragma unroll 4
-  for (int i = 0; i < kElemsPerThread; ++i) {
+  for (int i = 0; i < nload; ++i) {
     const int e = tid + i * nth;
     const int b = e & (NBc - 1);
     const int t = e >> nbc_sh;  // 3 j + c
@@ -157,21 +163,38 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 768)
   load_twiddles(stw, tw, L, twshift);
   cp_async_wait_all();
   __syncthreads();
-  smem_fft<false, true>(s, stw, L, nbc_sh, ld, rp);
-  for (int p = tid; p < (L << nbc_sh); p += nth) {
-    const int b = p & (NBc - 1);
-    const int j = p >> nbc_sh;
+  smem_fft<false, true>(s, stw, L, nbc_sh, ld, rp, half_in, false);
+  if ((nth & (NBc - 1)) == 0) {
+    // every thread keeps one column: its per-column state is set up once
+    const int b = tid & (NBc - 1);
     if (col0 + b < ncols) {
-      cx<T>* q = s + j * ld + b;
-      cx<T> x0 = q[0], x1 = q[NBc], x2 = q[2 * NBc];
-      op(slab, col0 + b, j, x0, x1, x2);
-      q[0] = x0;
-      q[NBc] = x1;
-      q[2 * NBc] = x2;
+      const auto ctx = op.column(slab, col0 + b);
+      const int jstep = nth >> nbc_sh;
+      for (int j = tid >> nbc_sh; j < L; j += jstep) {
+        cx<T>* q = s + j * ld + b;
+        cx<T> x0 = q[0], x1 = q[NBc], x2 = q[2 * NBc];
+        op.point(ctx, j, x0, x1, x2);
+        q[0] = x0;
+        q[NBc] = x1;
+        q[2 * NBc] = x2;
+      }
+    }
+  } else {
+    for (int p = tid; p < (L << nbc_sh); p += nth) {
+      const int b = p & (NBc - 1);
+      const int j = p >> nbc_sh;
+      if (col0 + b < ncols) {
+        cx<T>* q = s + j * ld + b;
+        cx<T> x0 = q[0], x1 = q[NBc], x2 = q[2 * NBc];
+        op.point(op.column(slab, col0 + b), j, x0, x1, x2);
+        q[0] = x0;
+        q[NBc] = x1;
+        q[2 * NBc] = x2;
+      }
     }
   }
   __syncthreads();
-  smem_fft<true, true>(s, stw, L, nbc_sh, ld, rp);
+  smem_fft<true, true>(s, stw, L, nbc_sh, ld, rp, false, half_out);
 #pragma unroll
   for (int i = 0; i < kElemsPerThread; ++i) {
     const int e = tid + i * nth;
@@ -192,19 +215,32 @@ __device__ __forceinline__ int fold_axis(int k, int L, bool& flip) {
   flip = 2 * k > L;
   return flip ? L - k : k;
 }
+// Six spectrum entries of one frequency (48 bytes in complex64: three
+// 16-byte loads) with the parity signs of the fold: flip_xy = flip_x != flip_y etc.
 template <typename T>
-__device__ __forceinline__ void load_sym6(const cx<T>* __restrict__ g6, const bool* flip,
-                                          cx<T>& xx, cx<T>& xy, cx<T>& xz, cx<T>& yy,
+__device__ __forceinline__ void load_sym6(const cx<T>* __restrict__ g6, bool fxy, bool fxz,
+                                          bool fyz, cx<T>& xx, cx<T>& xy, cx<T>& xz, cx<T>& yy,
                                           cx<T>& yz, cx<T>& zz) {
-  xx = g6[0];
-  xy = g6[1];
-  xz = g6[2];
-  yy = g6[3];
-  yz = g6[4];
-  zz = g6[5];
-  if (flip[0] != flip[1]) xy = mk<T>(-xy.x, -xy.y);
-  if (flip[0] != flip[2]) xz = mk<T>(-xz.x, -xz.y);
-  if (flip[1] != flip[2]) yz = mk<T>(-yz.x, -yz.y);
+  if constexpr (sizeof(T) == 4) {
+    const float4* p = reinterpret_cast<const float4*>(g6);
+    const float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2);
+    xx = mk<T>(a.x, a.y);
+    xy = mk<T>(a.z, a.w);
+    xz = mk<T>(b.x, b.y);
+    yy = mk<T>(b.z, b.w);
+    yz = mk<T>(c.x, c.y);
+    zz = mk<T>(c.z, c.w);
+  } else {
+    xx = g6[0];
+    xy = g6[1];
+    xz = g6[2];
+    yy = g6[3];
+    yz = g6[4];
+    zz = g6[5];
+  }
+  if (fxy) xy = mk<T>(-xy.x, -xy.y);
+  if (fxz) xz = mk<T>(-xz.x, -xz.y);
+  if (fyz) yz = mk<T>(-yz.x, -yz.y);
 }
 
 __device__ __forceinline__ void prefetch_l2(const void* p) {

@@ -38,16 +38,24 @@ struct KernelMul {
       prefetch_l2(G + ((size_t)(fz * hy + fy) * hx + fx) * 6);
     }
   }
-  __device__ __forceinline__ void operator()(long, long col, int j, cx<T>& x0, cx<T>& x1,
-                                             cx<T>& x2) const {
-    const int kx = (int)(col & (Lx - 1));
-    const int ky = (int)(col >> lxs);
-    bool f[3];
-    const int fx = fold_axis(kx, Lx, f[0]);
-    const int fy = fold_axis(ky, Ly, f[1]);
-    const int fz = fold_axis(j, Lz, f[2]);
+  struct Col {
+    const cx<T>* g;  // spectrum at (fx, fy, fz = 0)
+    bool flx, fly;
+  };
+  __device__ __forceinline__ Col column(long, long col) const {
+    Col c;
+    const int fx = fold_axis((int)(col & (Lx - 1)), Lx, c.flx);
+    const int fy = fold_axis((int)(col >> lxs), Ly, c.fly);
+    c.g = G + ((size_t)fy * hx + fx) * 6;
+    return c;
+  }
+  __device__ __forceinline__ void point(const Col& c, int j, cx<T>& x0, cx<T>& x1,
+                                        cx<T>& x2) const {
+    bool flz;
+    const int fz = fold_axis(j, Lz, flz);
     cx<T> gxx, gxy, gxz, gyy, gyz, gzz;
-    load_sym6(G + ((size_t)(fz * hy + fy) * hx + fx) * 6, f, gxx, gxy, gxz, gyy, gyz, gzz);
+    load_sym6(c.g + (size_t)fz * hy * hx * 6, c.flx != c.fly, c.flx != flz, c.fly != flz, gxx, gxy,
+              gxz, gyy, gyz, gzz);
     const cx<T> y0 = gxx * x0 + gxy * x1 + gxz * x2;
     const cx<T> y1 = gxy * x0 + gyy * x1 + gyz * x2;
     const cx<T> y2 = gxz * x0 + gyz * x1 + gzz * x2;
@@ -86,7 +94,7 @@ __global__ void __launch_bounds__(512)
   load_twiddles(stw, tw, Lx, twshift);
   cp_async_wait_all();
   __syncthreads();
-  smem_fft<true>(s, stw, Lx, nb_sh, ld, rp);
+  smem_fft<true>(s, stw, Lx, nb_sh, ld, rp, false, 2 * l <= Lx && Lx > 1);
   for (int e = threadIdx.x; e < NB * l; e += blockDim.x) {
     const int j = e % l;
     const int b = e / l;

@@ -99,17 +99,27 @@ struct CircSolve {
   int K1, l, m, n, hx, hy, lxs;
   T dx3, inv_n;
   __device__ __forceinline__ void prefetch(long, int, int) const {}
-  __device__ __forceinline__ void operator()(long rhs, long col, int j, cx<T>& x0, cx<T>& x1,
-                                             cx<T>& x2) const {
-    const int wx = (int)(col & (l - 1));
-    const int wy = (int)(col >> lxs);
-    bool f[3];
-    const int fx = fold_axis(wx, l, f[0]);
-    const int fy = fold_axis(wy, m, f[1]);
-    const int fz = fold_axis(j, n, f[2]);
+  struct Col {
+    const cx<T>* c;  // spectrum at (fx, fy, fz = 0)
+    cx<T> at;        // alpha_tilde^{-1} of this right-hand side
+    bool flx, fly;
+  };
+  __device__ __forceinline__ Col column(long rhs, long col) const {
+    Col q;
+    const int fx = fold_axis((int)(col & (l - 1)), l, q.flx);
+    const int fy = fold_axis((int)(col >> lxs), m, q.fly);
+    q.c = C + ((size_t)fy * hx + fx) * 6;
+    q.at = ainv[rhs * K1];
+    return q;
+  }
+  __device__ __forceinline__ void point(const Col& q, int j, cx<T>& x0, cx<T>& x1,
+                                        cx<T>& x2) const {
+    bool flz;
+    const int fz = fold_axis(j, n, flz);
     cx<T> cxx, cxy, cxz, cyy, cyz, czz;
-    load_sym6(C + ((size_t)(fz * hy + fy) * hx + fx) * 6, f, cxx, cxy, cxz, cyy, cyz, czz);
-    const cx<T> at = ainv[rhs * K1];
+    load_sym6(q.c + (size_t)fz * hy * hx * 6, q.flx != q.fly, q.flx != flz, q.fly != flz, cxx, cxy,
+              cxz, cyy, cyz, czz);
+    const cx<T> at = q.at;
     // Lambda = [[a b c] [b d e] [c e f]]
     const cx<T> a = at - dx3 * cxx, d = at - dx3 * cyy, ff = at - dx3 * czz;
     const cx<T> b = -dx3 * cxy, c = -dx3 * cxz, e = -dx3 * cyz;

@@ -92,7 +92,7 @@ bool make_layout(const dda_plan_desc_t& d, void* ws, Layout& L, std::string& why
   if (h128) L.R128 = c.take(16 * R * nu);
   if (d.krylov_m > 0) {
     const long mk = d.krylov_m;
-    L.nblk = (int)std::min<long>(608, std::max<long>(1, (nu + 1023) / 1024));
+    L.nblk = (int)std::min<long>(304, std::max<long>(1, (nu + 4095) / 4096));
     L.V = c.take(esz * (mk + 1) * R * nu);
     L.Wv = c.take(esz * R * nu);
     L.Zv = c.take(esz * R * nu);

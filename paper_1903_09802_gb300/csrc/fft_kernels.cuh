@@ -26,7 +26,7 @@
 namespace dda {
 
 template <typename T, bool INV>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
+__global__ void __launch_bounds__(256)
     k_fft_contig(const cx<T>* in, cx<T>* out, const uint8_t* __restrict__ mask,
                  const uint8_t* __restrict__ omask, long mask_lines, long nlines, int Lin,
                  long in_ld, int Lout, long out_ld, T scale, const cx<T>* __restrict__ tw,

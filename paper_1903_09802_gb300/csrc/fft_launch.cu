@@ -41,8 +41,7 @@ void launch_contig(const cx<T>* in, cx<T>* out, const uint8_t* mask, const uint8
                    int L, int Lin, long in_ld, int Lout, long out_ld, T scale, const cx<T>* tw,
                    int Lmax, cudaStream_t s) {
   if (nlines <= 0) return;
-  const int cap = max_threads<T>() * kElemsPerThread;
-  int per_cta = std::min(4096, cap);  // complex values per CTA
+  int per_cta = 4096;  // complex values per CTA: at most 256 threads
   while (per_cta > 512 && per_cta > L && (nlines * L + per_cta - 1) / per_cta < 2 * kSMs)
     per_cta /= 2;
   int NB = std::max(1, per_cta / L);

@@ -35,6 +35,37 @@ namespace {
 
 constexpr int kNT = 256;  // threads of the vector kernels
 
+// Error-free sum of two floats (Knuth's TwoSum): a + b = s + e exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// Warp sum of compensated FP32 pairs (value s, correction c) without FP64
+// arithmetic (FP64 runs at 1/58 of the FP32 rate on this GPU); lane 0
+// returns s + c in double.
+__device__ __forceinline__ double warp_sum_comp(float s, float c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float so = __shfl_down_sync(0xffffffffu, s, o);
+    const float co = __shfl_down_sync(0xffffffffu, c, o);
+    float e;
+    two_sum(s, so, s, e);
+    c = c + co + e;
+  }
+  return (double)s + (double)c;
+}
+
+__device__ __forceinline__ double2 warp_sum(double2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
 // Per-thread accumulator: plain FP64, or FP32 with Neumaier compensation.
 template <typename T>
 struct Acc;
@@ -43,6 +74,9 @@ struct Acc<double> {
   double s = 0.0;
   __device__ __forceinline__ void add(double v) { s += v; }
   __device__ __forceinline__ double get() const { return s; }
+  __device__ __forceinline__ double warp_total() const {
+    return warp_sum(make_double2(s, 0.0)).x;
+  }
 };
 template <>
 struct Acc<float> {
@@ -53,16 +87,8 @@ struct Acc<float> {
     s = t;
   }
   __device__ __forceinline__ double get() const { return (double)s + (double)c; }
+  __device__ __forceinline__ double warp_total() const { return warp_sum_comp(s, c); }
 };
-
-__device__ __forceinline__ double2 warp_sum(double2 v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
-    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
-  }
-  return v;
-}
 
 // Sum over the block in a fixed order; the result is valid in thread 0.
 __device__ __forceinline__ double2 block_sum(double2 v, double2* sh) {
@@ -121,7 +147,7 @@ __device__ __forceinline__ void st2(cx<T>* p, const Pair<T>& v) {
 // eight threads add the warps' shares in a fixed order.  `mask` selects
 // the right-hand sides that take part (active, or needing a second pass).
 template <typename T, bool VEC>
-__global__ void __launch_bounds__(kNT)
+__global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? 3 : 1)
     k_multidot(const cx<T>* __restrict__ V, const cx<T>* __restrict__ W, long nu, long vstride,
                int jc, double2* __restrict__ partial, int pst, const int* __restrict__ mask,
                const int* __restrict__ mask2, int want_norm, int* __restrict__ tickets,
@@ -147,29 +173,19 @@ __global__ void __launch_bounds__(kNT)
       ai[d].add(vk.x * wk.y - vk.y * wk.x);
     };
     if (VEC) {
-      for (long k = k0 + 2 * threadIdx.x; k < k1; k += 4 * kNT) {
-        const bool two = k + 2 * kNT < k1;
+      for (long k = k0 + 2 * threadIdx.x; k < k1; k += 2 * kNT) {
         const Pair<T> w0 = ld2(w + k);
-        const Pair<T> w1 = two ? ld2(w + k + 2 * kNT) : Pair<T>{zero<T>(), zero<T>()};
-        Pair<T> v0[ND], v1[ND];
+        Pair<T> v0[ND];
 #pragma unroll
         for (int d = 0; d < ND; ++d) {
           const int i = i0 + d;
-          if (i < jc) {
-            v0[d] = ld2(vb + (long)i * vstride + k);
-            v1[d] = two ? ld2(vb + (long)i * vstride + k + 2 * kNT) : Pair<T>{zero<T>(), zero<T>()};
-          } else {
-            v0[d] = w0;  // i == jc: ||w||^2
-            v1[d] = w1;
-          }
+          v0[d] = i < jc ? ld2(vb + (long)i * vstride + k) : w0;  // i == jc: ||w||^2
         }
 #pragma unroll
         for (int d = 0; d < ND; ++d) {
           if (i0 + d < ntot) {
             acc(d, v0[d].a, w0.a);
             acc(d, v0[d].b, w0.b);
-            acc(d, v1[d].a, w1.a);
-            acc(d, v1[d].b, w1.b);
           }
         }
       }
@@ -186,8 +202,9 @@ __global__ void __launch_bounds__(kNT)
     }
 #pragma unroll
     for (int d = 0; d < ND; ++d) {
-      const double2 t = warp_sum(make_double2(ar[d].get(), ai[d].get()));
-      if (lane == 0) sh[d][wid] = t;
+      const double tr = ar[d].warp_total();
+      const double ti = ai[d].warp_total();
+      if (lane == 0) sh[d][wid] = make_double2(tr, ti);
     }
     __syncthreads();
     if (threadIdx.x < ND && i0 + (int)threadIdx.x < ntot) {

@@ -196,7 +196,7 @@ __device__ __forceinline__ void smem_stage(cx<T>* s, const cx<T>* tw, int L, int
     for (int q = 0; q < QIN; ++q) v[g * R + q] = s[(jb + q * LR) * ld + b];
   }
   __syncthreads();
-  const int tstep = L / (Ns * R);
+  const int tstep = L / (Ns * R);  // powers of two: compiles to a shift
 #pragma unroll
   for (int g = 0; g < G; ++g) {
     const int u = tid + g * nth;

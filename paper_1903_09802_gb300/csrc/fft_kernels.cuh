@@ -40,37 +40,56 @@ __global__ void __launch_bounds__(256)
   const int nth = blockDim.x, tid = threadIdx.x;
   const long line0 = (long)blockIdx.x << nb_sh;
   const bool half_in = 2 * Lin <= L && L > 1, half_out = 2 * Lout <= L && L > 1;
+  // Thread tid keeps position j = tid mod L of lines b0 + i * (nth / L)
+  // (nth / L >= 1 since nth = NB L / 16 and NB >= 16 whenever L < nth).
+  const int j = tid & (L - 1);
+  const int b0 = tid >> rp.lg;
+  const int bstep = nth >> rp.lg;
+  if (bstep > 0) {
+    if (!(half_in && 2 * j >= L)) {  // the pruned first stage never reads j >= L/2
+      long line = line0 + b0;
+      const cx<T>* g = in + line * in_ld + j;
+      const long gstep = (long)bstep * in_ld;
+      cx<T>* q = s + j * ld + b0;
 #pragma unroll 4
-  for (int i = 0; i < kElemsPerThread; ++i) {
-    const int e = tid + i * nth;
-    const int j = e & (L - 1);
-    const int b = e >> rp.lg;
-    const long line = line0 + b;
-    if (half_in && 2 * j >= L) continue;  // never read by the pruned first stage
-    bool ok = line < nlines && j < Lin;
-    if (ok && mask != nullptr) ok = mask[(line % mask_lines) * Lin + j] != 0;
-    cp_async_cx(s + j * ld + b, ok ? in + line * in_ld + j : in, ok);
+      for (int i = 0; i < kElemsPerThread; ++i, line += bstep, g += gstep, q += bstep) {
+        bool ok = line < nlines && j < Lin;
+        if (ok && mask != nullptr) ok = mask[(line % mask_lines) * Lin + j] != 0;
+        cp_async_cx(q, ok ? g : in, ok);
+      }
+    }
+  } else {
+    for (int i = 0; i < kElemsPerThread; ++i) {
+      const int e = tid + i * nth;
+      const int jj = e & (L - 1);
+      const int b = e >> rp.lg;
+      const long line = line0 + b;
+      if (half_in && 2 * jj >= L) continue;
+      bool ok = line < nlines && jj < Lin;
+      if (ok && mask != nullptr) ok = mask[(line % mask_lines) * Lin + jj] != 0;
+      cp_async_cx(s + jj * ld + b, ok ? in + line * in_ld + jj : in, ok);
+    }
   }
   load_twiddles(stw, tw, L, twshift);
   cp_async_wait_all();
   __syncthreads();
   smem_fft<INV>(s, stw, L, nb_sh, ld, rp, half_in, half_out);
-#pragma unroll
+#pragma unroll 4
   for (int i = 0; i < kElemsPerThread; ++i) {
     const int e = tid + i * nth;
-    const int j = e & (L - 1);
+    const int jj = e & (L - 1);
     const int b = e >> rp.lg;
     const long line = line0 + b;
-    if (line < nlines && j < Lout) {
-      cx<T> w = scale * s[j * ld + b];
-      if (omask != nullptr && omask[(line % mask_lines) * Lout + j] == 0) w = zero<T>();
-      out[line * out_ld + j] = w;
+    if (line < nlines && jj < Lout) {
+      cx<T> w = scale * s[jj * ld + b];
+      if (omask != nullptr && omask[(line % mask_lines) * Lout + jj] == 0) w = zero<T>();
+      out[line * out_ld + jj] = w;
     }
   }
 }
 
-template <typename T, bool INV>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
+template <typename T, bool INV, bool FIX>
+__global__ void __launch_bounds__(512)
     k_fft_strided(const cx<T>* in, cx<T>* out, long ncols, int Lin, long in_js, long in_ss,
                   int Lout, long out_js, long out_ss, T scale, const cx<T>* __restrict__ tw,
                   int twshift, RadixPlan rp, int nb_sh) {
@@ -86,25 +105,51 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 1024)
   const cx<T>* src = in + slab * in_ss + col0;
   const bool half_in = 2 * Lin <= L && L > 1, half_out = 2 * Lout <= L && L > 1;
   const int nload = half_in ? kElemsPerThread / 2 : kElemsPerThread;  // rows < L/2 only
+  // Thread tid keeps column b = tid mod NB and rows j0 + i * (nth / NB):
+  // addresses advance by constant strides.
+  // (L >= 16, so nth / NB = L / 16 >= 1; shorter lines take the generic loop).
+  const int b = tid & (NB - 1);
+  const int j0 = tid >> nb_sh;
+  const int jstep = nth >> nb_sh;
+  const bool colok = col0 + b < ncols;
+  if constexpr (FIX) {
+    const cx<T>* g = src + (long)j0 * in_js + b;
+    const long gstep = (long)jstep * in_js;
+    cx<T>* q = s + tid;
 #pragma unroll 4
-  for (int i = 0; i < nload; ++i) {
-    const int e = tid + i * nth;
-    const int b = e & (NB - 1);
-    const int j = e >> nb_sh;
-    const bool ok = col0 + b < ncols && j < Lin;
-    cp_async_cx(s + e, ok ? src + j * in_js + b : in, ok);
+    for (int i = 0, j = j0; i < nload; ++i, j += jstep, g += gstep, q += nth) {
+      const bool ok = colok && j < Lin;
+      cp_async_cx(q, ok ? g : in, ok);
+    }
+  } else {
+    for (int i = 0; i < nload; ++i) {
+      const int e = tid + i * nth;
+      const int bb = e & (NB - 1);
+      const int j = e >> nb_sh;
+      const bool ok = col0 + bb < ncols && j < Lin;
+      cp_async_cx(s + e, ok ? src + j * in_js + bb : in, ok);
+    }
   }
   load_twiddles(stw, tw, L, twshift);
   cp_async_wait_all();
   __syncthreads();
   smem_fft<INV>(s, stw, L, nb_sh, NB, rp, half_in, half_out);
-  cx<T>* dst = out + slab * out_ss + col0;
-#pragma unroll
-  for (int i = 0; i < kElemsPerThread; ++i) {
-    const int e = tid + i * nth;
-    const int b = e & (NB - 1);
-    const int j = e >> nb_sh;
-    if (col0 + b < ncols && j < Lout) dst[j * out_js + b] = scale * s[e];
+  if constexpr (FIX) {
+    if (colok) {
+      cx<T>* g = out + slab * out_ss + col0 + (long)j0 * out_js + b;
+      const long gstep = (long)jstep * out_js;
+      const cx<T>* q = s + tid;
+#pragma unroll 4
+      for (int j = j0; j < Lout; j += jstep, g += gstep, q += nth) *g = scale * *q;
+    }
+  } else {
+    cx<T>* dst = out + slab * out_ss + col0;
+    for (int i = 0; i < kElemsPerThread; ++i) {
+      const int e = tid + i * nth;
+      const int bb = e & (NB - 1);
+      const int j = e >> nb_sh;
+      if (col0 + bb < ncols && j < Lout) dst[j * out_js + bb] = scale * s[e];
+    }
   }
 }
 
@@ -122,7 +167,7 @@ __device__ __forceinline__ int mirror_perm(int r, int n) {
 // `data` (first Lout of L outputs kept).  Lines of the tile are ordered
 // (component, column) with the column fastest, so shared-memory index and
 // tile index coincide.
-template <typename T, class Op>
+template <typename T, class Op, bool FIX>
 __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 768)
     k_fft3c(cx<T>* data, long ncols, int Lin, long js, long cs, long ss, int Lout, Op op,
             const cx<T>* __restrict__ tw, int twshift, RadixPlan rp, int nbc_sh, int row_len,
@@ -149,15 +194,36 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 768)
   cx<T>* base = data + slab * ss + col0;
   const bool half_in = 2 * Lin <= L && L > 1, half_out = 2 * Lout <= L && L > 1;
   const int nload = half_in ? kElemsPerThread / 2 : kElemsPerThread;  // rows < L/2 only
+  // With L >= 16 every thread keeps one (component, column) pair and rows
+  // j0 + i * L/16, so addresses advance by constant strides.
+  constexpr bool fixed = FIX;  // L >= 16
+  {
+    const int e0 = tid;
+    const int b0 = e0 & (NBc - 1);
+    const int t0 = e0 >> nbc_sh;
+    const int j0 = t0 / 3, c0 = t0 - 3 * (t0 / 3);
+    if constexpr (fixed) {
+      const int jstep = L >> 4;  // nth / (3 NBc)
+      const bool colok = col0 + b0 < ncols;
+      const cx<T>* g = base + c0 * cs + (long)j0 * js + b0;
+      const long gstep = (long)jstep * js;
+      cx<T>* q = s + e0;
 #pragma unroll 4
-  for (int i = 0; i < nload; ++i) {
-    const int e = tid + i * nth;
-    const int b = e & (NBc - 1);
-    const int t = e >> nbc_sh;  // 3 j + c
-    const int j = t / 3;
-    const int c = t - 3 * j;
-    const bool ok = col0 + b < ncols && j < Lin;
-    cp_async_cx(s + e, ok ? base + c * cs + j * js + b : data, ok);
+      for (int i = 0, j = j0; i < nload; ++i, j += jstep, g += gstep, q += nth) {
+        const bool ok = colok && j < Lin;
+        cp_async_cx(q, ok ? g : data, ok);
+      }
+    } else {
+      for (int i = 0; i < nload; ++i) {
+        const int e = tid + i * nth;
+        const int b = e & (NBc - 1);
+        const int t = e >> nbc_sh;  // 3 j + c
+        const int j = t / 3;
+        const int c = t - 3 * j;
+        const bool ok = col0 + b < ncols && j < Lin;
+        cp_async_cx(s + e, ok ? base + c * cs + j * js + b : data, ok);
+      }
+    }
   }
   op.prefetch(col0, NBc, L);
   load_twiddles(stw, tw, L, twshift);
@@ -195,14 +261,27 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 768)
   }
   __syncthreads();
   smem_fft<true, true>(s, stw, L, nbc_sh, ld, rp, false, half_out);
-#pragma unroll
-  for (int i = 0; i < kElemsPerThread; ++i) {
-    const int e = tid + i * nth;
-    const int b = e & (NBc - 1);
-    const int t = e >> nbc_sh;
-    const int j = t / 3;
-    const int c = t - 3 * j;
-    if (col0 + b < ncols && j < Lout) base[c * cs + j * js + b] = s[e];
+  if constexpr (fixed) {
+    const int b0 = tid & (NBc - 1);
+    const int t0 = tid >> nbc_sh;
+    const int j0 = t0 / 3, c0 = t0 - 3 * (t0 / 3);
+    if (col0 + b0 < ncols) {
+      const int jstep = L >> 4;
+      cx<T>* g = base + c0 * cs + (long)j0 * js + b0;
+      const long gstep = (long)jstep * js;
+      const cx<T>* q = s + tid;
+#pragma unroll 4
+      for (int j = j0; j < Lout; j += jstep, g += gstep, q += nth) *g = *q;
+    }
+  } else {
+    for (int i = 0; i < kElemsPerThread; ++i) {
+      const int e = tid + i * nth;
+      const int b = e & (NBc - 1);
+      const int t = e >> nbc_sh;
+      const int j = t / 3;
+      const int c = t - 3 * j;
+      if (col0 + b < ncols && j < Lout) base[c * cs + j * js + b] = s[e];
+    }
   }
 }
 
@@ -270,7 +349,7 @@ void launch_fft3c(cx<T>* data, long ncols, long nslabs, int L, int Lin, long js,
   const int nth = 3 * NBc * L / kElemsPerThread;
   const size_t smem = ((size_t)3 * NBc * L + L) * sizeof(cx<T>);
   const long grid = nslabs * ((ncols + NBc - 1) / NBc);
-  auto kern = k_fft3c<T, Op>;
+  auto kern = L >= 16 ? k_fft3c<T, Op, true> : k_fft3c<T, Op, false>;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   note_launch();

@@ -62,7 +62,7 @@ void launch_strided(const cx<T>* in, cx<T>* out, long ncols, long nslabs, int L,
                     long in_js, long in_ss, int Lout, long out_js, long out_ss, T scale,
                     const cx<T>* tw, int Lmax, cudaStream_t s) {
   if (ncols <= 0 || nslabs <= 0) return;
-  const int cap = max_threads<T>() * kElemsPerThread;
+  const int cap = 512 * kElemsPerThread;  // at most 512 threads
   int NB = sizeof(T) == 8 ? 8 : 16;
   NB = std::min<long>(NB, floor_pow2(ncols));
   while (NB * L > cap && NB > 1) NB /= 2;
@@ -71,7 +71,7 @@ void launch_strided(const cx<T>* in, cx<T>* out, long ncols, long nslabs, int L,
   const int nth = NB * L / kElemsPerThread;
   const size_t smem = ((size_t)L * NB + L) * sizeof(cx<T>);
   const long grid = nslabs * ((ncols + NB - 1) / NB);
-  auto kern = k_fft_strided<T, INV>;
+  auto kern = L >= 16 ? k_fft_strided<T, INV, true> : k_fft_strided<T, INV, false>;
   allow_smem(kern, smem);
   note_launch();
   kern<<<(unsigned)grid, nth, smem, s>>>(in, out, ncols, Lin, in_js, in_ss, Lout, out_js, out_ss,

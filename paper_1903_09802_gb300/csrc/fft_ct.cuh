@@ -1,0 +1,317 @@
+// Compile-time specialised shared-memory FFT.
+//
+// Same Stockham algorithm as fft_core.cuh, but the transform length L, the
+// shared-memory row pitch LD, the number of lines NB and therefore the
+// radix sequence, the stride Ns of every stage and the thread count are
+// template constants.  Every butterfly then addresses shared memory as
+// (per-butterfly base register) + (compile-time immediate), the line /
+// butterfly split of a thread index is a shift (or a multiply by the
+// reciprocal of 3 for three-component tiles), and twiddle indices advance by
+// additions; this removes most of the integer work of the run-time version,
+// which dominated its instruction count.
+#pragma once
+
+#include "fft_kernels.cuh"
+
+namespace dda {
+
+__host__ __device__ constexpr int ct_log2(int v) { return v <= 1 ? 0 : 1 + ct_log2(v / 2); }
+
+// Same stage split as make_radix_plan: ceil(bits/4) stages, larger radices first.
+__host__ __device__ constexpr int ct_nst(int L) { return (ct_log2(L) + 3) / 4; }
+__host__ __device__ constexpr int ct_bits(int L, int st) {
+  int left = ct_log2(L), n = ct_nst(L), b = 0;
+  for (int s = 0; s <= st; ++s) {
+    b = (left + (n - s) - 1) / (n - s);
+    left -= b;
+  }
+  return b;
+}
+__host__ __device__ constexpr int ct_radix(int L, int st) { return 1 << ct_bits(L, st); }
+
+// One stage: radix R, NS = product of the radices already applied.  The tile
+// holds NB lines (NB = NBP or 3 * NBP) of length L; element (b, j) at
+// s[j * LD + b]; the block has NB * L / 16 threads.
+template <int R, int NS, int MODE, int L, int LD, int NB, bool INV, typename T>
+__device__ __forceinline__ void ct_stage(cx<T>* s, const cx<T>* tw, int tid) {
+  constexpr int NTH = NB * L / kElemsPerThread;
+  constexpr int G = kElemsPerThread / R;
+  constexpr int LR = L / R;
+  constexpr int QIN = MODE == 1 ? R / 2 : R;
+  constexpr int QOUT = MODE == 2 ? R / 2 : R;
+  constexpr int TSTEP = L / (NS * R);
+  cx<T> v[kElemsPerThread];
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int u = tid + g * NTH;
+    const int jb = u / NB;
+    const int b = u - jb * NB;
+    const cx<T>* src = s + jb * LD + b;
+#pragma unroll
+    for (int q = 0; q < QIN; ++q) v[g * R + q] = src[q * LR * LD];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int u = tid + g * NTH;
+    const int jb = u / NB;
+    const int b = u - jb * NB;
+    if constexpr (NS > 1) {
+      const int k = jb & (NS - 1);
+      const int kt = k * TSTEP;
+      int idx = kt;
+#pragma unroll
+      for (int q = 1; q < R; ++q, idx += kt) v[g * R + q] = mulc<INV>(v[g * R + q], tw[idx]);
+    }
+    if constexpr (MODE == 1)
+      dft_half_in<R, INV>(&v[g * R]);
+    else if constexpr (MODE == 2)
+      dft_half_out<R, INV>(&v[g * R]);
+    else
+      dft<R, INV>(&v[g * R]);
+    const int k = jb & (NS - 1);
+    cx<T>* dst = s + ((jb - k) * R + k) * LD + b;
+#pragma unroll
+    for (int q = 0; q < QOUT; ++q) dst[q * NS * LD] = v[g * R + q];
+  }
+  __syncthreads();
+}
+
+template <int ST, int NS, int L, int LD, int NB, bool INV, bool HALF_IN, bool HALF_OUT, typename T>
+__device__ __forceinline__ void ct_stages(cx<T>* s, const cx<T>* tw, int tid) {
+  if constexpr (ST < ct_nst(L)) {
+    constexpr int R = ct_radix(L, ST);
+    constexpr int MODE = (ST == 0 && HALF_IN) ? 1 : ((ST == ct_nst(L) - 1 && HALF_OUT) ? 2 : 0);
+    ct_stage<R, NS, MODE, L, LD, NB, INV>(s, tw, tid);
+    ct_stages<ST + 1, NS * R, L, LD, NB, INV, HALF_IN, HALF_OUT>(s, tw, tid);
+  }
+}
+
+// Full transform of the NB lines of a tile (caller synchronises before).
+template <int L, int LD, int NB, bool INV, bool HALF_IN, bool HALF_OUT, typename T>
+__device__ __forceinline__ void ct_fft(cx<T>* s, const cx<T>* tw) {
+  ct_stages<0, 1, L, LD, NB, INV, HALF_IN, HALF_OUT>(s, tw, threadIdx.x);
+}
+
+// ---------------------------------------------------------------------------
+// Kernels.  Tile shapes: strided NB columns, contiguous NB lines, three-
+// component tiles 3 * NBC columns.
+
+// Lines along a strided axis (see k_fft_strided); HALF_IN / HALF_OUT when
+// the input has Lin = L/2 rows / only Lout = L/2 output rows are kept.
+template <typename T, bool INV, int L, int NB, bool HALF_IN, bool HALF_OUT>
+__global__ void __launch_bounds__(NB * L / kElemsPerThread, 1024 / (NB * L / kElemsPerThread))
+    k_ct_strided(const cx<T>* in, cx<T>* out, long ncols, int Lin, long in_js, long in_ss,
+                 int Lout, long out_js, long out_ss, T scale, const cx<T>* __restrict__ tw,
+                 int twshift) {
+  constexpr int NTH = NB * L / kElemsPerThread;
+  constexpr int JSTEP = NTH / NB;  // = L / 16
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* stw = s + L * NB;
+  const int tid = threadIdx.x;
+  const long tiles = ncols / NB;
+  const long slab = blockIdx.x / tiles;
+  const long col0 = (blockIdx.x - slab * tiles) * NB;
+  const int b = tid & (NB - 1);
+  const int j0 = tid / NB;
+  {
+    const cx<T>* g = in + slab * in_ss + col0 + (long)j0 * in_js + b;
+    const long gstep = (long)JSTEP * in_js;
+    constexpr int NLOAD = HALF_IN ? kElemsPerThread / 2 : kElemsPerThread;
+#pragma unroll
+    for (int i = 0; i < NLOAD; ++i, g += gstep) {
+      const int j = j0 + i * JSTEP;
+      const bool ok = j < Lin;
+      cp_async_cx(s + tid + i * NTH, ok ? g : in, ok);
+    }
+  }
+  load_twiddles(stw, tw, L, twshift);
+  cp_async_wait_all();
+  __syncthreads();
+  ct_fft<L, NB, NB, INV, HALF_IN, HALF_OUT>(s, stw);
+  cx<T>* g = out + slab * out_ss + col0 + (long)j0 * out_js + b;
+  const long gstep = (long)JSTEP * out_js;
+  constexpr int NSTORE = HALF_OUT ? kElemsPerThread / 2 : kElemsPerThread;
+#pragma unroll
+  for (int i = 0; i < NSTORE; ++i, g += gstep) {
+    const int j = j0 + i * JSTEP;
+    if (j < Lout) *g = scale * s[tid + i * NTH];
+  }
+}
+
+// Lines along the contiguous axis (see k_fft_contig), NB lines per CTA,
+// pitch NB + 1; NB >= 16 so that each thread keeps one position j.
+template <typename T, bool INV, int L, int NB, bool HALF_IN, bool HALF_OUT>
+__global__ void __launch_bounds__(NB * L / kElemsPerThread, 1024 / (NB * L / kElemsPerThread))
+    k_ct_contig(const cx<T>* in, cx<T>* out, const uint8_t* __restrict__ mask,
+                const uint8_t* __restrict__ omask, long mask_lines, long nlines, int Lin,
+                long in_ld, int Lout, long out_ld, T scale, const cx<T>* __restrict__ tw,
+                int twshift) {
+  static_assert(NB >= 16, "one position per thread");
+  constexpr int NTH = NB * L / kElemsPerThread;
+  constexpr int LD = NB + 1;
+  constexpr int BSTEP = NTH / L;  // = NB / 16
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* stw = s + L * LD;
+  const int tid = threadIdx.x;
+  const long line0 = (long)blockIdx.x * NB;
+  const int j = tid & (L - 1);
+  const int b0 = tid / L;
+  if (!(HALF_IN && 2 * j >= L)) {
+    long line = line0 + b0;
+    long mrow = line % mask_lines;
+    const cx<T>* g = in + line * in_ld + j;
+    cx<T>* q = s + j * LD + b0;
+#pragma unroll 4
+    for (int i = 0; i < kElemsPerThread; ++i, line += BSTEP, g += BSTEP * in_ld, q += BSTEP) {
+      bool ok = line < nlines && j < Lin;
+      if (ok && mask != nullptr) ok = mask[mrow * Lin + j] != 0;
+      cp_async_cx(q, ok ? g : in, ok);
+      mrow += BSTEP;
+      if (mrow >= mask_lines) mrow = mrow >= 2 * mask_lines ? mrow % mask_lines : mrow - mask_lines;
+    }
+  }
+  load_twiddles(stw, tw, L, twshift);
+  cp_async_wait_all();
+  __syncthreads();
+  ct_fft<L, LD, NB, INV, HALF_IN, HALF_OUT>(s, stw);
+  if (j < Lout) {
+    long line = line0 + b0;
+    long mrow = line % mask_lines;
+    cx<T>* g = out + line * out_ld + j;
+    const cx<T>* q = s + j * LD + b0;
+#pragma unroll 4
+    for (int i = 0; i < kElemsPerThread && line < nlines;
+         ++i, line += BSTEP, g += BSTEP * out_ld, q += BSTEP) {
+      cx<T> w = scale * *q;
+      if (omask != nullptr && omask[mrow * Lout + j] == 0) w = zero<T>();
+      *g = w;
+      mrow += BSTEP;
+      if (mrow >= mask_lines) mrow = mrow >= 2 * mask_lines ? mrow % mask_lines : mrow - mask_lines;
+    }
+  }
+}
+
+// Three components of NBC neighbouring columns (see k_fft3c).
+template <typename T, class Op, int L, int NBC, bool HALF_IN, bool HALF_OUT>
+__global__ void __launch_bounds__(3 * NBC * L / kElemsPerThread,
+                                  (768 / (3 * NBC * L / kElemsPerThread)) > 0
+                                      ? 768 / (3 * NBC * L / kElemsPerThread)
+                                      : 1)
+    k_ct_fft3c(cx<T>* data, long ncols, int Lin, long js, long cs, long ss, int Lout, Op op,
+               const cx<T>* __restrict__ tw, int twshift, int row_len, int nrows) {
+  constexpr int LD = 3 * NBC;
+  constexpr int NTH = LD * L / kElemsPerThread;
+  constexpr int JSTEP = L / 16;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* stw = s + L * LD;
+  const int tid = threadIdx.x;
+  const long tiles = ncols / NBC;
+  const long slab = blockIdx.x / tiles;
+  const int tt = (int)(blockIdx.x - slab * tiles);
+  long col0;
+  if (row_len >= NBC && nrows > 0) {
+    const int row_tiles = row_len / NBC;
+    const int r = tt / row_tiles;
+    const int ti = tt - r * row_tiles;
+    col0 = (long)mirror_perm(r, nrows) * row_len + (long)mirror_perm(ti, row_tiles) * NBC;
+  } else {
+    col0 = (long)tt * NBC;
+  }
+  cx<T>* base = data + slab * ss + col0;
+  const int b0 = tid & (NBC - 1);
+  const int t0 = tid / NBC;  // 3 j0 + c0
+  const int j0 = t0 / 3, c0 = t0 - 3 * j0;
+  {
+    const cx<T>* g = base + c0 * cs + (long)j0 * js + b0;
+    const long gstep = (long)JSTEP * js;
+    constexpr int NLOAD = HALF_IN ? kElemsPerThread / 2 : kElemsPerThread;
+#pragma unroll
+    for (int i = 0; i < NLOAD; ++i, g += gstep) {
+      const bool ok = j0 + i * JSTEP < Lin;
+      cp_async_cx(s + tid + i * NTH, ok ? g : data, ok);
+    }
+  }
+  op.prefetch(col0, NBC, L);
+  load_twiddles(stw, tw, L, twshift);
+  cp_async_wait_all();
+  __syncthreads();
+  ct_fft<L, LD, LD, false, HALF_IN, false>(s, stw);
+  {
+    // every thread keeps one column (NTH is a multiple of NBC)
+    const auto ctx = op.column(slab, col0 + b0);
+    constexpr int PSTEP = NTH / NBC;
+#pragma unroll 2
+    for (int j = tid / NBC; j < L; j += PSTEP) {
+      cx<T>* q = s + j * LD + b0;
+      cx<T> x0 = q[0], x1 = q[NBC], x2 = q[2 * NBC];
+      op.point(ctx, j, x0, x1, x2);
+      q[0] = x0;
+      q[NBC] = x1;
+      q[2 * NBC] = x2;
+    }
+  }
+  __syncthreads();
+  ct_fft<L, LD, LD, true, false, HALF_OUT>(s, stw);
+  {
+    cx<T>* g = base + c0 * cs + (long)j0 * js + b0;
+    const long gstep = (long)JSTEP * js;
+    constexpr int NSTORE = HALF_OUT ? kElemsPerThread / 2 : kElemsPerThread;
+#pragma unroll
+    for (int i = 0; i < NSTORE; ++i, g += gstep)
+      if (j0 + i * JSTEP < Lout) *g = s[tid + i * NTH];
+  }
+}
+
+// Three-component pass: compile-time kernel for complex64 when the tile
+// shape allows (L in 32..512, 8-column tiles), the run-time kernel otherwise.
+template <int L, class Op, bool HI, bool HO>
+void ct_fft3c_launch(cx<float>* data, long ncols, long nslabs, int Lin, long js, long cs, long ss,
+                     int Lout, const Op& op, const cx<float>* tw, int Lmax, int row_len, int nrows,
+                     cudaStream_t s) {
+  constexpr int NBC = 8;
+  constexpr int NTH = 3 * NBC * L / kElemsPerThread;
+  const size_t smem = ((size_t)3 * NBC * L + L) * sizeof(cx<float>);
+  auto kern = k_ct_fft3c<float, Op, L, NBC, HI, HO>;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const long grid = nslabs * (ncols / NBC);
+  note_launch();
+  kern<<<(unsigned)grid, NTH, smem, s>>>(data, ncols, Lin, js, cs, ss, Lout, op, tw, Lmax / L,
+                                         row_len, nrows);
+}
+
+template <class Op, bool HI, bool HO>
+bool ct_fft3c_dispatch(cx<float>* data, long ncols, long nslabs, int L, int Lin, long js, long cs,
+                       long ss, int Lout, const Op& op, const cx<float>* tw, int Lmax, int row_len,
+                       int nrows, cudaStream_t s) {
+  switch (L) {
+    case 32: ct_fft3c_launch<32, Op, HI, HO>(data, ncols, nslabs, Lin, js, cs, ss, Lout, op, tw, Lmax, row_len, nrows, s); return true;
+    case 64: ct_fft3c_launch<64, Op, HI, HO>(data, ncols, nslabs, Lin, js, cs, ss, Lout, op, tw, Lmax, row_len, nrows, s); return true;
+    case 128: ct_fft3c_launch<128, Op, HI, HO>(data, ncols, nslabs, Lin, js, cs, ss, Lout, op, tw, Lmax, row_len, nrows, s); return true;
+    case 256: ct_fft3c_launch<256, Op, HI, HO>(data, ncols, nslabs, Lin, js, cs, ss, Lout, op, tw, Lmax, row_len, nrows, s); return true;
+    case 512: ct_fft3c_launch<512, Op, HI, HO>(data, ncols, nslabs, Lin, js, cs, ss, Lout, op, tw, Lmax, row_len, nrows, s); return true;
+    default: return false;
+  }
+}
+
+// Dispatcher used by the operator: HI / HO are fixed per call site (the
+// matvec's z pass has both, the preconditioner's neither).
+template <bool HI, bool HO, typename T, class Op>
+void launch_fft3c_any(cx<T>* data, long ncols, long nslabs, int L, int Lin, long js, long cs,
+                      long ss, int Lout, const Op& op, const cx<T>* tw, int Lmax, int row_len,
+                      int nrows, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    const bool hi = 2 * Lin <= L, ho = 2 * Lout <= L;
+    if (hi == HI && ho == HO && ncols % 8 == 0 && ncols >= 8 &&
+        ct_fft3c_dispatch<Op, HI, HO>(data, ncols, nslabs, L, Lin, js, cs, ss, Lout, op, tw, Lmax,
+                                      row_len, nrows, s))
+      return;
+  }
+  launch_fft3c<T>(data, ncols, nslabs, L, Lin, js, cs, ss, Lout, op, tw, Lmax, row_len, nrows, s);
+}
+
+}  // namespace dda

@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 
 #include "fft_core.cuh"
 
@@ -48,14 +49,17 @@ __global__ void __launch_bounds__(256)
   if (bstep > 0) {
     if (!(half_in && 2 * j >= L)) {  // the pruned first stage never reads j >= L/2
       long line = line0 + b0;
+      long mrow = line % mask_lines;  // mask row, advanced incrementally
       const cx<T>* g = in + line * in_ld + j;
       const long gstep = (long)bstep * in_ld;
       cx<T>* q = s + j * ld + b0;
 #pragma unroll 4
       for (int i = 0; i < kElemsPerThread; ++i, line += bstep, g += gstep, q += bstep) {
         bool ok = line < nlines && j < Lin;
-        if (ok && mask != nullptr) ok = mask[(line % mask_lines) * Lin + j] != 0;
+        if (ok && mask != nullptr) ok = mask[mrow * Lin + j] != 0;
         cp_async_cx(q, ok ? g : in, ok);
+        mrow += bstep;
+        if (mrow >= mask_lines) mrow = mrow >= 2 * mask_lines ? mrow % mask_lines : mrow - mask_lines;
       }
     }
   } else {
@@ -74,16 +78,34 @@ __global__ void __launch_bounds__(256)
   cp_async_wait_all();
   __syncthreads();
   smem_fft<INV>(s, stw, L, nb_sh, ld, rp, half_in, half_out);
+  if (bstep > 0) {
+    if (j < Lout) {
+      long line = line0 + b0;
+      long mrow = line % mask_lines;
+      cx<T>* g = out + line * out_ld + j;
+      const long gstep = (long)bstep * out_ld;
+      const cx<T>* q = s + j * ld + b0;
 #pragma unroll 4
-  for (int i = 0; i < kElemsPerThread; ++i) {
-    const int e = tid + i * nth;
-    const int jj = e & (L - 1);
-    const int b = e >> rp.lg;
-    const long line = line0 + b;
-    if (line < nlines && jj < Lout) {
-      cx<T> w = scale * s[jj * ld + b];
-      if (omask != nullptr && omask[(line % mask_lines) * Lout + jj] == 0) w = zero<T>();
-      out[line * out_ld + jj] = w;
+      for (int i = 0; i < kElemsPerThread && line < nlines;
+           ++i, line += bstep, g += gstep, q += bstep) {
+        cx<T> w = scale * *q;
+        if (omask != nullptr && omask[mrow * Lout + j] == 0) w = zero<T>();
+        *g = w;
+        mrow += bstep;
+        if (mrow >= mask_lines) mrow = mrow >= 2 * mask_lines ? mrow % mask_lines : mrow - mask_lines;
+      }
+    }
+  } else {
+    for (int i = 0; i < kElemsPerThread; ++i) {
+      const int e = tid + i * nth;
+      const int jj = e & (L - 1);
+      const int b = e >> rp.lg;
+      const long line = line0 + b;
+      if (line < nlines && jj < Lout) {
+        cx<T> w = scale * s[jj * ld + b];
+        if (omask != nullptr && omask[(line % mask_lines) * Lout + jj] == 0) w = zero<T>();
+        out[line * out_ld + jj] = w;
+      }
     }
   }
 }
@@ -341,7 +363,11 @@ void launch_fft3c(cx<T>* data, long ncols, long nslabs, int L, int Lin, long js,
                   cudaStream_t s) {
   if (ncols <= 0 || nslabs <= 0) return;
   const int cap = (sizeof(T) == 8 ? 512 : 768) * kElemsPerThread;
-  int NBc = sizeof(T) == 8 ? 8 : 16;
+  static const int nbc_env = [] {
+    const char* v = getenv("DDA_FFT3C_COLS");
+    return v ? atoi(v) : 0;
+  }();
+  int NBc = nbc_env > 0 ? nbc_env : 8;  // 8 columns: two or more CTAs per SM
   NBc = (int)std::min<long>(NBc, floor_pow2_l(ncols));
   while (3 * NBc * L > cap && NBc > 1) NBc /= 2;
   while (NBc > 1 && 3 * NBc * L > 1536 && nslabs * ((ncols + NBc - 1) / NBc) < 2 * 152) NBc /= 2;

@@ -11,7 +11,7 @@
 //                 FFT, only the n box planes written back
 //   4 y inverse   buf2 -> buf1 (rows m..2m-1 dropped)
 //   5 x inverse   buf1 -> y: columns l..2l-1 dropped, diagonal term added
-#include "fft_kernels.cuh"
+#include "fft_ct.cuh"
 #include "plan.hpp"
 
 namespace dda {
@@ -95,19 +95,48 @@ __global__ void __launch_bounds__(512)
   cp_async_wait_all();
   __syncthreads();
   smem_fft<true>(s, stw, Lx, nb_sh, ld, rp, false, 2 * l <= Lx && Lx > 1);
-  for (int e = threadIdx.x; e < NB * l; e += blockDim.x) {
-    const int j = e % l;
-    const int b = e / l;
-    const long line = line0 + b;
-    if (line < nlines) {
-      const long vox = (line % nm) * l + j;
-      const long rhs = line / (3 * nm);
-      const int mt = mat[vox];
+  // Stores: element e = tid + i * nth of the NB x l outputs; when l divides
+  // nth every thread keeps one column j and steps over lines by nth / l, so
+  // the voxel row and right-hand side advance incrementally.
+  const int lsh = rp.lg - 1;  // l = Lx / 2
+  if (2 * l == Lx && (nth & (l - 1)) == 0) {
+    const int j = tid & (l - 1);
+    const int b0 = tid >> lsh;
+    const int bstep = nth >> lsh;
+    long line = line0 + b0;
+    long vrow = line % nm;  // (z, y) row of the voxel
+    long rhs = line / (3 * nm);
+    long rem = line - rhs * 3 * nm;
+    for (int b = b0; b < NB && line < nlines; b += bstep, line += bstep) {
+      const int mt = mat[vrow * l + j];
       const cx<T> a = ainv[rhs * K1 + mt];
       const cx<T> xv = x[line * l + j];
       cx<T> out = a * xv;
       if (mt != 0) out = out - coef * s[j * ld + b];
       y[line * l + j] = out;
+      vrow += bstep;
+      rem += bstep;
+      if (vrow >= nm) vrow = vrow >= 2 * nm ? vrow % nm : vrow - nm;
+      if (rem >= 3 * nm) {
+        rhs += rem / (3 * nm);
+        rem %= 3 * nm;
+      }
+    }
+  } else {
+    for (int e = tid; e < NB * l; e += nth) {
+      const int j = e % l;
+      const int b = e / l;
+      const long line = line0 + b;
+      if (line < nlines) {
+        const long vox = (line % nm) * l + j;
+        const long rhs = line / (3 * nm);
+        const int mt = mat[vox];
+        const cx<T> a = ainv[rhs * K1 + mt];
+        const cx<T> xv = x[line * l + j];
+        cx<T> out = a * xv;
+        if (mt != 0) out = out - coef * s[j * ld + b];
+        y[line * l + j] = out;
+      }
     }
   }
 }
@@ -142,8 +171,8 @@ void matvec_impl(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t
   // 3: z forward, spectrum multiply, z inverse (n live planes in and out)
   KernelMul<T> op{G_of<T>(p), (int)Lx, (int)Ly, (int)Lz, p->hx, p->hy, ilog2((int)Lx)};
   p->prof.begin(PROF_MV_Z, s);
-  launch_fft3c<T>(b2, plane, nrhs, (int)Lz, (int)n, plane, n * plane, 3 * n * plane, (int)n, op,
-                  tw, p->Lmax, (int)Lx, (int)Ly, s);
+  launch_fft3c_any<true, true>(b2, plane, nrhs, (int)Lz, (int)n, plane, n * plane, 3 * n * plane,
+                               (int)n, op, tw, p->Lmax, (int)Lx, (int)Ly, s);
   p->prof.end(s);
   // 4: y inverse, 2m -> m
   p->prof.begin(PROF_MV_YI, s);

@@ -20,7 +20,7 @@
 // solved per frequency (closed-form inverse of a complex symmetric 3x3
 // matrix), inverse FFT.  Lambda is formed on the fly from the stored Chat and
 // the right-hand side's alpha_tilde, so one build serves every incident wave.
-#include "fft_kernels.cuh"
+#include "fft_ct.cuh"
 #include "plan.hpp"
 
 namespace dda {
@@ -176,8 +176,8 @@ void precond_apply_impl(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cudaS
                   (T)(p->d.dx * p->d.dx * p->d.dx), (T)(1.0 / (double)p->nvox)};
   p->prof.end(s);
   p->prof.begin(PROF_PC_Z, s);
-  launch_fft3c<T>(t, plane, nrhs, (int)n, (int)n, plane, n * plane, 3 * n * plane, (int)n, op, tw,
-                  p->Lmax, (int)l, (int)m, s);
+  launch_fft3c_any<false, false>(t, plane, nrhs, (int)n, (int)n, plane, n * plane, 3 * n * plane,
+                                 (int)n, op, tw, p->Lmax, (int)l, (int)m, s);
   p->prof.end(s);
   p->prof.begin(PROF_PC_YI, s);
   if (m > 1)
@@ -208,8 +208,8 @@ void precond_apply_into(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cx<T>
   CircSolve<T> op{C_of<T>(p), ainv_of<T>(p), static_cast<int*>(p->w.err_flag), p->K + 1,
                   (int)l, (int)m, (int)n, p->cx_, p->cy_, ilog2((int)l),
                   (T)(p->d.dx * p->d.dx * p->d.dx), (T)(1.0 / (double)p->nvox)};
-  launch_fft3c<T>(t, plane, nrhs, (int)n, (int)n, plane, n * plane, 3 * n * plane, (int)n, op, tw,
-                  p->Lmax, (int)l, (int)m, s);
+  launch_fft3c_any<false, false>(t, plane, nrhs, (int)n, (int)n, plane, n * plane, 3 * n * plane,
+                                 (int)n, op, tw, p->Lmax, (int)l, (int)m, s);
   if (m > 1)
     launch_strided<T, true>(t, t, l, (long)nrhs * 3 * n, (int)m, (int)m, l, plane, (int)m, l, plane,
                             T(1), tw, p->Lmax, s);

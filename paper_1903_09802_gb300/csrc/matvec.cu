@@ -141,6 +141,93 @@ __global__ void __launch_bounds__(512)
   }
 }
 
+// Compile-time variant of pass 5 (complex64, Lx in 32..512): NB lines of
+// pitch NB + 1, every thread keeps one position j (NB >= 16).
+template <typename T, int LX, int NB>
+__global__ void __launch_bounds__(NB * LX / kElemsPerThread, 1024 / (NB * LX / kElemsPerThread))
+    k_ct_mv_epilogue(const cx<T>* __restrict__ buf1, const cx<T>* __restrict__ x,
+                     cx<T>* __restrict__ y, const uint8_t* __restrict__ mat,
+                     const cx<T>* __restrict__ ainv, int K1, long nlines, long nm, T coef,
+                     const cx<T>* __restrict__ tw, int twshift) {
+  static_assert(NB >= 16, "one position per thread");
+  constexpr int NTH = NB * LX / kElemsPerThread;
+  constexpr int LD = NB + 1;
+  constexpr int BSTEP = NTH / LX;
+  constexpr int l = LX / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* stw = s + LX * LD;
+  const int tid = threadIdx.x;
+  const long line0 = (long)blockIdx.x * NB;
+  {
+    const int j = tid & (LX - 1);
+    const int b0 = tid / LX;
+    long line = line0 + b0;
+    const cx<T>* g = buf1 + line * LX + j;
+    cx<T>* q = s + j * LD + b0;
+#pragma unroll 4
+    for (int i = 0; i < kElemsPerThread; ++i, line += BSTEP, g += BSTEP * LX, q += BSTEP) {
+      const bool ok = line < nlines;
+      cp_async_cx(q, ok ? g : buf1, ok);
+    }
+  }
+  load_twiddles(stw, tw, LX, twshift);
+  cp_async_wait_all();
+  __syncthreads();
+  ct_fft<LX, LD, NB, true, false, true>(s, stw);
+  // outputs: NB lines x l positions; thread keeps j = tid mod l
+  const int j = tid & (l - 1);
+  const int b0 = tid / l;
+  constexpr int OSTEP = NTH / l;
+  long line = line0 + b0;
+  long vrow = line % nm;
+  long rhs = line / (3 * nm);
+  long rem = line - rhs * 3 * nm;
+#pragma unroll 4
+  for (int b = b0; b < NB; b += OSTEP, line += OSTEP) {
+    if (line >= nlines) break;
+    const int mt = mat[vrow * l + j];
+    const cx<T> a = ainv[rhs * K1 + mt];
+    const cx<T> xv = x[line * l + j];
+    cx<T> out = a * xv;
+    if (mt != 0) out = out - coef * s[j * LD + b];
+    y[line * l + j] = out;
+    vrow += OSTEP;
+    rem += OSTEP;
+    if (vrow >= nm) vrow = vrow >= 2 * nm ? vrow % nm : vrow - nm;
+    if (rem >= 3 * nm) {
+      rhs += rem / (3 * nm);
+      rem %= 3 * nm;
+    }
+  }
+}
+
+template <int LX>
+void ct_epilogue_launch(dda_plan_s* p, const cx<float>* b1, const cx<float>* x, cx<float>* y,
+                        long lines, long nm, float coef, cudaStream_t s) {
+  constexpr int NB = (4096 / LX) > 16 ? 4096 / LX : 16;
+  const size_t smem = ((size_t)LX * (NB + 1) + LX) * sizeof(cx<float>);
+  auto kern = k_ct_mv_epilogue<float, LX, NB>;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  note_launch();
+  kern<<<(unsigned)((lines + NB - 1) / NB), NB * LX / kElemsPerThread, smem, s>>>(
+      b1, x, y, p->mat, ainv_of<float>(p), p->K + 1, lines, nm, coef, tw_of<float>(p),
+      p->Lmax / LX);
+}
+
+bool ct_epilogue(dda_plan_s* p, const cx<float>* b1, const cx<float>* x, cx<float>* y, long lines,
+                 long nm, float coef, cudaStream_t s) {
+  switch (p->Lx) {
+    case 32: ct_epilogue_launch<32>(p, b1, x, y, lines, nm, coef, s); return true;
+    case 64: ct_epilogue_launch<64>(p, b1, x, y, lines, nm, coef, s); return true;
+    case 128: ct_epilogue_launch<128>(p, b1, x, y, lines, nm, coef, s); return true;
+    case 256: ct_epilogue_launch<256>(p, b1, x, y, lines, nm, coef, s); return true;
+    case 512: ct_epilogue_launch<512>(p, b1, x, y, lines, nm, coef, s); return true;
+    default: return false;
+  }
+}
+
 inline int ilog2(int v) {
   int b = 0;
   while ((1 << b) < v) ++b;
@@ -180,6 +267,15 @@ void matvec_impl(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t
                           m * Lx, T(1), tw, p->Lmax, s);
   p->prof.end(s);
   // 5: x inverse and the diagonal
+  if constexpr (sizeof(T) == 4) {
+    if (Lx >= 32 && Lx <= 512) {
+      const float coef = (float)(p->d.dx * p->d.dx * p->d.dx / (double)p->P);
+      p->prof.begin(PROF_MV_XI, s);
+      ct_epilogue(p, b1, x, y, lines, nm, coef, s);
+      p->prof.end(s);
+      return;
+    }
+  }
   {
     const int cap = 512 * kElemsPerThread;
     int per_cta = std::min(4096, cap);

@@ -92,6 +92,9 @@ typedef struct {
                             inside FP64 iterative refinement                          */
   double inner_tol;      /* a cycle ends early once its residual estimate falls below
                             inner_tol times the cycle's starting residual (0: only tol) */
+  double reorth_eta;     /* second Gram-Schmidt pass when ||w_after|| < reorth_eta *
+                            ||w_before|| (0: never, > 1: always; 1/sqrt(2) is the classical
+                            choice of Daniel, Gragg, Kaufman & Stewart)                      */
 } dda_solve_opts_t;
 
 typedef struct {
@@ -188,7 +191,7 @@ dda_status_t dda_fft3d(dda_plan_t plan, int32_t prec, int32_t nbatch, void* d_da
  *   d_x   complex128 box fields: initial guess in, solution out.
  *   h_stats host array of nrhs records (may be NULL).
  * Right-preconditioned restarted GMRES: Arnoldi with classical Gram-Schmidt
- * and a second pass whenever the first removed more than half of ||w||^2
+ * and a second pass whenever the first left less than reorth_eta of ||w||
  * (selective reorthogonalisation); dots and norms summed in FP64 across
  * threads (complex64 vectors: FP32 products with compensated FP32 per-thread
  * sums); Givens rotations and the small least-squares solve in FP64 on the

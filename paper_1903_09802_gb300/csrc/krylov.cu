@@ -8,8 +8,8 @@
 //      refinement when the cycle itself runs in complex64),
 //   2. runs Arnoldi on A P^{-1} from v0 = r/||r||: w = A P^{-1} v_j,
 //      classical Gram-Schmidt (h = V^H w, w -= V h) with a second pass when
-//      the first removed more than half of ||w||^2 (selective
-//      reorthogonalisation), FP64
+//      the first left less than eta of ||w|| (selective reorthogonalisation,
+//      eta = 1/sqrt(2) by default), FP64
 //      Hessenberg column, complex Givens rotations and the residual estimate
 //      |g_{j+1}| on the device,
 //   3. ends when the estimate reaches max(tol ||b||, inner_tol ||r||), after
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(kNT)
              const double2* __restrict__ hcol, int m, double2* __restrict__ partial, int pst,
              const int* __restrict__ mask, const int* __restrict__ mask2, int* __restrict__ tickets,
              double* __restrict__ scal, int pass, int* __restrict__ reorth,
-             int* __restrict__ reorth_count) {
+             int* __restrict__ reorth_count, double eta2) {
   __shared__ cx<T> hs[520];
   __shared__ double2 sh[32];
   __shared__ int s_last;
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(kNT)
   if (threadIdx.x == 0) partial[((long)r * gridDim.x + blockIdx.x) * pst + pst - 1] = t;
   // Last block: ||w||^2 after this pass, and after the first pass the
   // selective-reorthogonalisation test (Daniel, Gragg, Kaufman & Stewart):
-  // a second pass runs when the first removed more than half of ||w||^2.
+  // a second pass runs when ||w_after||^2 < eta^2 ||w_before||^2.
   __threadfence();
   if (threadIdx.x == 0) s_last = atomicAdd(&tickets[r], 1) == (int)gridDim.x - 1;
   __syncthreads();
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(kNT)
   if (threadIdx.x == 0) {
     scal[(long)r * 16 + 8] = n2;
     if (pass == 0) {
-      const int need = !(n2 >= 0.5 * scal[(long)r * 16 + 7]);
+      const int need = !(n2 >= eta2 * scal[(long)r * 16 + 7]);
       reorth[r] = need;
       reorth_count[r] += need;
     }
@@ -575,6 +575,7 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
   const bool prec = o.precond == 3;
   const double brk = sizeof(T) == 8 ? 1e-13 : 1e-6;
   const bool vec = (nu % 2) == 0;  // 16-byte pairs stay aligned
+  const double eta2 = o.reorth_eta * o.reorth_eta;
 
   if (!p->pinned) {
     if (cudaHostAlloc(&p->pinned, 64, cudaHostAllocDefault) != cudaSuccess) {
@@ -659,12 +660,12 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
         if (vec)
           k_update<T, true><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.hcol, m, st.partial,
                                                   pst, st.active, mask2, st.tickets + nrhs,
-                                                  st.scal, pass, st.reorth, st.reorth_count);
+                                                  st.scal, pass, st.reorth, st.reorth_count, eta2);
         else
           k_update<T, false><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.hcol, m,
                                                    st.partial, pst, st.active, mask2,
                                                    st.tickets + nrhs, st.scal, pass, st.reorth,
-                                                   st.reorth_count);
+                                                   st.reorth_count, eta2);
         p->prof.end(s);
       }
       note_launch();
@@ -738,7 +739,7 @@ extern "C" dda_status_t dda_solve(dda_plan_t p, int32_t nrhs, const void* d_b, v
     return fail(DDA_ERR_INVALID_ARG, "dda_solve: nrhs must be 1..(incidences set)");
   const dda_solve_opts_t& o = *opts;
   if (!(o.tol > 0) || o.max_iters < 1 || o.restart < 1 || o.restart > p->d.krylov_m ||
-      !(o.inner_tol >= 0) || (o.precond != 0 && o.precond != 3))
+      !(o.inner_tol >= 0) || !(o.reorth_eta >= 0) || (o.precond != 0 && o.precond != 3))
     return fail(DDA_ERR_INVALID_ARG, "dda_solve: invalid options");
   if (o.precond == 3 && !p->precond_built)
     return fail(DDA_ERR_NO_PRECOND, "dda_solve: call dda_precond_build first");

@@ -163,23 +163,6 @@ class Runner:
         return out
 
 
-def algorithmic_bytes(name, case, nrhs=2):
-    """Bytes one launch of a kernel class must move (complex64 fields)."""
-    l, m, n = case.dims
-    nvox = l * m * n
-    u = 8 * nvox
-    spec = 8 * 6 * (l + 1) * (m + 1) * (n + 1)
-    circ = 8 * 6 * (l // 2 + 1) * (m // 2 + 1) * (n // 2 + 1)
-    per_rhs = {
-        "mv_x_fwd": 9 * u, "mv_y_fwd": 18 * u, "mv_z_mul": 24 * u, "mv_y_inv": 18 * u,
-        "mv_x_inv": 12 * u, "pc_x_fwd": 6 * u, "pc_y_fwd": 6 * u, "pc_z_solve": 6 * u,
-        "pc_y_inv": 6 * u, "pc_x_inv": 6 * u,
-    }[name]
-    shared = {"mv_x_fwd": nvox, "mv_x_inv": nvox, "pc_x_fwd": nvox, "pc_x_inv": nvox,
-              "mv_z_mul": spec, "pc_z_solve": circ}.get(name, 0)
-    return per_rhs * nrhs + shared
-
-
 def traffic_from_profiles(kernel):
     """dram bytes per launch recorded by the committed ncu summary, if still current."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_64cube.md")
@@ -208,27 +191,30 @@ def source_hash():
 
 
 def roofline(runner, peak, peak_kind):
-    """Dominant kernel over one profiled (untimed) step, from CUDA events."""
+    """Dominant kernel class over one profiled (untimed) step: CUDA-event
+    durations and the algorithmic bytes the library states for each launch."""
     runner.profile, runner.prof = True, []
     runner.step()
     runner.profile = False
     tot = {}
     for case, prof in runner.prof:
-        for name, (ms, cnt) in prof.items():
+        for name, (ms, cnt, nbytes) in prof.items():
             t = tot.setdefault(name, [0.0, 0, 0.0])
             t[0] += ms
             t[1] += cnt
-            if cnt and not name.startswith("gs_"):
-                t[2] += algorithmic_bytes(name, case) * cnt
-    dom = max((k for k in tot if not k.startswith("gs_")), key=lambda k: tot[k][0])
+            t[2] += nbytes
+    dom = max(tot, key=lambda k: tot[k][0])
     ms, cnt, nbytes = tot[dom]
     achieved = nbytes / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
-    share = {k: round(v[0] / sum(x[0] for x in tot.values()), 4) for k, v in tot.items() if v[0] > 0}
+    total_ms = sum(x[0] for x in tot.values())
+    share = {k: round(v[0] / total_ms, 4) for k, v in tot.items() if v[0] > 0}
+    per_class = {k: round(v[2] / (v[0] * 1e-3) / 1e9, 1) for k, v in tot.items() if v[0] > 0}
     return {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
             "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s", "frac": round(achieved / peak, 4),
             "avg_launch_us": round(ms / cnt * 1e3, 2) if cnt else None,
             "algorithmic_bytes_per_launch": round(nbytes / cnt) if cnt else None,
-            "traffic": traffic_from_profiles(dom), "share_of_profiled_kernel_time": share}
+            "traffic": traffic_from_profiles(dom), "share_of_profiled_kernel_time": share,
+            "achieved_gbs_by_class": per_class}
 
 
 def oracle_iterations():

@@ -224,11 +224,17 @@ dda_status_t dda_cross_sections(dda_plan_t plan, int32_t nrhs, const void* d_c, 
  * launch count: index 0..4 matvec passes (x forward, y forward, z with the
  * spectrum multiply, y inverse, x inverse with the diagonal), 5..9 the
  * preconditioner's passes in the same order, 10 Gram-Schmidt dots,
- * 11 Gram-Schmidt update; n entries are written (n <= 12); reset != 0 zeroes
- * the sums.  Events add a few microseconds per launch. */
+ * 11 Gram-Schmidt update (first pass only); n entries are written
+ * (n <= 12); reset != 0 zeroes the sums.  h_bytes (may be NULL) receives the
+ * summed algorithmic bytes of the timed launches: per right-hand side and
+ * with u = one box field (3 l m n values), matvec passes 9u (+mask), 18u,
+ * 24u (+ the kernel spectrum once), 18u, 12u (+mask); preconditioner
+ * passes 6u each (+mask, + the circulant spectrum once for the middle one);
+ * Gram-Schmidt dots (j+2)u, update (j+3)u at Arnoldi step j.  Events add a
+ * few microseconds per launch. */
 dda_status_t dda_profile_enable(dda_plan_t plan, int32_t on);
-dda_status_t dda_profile_read(dda_plan_t plan, double* h_ms, int64_t* h_count, int32_t n,
-                              int32_t reset);
+dda_status_t dda_profile_read(dda_plan_t plan, double* h_ms, int64_t* h_count, double* h_bytes,
+                              int32_t n, int32_t reset);
 
 /* Release the host-side plan object (device memory stays the caller's). */
 void dda_plan_destroy(dda_plan_t plan);

@@ -245,24 +245,26 @@ void matvec_impl(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t
   const long nm = n * m;
   const long lines = (long)nrhs * 3 * nm;
   const long plane = Ly * Lx;
+  const double u = (double)nrhs * 3 * p->nvox * sizeof(cx<T>);  // box fields of the batch
+  const double spec = 6.0 * p->hx * p->hy * p->hz * sizeof(cx<T>);
   // 1: x forward of the masked field, l -> 2l
-  p->prof.begin(PROF_MV_XF, s);
+  p->prof.begin(PROF_MV_XF, s, 3 * u + p->nvox);
   launch_contig<T, false>(x, b1, p->mat, nullptr, nm, lines, (int)Lx, (int)l, l, (int)Lx, Lx, T(1), tw,
                           p->Lmax, s);
   p->prof.end(s);
   // 2: y forward, m -> 2m
-  p->prof.begin(PROF_MV_YF, s);
+  p->prof.begin(PROF_MV_YF, s, 6 * u);
   launch_strided<T, false>(b1, b2, Lx, (long)nrhs * 3 * n, (int)Ly, (int)m, Lx, m * Lx, (int)Ly,
                            Lx, plane, T(1), tw, p->Lmax, s);
   p->prof.end(s);
   // 3: z forward, spectrum multiply, z inverse (n live planes in and out)
   KernelMul<T> op{G_of<T>(p), (int)Lx, (int)Ly, (int)Lz, p->hx, p->hy, ilog2((int)Lx)};
-  p->prof.begin(PROF_MV_Z, s);
+  p->prof.begin(PROF_MV_Z, s, 8 * u + spec);
   launch_fft3c_any<true, true>(b2, plane, nrhs, (int)Lz, (int)n, plane, n * plane, 3 * n * plane,
                                (int)n, op, tw, p->Lmax, (int)Lx, (int)Ly, s);
   p->prof.end(s);
   // 4: y inverse, 2m -> m
-  p->prof.begin(PROF_MV_YI, s);
+  p->prof.begin(PROF_MV_YI, s, 6 * u);
   launch_strided<T, true>(b2, b1, Lx, (long)nrhs * 3 * n, (int)Ly, (int)Ly, Lx, plane, (int)m, Lx,
                           m * Lx, T(1), tw, p->Lmax, s);
   p->prof.end(s);
@@ -270,7 +272,7 @@ void matvec_impl(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t
   if constexpr (sizeof(T) == 4) {
     if (Lx >= 32 && Lx <= 512) {
       const float coef = (float)(p->d.dx * p->d.dx * p->d.dx / (double)p->P);
-      p->prof.begin(PROF_MV_XI, s);
+      p->prof.begin(PROF_MV_XI, s, 4 * u + p->nvox);
       ct_epilogue(p, b1, x, y, lines, nm, coef, s);
       p->prof.end(s);
       return;
@@ -289,7 +291,7 @@ void matvec_impl(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const T coef = (T)(p->d.dx * p->d.dx * p->d.dx / (double)p->P);
-    p->prof.begin(PROF_MV_XI, s);
+    p->prof.begin(PROF_MV_XI, s, 4 * u + p->nvox);
     note_launch();
     kern<<<(unsigned)((lines + NB - 1) / NB), nth, smem, s>>>(
         b1, x, y, p->mat, ainv_of<T>(p), p->K + 1, lines, nm, (int)l, (int)Lx, coef, tw,

@@ -17,9 +17,9 @@ cudaEvent_t Profiler::get() {
   return e;
 }
 
-void Profiler::begin(int id, cudaStream_t s) {
+void Profiler::begin(int id, cudaStream_t s, double nbytes) {
   if (!on) return;
-  Rec r{id, get(), get()};
+  Rec r{id, nbytes, get(), get()};
   cudaEventRecord(r.a, s);
   recs.push_back(r);
 }
@@ -37,6 +37,7 @@ void Profiler::collect() {
     if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
       ms[r.id] += t;
       count[r.id] += 1;
+      bytes[r.id] += r.bytes;
     }
     pool.push_back(r.a);
     pool.push_back(r.b);
@@ -63,17 +64,19 @@ extern "C" dda_status_t dda_profile_enable(dda_plan_t p, int32_t on) {
   return DDA_OK;
 }
 
-extern "C" dda_status_t dda_profile_read(dda_plan_t p, double* h_ms, int64_t* h_count, int32_t n,
-                                         int32_t reset) {
+extern "C" dda_status_t dda_profile_read(dda_plan_t p, double* h_ms, int64_t* h_count,
+                                         double* h_bytes, int32_t n, int32_t reset) {
   if (!p || !h_ms || !h_count) return fail(DDA_ERR_INVALID_ARG, "dda_profile_read: NULL argument");
   p->prof.collect();
   for (int i = 0; i < n && i < PROF_COUNT; ++i) {
     h_ms[i] = p->prof.ms[i];
     h_count[i] = p->prof.count[i];
+    if (h_bytes) h_bytes[i] = p->prof.bytes[i];
   }
   if (reset) {
     std::memset(p->prof.ms, 0, sizeof(p->prof.ms));
     std::memset(p->prof.count, 0, sizeof(p->prof.count));
+    std::memset(p->prof.bytes, 0, sizeof(p->prof.bytes));
   }
   return check_cuda("dda_profile_read");
 }

@@ -30,14 +30,17 @@ struct Profiler {
   bool on = false;
   struct Rec {
     int id;
+    double bytes;
     cudaEvent_t a, b;
   };
   std::vector<Rec> recs;   // events recorded since the last read
   std::vector<cudaEvent_t> pool;
   double ms[PROF_COUNT] = {};
   long count[PROF_COUNT] = {};
+  double bytes[PROF_COUNT] = {};
   cudaEvent_t get();
-  void begin(int id, cudaStream_t s);
+  // bytes: algorithmic bytes the bracketed launch moves (0 if not stated)
+  void begin(int id, cudaStream_t s, double nbytes = 0.0);
   void end(cudaStream_t s);
   void collect();           // synchronises the recorded events and accumulates
   ~Profiler();

@@ -100,7 +100,7 @@ _lib.dda_profile_enable.restype = ctypes.c_int
 _lib.dda_profile_enable.argtypes = [_vp, ctypes.c_int32]
 _lib.dda_profile_read.restype = ctypes.c_int
 _lib.dda_profile_read.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
-                                  ctypes.c_int32, ctypes.c_int32]
+                                  ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_int32]
 _lib.dda_plan_destroy.restype = None
 _lib.dda_plan_destroy.argtypes = [_vp]
 _lib.dda_last_error.restype = ctypes.c_char_p
@@ -266,11 +266,13 @@ class Plan:
         _check(_lib.dda_profile_enable(self._h, int(on)))
 
     def profile_read(self, reset: bool = True) -> dict:
+        """{kernel class: (milliseconds, launches, algorithmic bytes)} since the last read."""
         n = len(PROFILE_NAMES)
         ms = (ctypes.c_double * n)()
         cnt = (ctypes.c_int64 * n)()
-        _check(_lib.dda_profile_read(self._h, ms, cnt, n, int(reset)))
-        return {name: (ms[i], cnt[i]) for i, name in enumerate(PROFILE_NAMES)}
+        byt = (ctypes.c_double * n)()
+        _check(_lib.dda_profile_read(self._h, ms, cnt, byt, n, int(reset)))
+        return {name: (ms[i], cnt[i], byt[i]) for i, name in enumerate(PROFILE_NAMES)}
 
     def cross_sections(self, c: torch.Tensor) -> np.ndarray:
         c = c.contiguous()

@@ -188,3 +188,32 @@ def alpha_inv_box(mat: np.ndarray, alpha_per_material) -> np.ndarray:
     table = np.zeros(len(alpha_per_material) + 1, dtype=np.complex128)
     table[1:] = 1.0 / np.asarray(alpha_per_material, dtype=np.complex128)
     return table[mat]
+
+
+def matvec_rows(c_box: np.ndarray, mat: np.ndarray, alpha_inv_vox: np.ndarray,
+                alpha_tilde_inv: complex, k: float, dx: float, rows) -> np.ndarray:
+    """Selected rows of the box-form matvec by direct summation (no FFT).
+
+    rows: iterable of flat voxel indices into the (n, m, l) box.  Returns
+    (len(rows), 3): (A c) at those voxels, summing g(r_i - r_j) c_j over every
+    scatterer voxel j != i (eq. 12) and adding the diagonal (eq. 11); air rows
+    are alpha_tilde^{-1} c.
+    """
+    idx, r = ice_positions(mat, dx)
+    cj = c_box.reshape(3, -1)[:, idx].T                      # (n_ice, 3)
+    n, m, l = mat.shape
+    centres = voxel_centres(l, m, n, dx).reshape(-1, 3)
+    out = np.zeros((len(rows), 3), dtype=np.complex128)
+    flat_mat = mat.reshape(-1)
+    ci = c_box.reshape(3, -1)
+    for t, i in enumerate(rows):
+        if flat_mat[i] == 0:
+            out[t] = alpha_tilde_inv * ci[:, i]
+            continue
+        R = centres[i][None, :] - r
+        self_ = np.all(R == 0.0, axis=1)
+        R[self_] = 1.0
+        g = green_tensor(R, k)
+        g[self_] = 0.0
+        out[t] = alpha_inv_vox.reshape(-1)[i] * ci[:, i] - dx ** 3 * np.einsum("jab,jb->a", g, cj)
+    return out

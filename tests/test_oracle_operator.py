@@ -96,3 +96,17 @@ def test_air_padding_leaves_solution_unchanged():
     # and the direct solve agrees with GMRES
     xd = p0.solve_direct()
     assert np.linalg.norm(operator.box_to_ice(xd, mat) - v0) / np.linalg.norm(v0) < 1e-10
+
+
+def test_matvec_rows_equal_dense_rows():
+    rng = np.random.default_rng(21)
+    l, m, n = 6, 5, 4
+    mat = _random_mask((n, m, l), rng)
+    k, dx = 1.4, 0.3
+    ainv = operator.alpha_inv_box(mat, [physics.alpha_ldr(1.9 + 0.1j, k, dx, 0.3)])
+    c = random_field((3, n, m, l), rng)
+    full = operator.fft_matvec(c, mat, ainv, 4.0 - 1.0j, k, dx)
+    rows = list(range(0, l * m * n, 7))
+    got = operator.matvec_rows(c, mat, ainv, 4.0 - 1.0j, k, dx, rows)
+    want = full.reshape(3, -1)[:, rows].T
+    assert np.allclose(got, want, rtol=0, atol=1e-12 * np.abs(full).max())

@@ -92,7 +92,9 @@ bool make_layout(const dda_plan_desc_t& d, void* ws, Layout& L, std::string& why
   if (h128) L.R128 = c.take(16 * R * nu);
   if (d.krylov_m > 0) {
     const long mk = d.krylov_m;
-    L.nblk = (int)std::min<long>(304, std::max<long>(1, (nu + 4095) / 4096));
+    // Gram-Schmidt reduction blocks per right-hand side: at most one wave of
+    // 3 blocks x 152 SMs, chunks of at least 512 values
+    L.nblk = (int)std::min<long>(456, std::max<long>(1, (nu + 511) / 512));
     L.V = c.take(esz * (mk + 1) * R * nu);
     L.Wv = c.take(esz * R * nu);
     L.Zv = c.take(esz * R * nu);

@@ -563,7 +563,8 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
                         const dda_solve_opts_t& o, dda_rhs_stats_t* stats, cudaStream_t s) {
   const long nu = 3 * p->nvox;
   const int m = o.restart;
-  const int nblk = p->w.nblk;
+  // one wave of 3 blocks per SM over the whole batch
+  const int nblk = std::max(1, std::min(p->w.nblk, (456 + nrhs - 1) / nrhs));
   const int pst = m + 2;
   SolverState& st = p->w.st;
   cx<T>* V = static_cast<cx<T>*>(p->w.V);

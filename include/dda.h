@@ -236,6 +236,25 @@ dda_status_t dda_profile_enable(dda_plan_t plan, int32_t on);
 dda_status_t dda_profile_read(dda_plan_t plan, double* h_ms, int64_t* h_count, double* h_bytes,
                               int32_t n, int32_t reset);
 
+/* Right-hand side of the adjoint problem: d_b[rhs] = conj(E_inc) on scatterer
+ * voxels, 0 on air (complex128).  The DDA matrix is complex symmetric
+ * (A = A^T, Section 2.2), so the adjoint of the extinction functional is the
+ * solve A lambda = conj(E_inc) with the same plan, preconditioner and
+ * solver (dda_solve with d_b = this field). */
+dda_status_t dda_adjoint_rhs(dda_plan_t plan, int32_t nrhs, void* d_b, void* stream);
+
+/* Gradient of C_ext with respect to every voxel's permittivity, from the
+ * solution c (A c = E_inc) and the adjoint solution lambda (A lambda =
+ * conj(E_inc)), both complex128 box fields.  Perturbing eps_j changes only
+ * alpha_j^{-1} (Section 2.1), so with g_j = (lambda_j . c_j) d(alpha_j^{-1})/
+ * d(eps_j) (unconjugated over the 3 components) and
+ * d(alpha^{-1})/d(eps) = -4 pi/(eps-1)^2 + (b2 + b3 S)(k dx)^2:
+ *   d_grad[rhs][0][z][y][x] = dC_ext/dRe(eps) = -4 pi k dx^3 Im(g),
+ *   d_grad[rhs][1][z][y][x] = dC_ext/dIm(eps) = -4 pi k dx^3 Re(g),
+ * zero on air (device doubles, 2 * l*m*n per right-hand side). */
+dda_status_t dda_ext_gradient(dda_plan_t plan, int32_t nrhs, const void* d_c,
+                              const void* d_lambda, double* d_grad, void* stream);
+
 /* Release the host-side plan object (device memory stays the caller's). */
 void dda_plan_destroy(dda_plan_t plan);
 

@@ -82,6 +82,7 @@ bool make_layout(const dda_plan_desc_t& d, void* ws, Layout& L, std::string& why
   L.ainv128 = c.take(R * K1 * 16);
   L.ainv64 = c.take(R * K1 * 8);
   L.incd = static_cast<double*>(c.take(R * 6 * sizeof(double)));
+  L.dainv128 = c.take(R * K1 * 16);
   L.buf1 = c.take(esz * R * 3 * n * m * Lx);
   size_t b2 = esz * R * 3 * n * Ly * Lx;
   b2 = std::max(b2, (size_t)P * 16);     // Green-function spectrum build (complex128)
@@ -193,7 +194,7 @@ __global__ void k_compress(const double2* full, long Lx, long Ly, long Lz, long 
 
 // E_inc = pol exp(i k dir . r) on scatterer voxels, r from the box centre.
 __global__ void k_incident(double2* b, const uint8_t* mat, const double* inc, int nrhs, long l,
-                           long m, long n, double dx, double k) {
+                           long m, long n, double dx, double k, double sgn) {
   const long nvox = l * m * n;
   const long tot = nvox * nrhs;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < tot;
@@ -207,7 +208,7 @@ __global__ void k_incident(double2* b, const uint8_t* mat, const double* inc, in
                    pz = dx * (z - 0.5 * (n - 1));
       double sn, cs;
       sincos(k * (d[0] * px + d[1] * py + d[2] * pz), &sn, &cs);
-      for (int c = 0; c < 3; ++c) out[c] = make_double2(d[3 + c] * cs, d[3 + c] * sn);
+      for (int c = 0; c < 3; ++c) out[c] = make_double2(d[3 + c] * cs, sgn * d[3 + c] * sn);
     }
     for (int c = 0; c < 3; ++c) b[(r * 3 + c) * nvox + v] = out[c];
   }
@@ -347,6 +348,7 @@ extern "C" dda_status_t dda_set_incidence(dda_plan_t p, int32_t nrhs, const dda_
   std::vector<double> h(nrhs * 6);
   p->ainv_host.assign((size_t)nrhs * K1 * 2, 0.0);
   p->ainv_host32.assign((size_t)nrhs * K1 * 2, 0.0f);
+  p->dainv_host.assign((size_t)nrhs * K1 * 2, 0.0);
   // most frequent non-air material, ties to the lowest index
   int tilde = 1;
   for (int mt = 2; mt <= p->K; ++mt)
@@ -377,6 +379,11 @@ extern "C" dda_status_t dda_set_incidence(dda_plan_t p, int32_t nrhs, const dda_
           std::complex<double>(0.0, 2.0 / 3.0) * (kd * kd * kd);
       const std::complex<double> alpha = acm / (1.0 + acm * corr);
       ainv[mt] = 1.0 / alpha;
+      // d(1/alpha)/d(eps): 1/alpha = (4 pi/3)(eps+2)/(eps-1) + corr(eps)
+      const std::complex<double> dinv =
+          -4.0 * kPi / ((eps - 1.0) * (eps - 1.0)) + (0.1648469 + (-1.7700004) * S) * (kd * kd);
+      p->dainv_host[(r * K1 + mt) * 2] = dinv.real();
+      p->dainv_host[(r * K1 + mt) * 2 + 1] = dinv.imag();
     }
     ainv[0] = ainv[tilde];  // air rows and the preconditioner use alpha_tilde
     for (int mt = 0; mt < K1; ++mt) {
@@ -395,6 +402,8 @@ extern "C" dda_status_t dda_set_incidence(dda_plan_t p, int32_t nrhs, const dda_
                   cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(p->w.ainv64, p->ainv_host32.data(), p->ainv_host32.size() * sizeof(float),
                   cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(p->w.dainv128, p->dainv_host.data(), p->dainv_host.size() * sizeof(double),
+                  cudaMemcpyHostToDevice, s);
   p->inc.assign(inc, inc + nrhs);
   p->nrhs_inc = nrhs;
   return check_cuda("dda_set_incidence");
@@ -408,8 +417,20 @@ extern "C" dda_status_t dda_incident_field(dda_plan_t p, int32_t nrhs, void* d_b
   note_launch();
   k_incident<<<grid_for(p->nvox * nrhs, 256), 256, 0, s>>>(static_cast<double2*>(d_b), p->mat,
                                                           p->w.incd, nrhs, p->l, p->m, p->n,
-                                                          p->d.dx, p->d.k);
+                                                          p->d.dx, p->d.k, 1.0);
   return check_cuda("dda_incident_field");
+}
+
+extern "C" dda_status_t dda_adjoint_rhs(dda_plan_t p, int32_t nrhs, void* d_b, void* stream) {
+  if (!p || !d_b) return fail(DDA_ERR_INVALID_ARG, "dda_adjoint_rhs: NULL argument");
+  if (nrhs < 1 || nrhs > p->nrhs_inc)
+    return fail(DDA_ERR_INVALID_ARG, "dda_adjoint_rhs: nrhs above the incidence count set");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  note_launch();
+  k_incident<<<grid_for(p->nvox * nrhs, 256), 256, 0, s>>>(static_cast<double2*>(d_b), p->mat,
+                                                          p->w.incd, nrhs, p->l, p->m, p->n,
+                                                          p->d.dx, p->d.k, -1.0);
+  return check_cuda("dda_adjoint_rhs");
 }
 
 extern "C" dda_status_t dda_fft3d(dda_plan_t p, int32_t prec, int32_t nbatch, void* d_data,

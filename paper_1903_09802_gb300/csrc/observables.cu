@@ -10,6 +10,7 @@
 //   Im(p^H G p) = dx^3 [ sum Im(alpha^{-1}) |c|^2 - Im sum conj(c) . y ].
 // Because G is complex symmetric, Im(p^H G p) = p^H Im(G) p, the quadratic
 // form of the scattered power.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -76,11 +77,59 @@ __global__ void __launch_bounds__(kNT)
   }
 }
 
+// grad[rhs][0][v] = dC_ext/dRe(eps_v), grad[rhs][1][v] = dC_ext/dIm(eps_v):
+// g = (lambda_v . c_v) d(alpha^{-1})/d(eps) (unconjugated over components),
+// dRe = pref Im(g), dIm = pref Re(g), pref = -4 pi k dx^3; zero on air.
+__global__ void k_ext_gradient(const double2* __restrict__ c, const double2* __restrict__ lam,
+                               const uint8_t* __restrict__ mat, const double2* __restrict__ dainv,
+                               int K1, long nvox, int nrhs, double pref, double* __restrict__ grad) {
+  const long tot = nvox * nrhs;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < tot;
+       i += (long)gridDim.x * blockDim.x) {
+    const long v = i % nvox, r = i / nvox;
+    const int mt = mat[v];
+    double gre = 0.0, gim = 0.0;
+    if (mt != 0) {
+      double sx = 0.0, sy = 0.0;
+      for (int q = 0; q < 3; ++q) {
+        const double2 a = lam[(r * 3 + q) * nvox + v], b = c[(r * 3 + q) * nvox + v];
+        sx += a.x * b.x - a.y * b.y;
+        sy += a.x * b.y + a.y * b.x;
+      }
+      const double2 d = dainv[r * K1 + mt];
+      const double gx = sx * d.x - sy * d.y, gy = sx * d.y + sy * d.x;
+      gre = pref * gy;
+      gim = pref * gx;
+    }
+    grad[(r * 2 + 0) * nvox + v] = gre;
+    grad[(r * 2 + 1) * nvox + v] = gim;
+  }
+}
+
 }  // namespace
 
 }  // namespace dda
 
 using namespace dda;
+
+extern "C" dda_status_t dda_ext_gradient(dda_plan_t p, int32_t nrhs, const void* d_c,
+                                         const void* d_lambda, double* d_grad, void* stream) {
+  if (!p || !d_c || !d_lambda || !d_grad)
+    return fail(DDA_ERR_INVALID_ARG, "dda_ext_gradient: NULL argument");
+  if (nrhs < 1 || nrhs > p->nrhs_inc)
+    return fail(DDA_ERR_INVALID_ARG, "dda_ext_gradient: nrhs must be 1..(incidences set)");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const double pi = 3.14159265358979323846;
+  const double pref = -4.0 * pi * p->d.k * p->d.dx * p->d.dx * p->d.dx;
+  const long tot = p->nvox * nrhs;
+  const unsigned grid = (unsigned)std::min<long>(std::max<long>((tot + 255) / 256, 1), 152L * 32);
+  note_launch();
+  k_ext_gradient<<<grid, 256, 0, s>>>(static_cast<const double2*>(d_c),
+                                      static_cast<const double2*>(d_lambda), p->mat,
+                                      static_cast<const double2*>(p->w.dainv128), p->K + 1,
+                                      p->nvox, nrhs, pref, d_grad);
+  return check_cuda("dda_ext_gradient");
+}
 
 extern "C" dda_status_t dda_cross_sections(dda_plan_t p, int32_t nrhs, const void* d_c,
                                            double* h_out, void* stream) {

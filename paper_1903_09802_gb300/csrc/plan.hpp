@@ -74,6 +74,7 @@ struct Layout {
   void* ainv128 = nullptr;
   void* ainv64 = nullptr;
   double* incd = nullptr;  // [rhs][6]: direction, polarisation
+  void* dainv128 = nullptr;  // d(alpha^{-1})/d(eps) per (rhs, material), entry 0 unused
   int nblk = 1;            // reduction blocks per right-hand side
   // FFT scratch
   void* buf1 = nullptr;
@@ -111,6 +112,7 @@ struct dda_plan_s {
   std::vector<dda_incidence_t> inc;      // incidence per RHS
   std::vector<double> ainv_host;         // [rhs][K+1][2]
   std::vector<float> ainv_host32;
+  std::vector<double> dainv_host;        // [rhs][K+1][2]
   int* pinned = nullptr;                 // host-pinned words polled by the solver
   dda::Profiler prof;                    // optional kernel timing
 };

@@ -34,7 +34,7 @@ STATUS = {
 EXPORTS = ("dda_workspace_size", "dda_plan_create", "dda_set_incidence", "dda_incident_field",
            "dda_matvec", "dda_precond_build", "dda_precond_apply", "dda_precond_apply_noalloc",
            "dda_fft3d", "dda_solve",
-           "dda_cross_sections", "dda_profile_enable", "dda_profile_read", "dda_plan_destroy",
+           "dda_cross_sections", "dda_adjoint_rhs", "dda_ext_gradient", "dda_profile_enable", "dda_profile_read", "dda_plan_destroy",
            "dda_last_error", "dda_launch_count")
 
 PROFILE_NAMES = ("mv_x_fwd", "mv_y_fwd", "mv_z_mul", "mv_y_inv", "mv_x_inv", "pc_x_fwd", "pc_y_fwd",
@@ -96,6 +96,10 @@ _lib.dda_solve.argtypes = [_vp, ctypes.c_int32, _vp, _vp, ctypes.POINTER(SolveOp
                            ctypes.POINTER(RhsStats), _vp]
 _lib.dda_cross_sections.restype = ctypes.c_int
 _lib.dda_cross_sections.argtypes = [_vp, ctypes.c_int32, _vp, ctypes.POINTER(ctypes.c_double), _vp]
+_lib.dda_adjoint_rhs.restype = ctypes.c_int
+_lib.dda_adjoint_rhs.argtypes = [_vp, ctypes.c_int32, _vp, _vp]
+_lib.dda_ext_gradient.restype = ctypes.c_int
+_lib.dda_ext_gradient.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp]
 _lib.dda_profile_enable.restype = ctypes.c_int
 _lib.dda_profile_enable.argtypes = [_vp, ctypes.c_int32]
 _lib.dda_profile_read.restype = ctypes.c_int
@@ -261,6 +265,29 @@ class Plan:
         return SolveResult(x, [s.iters for s in stats], [s.cycles for s in stats],
                            [bool(s.converged) for s in stats], [s.rel_resid for s in stats], st,
                            [s.reorth for s in stats])
+
+    def adjoint_rhs(self, nrhs: int | None = None) -> torch.Tensor:
+        nrhs = nrhs or self.nrhs
+        b = torch.empty(self.field_shape(nrhs), dtype=torch.complex128, device=self.mat.device)
+        _check(_lib.dda_adjoint_rhs(self._h, nrhs, _ptr(b), _stream()))
+        return b
+
+    def ext_gradient_from(self, c: torch.Tensor, lam: torch.Tensor) -> torch.Tensor:
+        """(nrhs, 2, n, m, l) float64: dC_ext/dRe(eps), dC_ext/dIm(eps) per voxel."""
+        c, lam = c.contiguous(), lam.contiguous()
+        nrhs = c.shape[0]
+        l, m, n = self.shape
+        g = torch.empty((nrhs, 2, n, m, l), dtype=torch.float64, device=self.mat.device)
+        _check(_lib.dda_ext_gradient(self._h, nrhs, _ptr(c), _ptr(lam), _ptr(g), _stream()))
+        return g
+
+    def ext_gradient(self, c: torch.Tensor | None = None, **solve_kw):
+        """Solve (if c is None), solve the adjoint A lambda = conj(E_inc) with the
+        same operator, and return (c, lambda, gradient)."""
+        if c is None:
+            c = self.solve(**solve_kw).x
+        lam = self.solve(b=self.adjoint_rhs(c.shape[0]), **solve_kw).x
+        return c, lam, self.ext_gradient_from(c, lam)
 
     def profile(self, on: bool = True):
         _check(_lib.dda_profile_enable(self._h, int(on)))

@@ -43,7 +43,7 @@ def test_adjoint_rhs_and_gradient_arithmetic():
 @pytest.mark.gpu
 def test_gpu_gradient_matches_finite_differences():
     dda = dda_module()
-    l = m = n = 6
+    l = m = n = 8  # prism of ~140 voxels in an air-padded 8^3 box
     dx, k = 0.25, 2.2
     mat = hex_prism_mask(l, m, n, dx, 0.75, 1.5)
     d, e = _dirs()

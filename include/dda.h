@@ -95,6 +95,9 @@ typedef struct {
   double reorth_eta;     /* second Gram-Schmidt pass when ||w_after|| < reorth_eta *
                             ||w_before|| (0: never, > 1: always; 1/sqrt(2) is the classical
                             choice of Daniel, Gragg, Kaufman & Stewart)                      */
+  int32_t method;        /* 0: GMRES(restart); 1: BiCG-Stab (van der Vorst), the paper's
+                            second solver (Section 4), restart = iterations per
+                            refinement cycle; the plan needs krylov_m >= 7             */
 } dda_solve_opts_t;
 
 typedef struct {

@@ -117,3 +117,56 @@ def gmres(matvec, b: np.ndarray, x0: np.ndarray | None = None, tol: float = 1e-6
         converged = np.linalg.norm(r) / bnorm <= tol
     return x.reshape(shape), dict(iters=iters, restarts=restarts, history=history,
                                   converged=bool(converged))
+
+
+def bicgstab(matvec, b: np.ndarray, x0: np.ndarray | None = None, tol: float = 1e-6,
+             maxiter: int = 4000, precond=None):
+    """Right-preconditioned BiCG-Stab (van der Vorst), the paper's second solver (Section 4).
+
+    Solves A M u = b, x = M u, with the shadow residual r_hat = r0 and the
+    conjugated inner product.  Stops when the true-residual recurrence
+    ||r|| / ||b|| <= tol (checked after each half step).  Returns
+    (x, info) with info = {iters, history, converged}; one iteration is two
+    matvecs and two preconditioner applies.
+    """
+    shape = b.shape
+    bf = b.reshape(-1).astype(np.complex128)
+    M = precond if precond is not None else (lambda v: v)
+    A = lambda v: matvec(v.reshape(shape)).reshape(-1)
+    Mv = lambda v: M(v.reshape(shape)).reshape(-1)
+    x = np.zeros_like(bf) if x0 is None else x0.reshape(-1).astype(np.complex128).copy()
+    bnorm = np.linalg.norm(bf)
+    if bnorm == 0:
+        return np.zeros(shape, dtype=np.complex128), dict(iters=0, history=[], converged=True)
+    r = bf - A(x)
+    rhat = r.copy()
+    rho = alpha = omega = 1.0 + 0j
+    v = np.zeros_like(bf)
+    p = np.zeros_like(bf)
+    history = []
+    converged = np.linalg.norm(r) / bnorm <= tol
+    it = 0
+    while not converged and it < maxiter:
+        rho_new = np.vdot(rhat, r)
+        beta = (rho_new / rho) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        ph = Mv(p)
+        v = A(ph)
+        alpha = rho_new / np.vdot(rhat, v)
+        s = r - alpha * v
+        it += 1
+        if np.linalg.norm(s) / bnorm <= tol:
+            x = x + alpha * ph
+            history.append(np.linalg.norm(s) / bnorm)
+            converged = True
+            break
+        sh = Mv(s)
+        t = A(sh)
+        omega = np.vdot(t, s) / np.vdot(t, t)
+        x = x + alpha * ph + omega * sh
+        r = s - omega * t
+        rho = rho_new
+        res = np.linalg.norm(r) / bnorm
+        history.append(res)
+        converged = res <= tol
+    return x.reshape(shape), dict(iters=it, history=history, converged=bool(converged))

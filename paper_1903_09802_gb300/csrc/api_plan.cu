@@ -117,6 +117,7 @@ bool make_layout(const dda_plan_desc_t& d, void* ws, Layout& L, std::string& why
     s.reorth = static_cast<int*>(c.take(4 * R));
     s.reorth_count = static_cast<int*>(c.take(4 * R));
     s.tickets = static_cast<int*>(c.take(8 * R));
+    s.bscal = static_cast<double*>(c.take(8 * 16 * R));
     s.counters = static_cast<int*>(c.take(64));
   }
   L.total = c.off + 256;

@@ -15,6 +15,8 @@
 //   3. ends when the estimate reaches max(tol ||b||, inner_tol ||r||), after
 //      `restart` steps or on breakdown, then solves the triangular system,
 //      forms u = V y and adds P^{-1} u to x in complex128.
+// With method = 1 each cycle runs right-preconditioned BiCG-Stab instead
+// (restart = iterations per cycle), on the same refinement loop.
 // Dots and norms of complex64 vectors multiply in FP32 and sum per thread
 // with compensated (Neumaier) FP32 addition, then across threads and blocks
 // in FP64 in a fixed order, so results are reproducible run to run; the
@@ -558,6 +560,259 @@ __global__ void __launch_bounds__(kNT)
   }
 }
 
+// ---------------------------------------------------------------------------
+// BiCG-Stab (van der Vorst), right-preconditioned, the paper's second solver
+// (Section 4).  Per right-hand side the device holds rho, alpha, omega and two
+// dot products in bs[r * 16 + ...]: 0-1 rho, 2-3 alpha, 4-5 omega, 6-7 dot A,
+// 8-9 dot B, 10 ||s||^2 or ||r||^2, 11 target^2, 12 state (1: converged at the
+// half step).
+
+// bs[slot..slot+1] = conj(a) . b per right-hand side, and optionally
+// bs[slot+2..slot+3] = conj(a2) . b2; last block reduces in a fixed order.
+template <typename T, int ND>
+__global__ void __launch_bounds__(kNT)
+    k_bdots(const cx<T>* __restrict__ a, const cx<T>* __restrict__ b,
+            const cx<T>* __restrict__ a2, const cx<T>* __restrict__ b2, long nu,
+            const int* __restrict__ mask, double2* __restrict__ partial,
+            int* __restrict__ tickets, double* __restrict__ bs, int slot) {
+  __shared__ double2 sh[ND][kNT / 32];
+  __shared__ int s_last;
+  const int r = blockIdx.y;
+  if (!mask[r]) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long k0, k1;
+  chunk_of(nu, gridDim.x, k0, k1);
+  Acc<T> ar[ND], ai[ND];
+  for (long k = k0 + threadIdx.x; k < k1; k += kNT) {
+    const cx<T> x = a[r * nu + k], y = b[r * nu + k];
+    ar[0].add(x.x * y.x + x.y * y.y);
+    ai[0].add(x.x * y.y - x.y * y.x);
+    if (ND > 1) {
+      const cx<T> x2 = a2[r * nu + k], y2 = b2[r * nu + k];
+      ar[ND - 1].add(x2.x * y2.x + x2.y * y2.y);
+      ai[ND - 1].add(x2.x * y2.y - x2.y * y2.x);
+    }
+  }
+#pragma unroll
+  for (int d = 0; d < ND; ++d) {
+    const double tr = ar[d].warp_total(), ti = ai[d].warp_total();
+    if (lane == 0) sh[d][wid] = make_double2(tr, ti);
+  }
+  __syncthreads();
+  if (threadIdx.x < ND) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int q = 0; q < kNT / 32; ++q) {
+      acc.x += sh[threadIdx.x][q].x;
+      acc.y += sh[threadIdx.x][q].y;
+    }
+    partial[((long)r * gridDim.x + blockIdx.x) * ND + threadIdx.x] = acc;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&tickets[r], 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (!s_last || threadIdx.x >= 32) return;
+  __threadfence();
+  for (int d = 0; d < ND; ++d) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int bb = threadIdx.x; bb < (int)gridDim.x; bb += 32) {
+      const double2 v = __ldcg(&partial[((long)r * gridDim.x + bb) * ND + d]);
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    acc = warp_sum(acc);
+    if (threadIdx.x == 0) {
+      bs[(long)r * 16 + slot + 2 * d] = acc.x;
+      bs[(long)r * 16 + slot + 2 * d + 1] = acc.y;
+    }
+  }
+  if (threadIdx.x == 0) tickets[r] = 0;
+}
+
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+  const double dn = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / dn, (a.y * b.x - a.x * b.y) / dn);
+}
+__device__ __forceinline__ double2 cmul2(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// op 0: beta = (rho_new/rho)(alpha/omega) -> slots 8-9, rho = rho_new (dot A);
+// op 1: alpha = rho / (rhat . v) (dot A); op 2: omega = (t . s)/(t . t) (dots A, B);
+// op 3: mark the half-step correction of d as applied.
+// A zero denominator is a breakdown: the cycle of that right-hand side ends.
+__global__ void k_bscalar(int op, double* __restrict__ bs, int* __restrict__ active,
+                          int* __restrict__ flags, int nrhs) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  double* q = bs + (long)r * 16;
+  if (op == 3) {  // the half-step update of d has been applied
+    if (q[12] == 1.0) q[12] = 2.0;
+    return;
+  }
+  if (!active[r]) return;
+  const double2 rho = make_double2(q[0], q[1]), alpha = make_double2(q[2], q[3]);
+  const double2 omega = make_double2(q[4], q[5]), da = make_double2(q[6], q[7]);
+  const double2 db = make_double2(q[8], q[9]);
+  double2 out;
+  if (op == 0) {
+    if (!(rho.x * rho.x + rho.y * rho.y > 0.0) || !(omega.x * omega.x + omega.y * omega.y > 0.0)) {
+      flags[r] |= 2;
+      active[r] = 0;
+      return;
+    }
+    out = cmul2(cdiv(da, rho), cdiv(alpha, omega));
+    q[0] = da.x;
+    q[1] = da.y;
+    q[8] = out.x;
+    q[9] = out.y;
+  } else if (op == 1) {
+    if (!(da.x * da.x + da.y * da.y > 0.0)) {
+      flags[r] |= 2;
+      active[r] = 0;
+      return;
+    }
+    out = cdiv(rho, da);
+    q[2] = out.x;
+    q[3] = out.y;
+  } else {
+    if (!(db.x * db.x + db.y * db.y > 0.0)) {
+      flags[r] |= 2;
+      active[r] = 0;
+      return;
+    }
+    out = cdiv(da, db);
+    q[4] = out.x;
+    q[5] = out.y;
+  }
+  if (!isfinite(out.x) || !isfinite(out.y)) {
+    flags[r] |= 1;
+    active[r] = 0;
+  }
+}
+
+// mode 0: p = r + beta (p - omega v)
+// mode 1: s = r - alpha v, and ||s||^2 (last block: converged at the half step?)
+// mode 2: d += alpha ph (right-hand sides converged at the half step only)
+// mode 3: d += alpha ph + omega sh, r = s - omega t, and ||r||^2 (last block:
+//         converged?)
+template <typename T>
+__global__ void __launch_bounds__(kNT)
+    k_baxpy(int mode, cx<T>* __restrict__ X, cx<T>* __restrict__ Y, const cx<T>* __restrict__ A1,
+            const cx<T>* __restrict__ A2, const cx<T>* __restrict__ A3,
+            cx<T>* __restrict__ D, long nu, const double* __restrict__ bs_in,
+            double* __restrict__ bs, int* __restrict__ active, int* __restrict__ iters,
+            double2* __restrict__ partial, int* __restrict__ tickets) {
+  __shared__ double2 sh[32];
+  __shared__ int s_last;
+  const int r = blockIdx.y;
+  const double* q = bs_in + (long)r * 16;
+  if (mode == 2) {
+    if (q[12] != 1.0) return;
+  } else if (!active[r]) {
+    return;
+  }
+  const cx<T> beta = mk<T>((T)q[8], (T)q[9]), alpha = mk<T>((T)q[2], (T)q[3]);
+  const cx<T> omega = mk<T>((T)q[4], (T)q[5]);
+  long k0, k1;
+  chunk_of(nu, gridDim.x, k0, k1);
+  const long o = r * nu;
+  Acc<T> nn;
+  for (long k = k0 + threadIdx.x; k < k1; k += kNT) {
+    if (mode == 0) {  // X = p, A1 = r, A2 = v
+      X[o + k] = A1[o + k] + beta * (X[o + k] - omega * A2[o + k]);
+    } else if (mode == 1) {  // Y = s, A1 = r, A2 = v
+      const cx<T> v = A1[o + k] - alpha * A2[o + k];
+      Y[o + k] = v;
+      nn.add(norm2(v));
+    } else if (mode == 2) {  // D += alpha ph (A1 = ph)
+      D[o + k] = D[o + k] + alpha * A1[o + k];
+    } else {  // D += alpha ph + omega sh; X = r = s - omega t (A1 ph, A2 sh, A3 t, Y s)
+      D[o + k] = D[o + k] + alpha * A1[o + k] + omega * A2[o + k];
+      const cx<T> v = Y[o + k] - omega * A3[o + k];
+      X[o + k] = v;
+      nn.add(norm2(v));
+    }
+  }
+  if (mode == 0 || mode == 2) return;
+  const double2 t = block_sum(make_double2(nn.get(), 0.0), sh);
+  if (threadIdx.x == 0) partial[(long)r * gridDim.x + blockIdx.x] = t;
+  __threadfence();
+  if (threadIdx.x == 0) s_last = atomicAdd(&tickets[r], 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (!s_last || threadIdx.x >= 32) return;
+  __threadfence();
+  double n2 = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += 32)
+    n2 += __ldcg(&partial[(long)r * gridDim.x + b]).x;
+  n2 = warp_sum(make_double2(n2, 0.0)).x;
+  if (threadIdx.x == 0) {
+    double* w = bs + (long)r * 16;
+    w[10] = n2;
+    const bool conv = !(n2 > w[11]);
+    if (mode == 1) {
+      w[12] = conv ? 1.0 : 0.0;
+      if (conv) {
+        active[r] = 0;
+        iters[r] += 1;
+      }
+    } else {
+      iters[r] += 1;
+      if (conv || !isfinite(n2)) active[r] = 0;
+    }
+    tickets[r] = 0;
+  }
+}
+
+// Start a BiCG-Stab cycle on the residual R (complex128): r = rhat = R in the
+// inner precision, p = v = d = 0, rho = alpha = omega = 1, target^2.
+template <typename T>
+__global__ void __launch_bounds__(kNT)
+    k_bstart(const double2* __restrict__ R, cx<T>* __restrict__ r0, cx<T>* __restrict__ rhat,
+             cx<T>* __restrict__ p, cx<T>* __restrict__ v, cx<T>* __restrict__ D, long nu,
+             const double* __restrict__ scal, double* __restrict__ bs, const int* __restrict__ run,
+             int* __restrict__ active, double tol, double inner_tol) {
+  const int r = blockIdx.y;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    active[r] = run[r];
+    double* q = bs + (long)r * 16;
+    q[0] = 1.0; q[1] = 0.0; q[2] = 1.0; q[3] = 0.0; q[4] = 1.0; q[5] = 0.0;
+    q[12] = 0.0;
+    const double beta = scal[(long)r * 16 + 6];
+    const double tgt = fmax(tol * scal[(long)r * 16 + 2], inner_tol * beta);
+    q[11] = tgt * tgt;
+  }
+  long k0, k1;
+  chunk_of(nu, gridDim.x, k0, k1);
+  for (long k = k0 + threadIdx.x; k < k1; k += kNT) {
+    const double2 a = R[r * nu + k];
+    const cx<T> x = mk<T>((T)a.x, (T)a.y);
+    r0[r * nu + k] = x;
+    rhat[r * nu + k] = x;
+    p[r * nu + k] = zero<T>();
+    v[r * nu + k] = zero<T>();
+    D[r * nu + k] = zero<T>();
+  }
+}
+
+// x += d for right-hand sides that ran this cycle.
+template <typename T>
+__global__ void __launch_bounds__(kNT)
+    k_badd_x(double2* __restrict__ x, const cx<T>* __restrict__ d, const int* __restrict__ run,
+             long nu) {
+  const int r = blockIdx.y;
+  if (!run[r]) return;
+  long k0, k1;
+  chunk_of(nu, gridDim.x, k0, k1);
+  for (long k = k0 + threadIdx.x; k < k1; k += kNT) {
+    const cx<T> v = d[r * nu + k];
+    double2 a = x[r * nu + k];
+    a.x += (double)v.x;
+    a.y += (double)v.y;
+    x[r * nu + k] = a;
+  }
+}
+
 template <typename T>
 dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
                         const dda_solve_opts_t& o, dda_rhs_stats_t* stats, cudaStream_t s) {
@@ -627,14 +882,80 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
     if (nrun == 0) break;
     for (int r = 0; r < nrhs; ++r) ncyc[r] += run[r];
     cudaMemcpyAsync(st.run, run.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s);
-    note_launch();
-    k_start_cycle<T><<<vgrid, kNT, 0, s>>>(R, V, nu, st.scal, st.g, m, st.run, st.active,
-                                           st.jlen, o.tol, o.inner_tol);
-    // Arnoldi steps
     int maxit_left = 0;
     for (int r = 0; r < nrhs; ++r)
       if (run[r]) maxit_left = std::max(maxit_left, o.max_iters - hits[r]);
     const int steps = std::min(m, maxit_left);
+    if (o.method == 1) {
+      // BiCG-Stab cycle in the inner precision on the FP64 residual R
+      cx<T>* Vr = V;
+      cx<T>* Vrh = V + vstride;
+      cx<T>* Vp = V + 2 * vstride;
+      cx<T>* Vv = V + 3 * vstride;
+      cx<T>* Vs = V + 4 * vstride;
+      cx<T>* Vt = V + 5 * vstride;
+      cx<T>* Vph = prec ? V + 6 * vstride : Vp;
+      cx<T>* Vsh = prec ? V + 7 * vstride : Vs;
+      cx<T>* D = Z;
+      double* bs = st.bscal;
+      int* tk2 = st.tickets + nrhs;
+      const unsigned sg = (nrhs + 63) / 64;
+      note_launch();
+      k_bstart<T><<<vgrid, kNT, 0, s>>>(R, Vr, Vrh, Vp, Vv, D, nu, st.scal, bs, st.run, st.active,
+                                        o.tol, o.inner_tol);
+      for (int it = 0; it < steps; ++it) {
+        note_launch();
+        k_bdots<T, 1><<<vgrid, kNT, 0, s>>>(Vrh, Vr, nullptr, nullptr, nu, st.active, st.partial,
+                                            st.tickets, bs, 6);
+        note_launch();
+        k_bscalar<<<sg, 64, 0, s>>>(0, bs, st.active, st.flags, nrhs);
+        note_launch();
+        k_baxpy<T><<<vgrid, kNT, 0, s>>>(0, Vp, nullptr, Vr, Vv, nullptr, nullptr, nu, bs, bs,
+                                         st.active, st.iters, st.partial, tk2);
+        if (prec) precond_apply_impl<T>(p, nrhs, Vp, Vph, s);
+        matvec_impl<T>(p, nrhs, Vph, Vv, s);
+        note_launch();
+        k_bdots<T, 1><<<vgrid, kNT, 0, s>>>(Vrh, Vv, nullptr, nullptr, nu, st.active, st.partial,
+                                            st.tickets, bs, 6);
+        note_launch();
+        k_bscalar<<<sg, 64, 0, s>>>(1, bs, st.active, st.flags, nrhs);
+        note_launch();
+        k_baxpy<T><<<vgrid, kNT, 0, s>>>(1, nullptr, Vs, Vr, Vv, nullptr, nullptr, nu, bs, bs,
+                                         st.active, st.iters, st.partial, tk2);
+        note_launch();
+        k_baxpy<T><<<vgrid, kNT, 0, s>>>(2, nullptr, nullptr, Vph, nullptr, nullptr, D, nu, bs, bs,
+                                         st.active, st.iters, st.partial, tk2);
+        note_launch();
+        k_bscalar<<<sg, 64, 0, s>>>(3, bs, st.active, st.flags, nrhs);
+        if (prec) precond_apply_impl<T>(p, nrhs, Vs, Vsh, s);
+        matvec_impl<T>(p, nrhs, Vsh, Vt, s);
+        note_launch();
+        k_bdots<T, 2><<<vgrid, kNT, 0, s>>>(Vt, Vs, Vt, Vt, nu, st.active, st.partial, st.tickets,
+                                            bs, 6);
+        note_launch();
+        k_bscalar<<<sg, 64, 0, s>>>(2, bs, st.active, st.flags, nrhs);
+        note_launch();
+        k_baxpy<T><<<vgrid, kNT, 0, s>>>(3, Vr, Vs, Vph, Vsh, Vt, D, nu, bs, bs, st.active,
+                                         st.iters, st.partial, tk2);
+        note_launch();
+        k_count_active<<<1, 32, 0, s>>>(st.active, nrhs, st.counters + (it & 1));
+        cudaMemcpyAsync(p->pinned + (it & 1), st.counters + (it & 1), sizeof(int),
+                        cudaMemcpyDeviceToHost, s);
+        cudaEventRecord(ev[it & 1], s);
+        if (it >= 1) {
+          cudaEventSynchronize(ev[(it - 1) & 1]);
+          if (p->pinned[(it - 1) & 1] == 0) break;
+        }
+      }
+      note_launch();
+      k_badd_x<T><<<vgrid, kNT, 0, s>>>(x, D, st.run, nu);
+      if ((status = check_cuda("dda_solve")) != DDA_OK) break;
+      continue;
+    }
+    note_launch();
+    k_start_cycle<T><<<vgrid, kNT, 0, s>>>(R, V, nu, st.scal, st.g, m, st.run, st.active,
+                                           st.jlen, o.tol, o.inner_tol);
+    // Arnoldi steps
     for (int j = 0; j < steps; ++j) {
       const cx<T>* vj = V + (long)j * vstride;
       const cx<T>* src = vj;
@@ -749,6 +1070,10 @@ extern "C" dda_status_t dda_solve(dda_plan_t p, int32_t nrhs, const void* d_b, v
     return fail(DDA_ERR_NO_PRECOND, "dda_solve: call dda_precond_build first");
   if (!p->has128) return fail(DDA_ERR_INVALID_ARG, "dda_solve: the residual needs complex128 data");
   if (o.restart + 2 > 518) return fail(DDA_ERR_INVALID_ARG, "dda_solve: restart above 512");
+  if (o.method != 0 && o.method != 1)
+    return fail(DDA_ERR_INVALID_ARG, "dda_solve: method must be 0 (GMRES) or 1 (BiCG-Stab)");
+  if (o.method == 1 && p->d.krylov_m < 7)
+    return fail(DDA_ERR_INVALID_ARG, "dda_solve: BiCG-Stab needs a plan with krylov_m >= 7");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const double2* b = static_cast<const double2*>(d_b);
   if (!b) {

@@ -58,6 +58,7 @@ struct SolverState {
   int* reorth;       // [rhs] 1 when this step needs a second Gram-Schmidt pass
   int* reorth_count; // [rhs] steps that took a second pass
   int* tickets;      // [2][rhs] last-block counters of the Gram-Schmidt kernels
+  double* bscal;     // [rhs][16] BiCG-Stab scalars
   int* counters;     // [16] 0: RHS still iterating in the current cycle
 };
 

@@ -23,6 +23,7 @@ if not os.path.exists(LIB_PATH):
 _lib = ctypes.CDLL(LIB_PATH)
 
 C128, C64 = 0, 1
+GMRES, BICGSTAB = 0, 1
 PLAN_C128, PLAN_C64 = 1, 2
 
 STATUS = {
@@ -62,7 +63,7 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iters", ctypes.c_int32),
                 ("restart", ctypes.c_int32), ("precond", ctypes.c_int32),
                 ("inner_prec", ctypes.c_int32), ("inner_tol", ctypes.c_double),
-                ("reorth_eta", ctypes.c_double)]
+                ("reorth_eta", ctypes.c_double), ("method", ctypes.c_int32)]
 
 
 class RhsStats(ctypes.Structure):
@@ -250,13 +251,14 @@ class Plan:
     def solve(self, b: torch.Tensor | None = None, x0: torch.Tensor | None = None,
               tol: float = 1e-6, max_iters: int = 2000, restart: int = 50, precond: int = 3,
               inner_prec: int = C128, inner_tol: float = 0.0, raise_on_error: bool = True,
-              nrhs: int | None = None, reorth_eta: float = 0.5 ** 0.5) -> SolveResult:
+              nrhs: int | None = None, reorth_eta: float = 0.5 ** 0.5,
+              method: int = 0) -> SolveResult:
         nrhs = nrhs or (b.shape[0] if b is not None else self.nrhs)
         if x0 is None:
             x = torch.zeros(self.field_shape(nrhs), dtype=torch.complex128, device=self.mat.device)
         else:
             x = x0.clone().contiguous()
-        opts = SolveOpts(tol, max_iters, restart, precond, inner_prec, inner_tol, reorth_eta)
+        opts = SolveOpts(tol, max_iters, restart, precond, inner_prec, inner_tol, reorth_eta, method)
         stats = (RhsStats * nrhs)()
         bp = _ptr(b.contiguous()) if b is not None else ctypes.c_void_p(0)
         st = _lib.dda_solve(self._h, nrhs, bp, _ptr(x), ctypes.byref(opts), stats, _stream())

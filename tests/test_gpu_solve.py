@@ -131,3 +131,28 @@ def test_precond_required_before_use():
     with pytest.raises(dda.DDAError) as e:
         plan.solve(tol=1e-6, restart=10, precond=3)
     assert "DDA_ERR_NO_PRECOND" in str(e.value)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precond", [0, 3])
+def test_bicgstab_matches_direct_and_oracle(case16, precond):
+    dda, case, prob, xd, plan = case16
+    from oracle import krylov
+    res = plan.solve(tol=1e-6, restart=200, precond=precond, inner_prec=dda.C128,
+                     method=dda.BICGSTAB)
+    x = res.x[0].cpu().numpy()
+    assert res.converged[0] and _true_resid(prob, x) <= 1e-6
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-4
+    G = prob.kernel_spectrum()
+    _, info = krylov.bicgstab(lambda v: prob.matvec(v, G), prob.rhs(), tol=1e-6,
+                              precond=prob.precond3() if precond else None)
+    assert abs(res.iters[0] - info["iters"]) <= max(3, info["iters"] // 10)
+
+
+@pytest.mark.gpu
+def test_bicgstab_mixed_precision(case16):
+    dda, case, prob, xd, plan = case16
+    res = plan.solve(tol=1e-6, restart=30, precond=3, inner_prec=dda.C64, inner_tol=1e-4,
+                     method=dda.BICGSTAB)
+    x = res.x[0].cpu().numpy()
+    assert res.converged[0] and _true_resid(prob, x) <= 1e-6

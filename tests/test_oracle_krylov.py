@@ -58,3 +58,24 @@ def test_gmres_dda_prism_matches_direct():
         assert err < 1e-8, (pre, err)
         r = p.rhs() - p.matvec(x)
         assert np.linalg.norm(r) / np.linalg.norm(p.rhs()) <= 1e-10
+
+
+def test_bicgstab_random_and_dda():
+    rng = np.random.default_rng(17)
+    n = 40
+    A = np.eye(n) * 4 + random_field((n, n), rng) / np.sqrt(n)
+    b = random_field(n, rng)
+    Minv = np.linalg.inv(np.diag(np.diag(A)))
+    x, info = krylov.bicgstab(lambda v: A @ v, b, tol=1e-12, precond=lambda v: Minv @ v)
+    assert info["converged"]
+    assert np.linalg.norm(x - np.linalg.solve(A, b)) / np.linalg.norm(b) < 1e-10
+    l = m = n3 = 8
+    dx, k = 2.0 / 8, 2.5
+    mat = hex_prism_mask(l, m, n3, dx, 1.0, 2.0)
+    p = Problem(mat=mat, dx=dx, k=k, eps=[1.31 ** 2], d=np.array([0, 0, 1.0]), e=np.array([1.0, 0, 0]))
+    xd = p.solve_direct()
+    G = p.kernel_spectrum()
+    for M in (None, p.precond3()):
+        x, info = krylov.bicgstab(lambda v: p.matvec(v, G), p.rhs(), tol=1e-10, precond=M)
+        assert info["converged"]
+        assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-8

@@ -86,7 +86,8 @@ typedef struct {
 typedef struct {
   double tol;            /* stop when ||b - A x||_2 / ||b||_2 <= tol (FP64 residual)  */
   int32_t max_iters;     /* cap on inner GMRES iterations per right-hand side          */
-  int32_t restart;       /* GMRES(m) restart length, 1 <= restart <= plan krylov_m     */
+  int32_t restart;       /* GMRES(m) restart length, 1 <= restart <= plan krylov_m;
+                            BiCG-Stab: iterations per refinement cycle (any >= 1)     */
   int32_t precond;       /* 0: none, 3: three-level circulant (dda_precond_build first) */
   int32_t inner_prec;    /* DDA_C128: plain FP64 GMRES; DDA_C64: complex64 GMRES cycles
                             inside FP64 iterative refinement                          */

@@ -1063,13 +1063,15 @@ extern "C" dda_status_t dda_solve(dda_plan_t p, int32_t nrhs, const void* d_b, v
   if (nrhs < 1 || nrhs > p->nrhs_inc)
     return fail(DDA_ERR_INVALID_ARG, "dda_solve: nrhs must be 1..(incidences set)");
   const dda_solve_opts_t& o = *opts;
-  if (!(o.tol > 0) || o.max_iters < 1 || o.restart < 1 || o.restart > p->d.krylov_m ||
+  if (!(o.tol > 0) || o.max_iters < 1 || o.restart < 1 ||
+      (o.method == 0 && o.restart > p->d.krylov_m) ||
       !(o.inner_tol >= 0) || !(o.reorth_eta >= 0) || (o.precond != 0 && o.precond != 3))
     return fail(DDA_ERR_INVALID_ARG, "dda_solve: invalid options");
   if (o.precond == 3 && !p->precond_built)
     return fail(DDA_ERR_NO_PRECOND, "dda_solve: call dda_precond_build first");
   if (!p->has128) return fail(DDA_ERR_INVALID_ARG, "dda_solve: the residual needs complex128 data");
-  if (o.restart + 2 > 518) return fail(DDA_ERR_INVALID_ARG, "dda_solve: restart above 512");
+  if (o.method == 0 && o.restart + 2 > 518)
+    return fail(DDA_ERR_INVALID_ARG, "dda_solve: restart above 512");
   if (o.method != 0 && o.method != 1)
     return fail(DDA_ERR_INVALID_ARG, "dda_solve: method must be 0 (GMRES) or 1 (BiCG-Stab)");
   if (o.method == 1 && p->d.krylov_m < 7)

@@ -19,7 +19,9 @@ elapsed device time of K steps / (12 K N).  L2 is flushed (a 512 MB write)
 before every timed step.  The JSON line also carries the roofline of the
 dominant kernel measured live with CUDA events, the CPU oracle timed on a
 bounded sample, the end-to-end figure through host buffers, the number of
-library kernel launches and the SM clocks sampled during the timed region.
+library kernel launches, the SM clocks sampled during the timed region and,
+untimed, solver comparisons on the two 64^3 systems (no preconditioner,
+plain complex128, BiCG-Stab).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -217,6 +219,41 @@ def roofline(runner, peak, peak_kind):
             "achieved_gbs_by_class": per_class}
 
 
+def compare_solvers(runner):
+    """Untimed side measurements on the two 64^3 systems of the sweep (m = 1.31
+    and 1.31 + 0.05i, both polarisations): solve time per right-hand side and
+    iterations for the variants the paper and the benchmark spec compare."""
+    import torch
+    dda = runner.dda
+    variants = {
+        "gmres_3level_c64_fp64ir": dict(precond=3, inner_prec=dda.C64, inner_tol=1e-4,
+                                        reorth_eta=REORTH_ETA),
+        "gmres_none_c64_fp64ir": dict(precond=0, inner_prec=dda.C64, inner_tol=1e-4,
+                                      reorth_eta=REORTH_ETA),
+        "gmres_3level_c128": dict(precond=3, inner_prec=dda.C128, reorth_eta=REORTH_ETA),
+        "bicgstab_3level_c64_fp64ir": dict(precond=3, inner_prec=dda.C64, inner_tol=1e-4,
+                                           method=dda.BICGSTAB),
+    }
+    out = {}
+    for i, case in enumerate(runner.cases):
+        if case.dims != (64, 64, 64):
+            continue
+        plan = dda.Plan(runner.masks[i], case.eps, case.dx, case.k, max_rhs=2, krylov_m=50)
+        plan.set_incidence(case.dirs, case.pols)
+        plan.precond_build()
+        key = f"m={complex(case.eps[0]) ** 0.5:.2f}"
+        out[key] = {}
+        for name, kw in variants.items():
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = plan.solve(tol=1e-6, restart=50, max_iters=3000, raise_on_error=False, **kw)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            out[key][name] = {"ms_per_solve": round(1e3 * dt / case.nrhs, 2), "iters": res.iters,
+                              "converged": all(res.converged)}
+    return out
+
+
 def oracle_iterations():
     """Iteration counts of the oracle's own solves of the workload, written by
     oracle/iteration_counts.py (key: box dims, eps, rhs)."""
@@ -348,6 +385,7 @@ def run_ours(args, rank, world):
 
     peak, peak_kind = read_peak()
     roof = roofline(runner, peak, peak_kind)
+    comparisons = compare_solvers(runner) if not args.no_compare else None
     if rank != 0:
         return
     value = total_ms / (args.steps * nsolve * world)
@@ -367,6 +405,8 @@ def run_ours(args, rank, world):
         "roofline": roof,
         "clocks": clk.summary(),
     }
+    if comparisons is not None:
+        line["comparisons"] = comparisons
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(its)
     print(json.dumps(line), flush=True)
@@ -412,6 +452,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the untimed solver comparisons")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -74,6 +74,8 @@ typedef struct {
   int32_t max_rhs;       /* largest right-hand-side batch used with this plan   */
   int32_t krylov_m;      /* GMRES restart length to reserve (0: no solver)      */
   int32_t precisions;    /* DDA_PLAN_C128 | DDA_PLAN_C64                         */
+  int32_t precond2;      /* 1: reserve the 2-level preconditioner's dense blocks
+                            (l m (3n)^2 complex64 values) and its build scratch  */
 } dda_plan_desc_t;
 
 /* Plane wave E_inc = pol * exp(i k dir . r), r measured from the box centre.
@@ -88,7 +90,8 @@ typedef struct {
   int32_t max_iters;     /* cap on inner GMRES iterations per right-hand side          */
   int32_t restart;       /* GMRES(m) restart length, 1 <= restart <= plan krylov_m;
                             BiCG-Stab: iterations per refinement cycle (any >= 1)     */
-  int32_t precond;       /* 0: none, 3: three-level circulant (dda_precond_build first) */
+  int32_t precond;       /* 0: none; 3: three-level circulant (dda_precond_build first);
+                            2: the paper's 2-level circulant (dda_precond2_build first) */
   int32_t inner_prec;    /* DDA_C128: plain FP64 GMRES; DDA_C64: complex64 GMRES cycles
                             inside FP64 iterative refinement                          */
   double inner_tol;      /* a cycle ends early once its residual estimate falls below
@@ -182,6 +185,22 @@ dda_status_t dda_precond_apply(dda_plan_t plan, int32_t prec, int32_t nrhs, cons
  * on any streams, race and give wrong results.  Allocates nothing. */
 dda_status_t dda_precond_apply_noalloc(dda_plan_t plan, int32_t prec, int32_t nrhs,
                                        const void* d_v, void* d_z, void* stream);
+
+/* The paper's 2-level circulant preconditioner (Section 3.1, eqs. 17-19):
+ * T. Chan's circulant (eq. 13) on the x and y levels, the z level kept
+ * Toeplitz, so after a 2-D DFT every frequency pair (wx, wy) carries a dense
+ * 3n x 3n block alpha_tilde^{-1} I - dx^3 Chat2(wx, wy), inverted on the GPU
+ * (Gauss-Jordan with partial pivoting, complex64) and stored.  alpha_tilde is
+ * that of the first right-hand side of the current incidence (call after
+ * dda_set_incidence; the blocks serve the whole batch).  Needs a plan with
+ * desc.precond2 = 1.  DDA_ERR_SINGULAR_PRECOND if a block is singular. */
+dda_status_t dda_precond2_build(dda_plan_t plan, void* stream);
+
+/* z = M o P2^{-1}(M o v) (restricted to the scatterer as dda_precond_apply):
+ * masked 2-D FFT, dense block times the (component, z) vector of every
+ * frequency pair, inverse FFT.  v and z may be the same buffer. */
+dda_status_t dda_precond2_apply(dda_plan_t plan, int32_t prec, int32_t nrhs, const void* d_v,
+                                void* d_z, void* stream);
 
 /* In-place unnormalised 3-D DFT (inverse: sign +, scaled by 1/(l m n)) of
  * nbatch complex l x m x n arrays [batch][z][y][x].  Same kernels as the

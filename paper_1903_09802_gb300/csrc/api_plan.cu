@@ -43,6 +43,7 @@ bool valid_desc(const dda_plan_desc_t& d, std::string& why, dda_status_t& st) {
   if (d.n_materials < 1 || d.n_materials > 255) return why = "n_materials must be 1..255", false;
   if (d.max_rhs < 1 || d.max_rhs > 4096) return why = "max_rhs must be 1..4096", false;
   if (d.krylov_m < 0 || d.krylov_m > 512) return why = "krylov_m must be 0..512", false;
+  if (d.precond2 != 0 && d.precond2 != 1) return why = "precond2 must be 0 or 1", false;
   if ((d.precisions & (DDA_PLAN_C128 | DDA_PLAN_C64)) == 0 ||
       (d.precisions & ~(DDA_PLAN_C128 | DDA_PLAN_C64)) != 0)
     return why = "precisions must be a non-empty set of DDA_PLAN_C128 | DDA_PLAN_C64", false;
@@ -89,6 +90,10 @@ bool make_layout(const dda_plan_desc_t& d, void* ws, Layout& L, std::string& why
   b2 = std::max(b2, (size_t)nvox * 96);  // circulant build: six complex128 components
   L.buf2 = c.take(b2);
   L.err_flag = c.take(64);
+  if (d.precond2) {
+    L.P2 = c.take((size_t)l * m * (3 * n) * (3 * n) * 8);
+    L.C2 = c.take((size_t)6 * (2 * n - 1) * l * m * 16);
+  }
   // complex128 field batch: the solver's residual and the cross sections' A c
   if (h128) L.R128 = c.take(16 * R * nu);
   if (d.krylov_m > 0) {

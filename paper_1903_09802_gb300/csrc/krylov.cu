@@ -828,7 +828,13 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
   double2* R = static_cast<double2*>(p->w.R128);
   const long vstride = (long)nrhs * nu;
   const dim3 vgrid(nblk, nrhs);
-  const bool prec = o.precond == 3;
+  const bool prec = o.precond != 0;
+  auto apply_prec = [&](const cx<T>* in, cx<T>* out) {
+    if (o.precond == 2)
+      precond2_apply<T>(p, nrhs, in, out, s);
+    else
+      precond_apply_impl<T>(p, nrhs, in, out, s);
+  };
   const double brk = sizeof(T) == 8 ? 1e-13 : 1e-6;
   const bool vec = (nu % 2) == 0;  // 16-byte pairs stay aligned
   const double eta2 = o.reorth_eta * o.reorth_eta;
@@ -912,7 +918,7 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
         note_launch();
         k_baxpy<T><<<vgrid, kNT, 0, s>>>(0, Vp, nullptr, Vr, Vv, nullptr, nullptr, nu, bs, bs,
                                          st.active, st.iters, st.partial, tk2);
-        if (prec) precond_apply_impl<T>(p, nrhs, Vp, Vph, s);
+        if (prec) apply_prec(Vp, Vph);
         matvec_impl<T>(p, nrhs, Vph, Vv, s);
         note_launch();
         k_bdots<T, 1><<<vgrid, kNT, 0, s>>>(Vrh, Vv, nullptr, nullptr, nu, st.active, st.partial,
@@ -927,7 +933,7 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
                                          st.active, st.iters, st.partial, tk2);
         note_launch();
         k_bscalar<<<sg, 64, 0, s>>>(3, bs, st.active, st.flags, nrhs);
-        if (prec) precond_apply_impl<T>(p, nrhs, Vs, Vsh, s);
+        if (prec) apply_prec(Vs, Vsh);
         matvec_impl<T>(p, nrhs, Vsh, Vt, s);
         note_launch();
         k_bdots<T, 2><<<vgrid, kNT, 0, s>>>(Vt, Vs, Vt, Vt, nu, st.active, st.partial, st.tickets,
@@ -960,7 +966,7 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
       const cx<T>* vj = V + (long)j * vstride;
       const cx<T>* src = vj;
       if (prec) {
-        precond_apply_impl<T>(p, nrhs, vj, Z, s);
+        apply_prec(vj, Z);
         src = Z;
       }
       matvec_impl<T>(p, nrhs, src, W, s);
@@ -1017,7 +1023,7 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
     k_combine<T><<<vgrid, kNT, 0, s>>>(V, st.y, st.jlen, W, nu, vstride, m);
     const cx<T>* upd = W;
     if (prec) {
-      precond_apply_impl<T>(p, nrhs, W, Z, s);
+      apply_prec(W, Z);
       upd = Z;
     }
     note_launch();
@@ -1065,10 +1071,13 @@ extern "C" dda_status_t dda_solve(dda_plan_t p, int32_t nrhs, const void* d_b, v
   const dda_solve_opts_t& o = *opts;
   if (!(o.tol > 0) || o.max_iters < 1 || o.restart < 1 ||
       (o.method == 0 && o.restart > p->d.krylov_m) ||
-      !(o.inner_tol >= 0) || !(o.reorth_eta >= 0) || (o.precond != 0 && o.precond != 3))
+      !(o.inner_tol >= 0) || !(o.reorth_eta >= 0) ||
+      (o.precond != 0 && o.precond != 2 && o.precond != 3))
     return fail(DDA_ERR_INVALID_ARG, "dda_solve: invalid options");
   if (o.precond == 3 && !p->precond_built)
     return fail(DDA_ERR_NO_PRECOND, "dda_solve: call dda_precond_build first");
+  if (o.precond == 2 && !p->precond2_built)
+    return fail(DDA_ERR_NO_PRECOND, "dda_solve: call dda_precond2_build first");
   if (!p->has128) return fail(DDA_ERR_INVALID_ARG, "dda_solve: the residual needs complex128 data");
   if (o.method == 0 && o.restart + 2 > 518)
     return fail(DDA_ERR_INVALID_ARG, "dda_solve: restart above 512");

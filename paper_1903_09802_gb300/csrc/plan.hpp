@@ -68,6 +68,8 @@ struct Layout {
   void* G64 = nullptr;
   void* C128 = nullptr;
   void* C64 = nullptr;
+  void* P2 = nullptr;   // 2-level preconditioner: l m (3n)^2 complex64 inverse blocks
+  void* C2 = nullptr;   // its build scratch: 6 (2n-1) l m complex128
   // twiddles for the largest transform length
   void* tw128 = nullptr;
   void* tw64 = nullptr;
@@ -109,6 +111,7 @@ struct dda_plan_s {
   dda::Layout w;
   bool has128, has64;
   bool precond_built = false;
+  bool precond2_built = false;
   int nrhs_inc = 0;                      // RHS count of the last dda_set_incidence
   std::vector<dda_incidence_t> inc;      // incidence per RHS
   std::vector<double> ainv_host;         // [rhs][K+1][2]
@@ -143,6 +146,8 @@ template <typename T>
 void matvec_impl(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t s);
 template <typename T>
 void precond_apply_impl(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cudaStream_t s);
+template <typename T>
+void precond2_apply(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cudaStream_t s);
 template <typename T>
 void precond_apply_into(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cx<T>* t,
                         cudaStream_t s);

@@ -34,6 +34,7 @@ STATUS = {
 
 EXPORTS = ("dda_workspace_size", "dda_plan_create", "dda_set_incidence", "dda_incident_field",
            "dda_matvec", "dda_precond_build", "dda_precond_apply", "dda_precond_apply_noalloc",
+           "dda_precond2_build", "dda_precond2_apply",
            "dda_fft3d", "dda_solve",
            "dda_cross_sections", "dda_adjoint_rhs", "dda_ext_gradient", "dda_profile_enable", "dda_profile_read", "dda_plan_destroy",
            "dda_last_error", "dda_launch_count")
@@ -52,7 +53,8 @@ class PlanDesc(ctypes.Structure):
     _fields_ = [("l", ctypes.c_int32), ("m", ctypes.c_int32), ("n", ctypes.c_int32),
                 ("dx", ctypes.c_double), ("k", ctypes.c_double),
                 ("n_materials", ctypes.c_int32), ("max_rhs", ctypes.c_int32),
-                ("krylov_m", ctypes.c_int32), ("precisions", ctypes.c_int32)]
+                ("krylov_m", ctypes.c_int32), ("precisions", ctypes.c_int32),
+                ("precond2", ctypes.c_int32)]
 
 
 class Incidence(ctypes.Structure):
@@ -88,6 +90,10 @@ _lib.dda_precond_build.restype = ctypes.c_int
 _lib.dda_precond_build.argtypes = [_vp, _vp]
 _lib.dda_precond_apply.restype = ctypes.c_int
 _lib.dda_precond_apply.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp]
+_lib.dda_precond2_build.restype = ctypes.c_int
+_lib.dda_precond2_build.argtypes = [_vp, _vp]
+_lib.dda_precond2_apply.restype = ctypes.c_int
+_lib.dda_precond2_apply.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp]
 _lib.dda_precond_apply_noalloc.restype = ctypes.c_int
 _lib.dda_precond_apply_noalloc.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp]
 _lib.dda_fft3d.restype = ctypes.c_int
@@ -149,8 +155,8 @@ def _prec_of(t: torch.Tensor) -> int:
 
 
 def workspace_size(l, m, n, dx, k, n_materials=1, max_rhs=1, krylov_m=0,
-                   precisions=PLAN_C128 | PLAN_C64) -> int:
-    d = PlanDesc(l, m, n, dx, k, n_materials, max_rhs, krylov_m, precisions)
+                   precisions=PLAN_C128 | PLAN_C64, precond2=0) -> int:
+    d = PlanDesc(l, m, n, dx, k, n_materials, max_rhs, krylov_m, precisions, int(bool(precond2)))
     return int(_lib.dda_workspace_size(ctypes.byref(d)))
 
 
@@ -169,7 +175,8 @@ class Plan:
     """A DDA problem on one box: geometry, materials, wavenumber, workspace."""
 
     def __init__(self, mat: torch.Tensor, eps, dx: float, k: float, max_rhs: int = 1,
-                 krylov_m: int = 0, precisions: int = PLAN_C128 | PLAN_C64):
+                 krylov_m: int = 0, precisions: int = PLAN_C128 | PLAN_C64,
+                 precond2: bool = False):
         if mat.dtype != torch.uint8 or not mat.is_cuda or mat.dim() != 3:
             raise TypeError("mat must be a (n, m, l) uint8 CUDA tensor")
         self.mat = mat.contiguous()
@@ -177,7 +184,7 @@ class Plan:
         self.shape = (l, m, n)
         eps = [complex(e) for e in eps]
         self.desc = PlanDesc(l, m, n, float(dx), float(k), len(eps), int(max_rhs), int(krylov_m),
-                             int(precisions))
+                             int(precisions), int(bool(precond2)))
         size = int(_lib.dda_workspace_size(ctypes.byref(self.desc)))
         if size == 0:
             raise DDAError(1, last_error())
@@ -232,6 +239,16 @@ class Plan:
         v = v.contiguous()
         z = torch.empty_like(v) if out is None else out
         _check(_lib.dda_precond_apply(self._h, _prec_of(v), v.shape[0], _ptr(v), _ptr(z), _stream()))
+        return z
+
+    def precond2_build(self):
+        """The paper's 2-level preconditioner (needs a plan made with precond2=True)."""
+        _check(_lib.dda_precond2_build(self._h, _stream()))
+
+    def precond2_apply(self, v: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        v = v.contiguous()
+        z = torch.empty_like(v) if out is None else out
+        _check(_lib.dda_precond2_apply(self._h, _prec_of(v), v.shape[0], _ptr(v), _ptr(z), _stream()))
         return z
 
     def precond_apply_noalloc(self, v: torch.Tensor, out: torch.Tensor) -> torch.Tensor:

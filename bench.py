@@ -233,16 +233,24 @@ def compare_solvers(runner):
         "gmres_3level_c128": dict(precond=3, inner_prec=dda.C128, reorth_eta=REORTH_ETA),
         "bicgstab_3level_c64_fp64ir": dict(precond=3, inner_prec=dda.C64, inner_tol=1e-4,
                                            method=dda.BICGSTAB),
+        "gmres_2level_c64_fp64ir": dict(precond=2, inner_prec=dda.C64, inner_tol=1e-4,
+                                        reorth_eta=REORTH_ETA),
     }
     out = {}
     for i, case in enumerate(runner.cases):
         if case.dims != (64, 64, 64):
             continue
-        plan = dda.Plan(runner.masks[i], case.eps, case.dx, case.k, max_rhs=2, krylov_m=50)
+        plan = dda.Plan(runner.masks[i], case.eps, case.dx, case.k, max_rhs=2, krylov_m=50,
+                        precond2=True)
         plan.set_incidence(case.dirs, case.pols)
         plan.precond_build()
         key = f"m={complex(case.eps[0]) ** 0.5:.2f}"
         out[key] = {}
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.precond2_build()  # the paper's 2-level blocks: FP64 build, complex64 inverses
+        torch.cuda.synchronize()
+        out[key]["precond2_build_ms"] = round(1e3 * (time.perf_counter() - t0), 2)
         for name, kw in variants.items():
             torch.cuda.synchronize()
             t0 = time.perf_counter()

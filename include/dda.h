@@ -75,7 +75,8 @@ typedef struct {
   int32_t krylov_m;      /* GMRES restart length to reserve (0: no solver)      */
   int32_t precisions;    /* DDA_PLAN_C128 | DDA_PLAN_C64                         */
   int32_t precond2;      /* 1: reserve the 2-level preconditioner's dense blocks
-                            (l m (3n)^2 complex64 values) and its build scratch  */
+                            ((l/2+1)(m/2+1)(3n)^2 complex64 values, the other
+                            frequency pairs follow by parity) and build scratch */
 } dda_plan_desc_t;
 
 /* Plane wave E_inc = pol * exp(i k dir . r), r measured from the box centre.
@@ -247,8 +248,9 @@ dda_status_t dda_cross_sections(dda_plan_t plan, int32_t nrhs, const void* d_c, 
  * launch count: index 0..4 matvec passes (x forward, y forward, z with the
  * spectrum multiply, y inverse, x inverse with the diagonal), 5..9 the
  * preconditioner's passes in the same order, 10 Gram-Schmidt dots,
- * 11 Gram-Schmidt update (first pass only); n entries are written
- * (n <= 12); reset != 0 zeroes the sums.  h_bytes (may be NULL) receives the
+ * 11 Gram-Schmidt update (first pass only), 12 the 2-level
+ * preconditioner's block pass (its FFT passes count as 5, 6, 8, 9); n entries
+ * are written (n <= 13); reset != 0 zeroes the sums.  h_bytes (may be NULL) receives the
  * summed algorithmic bytes of the timed launches: per right-hand side and
  * with u = one box field (3 l m n values), matvec passes 9u (+mask), 18u,
  * 24u (+ the kernel spectrum once), 18u, 12u (+mask); preconditioner

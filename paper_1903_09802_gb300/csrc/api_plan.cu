@@ -91,7 +91,7 @@ bool make_layout(const dda_plan_desc_t& d, void* ws, Layout& L, std::string& why
   L.buf2 = c.take(b2);
   L.err_flag = c.take(64);
   if (d.precond2) {
-    L.P2 = c.take((size_t)l * m * (3 * n) * (3 * n) * 8);
+    L.P2 = c.take((size_t)(l / 2 + 1) * (m / 2 + 1) * (3 * n) * (3 * n) * 8);
     L.C2 = c.take((size_t)6 * (2 * n - 1) * l * m * 16);
   }
   // complex128 field batch: the solver's residual and the cross sections' A c

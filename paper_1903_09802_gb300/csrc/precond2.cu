@@ -8,8 +8,17 @@
 // frequency pair (wx, wy) one dense 3n x 3n block
 //   B[(a, z), (b, z')] = alpha_tilde^{-1} delta - dx^3 Chat2_ab(z - z'; wx, wy),
 // which is inverted (Gauss-Jordan with partial pivoting, one CTA per block,
-// complex64) and stored: l m (3n)^2 values.  alpha_tilde is that of the first
+// complex64; the transpose is assembled and inverted, so the inverse lies in
+// memory column-major) and stored.  alpha_tilde is that of the first
 // right-hand side of the current incidence set.
+//
+// Only the quadrant 0 <= wx <= l/2, 0 <= wy <= m/2 is built and stored,
+// (l/2 + 1)(m/2 + 1) blocks: every block of the Green tensor is even or odd
+// in x and in y (odd in x: xy, xz; odd in y: xy, yz), T. Chan's circulant
+// keeps that parity, so its DFT is even or odd in wx and wy, and
+//   B(l - wx, wy) = Sx B(wx, wy) Sx,   Sx = diag(-1 on the x component, 1, 1),
+// likewise in y; the same holds for the inverse.  The apply flips the signs
+// of the x (y) component before and after the product for wx > l/2 (wy > m/2).
 //
 // Apply, restricted to the scatterer like the 3-level form:
 // z = M o P2^{-1}(M o v): masked x and y FFTs, per frequency pair the dense
@@ -80,15 +89,19 @@ __global__ void k_chan2(double2* out, long l, long m, long n, double dx, double 
   }
 }
 
-// blocks[f][i][j], f = wy * l + wx, i = a n + z, j = b n + z'.
+// blocksT[fq][j][i] = B[i][j] (the transpose, whose inverse is the transposed
+// inverse the apply reads column-wise), fq = wy * (l/2 + 1) + wx over the
+// stored quadrant, i = a n + z, j = b n + z'.
 __global__ void k_assemble2(const double2* __restrict__ chat, float2* __restrict__ blocks, long l,
                             long m, long n, double dx3, double2 at) {
   const long N = 3 * n, plane = l * m, nr = 2 * n - 1;
-  const long tot = plane * N * N;
+  const long hx = l / 2 + 1, hy = m / 2 + 1;
+  const long tot = hx * hy * N * N;
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < tot;
        t += (long)gridDim.x * blockDim.x) {
-    const long f = t / (N * N), ij = t % (N * N);
-    const long i = ij / N, j = ij % N;
+    const long fq = t / (N * N), ij = t % (N * N);
+    const long f = (fq / hx) * l + fq % hx;
+    const long j = ij / N, i = ij % N;
     const int a = (int)(i / n), b = (int)(j / n);
     const long z = i % n, zp = j % n;
     const double2 c = chat[((long)comp_of(a, b) * nr + (z - zp + n - 1)) * plane + f];
@@ -205,40 +218,212 @@ __global__ void __launch_bounds__(1024)
   }
 }
 
-// Per frequency pair f: gather the 3n-vector (component, z) of each right-hand
-// side from t[rhs][c][z][f], multiply by the inverse block, scale by 1/(l m)
-// (the inverse transforms are unnormalised) and scatter back.
-template <typename T>
+// One CTA per stored block (wxq, wyq) serves every frequency pair that mirrors
+// onto it (up to four) for right-hand sides r0 .. r0 + nr - 1: it gathers
+// those 3n-vectors (component, z) from t[rhs][c][z][wy][wx] into shared
+// memory with the mirror's component signs, multiplies them by the block
+// (read once, coalesced: blocksT holds each inverse transposed, one thread
+// per output row), and scatters the signed, 1/(l m)-scaled results back (the
+// inverse transforms are unnormalised).  Vectors are taken VC at a time.
+template <typename T, int VC>
 __global__ void __launch_bounds__(256)
-    k_block_apply(cx<T>* __restrict__ t, const float2* __restrict__ blocks, int nrhs, long n,
-                  long plane, T scale) {
+    k_block_apply(cx<T>* __restrict__ t, const float2* __restrict__ blocksT, int r0, int nr, long l,
+                  long m, long n, T scale) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const long N = 3 * n;
-  cx<T>* vin = reinterpret_cast<cx<T>*>(smem_raw);  // [nrhs][N]
-  const long f = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
-  for (long e = tid; e < (long)nrhs * N; e += blockDim.x) {
-    const long r = e / N, i = e % N;
-    vin[e] = t[(r * N + i) * plane + f];  // (r, c, z) = r*3n + (c n + z)
+  float2* vin = reinterpret_cast<float2*>(smem_raw);  // [chunk][j][VC]
+  const long N = 3 * n, plane = l * m, hx = l / 2 + 1;
+  const long fq = blockIdx.x, wxq = fq % hx, wyq = fq / hx;
+  const int nfx = (wxq != 0 && 2 * wxq != l) ? 2 : 1;
+  const int nfy = (wyq != 0 && 2 * wyq != m) ? 2 : 1;
+  const int nf = nfx * nfy, nv = nf * nr, nch = (nv + VC - 1) / VC;
+  // vector v: mirror q = v % nf (q % nfx mirrors x, q / nfx mirrors y), rhs v / nf
+  for (long e = threadIdx.x; e < (long)nch * N * VC; e += blockDim.x) {
+    const int v = (int)(e % VC) + VC * (int)(e / (N * VC));
+    const long j = (e / VC) % N;
+    float2 x = make_float2(0.f, 0.f);
+    if (v < nv) {
+      const int q = v % nf, rr = v / nf;
+      const bool fx = (q % nfx) != 0, fy = (q / nfx) != 0;
+      const long f = (fy ? m - wyq : wyq) * l + (fx ? l - wxq : wxq);
+      const long c = j / n;
+      const cx<T> a = t[((long)(r0 + rr) * N + j) * plane + f];
+      const float sg = ((c == 0 && fx) || (c == 1 && fy)) ? -1.f : 1.f;
+      x = make_float2(sg * (float)a.x, sg * (float)a.y);
+    }
+    vin[e] = x;
   }
   __syncthreads();
-  const float2* B = blocks + (size_t)f * N * N;
-  for (long i = wid; i < N; i += nw) {
-    const float2* row = B + i * N;
-    for (int r = 0; r < nrhs; ++r) {
-      float ax = 0.f, ay = 0.f;
-      for (long j = lane; j < N; j += 32) {
-        const float2 b = __ldg(row + j);
-        const cx<T> v = vin[(long)r * N + j];
-        ax += b.x * (float)v.x - b.y * (float)v.y;
-        ay += b.x * (float)v.y + b.y * (float)v.x;
+  const float2* B = blocksT + (size_t)fq * N * N;
+  for (long i = threadIdx.x; i < N; i += blockDim.x) {
+    const long c = i / n;
+    for (int ch = 0; ch < nch; ++ch) {
+      float ax[VC], ay[VC];
+#pragma unroll
+      for (int s = 0; s < VC; ++s) ax[s] = ay[s] = 0.f;
+      const float4* vv = reinterpret_cast<const float4*>(vin + (size_t)ch * N * VC);
+#pragma unroll 4
+      for (long j = 0; j < N; ++j) {
+        const float2 b = __ldg(B + j * N + i);
+#pragma unroll
+        for (int h = 0; h < VC / 2; ++h) {
+          const float4 x = vv[j * (VC / 2) + h];
+          ax[2 * h] += b.x * x.x - b.y * x.y;
+          ay[2 * h] += b.x * x.y + b.y * x.x;
+          ax[2 * h + 1] += b.x * x.z - b.y * x.w;
+          ay[2 * h + 1] += b.x * x.w + b.y * x.z;
+        }
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        ax += __shfl_down_sync(0xffffffffu, ax, o);
-        ay += __shfl_down_sync(0xffffffffu, ay, o);
+      for (int s = 0; s < VC; ++s) {
+        const int v = ch * VC + s;
+        if (v < nv) {
+          const int q = v % nf, rr = v / nf;
+          const bool fx = (q % nfx) != 0, fy = (q / nfx) != 0;
+          const long f = (fy ? m - wyq : wyq) * l + (fx ? l - wxq : wxq);
+          const T sc = ((c == 0 && fx) || (c == 1 && fy)) ? -scale : scale;
+          t[((long)(r0 + rr) * N + i) * plane + f] = mk<T>(sc * (T)ax[s], sc * (T)ay[s]);
+        }
       }
-      if (lane == 0) t[((long)r * N + i) * plane + f] = mk<T>(scale * (T)ax, scale * (T)ay);
+    }
+  }
+}
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  const unsigned saddr = static_cast<unsigned>(__cvta_generic_to_shared(sdst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int K>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(K) : "memory");
+}
+
+constexpr int kP2Stages = 4;  // tiles in the shared-memory ring
+constexpr int kP2Rows = 8;    // block rows per tile
+
+// Multiply-accumulate one block row (b, one value per output row of this
+// thread) into the accumulators, against the VC vector entries of that row.
+template <int VC, int RPT>
+__device__ __forceinline__ void p2_mac(float (&ax)[RPT][VC], float (&ay)[RPT][VC],
+                                       const float2 (&b)[RPT], const float4* __restrict__ x4) {
+#pragma unroll
+  for (int h = 0; h < VC / 2; ++h) {
+    const float4 x = x4[h];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      ax[u][2 * h] = fmaf(b[u].x, x.x, fmaf(-b[u].y, x.y, ax[u][2 * h]));
+      ay[u][2 * h] = fmaf(b[u].x, x.y, fmaf(b[u].y, x.x, ay[u][2 * h]));
+      ax[u][2 * h + 1] = fmaf(b[u].x, x.z, fmaf(-b[u].y, x.w, ax[u][2 * h + 1]));
+      ay[u][2 * h + 1] = fmaf(b[u].x, x.w, fmaf(b[u].y, x.z, ay[u][2 * h + 1]));
+    }
+  }
+}
+
+// The same product with the block streamed through shared memory: tiles of
+// kP2Rows block rows are copied with cp.async, kP2Stages - 1 tiles ahead of
+// the one being multiplied, so that many bytes are in flight per SM while
+// each thread works on RPT output rows from shared memory.  Needs N even
+// (16-byte copies) and N <= RPT * blockDim.x.
+template <typename T, int VC, int RPT>
+__global__ void __launch_bounds__(256)
+    k_block_apply_pipe(cx<T>* __restrict__ t, const float2* __restrict__ blocksT, int r0, int nr,
+                       long l, long m, long n, T scale) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = 3 * (int)n;
+  const long plane = l * m, hx = l / 2 + 1;
+  const long fq = blockIdx.x, wxq = fq % hx, wyq = fq / hx;
+  const int nfx = (wxq != 0 && 2 * wxq != l) ? 2 : 1;
+  const int nfy = (wyq != 0 && 2 * wyq != m) ? 2 : 1;
+  const int nf = nfx * nfy, nv = nf * nr, nch = (nv + VC - 1) / VC;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  float2* sB = reinterpret_cast<float2*>(smem_raw);       // [kP2Stages][kP2Rows][N]
+  float2* vin = sB + kP2Stages * kP2Rows * N;            // [chunk][j][VC]
+  for (int e = tid; e < nch * N * VC; e += nth) {
+    const int v = e % VC + VC * (e / (N * VC));
+    const int j = (e / VC) % N;
+    float2 x = make_float2(0.f, 0.f);
+    if (v < nv) {
+      const int q = v % nf, rr = v / nf;
+      const bool fx = (q % nfx) != 0, fy = (q / nfx) != 0;
+      const long f = (fy ? m - wyq : wyq) * l + (fx ? l - wxq : wxq);
+      const int c = j / (int)n;
+      const cx<T> a = t[((long)(r0 + rr) * N + j) * plane + f];
+      const float sg = ((c == 0 && fx) || (c == 1 && fy)) ? -1.f : 1.f;
+      x = make_float2(sg * (float)a.x, sg * (float)a.y);
+    }
+    vin[e] = x;
+  }
+  const float2* B = blocksT + (size_t)fq * N * N;
+  const int ntiles = (N + kP2Rows - 1) / kP2Rows;
+  auto issue = [&](int tile) {
+    if (tile < ntiles) {
+      const int j0 = tile * kP2Rows;
+      const int rows = min(N - j0, kP2Rows);
+      const int chunks = rows * N / 2;  // 16-byte pieces
+      float2* dst = sB + (tile % kP2Stages) * kP2Rows * N;
+      const float2* src = B + (size_t)j0 * N;
+      for (int c = tid; c < chunks; c += nth) cp_async16(dst + 2 * c, src + 2 * c);
+    }
+    cp_async_commit();
+  };
+  for (int ch = 0; ch < nch; ++ch) {
+    float ax[RPT][VC], ay[RPT][VC];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u)
+#pragma unroll
+      for (int s = 0; s < VC; ++s) ax[u][s] = ay[u][s] = 0.f;
+    const float4* vv = reinterpret_cast<const float4*>(vin + ch * N * VC);
+    for (int st = 0; st < kP2Stages - 1; ++st) issue(st);
+    for (int tile = 0; tile < ntiles; ++tile) {
+      issue(tile + kP2Stages - 1);
+      cp_async_wait<kP2Stages - 1>();
+      __syncthreads();  // the tile (and, first time round, vin) visible to all threads
+      const float2* tb = sB + (tile % kP2Stages) * kP2Rows * N;
+      const float4* x4 = vv + tile * kP2Rows * (VC / 2);
+      const int rows = min(N - tile * kP2Rows, kP2Rows);
+      if (rows == kP2Rows) {
+#pragma unroll
+        for (int jj = 0; jj < kP2Rows; ++jj) {
+          float2 b[RPT];
+#pragma unroll
+          for (int u = 0; u < RPT; ++u) {
+            const int i = tid + u * nth;
+            b[u] = (RPT == 1 || i < N) ? tb[jj * N + i] : make_float2(0.f, 0.f);
+          }
+          p2_mac<VC, RPT>(ax, ay, b, x4 + jj * (VC / 2));
+        }
+      } else {
+        for (int jj = 0; jj < rows; ++jj) {
+          float2 b[RPT];
+#pragma unroll
+          for (int u = 0; u < RPT; ++u) {
+            const int i = tid + u * nth;
+            b[u] = (RPT == 1 || i < N) ? tb[jj * N + i] : make_float2(0.f, 0.f);
+          }
+          p2_mac<VC, RPT>(ax, ay, b, x4 + jj * (VC / 2));
+        }
+      }
+      __syncthreads();  // done with this stage before it is refilled
+    }
+    cp_async_wait<0>();
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      const int i = tid + u * nth;
+      if (i >= N) continue;
+      const int c = i / (int)n;
+#pragma unroll
+      for (int s = 0; s < VC; ++s) {
+        const int v = ch * VC + s;
+        if (v < nv) {
+          const int q = v % nf, rr = v / nf;
+          const bool fx = (q % nfx) != 0, fy = (q / nfx) != 0;
+          const long f = (fy ? m - wyq : wyq) * l + (fx ? l - wxq : wxq);
+          const T sc = ((c == 0 && fx) || (c == 1 && fy)) ? -scale : scale;
+          t[((long)(r0 + rr) * N + i) * plane + f] = mk<T>(sc * (T)ax[u][s], sc * (T)ay[u][s]);
+        }
+      }
     }
   }
 }
@@ -255,23 +440,70 @@ void precond2_apply_impl(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cuda
   const long l = p->l, m = p->m, n = p->n;
   const long lines = (long)nrhs * 3 * n * m;
   const long plane = l * m;
+  const double u = (double)nrhs * 3 * p->nvox * sizeof(cx<T>);
+  const double blk = (double)(l / 2 + 1) * (m / 2 + 1) * 9.0 * n * n * sizeof(float2);
+  p->prof.begin(PROF_PC_XF, s, 2 * u + p->nvox);
   launch_contig<T, false>(v, t, p->mat, nullptr, n * m, lines, (int)l, (int)l, l, (int)l, l, T(1), tw,
                           p->Lmax, s);
+  p->prof.end(s);
+  p->prof.begin(PROF_PC_YF, s, 2 * u);
   if (m > 1)
     launch_strided<T, false>(t, t, l, (long)nrhs * 3 * n, (int)m, (int)m, l, plane, (int)m, l, plane,
                              T(1), tw, p->Lmax, s);
-  const size_t smem = (size_t)nrhs * 3 * n * sizeof(cx<T>);
-  auto kern = k_block_apply<T>;
-  if (smem > 48 * 1024)
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  note_launch();
-  kern<<<(unsigned)plane, 256, smem, s>>>(t, static_cast<const float2*>(p->w.P2), nrhs, n, plane,
-                                          (T)(1.0 / (double)plane));
+  p->prof.end(s);
+  p->prof.begin(PROF_P2_BLOCK, s, 2 * u + blk);
+  {
+    // right-hand sides per launch: four mirrored vectors each, within shared memory
+    const long N = 3 * n;
+    const int VC = nrhs == 1 ? 4 : 8;
+    const unsigned nq = (unsigned)((l / 2 + 1) * (m / 2 + 1));
+    const float2* P2 = static_cast<const float2*>(p->w.P2);
+    const T scale = (T)(1.0 / (double)plane);
+    const bool pipe = N % 2 == 0 && N <= 512;
+    const size_t stage_bytes = pipe ? (size_t)kP2Stages * kP2Rows * N * 8 : 0;
+    const auto smem_of = [&](int nr) {
+      return stage_bytes + (size_t)((4 * nr + VC - 1) / VC) * VC * N * 8;
+    };
+    int group = nrhs;
+    while (group > 1 && smem_of(group) > 200 * 1024) --group;
+    const size_t smem = smem_of(group);
+    void (*kern)(cx<T>*, const float2*, int, int, long, long, long, T) = nullptr;
+    void (*kpipe)(cx<T>*, const float2*, int, int, long, long, long, T) = nullptr;
+    int nth;
+    if (pipe) {
+      const int rpt = N > 256 ? 2 : 1;
+      if (VC == 4)
+        kpipe = rpt == 1 ? k_block_apply_pipe<T, 4, 1> : k_block_apply_pipe<T, 4, 2>;
+      else
+        kpipe = rpt == 1 ? k_block_apply_pipe<T, 8, 1> : k_block_apply_pipe<T, 8, 2>;
+      nth = (int)((N / rpt + 31) / 32 * 32);
+      if (smem > 48 * 1024)
+        cudaFuncSetAttribute(kpipe, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    } else {
+      kern = VC == 4 ? k_block_apply<T, 4> : k_block_apply<T, 8>;
+      nth = (int)std::min<long>(256, (N + 31) / 32 * 32);
+      if (smem > 48 * 1024)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    for (int r0 = 0; r0 < nrhs; r0 += group) {
+      const int nr = std::min(group, nrhs - r0);
+      note_launch();
+      if (pipe)
+        kpipe<<<nq, nth, smem, s>>>(t, P2, r0, nr, l, m, n, scale);
+      else
+        kern<<<nq, nth, smem, s>>>(t, P2, r0, nr, l, m, n, scale);
+    }
+  }
+  p->prof.end(s);
+  p->prof.begin(PROF_PC_YI, s, 2 * u);
   if (m > 1)
     launch_strided<T, true>(t, t, l, (long)nrhs * 3 * n, (int)m, (int)m, l, plane, (int)m, l, plane,
                             T(1), tw, p->Lmax, s);
+  p->prof.end(s);
+  p->prof.begin(PROF_PC_XI, s, 2 * u + p->nvox);
   launch_contig<T, true>(t, z, nullptr, p->mat, n * m, lines, (int)l, (int)l, l, (int)l, l, T(1), tw,
                          p->Lmax, s);
+  p->prof.end(s);
 }
 
 }  // namespace
@@ -302,13 +534,14 @@ extern "C" dda_status_t dda_precond2_build(dda_plan_t p, void* stream) {
                                1.0, tw_of<double>(p), p->Lmax, s);
   const double2 at = make_double2(p->ainv_host[0], p->ainv_host[1]);  // rhs 0, entry 0
   const double dx3 = p->d.dx * p->d.dx * p->d.dx;
+  const long nq = (l / 2 + 1) * (m / 2 + 1);  // stored quadrant of frequency pairs
   note_launch();
-  k_assemble2<<<grid_for(l * m * N * N, 256), 256, 0, s>>>(c2, static_cast<float2*>(p->w.P2), l, m,
-                                                          n, dx3, at);
+  k_assemble2<<<grid_for(nq * N * N, 256), 256, 0, s>>>(c2, static_cast<float2*>(p->w.P2), l, m, n,
+                                                       dx3, at);
   cudaMemsetAsync(p->w.err_flag, 0, 4, s);
   const size_t smem = (size_t)N * (2 * sizeof(float2) + sizeof(int));
   note_launch();
-  k_gauss_jordan<<<(unsigned)(l * m), 1024, smem, s>>>(static_cast<float2*>(p->w.P2), (int)N,
+  k_gauss_jordan<<<(unsigned)nq, 1024, smem, s>>>(static_cast<float2*>(p->w.P2), (int)N,
                                                       static_cast<int*>(p->w.err_flag));
   int err = 0;
   cudaMemcpyAsync(&err, p->w.err_flag, sizeof(int), cudaMemcpyDeviceToHost, s);

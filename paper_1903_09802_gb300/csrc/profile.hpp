@@ -23,6 +23,7 @@ enum ProfId {
   PROF_PC_XI,
   PROF_AR_DOT,     // Gram-Schmidt dot products
   PROF_AR_UPD,     // Gram-Schmidt update and norm
+  PROF_P2_BLOCK,   // 2-level preconditioner: dense block per frequency pair
   PROF_COUNT
 };
 

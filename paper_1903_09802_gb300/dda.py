@@ -40,7 +40,7 @@ EXPORTS = ("dda_workspace_size", "dda_plan_create", "dda_set_incidence", "dda_in
            "dda_last_error", "dda_launch_count")
 
 PROFILE_NAMES = ("mv_x_fwd", "mv_y_fwd", "mv_z_mul", "mv_y_inv", "mv_x_inv", "pc_x_fwd", "pc_y_fwd",
-                 "pc_z_solve", "pc_y_inv", "pc_x_inv", "gs_dots", "gs_update")
+                 "pc_z_solve", "pc_y_inv", "pc_x_inv", "gs_dots", "gs_update", "p2_block")
 
 
 class DDAError(RuntimeError):

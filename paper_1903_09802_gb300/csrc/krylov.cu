@@ -259,6 +259,105 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? 3 : 1)
   if (threadIdx.x == 0) tickets[r] = 0;
 }
 
+// The same dot products with one warp per basis vector: warp q of a block
+// sums conj(V_i[k]) w[k] over the block's chunk for i = q, q + NW, ...
+// (index jc stands for ||w||^2), one compensated accumulator pair per lane
+// and one shuffle reduction per vector, no block barrier between vectors.
+// w is re-read by every warp of the block from L1.  Needs an even vector
+// length (16-byte pairs).  The last block of each right-hand side sums the
+// blocks' partials (four slots per warp at a time) into the Hessenberg
+// column as k_multidot does.
+constexpr int kDotNT = 128;
+template <typename T>
+__global__ void __launch_bounds__(kDotNT)
+    k_dots_w(const cx<T>* __restrict__ V, const cx<T>* __restrict__ W, long nu, long vstride,
+             int jc, double2* __restrict__ partial, int pst, const int* __restrict__ mask,
+             const int* __restrict__ mask2, int want_norm, int* __restrict__ tickets,
+             double2* __restrict__ hcol, double2* __restrict__ H, int m, int j, int pass,
+             double* __restrict__ scal) {
+  constexpr int NW = kDotNT / 32;
+  __shared__ int s_last;
+  const int r = blockIdx.y;
+  if (!mask[r] || (mask2 != nullptr && !mask2[r])) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  long k0, k1;
+  chunk_of(nu, gridDim.x, k0, k1);
+  const cx<T>* w = W + r * nu;
+  const cx<T>* vb = V + r * nu;
+  double2* out = partial + ((long)r * gridDim.x + blockIdx.x) * pst;
+  const int ntot = jc + (want_norm ? 1 : 0);
+  for (int i = wid; i < ntot; i += NW) {
+    Acc<T> ar, ai;
+    if (i < jc) {
+      const cx<T>* v = vb + (long)i * vstride;
+#pragma unroll 8
+      for (long k = k0 + 2 * lane; k < k1; k += 64) {
+        const Pair<T> a = ld2(v + k);
+        const Pair<T> b = ld2(w + k);
+        ar.add(a.a.x * b.a.x + a.a.y * b.a.y);
+        ai.add(a.a.x * b.a.y - a.a.y * b.a.x);
+        ar.add(a.b.x * b.b.x + a.b.y * b.b.y);
+        ai.add(a.b.x * b.b.y - a.b.y * b.b.x);
+      }
+    } else {
+#pragma unroll 8
+      for (long k = k0 + 2 * lane; k < k1; k += 64) {
+        const Pair<T> b = ld2(w + k);
+        ar.add(norm2(b.a));
+        ar.add(norm2(b.b));
+      }
+    }
+    const double tr = ar.warp_total();
+    const double ti = ai.warp_total();
+    if (lane == 0) out[i < jc ? i : pst - 2] = make_double2(tr, ti);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&tickets[r], 1) == (int)gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const int nblk = gridDim.x;
+  constexpr int SB = 4;  // slots per warp at a time: more loads in flight
+  for (int i0 = wid * SB; i0 < ntot; i0 += NW * SB) {
+    double2 a[SB];
+#pragma unroll
+    for (int u = 0; u < SB; ++u) a[u] = make_double2(0.0, 0.0);
+    for (int b = lane; b < nblk; b += 32) {
+      const double2* pb = partial + ((long)r * nblk + b) * pst;
+#pragma unroll
+      for (int u = 0; u < SB; ++u) {
+        const int i = i0 + u;
+        if (i < ntot) {
+          const double2 v = __ldcg(pb + (i < jc ? i : pst - 2));
+          a[u].x += v.x;
+          a[u].y += v.y;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < SB; ++u) {
+      const int i = i0 + u;
+      const double2 t = warp_sum(a[u]);
+      if (lane == 0 && i < ntot) {
+        if (i < jc) {
+          hcol[(long)r * (m + 2) + i] = t;
+          double2* h = H + (long)r * (m + 1) * m + (long)j * (m + 1) + i;
+          if (pass == 0) {
+            *h = t;
+          } else {
+            h->x += t.x;
+            h->y += t.y;
+          }
+        } else {
+          scal[(long)r * 16 + 7] = t.x;  // ||w||^2 before Gram-Schmidt
+        }
+      }
+    }
+  }
+  if (threadIdx.x == 0) tickets[r] = 0;
+}
+
 // w -= sum_{i < jc} h_i V_i, and the block's share of ||w||^2 into
 // partial[...][pst - 1].  16-byte pairs, two per thread and trip (VEC).
 template <typename T, bool VEC>
@@ -828,6 +927,7 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
   double2* R = static_cast<double2*>(p->w.R128);
   const long vstride = (long)nrhs * nu;
   const dim3 vgrid(nblk, nrhs);
+  const dim3 dgrid(p->w.nblk, nrhs);  // warp-per-vector dots: the plan's full block count
   const bool prec = o.precond != 0;
   auto apply_prec = [&](const cx<T>* in, cx<T>* out) {
     if (o.precond == 2)
@@ -978,9 +1078,9 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
         if (pass == 0) p->prof.begin(PROF_AR_DOT, s, (j + 2) * vb);
         note_launch();
         if (vec)
-          k_multidot<T, true><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.partial, pst,
-                                                    st.active, mask2, pass == 0, st.tickets,
-                                                    st.hcol, st.H, m, j, pass, st.scal);
+          k_dots_w<T><<<dgrid, kDotNT, 0, s>>>(V, W, nu, vstride, j + 1, st.partial, pst,
+                                               st.active, mask2, pass == 0, st.tickets, st.hcol,
+                                               st.H, m, j, pass, st.scal);
         else
           k_multidot<T, false><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.partial, pst,
                                                      st.active, mask2, pass == 0, st.tickets,

@@ -171,9 +171,9 @@ dda_status_t dda_precond_apply(dda_plan_t plan, int32_t prec, int32_t nrhs, cons
                                void* d_z, void* stream);
 
 /* dda_precond_apply for callers that cannot allocate device memory during
- * the call: code running while a stream is captured into a CUDA graph,
- * hosts whose device memory is fixed at start-up, frameworks that own the
- * device through their own pool.  The paper has no counterpart; this is a
+ * the call: real-time or embedded hosts whose device memory is fixed at
+ * start-up, frameworks that own every byte of the device through their own
+ * pool and forbid allocations from outside it.  The paper has no counterpart; this is a
  * deployment variant.  Same arguments and result as dda_precond_apply, but
  * the transform's scratch (nrhs * 3 * l*m*n complex values) lives in a
  * 32 MiB array compiled into the library instead of the plan's workspace;
@@ -187,10 +187,10 @@ dda_status_t dda_precond_apply(dda_plan_t plan, int32_t prec, int32_t nrhs, cons
 dda_status_t dda_precond_apply_noalloc(dda_plan_t plan, int32_t prec, int32_t nrhs,
                                        const void* d_v, void* d_z, void* stream);
 
-/* The paper's 2-level circulant preconditioner (Section 3.1, eqs. 17-19):
- * T. Chan's circulant (eq. 13) on the x and y levels, the z level kept
- * Toeplitz, so after a 2-D DFT every frequency pair (wx, wy) carries a dense
- * 3n x 3n block alpha_tilde^{-1} I - dx^3 Chat2(wx, wy), inverted on the GPU
+/* The paper's 2-level circulant preconditioner (Section 3, eqs. 17-19; the
+ * block inversion of Section 3.1): T. Chan's circulant (eq. 13) on the x and
+ * y levels, the z level kept Toeplitz, so after a 2-D DFT every frequency
+ * pair (wx, wy) carries a dense 3n x 3n block alpha_tilde^{-1} I - dx^3 Chat2(wx, wy), inverted on the GPU
  * (Gauss-Jordan with partial pivoting, complex64) and stored.  alpha_tilde is
  * that of the first right-hand side of the current incidence (call after
  * dda_set_incidence; the blocks serve the whole batch).  Needs a plan with

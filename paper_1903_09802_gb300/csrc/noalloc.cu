@@ -1,9 +1,8 @@
 // dda_precond_apply_noalloc: the preconditioner apply for callers that must
-// not allocate device memory while they run.  Examples are code that
-// executes while a CUDA stream is being captured into a graph (an
-// allocation in a capturing stream is an error), real-time or embedded
-// hosts whose device memory is fixed at start-up, and frameworks that own
-// every byte of the device through their own pool.  The ordinary entry
+// not allocate device memory while they run.  Examples are real-time or
+// embedded hosts whose device memory is fixed at start-up, and frameworks
+// that own every byte of the device through their own pool and forbid
+// allocations from outside it.  The ordinary entry
 // point keeps its transform in the plan's workspace; this one keeps it in a
 // fixed array compiled into the library, so the call itself reserves
 // nothing.

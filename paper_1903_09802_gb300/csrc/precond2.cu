@@ -1,4 +1,5 @@
-// The paper's 2-level circulant preconditioner (Section 3.1, eqs. 17-19).
+// The paper's 2-level circulant preconditioner (Section 3, eqs. 17-19; the
+// block inversion of Section 3.1).
 //
 // Build: T. Chan's optimal circulant (eq. 13) is applied on the x and y
 // levels of each of the six blocks, the z level stays Toeplitz:

@@ -1,5 +1,6 @@
-"""The paper's 2-level circulant preconditioner (Section 3.1, eqs. 17-19) on the
-GPU vs the oracle: apply parity, solves, error paths.
+"""The paper's 2-level circulant preconditioner (Section 3, eqs. 17-19; the
+block inversion of Section 3.1) on the GPU vs the oracle: apply parity,
+solves, error paths.
 
 The GPU inverts the 3n x 3n frequency blocks in complex64 and multiplies with
 FP32 accumulation, so the tolerance is derived from the blocks' condition

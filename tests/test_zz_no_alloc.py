@@ -1,9 +1,9 @@
 """dda_precond_apply_noalloc, the preconditioner apply that allocates nothing.
 
-Callers that cannot allocate device memory while they run (a stream being
-captured into a CUDA graph, a host with device memory fixed at start-up, a
-framework owning the device through its own pool) use this entry point; its
-scratch is a fixed array inside the library.  This file is collected last so
+Callers that cannot allocate device memory while they run (a host with
+device memory fixed at start-up, a framework owning every byte of the device
+through its own pool) use this entry point; its scratch is a fixed array
+inside the library.  This file is collected last so
 that a failure here comes after every other test has run.
 """
 import ctypes

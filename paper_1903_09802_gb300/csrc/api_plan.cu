@@ -171,6 +171,7 @@ __device__ __forceinline__ bool padded_offset(long p, long l, long Lp, long& o) 
 // BTTB block is embedded in a circulant of twice the size per level).
 __global__ void k_green_generator(double2* out, int c, long l, long m, long n, long Lx, long Ly,
                                   long Lz, double dx, double k) {
+  pdl_entry();
   const long P = Lx * Ly * Lz;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < P;
        i += (long)gridDim.x * blockDim.x) {
@@ -188,6 +189,7 @@ __global__ void k_green_generator(double2* out, int c, long l, long m, long n, l
 // from the block's parity) as component c of the interleaved [..][6] store.
 __global__ void k_compress(const double2* full, long Lx, long Ly, long Lz, long hx, long hy,
                            long hz, int c, double2* out128, float2* out64) {
+  pdl_entry();
   const long H = hx * hy * hz;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < H;
        i += (long)gridDim.x * blockDim.x) {
@@ -201,6 +203,7 @@ __global__ void k_compress(const double2* full, long Lx, long Ly, long Lz, long 
 // E_inc = pol exp(i k dir . r) on scatterer voxels, r from the box centre.
 __global__ void k_incident(double2* b, const uint8_t* mat, const double* inc, int nrhs, long l,
                            long m, long n, double dx, double k, double sgn) {
+  pdl_entry();
   const long nvox = l * m * n;
   const long tot = nvox * nrhs;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < tot;

@@ -4,6 +4,8 @@
 
 #include <cuda_runtime.h>
 
+#include "launch.cuh"
+
 namespace dda {
 
 template <typename R>

@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(NB * L / kElemsPerThread, 1024 / (NB * L / kEl
     k_ct_strided(const cx<T>* in, cx<T>* out, long ncols, int Lin, long in_js, long in_ss,
                  int Lout, long out_js, long out_ss, T scale, const cx<T>* __restrict__ tw,
                  int twshift) {
+  pdl_entry();
   constexpr int NTH = NB * L / kElemsPerThread;
   constexpr int JSTEP = NTH / NB;  // = L / 16
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -148,6 +149,7 @@ __global__ void __launch_bounds__(NB * L / kElemsPerThread, 1024 / (NB * L / kEl
                 const uint8_t* __restrict__ omask, long mask_lines, long nlines, int Lin,
                 long in_ld, int Lout, long out_ld, T scale, const cx<T>* __restrict__ tw,
                 int twshift) {
+  pdl_entry();
   static_assert(NB >= 16, "one position per thread");
   constexpr int NTH = NB * L / kElemsPerThread;
   constexpr int LD = NB + 1;
@@ -202,6 +204,7 @@ __global__ void __launch_bounds__(3 * NBC * L / kElemsPerThread,
                                       : 1)
     k_ct_fft3c(cx<T>* data, long ncols, int Lin, long js, long cs, long ss, int Lout, Op op,
                const cx<T>* __restrict__ tw, int twshift, int row_len, int nrows) {
+  pdl_entry();
   constexpr int LD = 3 * NBC;
   constexpr int NTH = LD * L / kElemsPerThread;
   constexpr int JSTEP = L / 16;
@@ -280,7 +283,7 @@ void ct_fft3c_launch(cx<float>* data, long ncols, long nslabs, int Lin, long js,
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const long grid = nslabs * (ncols / NBC);
   note_launch();
-  kern<<<(unsigned)grid, NTH, smem, s>>>(data, ncols, Lin, js, cs, ss, Lout, op, tw, Lmax / L,
+  launch_k(kern, (unsigned)grid, NTH, smem, s, data, ncols, Lin, js, cs, ss, Lout, op, tw, Lmax / L,
                                          row_len, nrows);
 }
 

@@ -32,6 +32,7 @@ __global__ void __launch_bounds__(256)
                  const uint8_t* __restrict__ omask, long mask_lines, long nlines, int Lin,
                  long in_ld, int Lout, long out_ld, T scale, const cx<T>* __restrict__ tw,
                  int twshift, RadixPlan rp, int nb_sh) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
   const int L = 1 << rp.lg;
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(512)
     k_fft_strided(const cx<T>* in, cx<T>* out, long ncols, int Lin, long in_js, long in_ss,
                   int Lout, long out_js, long out_ss, T scale, const cx<T>* __restrict__ tw,
                   int twshift, RadixPlan rp, int nb_sh) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
   const int L = 1 << rp.lg;
@@ -194,6 +196,7 @@ __global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 768)
     k_fft3c(cx<T>* data, long ncols, int Lin, long js, long cs, long ss, int Lout, Op op,
             const cx<T>* __restrict__ tw, int twshift, RadixPlan rp, int nbc_sh, int row_len,
             int nrows) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
   const int L = 1 << rp.lg;
@@ -379,7 +382,7 @@ void launch_fft3c(cx<T>* data, long ncols, long nslabs, int L, int Lin, long js,
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   note_launch();
-  kern<<<(unsigned)grid, nth, smem, s>>>(data, ncols, Lin, js, cs, ss, Lout, op, tw, Lmax / L,
+  launch_k(kern, (unsigned)grid, nth, smem, s, data, ncols, Lin, js, cs, ss, Lout, op, tw, Lmax / L,
                                          make_radix_plan(L), ilog2i(NBc), row_len, nrows);
 }
 

@@ -43,7 +43,7 @@ void ct_strided_launch(const cx<float>* in, cx<float>* out, long ncols, long nsl
   auto kern = k_ct_strided<float, INV, L, NB, HI, HO>;
   allow_smem(kern, smem);
   note_launch();
-  kern<<<(unsigned)(nslabs * (ncols / NB)), NB * L / kElemsPerThread, smem, s>>>(
+  launch_k(kern, (unsigned)(nslabs * (ncols / NB)), NB * L / kElemsPerThread, smem, s,
       in, out, ncols, Lin, in_js, in_ss, Lout, out_js, out_ss, scale, tw, Lmax / L);
 }
 
@@ -77,7 +77,7 @@ void ct_contig_launch(const cx<float>* in, cx<float>* out, const uint8_t* mask,
   auto kern = k_ct_contig<float, INV, L, NB, HI, HO>;
   allow_smem(kern, smem);
   note_launch();
-  kern<<<(unsigned)((nlines + NB - 1) / NB), NB * L / kElemsPerThread, smem, s>>>(
+  launch_k(kern, (unsigned)((nlines + NB - 1) / NB), NB * L / kElemsPerThread, smem, s,
       in, out, mask, omask, mask_lines, nlines, Lin, in_ld, Lout, out_ld, scale, tw, Lmax / L);
 }
 
@@ -133,7 +133,7 @@ void launch_contig(const cx<T>* in, cx<T>* out, const uint8_t* mask, const uint8
   auto kern = k_fft_contig<T, INV>;
   allow_smem(kern, smem);
   note_launch();
-  kern<<<(unsigned)grid, nth, smem, s>>>(in, out, mask, omask, mask_lines, nlines, Lin, in_ld, Lout,
+  launch_k(kern, (unsigned)grid, nth, smem, s, in, out, mask, omask, mask_lines, nlines, Lin, in_ld, Lout,
                                          out_ld, scale, tw, Lmax / L, make_radix_plan(L),
                                          ilog2i(NB));
 }
@@ -171,7 +171,7 @@ void launch_strided(const cx<T>* in, cx<T>* out, long ncols, long nslabs, int L,
   auto kern = L >= 16 ? k_fft_strided<T, INV, true> : k_fft_strided<T, INV, false>;
   allow_smem(kern, smem);
   note_launch();
-  kern<<<(unsigned)grid, nth, smem, s>>>(in, out, ncols, Lin, in_js, in_ss, Lout, out_js, out_ss,
+  launch_k(kern, (unsigned)grid, nth, smem, s, in, out, ncols, Lin, in_js, in_ss, Lout, out_js, out_ss,
                                          scale, tw, Lmax / L, make_radix_plan(L), ilog2i(NB));
 }
 

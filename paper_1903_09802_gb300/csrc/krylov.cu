@@ -155,6 +155,7 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? 3 : 1)
                const int* __restrict__ mask2, int want_norm, int* __restrict__ tickets,
                double2* __restrict__ hcol, double2* __restrict__ H, int m, int j, int pass,
                double* __restrict__ scal) {
+  pdl_entry();
   constexpr int ND = 8;
   constexpr int NW = kNT / 32;
   __shared__ double2 sh[ND][NW];
@@ -275,6 +276,7 @@ __global__ void __launch_bounds__(kDotNT)
              const int* __restrict__ mask2, int want_norm, int* __restrict__ tickets,
              double2* __restrict__ hcol, double2* __restrict__ H, int m, int j, int pass,
              double* __restrict__ scal) {
+  pdl_entry();
   constexpr int NW = kDotNT / 32;
   __shared__ int s_last;
   const int r = blockIdx.y;
@@ -367,10 +369,14 @@ __global__ void __launch_bounds__(kNT)
              const int* __restrict__ mask, const int* __restrict__ mask2, int* __restrict__ tickets,
              double* __restrict__ scal, int pass, int* __restrict__ reorth,
              int* __restrict__ reorth_count, double eta2) {
+  pdl_entry();
   __shared__ cx<T> hs[520];
   __shared__ double2 sh[32];
   __shared__ int s_last;
-  const int r = blockIdx.y;
+  // Blocks run roughly in launch order; the dots pass just walked the basis
+  // from the first right-hand side's first chunk to the last one's last
+  // chunk, so this pass walks it backwards and starts on what is still in L2.
+  const int r = gridDim.y - 1 - blockIdx.y;
   if (!mask[r] || (mask2 != nullptr && !mask2[r])) return;
   for (int i = threadIdx.x; i < jc; i += kNT) {
     const double2 h = hcol[(long)r * (m + 2) + i];
@@ -378,7 +384,12 @@ __global__ void __launch_bounds__(kNT)
   }
   __syncthreads();
   long k0, k1;
-  chunk_of(nu, gridDim.x, k0, k1);
+  {
+    long chunk = (nu + gridDim.x - 1) / gridDim.x;
+    chunk += chunk & 1;
+    k0 = min(nu, (long)(gridDim.x - 1 - blockIdx.x) * chunk);
+    k1 = min(nu, k0 + chunk);
+  }
   cx<T>* w = W + r * nu;
   const cx<T>* vb = V + r * nu;
   Acc<T> nn;
@@ -469,6 +480,7 @@ __global__ void k_givens(double2* __restrict__ H, double* __restrict__ cs, doubl
                          double2* __restrict__ g, double* __restrict__ scal,
                          int* __restrict__ active, int* __restrict__ jlen, int* __restrict__ flags,
                          int* __restrict__ iters, int nrhs, int m, int j, double brk) {
+  pdl_entry();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrhs || !active[r]) return;
   const double n2 = scal[(long)r * 16 + 8];  // ||w||^2 after Gram-Schmidt
@@ -518,6 +530,7 @@ template <typename T>
 __global__ void __launch_bounds__(kNT)
     k_scale(const cx<T>* __restrict__ W, cx<T>* __restrict__ Vn, long nu,
             const double* __restrict__ scal, const int* __restrict__ active) {
+  pdl_entry();
   const int r = blockIdx.y;
   if (!active[r]) return;
   const T inv = (T)scal[(long)r * 16 + 5];
@@ -528,6 +541,7 @@ __global__ void __launch_bounds__(kNT)
 
 // Number of right-hand sides still iterating.
 __global__ void k_count_active(const int* __restrict__ active, int nrhs, int* __restrict__ out) {
+  pdl_entry();
   int c = 0;
   for (int r = threadIdx.x; r < nrhs; r += blockDim.x) c += active[r];
 #pragma unroll
@@ -538,6 +552,7 @@ __global__ void k_count_active(const int* __restrict__ active, int nrhs, int* __
 // Back substitution R y = g with the rotated (upper triangular) H.
 __global__ void k_trisolve(const double2* __restrict__ H, const double2* __restrict__ g,
                            const int* __restrict__ jlen, double2* __restrict__ y, int nrhs, int m) {
+  pdl_entry();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrhs) return;
   const int jl = jlen[r];
@@ -563,6 +578,7 @@ template <typename T>
 __global__ void __launch_bounds__(kNT)
     k_combine(const cx<T>* __restrict__ V, const double2* __restrict__ y,
               const int* __restrict__ jlen, cx<T>* __restrict__ U, long nu, long vstride, int m) {
+  pdl_entry();
   __shared__ cx<T> ys[520];
   const int r = blockIdx.y;
   const int jl = jlen[r];
@@ -586,6 +602,7 @@ template <typename T>
 __global__ void __launch_bounds__(kNT)
     k_add_x(double2* __restrict__ x, const cx<T>* __restrict__ z, const int* __restrict__ jlen,
             long nu) {
+  pdl_entry();
   const int r = blockIdx.y;
   if (jlen[r] == 0) return;
   long k0, k1;
@@ -603,6 +620,7 @@ __global__ void __launch_bounds__(kNT)
 __global__ void __launch_bounds__(kNT)
     k_residual(const double2* __restrict__ b, double2* __restrict__ ax, long nu,
                double2* __restrict__ part) {
+  pdl_entry();
   __shared__ double2 sh[32];
   const int r = blockIdx.y;
   long k0, k1;
@@ -622,6 +640,7 @@ __global__ void __launch_bounds__(kNT)
 
 __global__ void k_finish_norms(const double2* __restrict__ part, int nblk, int nrhs,
                                double* __restrict__ scal) {
+  pdl_entry();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrhs) return;
   double rr = 0.0, bb = 0.0;
@@ -640,6 +659,7 @@ __global__ void __launch_bounds__(kNT)
                   double* __restrict__ scal, double2* __restrict__ g, int m,
                   const int* __restrict__ run, int* __restrict__ active, int* __restrict__ jlen,
                   double tol, double inner_tol) {
+  pdl_entry();
   const int r = blockIdx.y;
   const double beta = scal[(long)r * 16 + 6];
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -674,6 +694,7 @@ __global__ void __launch_bounds__(kNT)
             const cx<T>* __restrict__ a2, const cx<T>* __restrict__ b2, long nu,
             const int* __restrict__ mask, double2* __restrict__ partial,
             int* __restrict__ tickets, double* __restrict__ bs, int slot) {
+  pdl_entry();
   __shared__ double2 sh[ND][kNT / 32];
   __shared__ int s_last;
   const int r = blockIdx.y;
@@ -742,6 +763,7 @@ __device__ __forceinline__ double2 cmul2(double2 a, double2 b) {
 // A zero denominator is a breakdown: the cycle of that right-hand side ends.
 __global__ void k_bscalar(int op, double* __restrict__ bs, int* __restrict__ active,
                           int* __restrict__ flags, int nrhs) {
+  pdl_entry();
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrhs) return;
   double* q = bs + (long)r * 16;
@@ -802,6 +824,7 @@ __global__ void __launch_bounds__(kNT)
             cx<T>* __restrict__ D, long nu, const double* __restrict__ bs_in,
             double* __restrict__ bs, int* __restrict__ active, int* __restrict__ iters,
             double2* __restrict__ partial, int* __restrict__ tickets) {
+  pdl_entry();
   __shared__ double2 sh[32];
   __shared__ int s_last;
   const int r = blockIdx.y;
@@ -871,6 +894,7 @@ __global__ void __launch_bounds__(kNT)
              cx<T>* __restrict__ p, cx<T>* __restrict__ v, cx<T>* __restrict__ D, long nu,
              const double* __restrict__ scal, double* __restrict__ bs, const int* __restrict__ run,
              int* __restrict__ active, double tol, double inner_tol) {
+  pdl_entry();
   const int r = blockIdx.y;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     active[r] = run[r];
@@ -899,6 +923,7 @@ template <typename T>
 __global__ void __launch_bounds__(kNT)
     k_badd_x(double2* __restrict__ x, const cx<T>* __restrict__ d, const int* __restrict__ run,
              long nu) {
+  pdl_entry();
   const int r = blockIdx.y;
   if (!run[r]) return;
   long k0, k1;
@@ -1011,40 +1036,40 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
                                         o.tol, o.inner_tol);
       for (int it = 0; it < steps; ++it) {
         note_launch();
-        k_bdots<T, 1><<<vgrid, kNT, 0, s>>>(Vrh, Vr, nullptr, nullptr, nu, st.active, st.partial,
+        launch_k(k_bdots<T, 1>, vgrid, kNT, 0, s, Vrh, Vr, nullptr, nullptr, nu, st.active, st.partial,
                                             st.tickets, bs, 6);
         note_launch();
-        k_bscalar<<<sg, 64, 0, s>>>(0, bs, st.active, st.flags, nrhs);
+        launch_k(k_bscalar, sg, 64, 0, s, 0, bs, st.active, st.flags, nrhs);
         note_launch();
-        k_baxpy<T><<<vgrid, kNT, 0, s>>>(0, Vp, nullptr, Vr, Vv, nullptr, nullptr, nu, bs, bs,
+        launch_k(k_baxpy<T>, vgrid, kNT, 0, s, 0, Vp, nullptr, Vr, Vv, nullptr, nullptr, nu, bs, bs,
                                          st.active, st.iters, st.partial, tk2);
         if (prec) apply_prec(Vp, Vph);
         matvec_impl<T>(p, nrhs, Vph, Vv, s);
         note_launch();
-        k_bdots<T, 1><<<vgrid, kNT, 0, s>>>(Vrh, Vv, nullptr, nullptr, nu, st.active, st.partial,
+        launch_k(k_bdots<T, 1>, vgrid, kNT, 0, s, Vrh, Vv, nullptr, nullptr, nu, st.active, st.partial,
                                             st.tickets, bs, 6);
         note_launch();
-        k_bscalar<<<sg, 64, 0, s>>>(1, bs, st.active, st.flags, nrhs);
+        launch_k(k_bscalar, sg, 64, 0, s, 1, bs, st.active, st.flags, nrhs);
         note_launch();
-        k_baxpy<T><<<vgrid, kNT, 0, s>>>(1, nullptr, Vs, Vr, Vv, nullptr, nullptr, nu, bs, bs,
+        launch_k(k_baxpy<T>, vgrid, kNT, 0, s, 1, nullptr, Vs, Vr, Vv, nullptr, nullptr, nu, bs, bs,
                                          st.active, st.iters, st.partial, tk2);
         note_launch();
-        k_baxpy<T><<<vgrid, kNT, 0, s>>>(2, nullptr, nullptr, Vph, nullptr, nullptr, D, nu, bs, bs,
+        launch_k(k_baxpy<T>, vgrid, kNT, 0, s, 2, nullptr, nullptr, Vph, nullptr, nullptr, D, nu, bs, bs,
                                          st.active, st.iters, st.partial, tk2);
         note_launch();
-        k_bscalar<<<sg, 64, 0, s>>>(3, bs, st.active, st.flags, nrhs);
+        launch_k(k_bscalar, sg, 64, 0, s, 3, bs, st.active, st.flags, nrhs);
         if (prec) apply_prec(Vs, Vsh);
         matvec_impl<T>(p, nrhs, Vsh, Vt, s);
         note_launch();
-        k_bdots<T, 2><<<vgrid, kNT, 0, s>>>(Vt, Vs, Vt, Vt, nu, st.active, st.partial, st.tickets,
+        launch_k(k_bdots<T, 2>, vgrid, kNT, 0, s, Vt, Vs, Vt, Vt, nu, st.active, st.partial, st.tickets,
                                             bs, 6);
         note_launch();
-        k_bscalar<<<sg, 64, 0, s>>>(2, bs, st.active, st.flags, nrhs);
+        launch_k(k_bscalar, sg, 64, 0, s, 2, bs, st.active, st.flags, nrhs);
         note_launch();
-        k_baxpy<T><<<vgrid, kNT, 0, s>>>(3, Vr, Vs, Vph, Vsh, Vt, D, nu, bs, bs, st.active,
+        launch_k(k_baxpy<T>, vgrid, kNT, 0, s, 3, Vr, Vs, Vph, Vsh, Vt, D, nu, bs, bs, st.active,
                                          st.iters, st.partial, tk2);
         note_launch();
-        k_count_active<<<1, 32, 0, s>>>(st.active, nrhs, st.counters + (it & 1));
+        launch_k(k_count_active, 1, 32, 0, s, st.active, nrhs, st.counters + (it & 1));
         cudaMemcpyAsync(p->pinned + (it & 1), st.counters + (it & 1), sizeof(int),
                         cudaMemcpyDeviceToHost, s);
         cudaEventRecord(ev[it & 1], s);
@@ -1078,36 +1103,36 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
         if (pass == 0) p->prof.begin(PROF_AR_DOT, s, (j + 2) * vb);
         note_launch();
         if (vec)
-          k_dots_w<T><<<dgrid, kDotNT, 0, s>>>(V, W, nu, vstride, j + 1, st.partial, pst,
+          launch_k(k_dots_w<T>, dgrid, kDotNT, 0, s, V, W, nu, vstride, j + 1, st.partial, pst,
                                                st.active, mask2, pass == 0, st.tickets, st.hcol,
                                                st.H, m, j, pass, st.scal);
         else
-          k_multidot<T, false><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.partial, pst,
+          launch_k(k_multidot<T, false>, vgrid, kNT, 0, s, V, W, nu, vstride, j + 1, st.partial, pst,
                                                      st.active, mask2, pass == 0, st.tickets,
                                                      st.hcol, st.H, m, j, pass, st.scal);
         if (pass == 0) p->prof.end(s);
         if (pass == 0) p->prof.begin(PROF_AR_UPD, s, (j + 3) * vb);
         note_launch();
         if (vec)
-          k_update<T, true><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.hcol, m, st.partial,
+          launch_k(k_update<T, true>, vgrid, kNT, 0, s, V, W, nu, vstride, j + 1, st.hcol, m, st.partial,
                                                   pst, st.active, mask2, st.tickets + nrhs,
                                                   st.scal, pass, st.reorth, st.reorth_count, eta2);
         else
-          k_update<T, false><<<vgrid, kNT, 0, s>>>(V, W, nu, vstride, j + 1, st.hcol, m,
+          launch_k(k_update<T, false>, vgrid, kNT, 0, s, V, W, nu, vstride, j + 1, st.hcol, m,
                                                    st.partial, pst, st.active, mask2,
                                                    st.tickets + nrhs, st.scal, pass, st.reorth,
                                                    st.reorth_count, eta2);
         if (pass == 0) p->prof.end(s);
       }
       note_launch();
-      k_givens<<<(nrhs + 63) / 64, 64, 0, s>>>(st.H, st.cs, st.sn, st.g, st.scal, st.active,
+      launch_k(k_givens, (nrhs + 63) / 64, 64, 0, s, st.H, st.cs, st.sn, st.g, st.scal, st.active,
                                                st.jlen, st.flags, st.iters, nrhs, m, j, brk);
       if (j + 1 < steps) {
         note_launch();
-        k_scale<T><<<vgrid, kNT, 0, s>>>(W, V + (long)(j + 1) * vstride, nu, st.scal, st.active);
+        launch_k(k_scale<T>, vgrid, kNT, 0, s, W, V + (long)(j + 1) * vstride, nu, st.scal, st.active);
       }
       note_launch();
-      k_count_active<<<1, 32, 0, s>>>(st.active, nrhs, st.counters + (j & 1));
+      launch_k(k_count_active, 1, 32, 0, s, st.active, nrhs, st.counters + (j & 1));
       cudaMemcpyAsync(p->pinned + (j & 1), st.counters + (j & 1), sizeof(int),
                       cudaMemcpyDeviceToHost, s);
       cudaEventRecord(ev[j & 1], s);

@@ -1,0 +1,53 @@
+// Kernel launch with programmatic dependent launch (PDL).
+//
+// Kernels of the solver loop follow one another on one stream, most of them
+// short (tens of microseconds at 64^3).  A launch made with the
+// programmatic-stream-serialization attribute may be scheduled while the
+// previous kernel of the stream is still finishing; it must then wait, with
+// griddepcontrol.wait, before touching anything that kernel writes.  Every
+// kernel of the library starts with pdl_entry(): the wait (a no-op when the
+// kernel was launched the ordinary way), then launch_dependents, which lets
+// the next kernel's CTAs become resident as soon as all of this grid's CTAs
+// are running.  Because every CTA waits before its first memory access, a
+// kernel completes only after its predecessor has, so ordering stays
+// transitive along the stream.  DDA_PDL=0 in the environment turns the
+// attribute off (ordinary launches).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdlib>
+#include <utility>
+
+namespace dda {
+
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+
+inline bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("DDA_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                     cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+}  // namespace dda

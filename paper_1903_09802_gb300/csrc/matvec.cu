@@ -75,6 +75,7 @@ __global__ void __launch_bounds__(512)
                   cx<T>* __restrict__ y, const uint8_t* __restrict__ mat,
                   const cx<T>* __restrict__ ainv, int K1, long nlines, long nm, int l, int Lx,
                   T coef, const cx<T>* __restrict__ tw, int twshift, RadixPlan rp, int nb_sh) {
+  pdl_entry();
   const int NB = 1 << nb_sh;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
@@ -149,6 +150,7 @@ __global__ void __launch_bounds__(NB * LX / kElemsPerThread, 1024 / (NB * LX / k
                      cx<T>* __restrict__ y, const uint8_t* __restrict__ mat,
                      const cx<T>* __restrict__ ainv, int K1, long nlines, long nm, T coef,
                      const cx<T>* __restrict__ tw, int twshift) {
+  pdl_entry();
   static_assert(NB >= 16, "one position per thread");
   constexpr int NTH = NB * LX / kElemsPerThread;
   constexpr int LD = NB + 1;
@@ -211,7 +213,7 @@ void ct_epilogue_launch(dda_plan_s* p, const cx<float>* b1, const cx<float>* x, 
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   note_launch();
-  kern<<<(unsigned)((lines + NB - 1) / NB), NB * LX / kElemsPerThread, smem, s>>>(
+  launch_k(kern, (unsigned)((lines + NB - 1) / NB), NB * LX / kElemsPerThread, smem, s,
       b1, x, y, p->mat, ainv_of<float>(p), p->K + 1, lines, nm, coef, tw_of<float>(p),
       p->Lmax / LX);
 }
@@ -293,7 +295,7 @@ void matvec_impl(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t
     const T coef = (T)(p->d.dx * p->d.dx * p->d.dx / (double)p->P);
     p->prof.begin(PROF_MV_XI, s, 4 * u + p->nvox);
     note_launch();
-    kern<<<(unsigned)((lines + NB - 1) / NB), nth, smem, s>>>(
+    launch_k(kern, (unsigned)((lines + NB - 1) / NB), nth, smem, s,
         b1, x, y, p->mat, ainv_of<T>(p), p->K + 1, lines, nm, (int)l, (int)Lx, coef, tw,
         p->Lmax / (int)Lx, make_radix_plan((int)Lx), ilog2i(NB));
     p->prof.end(s);

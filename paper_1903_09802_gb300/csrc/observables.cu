@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(kNT)
                 const uint8_t* __restrict__ mat, const double2* __restrict__ ainv, int K1,
                 const double* __restrict__ inc, long l, long m, long n, double dx, double k,
                 double* __restrict__ part) {
+  pdl_entry();
   __shared__ double sh[4][32];
   const int r = blockIdx.y;
   const long nvox = l * m * n;
@@ -83,6 +84,7 @@ __global__ void __launch_bounds__(kNT)
 __global__ void k_ext_gradient(const double2* __restrict__ c, const double2* __restrict__ lam,
                                const uint8_t* __restrict__ mat, const double2* __restrict__ dainv,
                                int K1, long nvox, int nrhs, double pref, double* __restrict__ grad) {
+  pdl_entry();
   const long tot = nvox * nrhs;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < tot;
        i += (long)gridDim.x * blockDim.x) {

@@ -33,6 +33,7 @@ __device__ const int kB[6] = {0, 1, 2, 1, 2, 2};
 // First column of the 3-level circulant of all six blocks, FP64, layout
 // [comp][z][y][x].
 __global__ void k_chan3(double2* out, long l, long m, long n, double dx, double k) {
+  pdl_entry();
   const long nvox = l * m * n;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nvox;
        i += (long)gridDim.x * blockDim.x) {
@@ -78,6 +79,7 @@ __global__ void k_chan3(double2* out, long l, long m, long n, double dx, double 
 // Keep 0..l/2, 0..m/2, 0..n/2 of the six spectra, interleaved [..][6].
 __global__ void k_compress6(const double2* full, long l, long m, long n, long hx, long hy,
                             long hz, double2* out128, float2* out64) {
+  pdl_entry();
   const long H = hx * hy * hz, nvox = l * m * n;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < H;
        i += (long)gridDim.x * blockDim.x) {

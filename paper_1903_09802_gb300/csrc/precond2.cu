@@ -49,6 +49,7 @@ __device__ __forceinline__ int comp_of(int a, int b) {
 
 // c2[comp][rz + n - 1][q][p], FP64.
 __global__ void k_chan2(double2* out, long l, long m, long n, double dx, double k) {
+  pdl_entry();
   const long nr = 2 * n - 1;
   const long plane = l * m;
   const long tot = plane * nr;
@@ -95,6 +96,7 @@ __global__ void k_chan2(double2* out, long l, long m, long n, double dx, double 
 // stored quadrant, i = a n + z, j = b n + z'.
 __global__ void k_assemble2(const double2* __restrict__ chat, float2* __restrict__ blocks, long l,
                             long m, long n, double dx3, double2 at) {
+  pdl_entry();
   const long N = 3 * n, plane = l * m, nr = 2 * n - 1;
   const long hx = l / 2 + 1, hy = m / 2 + 1;
   const long tot = hx * hy * N * N;
@@ -124,6 +126,7 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
 // the end.  Pivot row and pivot column are staged in shared memory each step.
 __global__ void __launch_bounds__(1024)
     k_gauss_jordan(float2* __restrict__ blocks, int N, int* __restrict__ err) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* rowk = reinterpret_cast<float2*>(smem_raw);  // [N]
   float2* colk = rowk + N;                            // [N]
@@ -230,6 +233,7 @@ template <typename T, int VC>
 __global__ void __launch_bounds__(256)
     k_block_apply(cx<T>* __restrict__ t, const float2* __restrict__ blocksT, int r0, int nr, long l,
                   long m, long n, T scale) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* vin = reinterpret_cast<float2*>(smem_raw);  // [chunk][j][VC]
   const long N = 3 * n, plane = l * m, hx = l / 2 + 1;
@@ -331,6 +335,7 @@ template <typename T, int VC, int RPT>
 __global__ void __launch_bounds__(256)
     k_block_apply_pipe(cx<T>* __restrict__ t, const float2* __restrict__ blocksT, int r0, int nr,
                        long l, long m, long n, T scale) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int N = 3 * (int)n;
   const long plane = l * m, hx = l / 2 + 1;
@@ -490,9 +495,9 @@ void precond2_apply_impl(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cuda
       const int nr = std::min(group, nrhs - r0);
       note_launch();
       if (pipe)
-        kpipe<<<nq, nth, smem, s>>>(t, P2, r0, nr, l, m, n, scale);
+        launch_k(kpipe, nq, nth, smem, s, t, P2, r0, nr, l, m, n, scale);
       else
-        kern<<<nq, nth, smem, s>>>(t, P2, r0, nr, l, m, n, scale);
+        launch_k(kern, nq, nth, smem, s, t, P2, r0, nr, l, m, n, scale);
     }
   }
   p->prof.end(s);

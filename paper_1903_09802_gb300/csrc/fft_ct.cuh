@@ -29,6 +29,15 @@ __host__ __device__ constexpr int ct_bits(int L, int st) {
 }
 __host__ __device__ constexpr int ct_radix(int L, int st) { return 1 << ct_bits(L, st); }
 
+// DDA_RR_FFT3C=0 in the environment selects the all-shared-memory z pass.
+inline bool rr_fft3c_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("DDA_RR_FFT3C");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
 // One stage: radix R, NS = product of the radices already applied.  The tile
 // holds NB lines (NB = NBP or 3 * NBP) of length L; element (b, j) at
 // s[j * LD + b]; the block has NB * L / 16 threads.
@@ -269,6 +278,150 @@ __global__ void __launch_bounds__(3 * NBC * L / kElemsPerThread,
   }
 }
 
+// Three-component pass of the matvec (zero-padded input, half output kept)
+// with the middle of the transform held in registers.  The forward transform
+// runs radix R1 then R2, the inverse R2 then R1 (Stockham, natural order at
+// both ends), so the butterfly a thread computes last in the forward
+// transform covers exactly the frequencies jb + R1 q (q < R2) that its first
+// inverse butterfly needs:
+//   A  cp.async: rows j < L/2 of the 3 x NBC lines into shared memory;
+//   B  forward radix R1 (NS = 1, upper input half zero), shared -> shared;
+//   C  forward radix R2 (NS = R1) for all three components of column b,
+//      shared -> registers;
+//   D  3x3 point operation on the R2 frequencies in registers;
+//   E  inverse radix R2 (NS = 1), registers -> shared;
+//   F  inverse radix R1 (NS = R2), only outputs j < L/2, shared -> global.
+// Every element crosses shared memory about 5.5 times instead of 12.  Tile:
+// NBC = 16 columns (128-byte rows) x 3 components; in C-E thread tid owns
+// column b = tid % 16, butterfly jb = tid / 16.
+template <class Op, int L, int R1, int R2>
+__global__ void __launch_bounds__(R1 * 16)
+    k_rr_fft3c(cx<float>* data, long ncols, long js, long cs, long ss, Op op,
+               const cx<float>* __restrict__ tw, int twshift, int row_len, int nrows) {
+  pdl_entry();
+  static_assert(R1 * R2 == L, "two stages");
+  using T = float;
+  constexpr int NBC = 16;
+  constexpr int NL = 3 * NBC;  // lines (component, column) of the tile
+  constexpr int LD = NL;       // shared row pitch
+  constexpr int NTH = R1 * NBC;
+  constexpr int NBF = NL * R2;                // butterflies of stage B (and F)
+  constexpr int GB = (NBF + NTH - 1) / NTH;   // per thread
+  constexpr int H = L / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* stw = s + L * LD;
+  const int tid = threadIdx.x;
+  const long tiles = ncols / NBC;
+  const long slab = blockIdx.x / tiles;
+  const int tt = (int)(blockIdx.x - slab * tiles);
+  long col0;
+  if (row_len >= NBC && nrows > 0) {
+    const int row_tiles = row_len / NBC;
+    const int r = tt / row_tiles;
+    const int ti = tt - r * row_tiles;
+    col0 = (long)mirror_perm(r, nrows) * row_len + (long)mirror_perm(ti, row_tiles) * NBC;
+  } else {
+    col0 = (long)tt * NBC;
+  }
+  cx<T>* base = data + slab * ss + col0;
+  // A
+#pragma unroll 4
+  for (int e = tid; e < H * NL; e += NTH) {
+    const int j = e / NL, line = e - j * NL;
+    const int c = line / NBC, b = line - c * NBC;
+    cp_async_cx(s + j * LD + line, base + c * cs + (long)j * js + b, true);
+  }
+  op.prefetch(col0, NBC, L);
+  load_twiddles(stw, tw, L, twshift);
+  cp_async_wait_all();
+  __syncthreads();
+  // B: inputs rows jb + q R2 (q < R1/2 non-zero), outputs rows jb R1 + q
+  {
+    cx<T> v[GB][R1];
+#pragma unroll
+    for (int g = 0; g < GB; ++g) {
+      const int u = tid + g * NTH;
+      if (u < NBF) {
+        const int jb = u / NL, line = u - jb * NL;
+#pragma unroll
+        for (int q = 0; q < R1 / 2; ++q) v[g][q] = s[(jb + q * R2) * LD + line];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int g = 0; g < GB; ++g) {
+      const int u = tid + g * NTH;
+      if (u < NBF) {
+        const int jb = u / NL, line = u - jb * NL;
+        dft_half_in<R1, false>(v[g]);
+#pragma unroll
+        for (int q = 0; q < R1; ++q) s[(jb * R1 + q) * LD + line] = v[g][q];
+      }
+    }
+    __syncthreads();
+  }
+  const int b = tid % NBC, jb = tid / NBC;  // jb < R1
+  cx<T> x[3][R2];
+  // C: inputs rows jb + q R1, twiddle w^(q jb), outputs frequencies jb + q R1
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+#pragma unroll
+    for (int q = 0; q < R2; ++q) x[c][q] = s[(jb + q * R1) * LD + c * NBC + b];
+#pragma unroll
+    for (int q = 1; q < R2; ++q) x[c][q] = mulc<false>(x[c][q], stw[q * jb]);
+    dft<R2, false>(x[c]);
+  }
+  // D
+  {
+    const auto ctx = op.column(slab, col0 + b);
+#pragma unroll
+    for (int q = 0; q < R2; ++q) op.point(ctx, jb + q * R1, x[0][q], x[1][q], x[2][q]);
+  }
+  // E: inverse radix R2 on the same frequencies, outputs rows jb R2 + q
+#pragma unroll
+  for (int c = 0; c < 3; ++c) dft<R2, true>(x[c]);
+  __syncthreads();  // every thread has read its stage-C inputs
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int q = 0; q < R2; ++q) s[(jb * R2 + q) * LD + c * NBC + b] = x[c][q];
+  __syncthreads();
+  // F: inputs rows j2 + q R2, twiddle conj(w)^(q j2), outputs rows j2 + q R2 < L/2
+#pragma unroll
+  for (int g = 0; g < GB; ++g) {
+    const int u = tid + g * NTH;
+    if (u < NBF) {
+      const int j2 = u / NL, line = u - j2 * NL;
+      const int c = line / NBC, bb = line - c * NBC;
+      cx<T> v[R1];
+#pragma unroll
+      for (int q = 0; q < R1; ++q) v[q] = s[(j2 + q * R2) * LD + line];
+#pragma unroll
+      for (int q = 1; q < R1; ++q) v[q] = mulc<true>(v[q], stw[q * j2]);
+      dft_half_out<R1, true>(v);
+      cx<T>* g = base + c * cs + bb;
+#pragma unroll
+      for (int q = 0; q < R1 / 2; ++q) g[(long)(j2 + q * R2) * js] = v[q];
+    }
+  }
+}
+
+template <int L, int R1, int R2, class Op>
+void rr_fft3c_launch(cx<float>* data, long ncols, long nslabs, long js, long cs, long ss,
+                     const Op& op, const cx<float>* tw, int Lmax, int row_len, int nrows,
+                     cudaStream_t s) {
+  constexpr int NBC = 16;
+  const size_t smem = ((size_t)3 * NBC * L + L) * sizeof(cx<float>);
+  auto kern = k_rr_fft3c<Op, L, R1, R2>;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const long grid = nslabs * (ncols / NBC);
+  note_launch();
+  launch_k(kern, (unsigned)grid, R1 * NBC, smem, s, data, ncols, js, cs, ss, op, tw, Lmax / L,
+           row_len, nrows);
+}
+
 // Three-component pass: compile-time kernel for complex64 when the tile
 // shape allows (L in 32..512, 8-column tiles), the run-time kernel otherwise.
 template <int L, class Op, bool HI, bool HO>
@@ -291,6 +444,19 @@ template <class Op, bool HI, bool HO>
 bool ct_fft3c_dispatch(cx<float>* data, long ncols, long nslabs, int L, int Lin, long js, long cs,
                        long ss, int Lout, const Op& op, const cx<float>* tw, int Lmax, int row_len,
                        int nrows, cudaStream_t s) {
+  if constexpr (HI && HO) {
+    if (ncols % 16 == 0 && rr_fft3c_enabled()) {
+      if (L == 64) {
+        rr_fft3c_launch<64, 8, 8>(data, ncols, nslabs, js, cs, ss, op, tw, Lmax, row_len, nrows, s);
+        return true;
+      }
+      if (L == 128) {
+        rr_fft3c_launch<128, 16, 8>(data, ncols, nslabs, js, cs, ss, op, tw, Lmax, row_len, nrows,
+                                    s);
+        return true;
+      }
+    }
+  }
   switch (L) {
     case 32: ct_fft3c_launch<32, Op, HI, HO>(data, ncols, nslabs, Lin, js, cs, ss, Lout, op, tw, Lmax, row_len, nrows, s); return true;
     case 64: ct_fft3c_launch<64, Op, HI, HO>(data, ncols, nslabs, Lin, js, cs, ss, Lout, op, tw, Lmax, row_len, nrows, s); return true;

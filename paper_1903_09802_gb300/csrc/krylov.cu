@@ -130,6 +130,29 @@ __device__ __forceinline__ Pair<T> ld2(const cx<T>* p) {
     return Pair<T>{p[0], p[1]};
   }
 }
+// The same load without allocating in L1 (normal L2 policy): basis vectors
+// stream through once per pass, so they should not evict the w chunk that
+// the warps of a block share from L1.
+template <typename T>
+__device__ __forceinline__ Pair<T> ld2_na(const cx<T>* p) {
+  if constexpr (sizeof(T) == 4) {
+    float4 v;
+    asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];\n"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return Pair<T>{mk<T>(v.x, v.y), mk<T>(v.z, v.w)};
+  } else {
+    double2 a, b;
+    asm("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];\n"
+                 : "=d"(a.x), "=d"(a.y)
+                 : "l"(p));
+    asm("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];\n"
+                 : "=d"(b.x), "=d"(b.y)
+                 : "l"(p + 1));
+    return Pair<T>{mk<T>(a.x, a.y), mk<T>(b.x, b.y)};
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ void st2(cx<T>* p, const Pair<T>& v) {
   if constexpr (sizeof(T) == 4) {
@@ -294,7 +317,7 @@ __global__ void __launch_bounds__(kDotNT)
       const cx<T>* v = vb + (long)i * vstride;
 #pragma unroll 8
       for (long k = k0 + 2 * lane; k < k1; k += 64) {
-        const Pair<T> a = ld2(v + k);
+        const Pair<T> a = ld2_na(v + k);
         const Pair<T> b = ld2(w + k);
         ar.add(a.a.x * b.a.x + a.a.y * b.a.y);
         ai.add(a.a.x * b.a.y - a.a.y * b.a.x);
@@ -473,16 +496,12 @@ __device__ __forceinline__ void givens(double2 a, double2 b, double& c, double2&
   rho = make_double2(ph.x * nr, ph.y * nr);
 }
 
-// One thread per right-hand side: finish column j of H (norm of w, earlier
-// rotations, new rotation), update g and the residual estimate, decide
-// whether the cycle of this right-hand side goes on.
-__global__ void k_givens(double2* __restrict__ H, double* __restrict__ cs, double2* __restrict__ sn,
-                         double2* __restrict__ g, double* __restrict__ scal,
-                         int* __restrict__ active, int* __restrict__ jlen, int* __restrict__ flags,
-                         int* __restrict__ iters, int nrhs, int m, int j, double brk) {
-  pdl_entry();
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrhs || !active[r]) return;
+__device__ __forceinline__ void givens_step(double2* __restrict__ H, double* __restrict__ cs,
+                                            double2* __restrict__ sn, double2* __restrict__ g,
+                                            double* __restrict__ scal, int* __restrict__ active,
+                                            int* __restrict__ jlen, int* __restrict__ flags,
+                                            int* __restrict__ iters, int m, int j, double brk,
+                                            int r) {
   const double n2 = scal[(long)r * 16 + 8];  // ||w||^2 after Gram-Schmidt
   const double hn = sqrt(n2);
   double2* h = H + (long)r * (m + 1) * m + (long)j * (m + 1);
@@ -523,6 +542,30 @@ __global__ void k_givens(double2* __restrict__ H, double* __restrict__ cs, doubl
   } else if (hn <= brk * sqrt(colnorm2)) {
     flags[r] |= 2;  // breakdown: the Krylov space is invariant, the cycle's solution is exact
     active[r] = 0;
+  }
+}
+
+// One thread per right-hand side: finish column j of H (norm of w, earlier
+// rotations, new rotation), update g and the residual estimate, decide
+// whether the cycle of this right-hand side goes on.
+__global__ void k_givens(double2* __restrict__ H, double* __restrict__ cs, double2* __restrict__ sn,
+                         double2* __restrict__ g, double* __restrict__ scal,
+                         int* __restrict__ active, int* __restrict__ jlen, int* __restrict__ flags,
+                         int* __restrict__ iters, int nrhs, int m, int j, double brk,
+                         int* __restrict__ count_out) {
+  pdl_entry();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nrhs && active[r]) givens_step(H, cs, sn, g, scal, active, jlen, flags, iters, m, j, brk, r);
+  // single-block launches also count the right-hand sides still iterating
+  if (count_out != nullptr) {
+    __syncthreads();
+    int c = r < nrhs ? active[r] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    __shared__ int wsum[2];
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) *count_out = wsum[0] + (blockDim.x > 32 ? wsum[1] : 0);
   }
 }
 
@@ -1125,14 +1168,19 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
         if (pass == 0) p->prof.end(s);
       }
       note_launch();
+      const bool one_block = nrhs <= 64;  // the Givens kernel counts the active RHS itself
       launch_k(k_givens, (nrhs + 63) / 64, 64, 0, s, st.H, st.cs, st.sn, st.g, st.scal, st.active,
-                                               st.jlen, st.flags, st.iters, nrhs, m, j, brk);
+               st.jlen, st.flags, st.iters, nrhs, m, j, brk,
+               one_block ? st.counters + (j & 1) : nullptr);
       if (j + 1 < steps) {
         note_launch();
-        launch_k(k_scale<T>, vgrid, kNT, 0, s, W, V + (long)(j + 1) * vstride, nu, st.scal, st.active);
+        launch_k(k_scale<T>, vgrid, kNT, 0, s, W, V + (long)(j + 1) * vstride, nu, st.scal,
+                 st.active);
       }
-      note_launch();
-      launch_k(k_count_active, 1, 32, 0, s, st.active, nrhs, st.counters + (j & 1));
+      if (!one_block) {
+        note_launch();
+        launch_k(k_count_active, 1, 32, 0, s, st.active, nrhs, st.counters + (j & 1));
+      }
       cudaMemcpyAsync(p->pinned + (j & 1), st.counters + (j & 1), sizeof(int),
                       cudaMemcpyDeviceToHost, s);
       cudaEventRecord(ev[j & 1], s);

@@ -292,16 +292,15 @@ __global__ void __launch_bounds__(3 * NBC * L / kElemsPerThread,
 //   E  inverse radix R2 (NS = 1), registers -> shared;
 //   F  inverse radix R1 (NS = R2), only outputs j < L/2, shared -> global.
 // Every element crosses shared memory about 5.5 times instead of 12.  Tile:
-// NBC = 16 columns (128-byte rows) x 3 components; in C-E thread tid owns
-// column b = tid % 16, butterfly jb = tid / 16.
-template <class Op, int L, int R1, int R2>
-__global__ void __launch_bounds__(R1 * 16)
+// NBC columns (16: 128-byte rows) x 3 components; in C-E thread tid owns
+// column b = tid % NBC, butterfly jb = tid / NBC.
+template <class Op, int L, int R1, int R2, int NBC>
+__global__ void __launch_bounds__(R1 * NBC)
     k_rr_fft3c(cx<float>* data, long ncols, long js, long cs, long ss, Op op,
                const cx<float>* __restrict__ tw, int twshift, int row_len, int nrows) {
   pdl_entry();
   static_assert(R1 * R2 == L, "two stages");
   using T = float;
-  constexpr int NBC = 16;
   constexpr int NL = 3 * NBC;  // lines (component, column) of the tile
   constexpr int LD = NL;       // shared row pitch
   constexpr int NTH = R1 * NBC;
@@ -407,13 +406,12 @@ __global__ void __launch_bounds__(R1 * 16)
   }
 }
 
-template <int L, int R1, int R2, class Op>
+template <int L, int R1, int R2, int NBC, class Op>
 void rr_fft3c_launch(cx<float>* data, long ncols, long nslabs, long js, long cs, long ss,
                      const Op& op, const cx<float>* tw, int Lmax, int row_len, int nrows,
                      cudaStream_t s) {
-  constexpr int NBC = 16;
   const size_t smem = ((size_t)3 * NBC * L + L) * sizeof(cx<float>);
-  auto kern = k_rr_fft3c<Op, L, R1, R2>;
+  auto kern = k_rr_fft3c<Op, L, R1, R2, NBC>;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const long grid = nslabs * (ncols / NBC);
@@ -445,14 +443,17 @@ bool ct_fft3c_dispatch(cx<float>* data, long ncols, long nslabs, int L, int Lin,
                        long ss, int Lout, const Op& op, const cx<float>* tw, int Lmax, int row_len,
                        int nrows, cudaStream_t s) {
   if constexpr (HI && HO) {
+    // (length 256 as 16 x 16 needs 48 register values per thread and 180
+    // registers: measured slower than the all-shared-memory kernel)
     if (ncols % 16 == 0 && rr_fft3c_enabled()) {
       if (L == 64) {
-        rr_fft3c_launch<64, 8, 8>(data, ncols, nslabs, js, cs, ss, op, tw, Lmax, row_len, nrows, s);
+        rr_fft3c_launch<64, 8, 8, 16>(data, ncols, nslabs, js, cs, ss, op, tw, Lmax, row_len,
+                                      nrows, s);
         return true;
       }
       if (L == 128) {
-        rr_fft3c_launch<128, 16, 8>(data, ncols, nslabs, js, cs, ss, op, tw, Lmax, row_len, nrows,
-                                    s);
+        rr_fft3c_launch<128, 16, 8, 16>(data, ncols, nslabs, js, cs, ss, op, tw, Lmax, row_len,
+                                        nrows, s);
         return true;
       }
     }

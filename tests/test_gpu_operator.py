@@ -11,9 +11,10 @@ from oracle.problem import Problem
 # (l, m, n): several FFT tiles per pass, ragged tails (lines not a multiple of
 # the tile), unequal edges, a 1-voxel-thick box; n = 32 and 64 take the
 # matvec's register-resident z pass (z transforms of length 64 and 128), with
-# rows of the padded plane shorter and longer than its 16-column tile.
+# rows of the padded plane shorter and longer than its column tile; n = 128
+# the all-shared-memory z pass of length 256.
 BOXES = [(4, 4, 4), (8, 4, 2), (16, 16, 16), (32, 16, 8), (2, 32, 16), (16, 8, 1),
-         (8, 4, 32), (4, 8, 64), (16, 8, 32)]
+         (8, 4, 32), (4, 8, 64), (16, 8, 32), (4, 4, 128)]
 
 
 def _two_material_box(l, m, n, rng):

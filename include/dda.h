@@ -77,6 +77,9 @@ typedef struct {
   int32_t precond2;      /* 1: reserve the 2-level preconditioner's dense blocks
                             ((l/2+1)(m/2+1)(3n)^2 complex64 values, the other
                             frequency pairs follow by parity) and build scratch */
+  int32_t circulant;     /* circulant of the preconditioners (Section 3): 0 T. Chan's
+                            optimal one (eq. 13), 1 Strang's (central diagonals kept;
+                            at p = L/2 of an even level the mean of t_{L/2}, t_{-L/2}) */
 } dda_plan_desc_t;
 
 /* Plane wave E_inc = pol * exp(i k dir . r), r measured from the box centre.

@@ -12,6 +12,10 @@ Oracle (test infrastructure only).
   3x3 blocks) preconditioner mentioned at the end of Section 3.2.
 * Preconditioner (eq. 20, Section 3.1): P = alpha_tilde^{-1} I - dx^3 C, with
   alpha_tilde the polarizability of the scatterer's material ("ice").
+* Strang's circulant, the alternative Section 3 names: keep the central
+  diagonals of the Toeplitz matrix, c_p = t_p for p < l/2 and c_p = t_{p-l}
+  for p > l/2; for even l the paper gives no rule at p = l/2, and the average
+  (t_{l/2} + t_{-l/2}) / 2 is taken (it keeps each block's parity).
 
 Each function here works from the Green function's values at signed offsets
 (operator.signed_tensor), so no symmetry table is used; the brute-force
@@ -54,6 +58,21 @@ def chan_axis(S: np.ndarray, axis: int) -> np.ndarray:
         out[p] = (L - p) / L * S[p + L - 1]
         if p > 0:
             out[p] += p / L * S[p - L + L - 1]
+    return np.moveaxis(out, 0, axis)
+
+
+def strang_axis(S: np.ndarray, axis: int) -> np.ndarray:
+    """Strang's circulant along one axis (same shapes as chan_axis)."""
+    S = np.moveaxis(S, axis, 0)
+    L = (S.shape[0] + 1) // 2
+    out = np.empty((L,) + S.shape[1:], dtype=np.complex128)
+    for p in range(L):
+        if 2 * p < L:
+            out[p] = S[p + L - 1]
+        elif 2 * p > L:
+            out[p] = S[p - L + L - 1]
+        else:
+            out[p] = 0.5 * (S[p + L - 1] + S[p - L + L - 1])
     return np.moveaxis(out, 0, axis)
 
 
@@ -123,20 +142,22 @@ def wrapped_average(T: np.ndarray, l: int, m: int, n: int,
 
 
 def multilevel_circulant(l: int, m: int, n: int, dx: float, k: float,
-                         levels=(True, True, True)) -> np.ndarray:
-    """Closed-form multilevel Chan circulant of all six blocks.
+                         levels=(True, True, True), kind: str = "chan") -> np.ndarray:
+    """Closed-form multilevel circulant of all six blocks.
 
-    Eq. (13) applied along each level marked True (x, y, z order).  Returns
-    (6, nz, ny, nx) where a circulant level has length L and a Toeplitz one
-    2L-1 (signed offset + L - 1).
+    Eq. (13) (kind "chan") or Strang's circulant (kind "strang") applied
+    along each level marked True (x, y, z order).  Returns (6, nz, ny, nx)
+    where a circulant level has length L and a Toeplitz one 2L-1 (signed
+    offset + L - 1).
     """
+    axis_op = {"chan": chan_axis, "strang": strang_axis}[kind]
     S = signed_tensor(l, m, n, dx, k)
     if levels[0]:
-        S = chan_axis(S, 3)
+        S = axis_op(S, 3)
     if levels[1]:
-        S = chan_axis(S, 2)
+        S = axis_op(S, 2)
     if levels[2]:
-        S = chan_axis(S, 1)
+        S = axis_op(S, 1)
     return S
 
 
@@ -150,14 +171,14 @@ def assemble_3x3(six: np.ndarray) -> np.ndarray:
 
 
 def precond3_lambda(l: int, m: int, n: int, dx: float, k: float,
-                    alpha_tilde_inv: complex) -> np.ndarray:
+                    alpha_tilde_inv: complex, kind: str = "chan") -> np.ndarray:
     """Per-frequency 3x3 symbol of the 3-level preconditioner, shape (n, m, l, 3, 3).
 
     Lambda(w) = alpha_tilde^{-1} I - dx^3 Chat(w), Chat = 3-D DFT of the
     3-level circulant's first column (a circulant is diagonalised by the DFT,
     Section 3).
     """
-    C = multilevel_circulant(l, m, n, dx, k, (True, True, True))
+    C = multilevel_circulant(l, m, n, dx, k, (True, True, True), kind)
     Chat = np.fft.fftn(C, axes=(1, 2, 3))
     lam = -dx ** 3 * assemble_3x3(Chat)
     lam += alpha_tilde_inv * np.eye(3)
@@ -195,7 +216,7 @@ def precond3_dense(l: int, m: int, n: int, dx: float, k: float,
 
 
 def precond2_blocks(l: int, m: int, n: int, dx: float, k: float,
-                    alpha_tilde_inv: complex) -> np.ndarray:
+                    alpha_tilde_inv: complex, kind: str = "chan") -> np.ndarray:
     """Inverted dense blocks of the paper's 2-level preconditioner (Section 3.1).
 
     Circulant along x and y, Toeplitz along z.  After the 2-D DFT over
@@ -203,7 +224,7 @@ def precond2_blocks(l: int, m: int, n: int, dx: float, k: float,
     B[(a, z), (b, z')] = alpha_tilde^{-1} d_ab d_zz' - dx^3 Chat2_ab(z - z'; wy, wx)
     (eq. 19).  Returns the inverses, shape (m, l, 3n, 3n).
     """
-    C2 = multilevel_circulant(l, m, n, dx, k, (True, True, False))  # (6, 2n-1, m, l)
+    C2 = multilevel_circulant(l, m, n, dx, k, (True, True, False), kind)  # (6, 2n-1, m, l)
     Chat2 = np.fft.fftn(C2, axes=(2, 3))
     zi, zj = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
     off = zi - zj + n - 1

@@ -66,20 +66,22 @@ class Problem:
         return operator.fft_matvec(c, self.mat, self.alpha_inv_vox, self.alpha_tilde_inv,
                                    self.k, self.dx, Ghat)
 
-    def precond3(self, restrict: bool = True):
-        """3-level preconditioner; restricted to the scatterer unless restrict=False."""
+    def precond3(self, restrict: bool = True, kind: str = "chan"):
+        """3-level preconditioner; restricted to the scatterer unless restrict=False.
+
+        kind: "chan" (eq. 13) or "strang" (Strang's circulant)."""
         l, m, n = self.dims
-        lam = circulant.precond3_lambda(l, m, n, self.dx, self.k, self.alpha_tilde_inv)
+        lam = circulant.precond3_lambda(l, m, n, self.dx, self.k, self.alpha_tilde_inv, kind)
         lam_inv = np.linalg.inv(lam)
         ice = (self.mat > 0)[None]
         if not restrict:
             return lambda v: circulant.precond3_apply(v, lam_inv)
         return lambda v: circulant.precond3_apply(v * ice, lam_inv) * ice
 
-    def precond2(self, restrict: bool = True):
+    def precond2(self, restrict: bool = True, kind: str = "chan"):
         """The paper's 2-level preconditioner; restricted to the scatterer by default."""
         l, m, n = self.dims
-        blocks = circulant.precond2_blocks(l, m, n, self.dx, self.k, self.alpha_tilde_inv)
+        blocks = circulant.precond2_blocks(l, m, n, self.dx, self.k, self.alpha_tilde_inv, kind)
         ice = (self.mat > 0)[None]
         if not restrict:
             return lambda v: circulant.precond2_apply(v, blocks)
@@ -93,7 +95,9 @@ class Problem:
     def solve_gmres(self, precond: str = "none", tol: float = 1e-6, restart: int = 50,
                     maxiter: int = 2000, side: str = "right"):
         Ghat = self.kernel_spectrum()
-        M = {"none": None, "3": self.precond3, "2": self.precond2}[precond]
+        M = {"none": None, "3": self.precond3, "2": self.precond2,
+             "3s": lambda: self.precond3(kind="strang"),
+             "2s": lambda: self.precond2(kind="strang")}[precond]
         M = M() if M is not None else None
         return krylov.gmres(lambda v: self.matvec(v, Ghat), self.rhs(), tol=tol,
                             restart=restart, maxiter=maxiter, precond=M, side=side)

@@ -44,6 +44,7 @@ bool valid_desc(const dda_plan_desc_t& d, std::string& why, dda_status_t& st) {
   if (d.max_rhs < 1 || d.max_rhs > 4096) return why = "max_rhs must be 1..4096", false;
   if (d.krylov_m < 0 || d.krylov_m > 512) return why = "krylov_m must be 0..512", false;
   if (d.precond2 != 0 && d.precond2 != 1) return why = "precond2 must be 0 or 1", false;
+  if (d.circulant != 0 && d.circulant != 1) return why = "circulant must be 0 (Chan) or 1 (Strang)", false;
   if ((d.precisions & (DDA_PLAN_C128 | DDA_PLAN_C64)) == 0 ||
       (d.precisions & ~(DDA_PLAN_C128 | DDA_PLAN_C64)) != 0)
     return why = "precisions must be a non-empty set of DDA_PLAN_C128 | DDA_PLAN_C64", false;

@@ -22,6 +22,16 @@ dda_status_t check_cuda(const char* where);
 
 inline bool is_pow2(long v) { return v > 0 && (v & (v - 1)) == 0; }
 
+// Weight of the Toeplitz entry at offset p (side 0) or p - L (side 1) in
+// entry p of a level's circulant: T. Chan's eq. 13 ((L - p)/L and p/L) or
+// Strang's (the nearer of the two offsets; both halves at p = L/2).
+__host__ __device__ inline double circ_weight(long p, long L, int side, int strang) {
+  if (side == 1 && p == 0) return 0.0;
+  if (!strang) return side ? (double)p / L : (double)(L - p) / L;
+  if (2 * p == L) return 0.5;
+  return (2 * p < L) == (side == 0) ? 1.0 : 0.0;
+}
+
 // Process-wide count of kernel launches made by the library (dda_launch_count).
 void note_launch();
 

@@ -31,8 +31,9 @@ __device__ const int kA[6] = {0, 0, 0, 1, 1, 2};
 __device__ const int kB[6] = {0, 1, 2, 1, 2, 2};
 
 // First column of the 3-level circulant of all six blocks, FP64, layout
-// [comp][z][y][x].
-__global__ void k_chan3(double2* out, long l, long m, long n, double dx, double k) {
+// [comp][z][y][x]; T. Chan's (eq. 13) or, with strang, Strang's circulant on
+// every level.
+__global__ void k_chan3(double2* out, long l, long m, long n, double dx, double k, int strang) {
   pdl_entry();
   const long nvox = l * m * n;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < nvox;
@@ -40,17 +41,17 @@ __global__ void k_chan3(double2* out, long l, long m, long n, double dx, double 
     const long p = i % l, q = (i / l) % m, r = i / (l * m);
     double acc[6][2] = {};
     for (int sa = 0; sa < 2; ++sa) {
-      if (sa == 1 && p == 0) continue;
+      const double wa = circ_weight(p, l, sa, strang);
+      if (wa == 0.0) continue;
       const long a = sa ? p - l : p;
-      const double wa = sa ? (double)p / l : (double)(l - p) / l;
       for (int sb = 0; sb < 2; ++sb) {
-        if (sb == 1 && q == 0) continue;
+        const double wb = circ_weight(q, m, sb, strang);
+        if (wb == 0.0) continue;
         const long b = sb ? q - m : q;
-        const double wb = sb ? (double)q / m : (double)(m - q) / m;
         for (int sc = 0; sc < 2; ++sc) {
-          if (sc == 1 && r == 0) continue;
+          const double wc = circ_weight(r, n, sc, strang);
+          if (wc == 0.0) continue;
           const long c = sc ? r - n : r;
-          const double wc = sc ? (double)r / n : (double)(n - r) / n;
           if ((a | b | c) == 0) continue;  // g(0) = 0: the self term is alpha^{-1}
           const double w = wa * wb * wc;
           const double X = dx * a, Y = dx * b, Z = dx * c;
@@ -239,7 +240,8 @@ extern "C" dda_status_t dda_precond_build(dda_plan_t p, void* stream) {
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double2* full = static_cast<double2*>(p->w.buf2);
   note_launch();
-  k_chan3<<<grid_for(p->nvox, 128), 128, 0, s>>>(full, p->l, p->m, p->n, p->d.dx, p->d.k);
+  k_chan3<<<grid_for(p->nvox, 128), 128, 0, s>>>(full, p->l, p->m, p->n, p->d.dx, p->d.k,
+                                                  p->d.circulant);
   fft3d_inplace<double, false>(reinterpret_cast<cx<double>*>(full), 6, p->l, p->m, p->n, 1.0,
                                tw_of<double>(p), p->Lmax, s);
   note_launch();

@@ -1,8 +1,9 @@
 // The paper's 2-level circulant preconditioner (Section 3, eqs. 17-19; the
 // block inversion of Section 3.1).
 //
-// Build: T. Chan's optimal circulant (eq. 13) is applied on the x and y
-// levels of each of the six blocks, the z level stays Toeplitz:
+// Build: T. Chan's optimal circulant (eq. 13; Strang's with the plan's
+// circulant = 1) is applied on the x and y levels of each of the six blocks,
+// the z level stays Toeplitz:
 //   c2(p, q, r) = sum_{a in {p, p-l}} sum_{b in {q, q-m}} w_l(a) w_m(b) g(a dx, b dx, r dx),
 // r = -(n-1) .. n-1, evaluated in FP64 directly at the signed offsets; a 2-D
 // DFT over (p, q) block-diagonalises the x and y levels, leaving for every
@@ -48,7 +49,7 @@ __device__ __forceinline__ int comp_of(int a, int b) {
 }
 
 // c2[comp][rz + n - 1][q][p], FP64.
-__global__ void k_chan2(double2* out, long l, long m, long n, double dx, double k) {
+__global__ void k_chan2(double2* out, long l, long m, long n, double dx, double k, int strang) {
   pdl_entry();
   const long nr = 2 * n - 1;
   const long plane = l * m;
@@ -59,13 +60,13 @@ __global__ void k_chan2(double2* out, long l, long m, long n, double dx, double 
     const long c = ri - (n - 1);
     double acc[6][2] = {};
     for (int sa = 0; sa < 2; ++sa) {
-      if (sa == 1 && p == 0) continue;
+      const double wa = circ_weight(p, l, sa, strang);
+      if (wa == 0.0) continue;
       const long a = sa ? p - l : p;
-      const double wa = sa ? (double)p / l : (double)(l - p) / l;
       for (int sb = 0; sb < 2; ++sb) {
-        if (sb == 1 && q == 0) continue;
+        const double wb = circ_weight(q, m, sb, strang);
+        if (wb == 0.0) continue;
         const long b = sb ? q - m : q;
-        const double wb = sb ? (double)q / m : (double)(m - q) / m;
         if ((a | b | c) == 0) continue;
         const double w = wa * wb;
         const double X = dx * a, Y = dx * b, Z = dx * c;
@@ -535,7 +536,8 @@ extern "C" dda_status_t dda_precond2_build(dda_plan_t p, void* stream) {
   const long l = p->l, m = p->m, n = p->n, N = 3 * n;
   double2* c2 = static_cast<double2*>(p->w.C2);
   note_launch();
-  k_chan2<<<grid_for(l * m * (2 * n - 1), 128), 128, 0, s>>>(c2, l, m, n, p->d.dx, p->d.k);
+  k_chan2<<<grid_for(l * m * (2 * n - 1), 128), 128, 0, s>>>(c2, l, m, n, p->d.dx, p->d.k,
+                                                              p->d.circulant);
   fft3d_inplace<double, false>(reinterpret_cast<cx<double>*>(c2), 6 * (2 * n - 1), (int)l, (int)m, 1,
                                1.0, tw_of<double>(p), p->Lmax, s);
   const double2 at = make_double2(p->ainv_host[0], p->ainv_host[1]);  // rhs 0, entry 0

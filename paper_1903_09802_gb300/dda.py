@@ -32,6 +32,8 @@ STATUS = {
     7: "DDA_ERR_SINGULAR_PRECOND", 8: "DDA_ERR_NAN", 9: "DDA_ERR_TIMEOUT", 10: "DDA_ERR_NO_PRECOND",
 }
 
+CIRCULANTS = {"chan": 0, "strang": 1}  # preconditioner circulant: eq. 13 or Strang's
+
 EXPORTS = ("dda_workspace_size", "dda_plan_create", "dda_set_incidence", "dda_incident_field",
            "dda_matvec", "dda_precond_build", "dda_precond_apply", "dda_precond_apply_noalloc",
            "dda_precond2_build", "dda_precond2_apply",
@@ -54,7 +56,7 @@ class PlanDesc(ctypes.Structure):
                 ("dx", ctypes.c_double), ("k", ctypes.c_double),
                 ("n_materials", ctypes.c_int32), ("max_rhs", ctypes.c_int32),
                 ("krylov_m", ctypes.c_int32), ("precisions", ctypes.c_int32),
-                ("precond2", ctypes.c_int32)]
+                ("precond2", ctypes.c_int32), ("circulant", ctypes.c_int32)]
 
 
 class Incidence(ctypes.Structure):
@@ -155,8 +157,9 @@ def _prec_of(t: torch.Tensor) -> int:
 
 
 def workspace_size(l, m, n, dx, k, n_materials=1, max_rhs=1, krylov_m=0,
-                   precisions=PLAN_C128 | PLAN_C64, precond2=0) -> int:
-    d = PlanDesc(l, m, n, dx, k, n_materials, max_rhs, krylov_m, precisions, int(bool(precond2)))
+                   precisions=PLAN_C128 | PLAN_C64, precond2=0, circulant="chan") -> int:
+    d = PlanDesc(l, m, n, dx, k, n_materials, max_rhs, krylov_m, precisions, int(bool(precond2)),
+                 CIRCULANTS[circulant])
     return int(_lib.dda_workspace_size(ctypes.byref(d)))
 
 
@@ -176,7 +179,7 @@ class Plan:
 
     def __init__(self, mat: torch.Tensor, eps, dx: float, k: float, max_rhs: int = 1,
                  krylov_m: int = 0, precisions: int = PLAN_C128 | PLAN_C64,
-                 precond2: bool = False):
+                 precond2: bool = False, circulant: str = "chan"):
         if mat.dtype != torch.uint8 or not mat.is_cuda or mat.dim() != 3:
             raise TypeError("mat must be a (n, m, l) uint8 CUDA tensor")
         self.mat = mat.contiguous()
@@ -184,7 +187,7 @@ class Plan:
         self.shape = (l, m, n)
         eps = [complex(e) for e in eps]
         self.desc = PlanDesc(l, m, n, float(dx), float(k), len(eps), int(max_rhs), int(krylov_m),
-                             int(precisions), int(bool(precond2)))
+                             int(precisions), int(bool(precond2)), CIRCULANTS[circulant])
         size = int(_lib.dda_workspace_size(ctypes.byref(self.desc)))
         if size == 0:
             raise DDAError(1, last_error())

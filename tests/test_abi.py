@@ -76,3 +76,14 @@ def test_null_plan_is_rejected(dda):
     assert dda.STATUS[lib.dda_precond_build(None, None)] == "DDA_ERR_INVALID_ARG"
     assert dda.STATUS[lib.dda_solve(None, 1, None, None, None, None, None)] == "DDA_ERR_INVALID_ARG"
     lib.dda_plan_destroy(None)
+
+
+def test_workspace_options_validated():
+    from paper_1903_09802_gb300 import dda
+    base = dda.workspace_size(16, 16, 8, 0.125, 5.0, 1, 2, 50)
+    assert dda.workspace_size(16, 16, 8, 0.125, 5.0, 1, 2, 50, precond2=1) > base
+    assert dda.workspace_size(16, 16, 8, 0.125, 5.0, 1, 2, 50, circulant="strang") == base
+    desc = dda.PlanDesc(16, 16, 8, 0.125, 5.0, 1, 2, 50, 3, 0, 2)  # circulant 2: unknown
+    assert dda._lib.dda_workspace_size(ctypes.byref(desc)) == 0
+    desc = dda.PlanDesc(16, 16, 8, 0.125, 5.0, 1, 2, 50, 3, 2, 0)  # precond2 2: invalid
+    assert dda._lib.dda_workspace_size(ctypes.byref(desc)) == 0

@@ -120,3 +120,25 @@ def test_incident_field_parity():
     for r in range(2):
         p = Problem(mat=mat, dx=dx, k=k, eps=[1.7], d=dirs[r], e=pols[r])
         assert rel_err(b[r], p.rhs()) < 1e-13
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("box", [(4, 4, 4), (8, 4, 2), (16, 8, 1), (2, 32, 16), (16, 16, 16)])
+def test_precond_apply_parity_strang(box):
+    """3-level preconditioner with Strang's circulant on every level."""
+    dda = dda_module()
+    l, m, n = box
+    rng = np.random.default_rng(500 + sum(box))
+    mat = hex_prism_mask(l, m, n, 2.0 / max(l, m), 1.0, 2.0)
+    if mat.sum() == 0:
+        mat[0, 0, 0] = 1
+    dx, k = 2.0 / max(l, m), 2.2
+    dirs, pols = _incidences()
+    plan = dda.Plan(to_dev(mat, torch.uint8), [1.31 ** 2], dx, k, max_rhs=2, circulant="strang")
+    plan.set_incidence(dirs, pols)
+    plan.precond_build()
+    v = random_field((2, 3, n, m, l), rng)
+    want = np.stack([Problem(mat=mat, dx=dx, k=k, eps=[1.31 ** 2], d=dirs[r], e=pols[r])
+                     .precond3(kind="strang")(v[r]) for r in range(2)])
+    assert rel_err(plan.precond_apply(to_dev(v)).cpu().numpy(), want) < 1e-10
+    assert rel_err(plan.precond_apply(to_dev(v, torch.complex64)).cpu().numpy(), want) < 2e-5

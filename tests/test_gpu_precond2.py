@@ -183,3 +183,30 @@ def test_precond2_error_paths():
     p2 = dda.Plan(to_dev(mat, torch.uint8), [1.7], 0.3, 2.0, max_rhs=1, precond2=True)
     with pytest.raises(dda.DDAError, match="incidence"):
         p2.precond2_build()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("box", [(4, 4, 4), (16, 8, 1), (32, 16, 8)])
+def test_precond2_apply_parity_strang(box):
+    """2-level preconditioner with Strang's circulant on x and y."""
+    dda = dda_module()
+    l, m, n = box
+    rng = np.random.default_rng(600 + sum(box))
+    mat = hex_prism_mask(l, m, n, 2.0 / max(l, m), 1.0, 2.0)
+    if mat.sum() == 0:
+        mat[0, 0, 0] = 1
+    dx, k = 2.0 / max(l, m), 2.2
+    dirs, pols = _incidences()
+    plan = dda.Plan(to_dev(mat, torch.uint8), [1.31 ** 2], dx, k, max_rhs=2, precond2=True,
+                    circulant="strang")
+    plan.set_incidence(dirs, pols)
+    plan.precond2_build()
+    v = random_field((2, 3, n, m, l), rng)
+    prob = Problem(mat=mat, dx=dx, k=k, eps=[1.31 ** 2], d=dirs[0], e=pols[0])
+    apply = prob.precond2(kind="strang")
+    want = np.stack([apply(v[r]) for r in range(2)])
+    l_, m_, n_ = prob.dims
+    binv = circulant.precond2_blocks(l_, m_, n_, dx, k, prob.alpha_tilde_inv, "strang")
+    kappa = max(np.linalg.cond(b) for b in binv.reshape(-1, 3 * n, 3 * n))
+    tol = 2e-6 + 4 * kappa * np.sqrt(3 * n) * EPS32
+    assert rel_err(plan.precond2_apply(to_dev(v)).cpu().numpy(), want) < tol

@@ -108,3 +108,56 @@ def test_precond2_blocks_invert_dense_2level():
     v = random_field((3, n, m, l), rng)
     Pv = (P @ v.reshape(-1)).reshape(v.shape)
     assert np.allclose(circulant.precond2_apply(Pv, inv), v, rtol=1e-11, atol=1e-11)
+
+
+# Strang's circulant (named in Section 3 as the alternative to eq. 13).
+
+def _strang_1d(t):
+    return circulant.strang_axis(t[:, None], 0)[:, 0]
+
+
+def test_strang_keeps_the_central_band():
+    # C[i, j] = T[i, j] wherever |i - j| < L/2, checked on the dense matrices
+    rng = np.random.default_rng(11)
+    for L in (1, 2, 5, 6, 8):
+        t = random_field(2 * L - 1, rng)
+        T = circulant.toeplitz_dense(t)
+        C = circulant.circulant_dense(_strang_1d(t))
+        i, j = np.meshgrid(np.arange(L), np.arange(L), indexing="ij")
+        band = 2 * np.abs(i - j) < L
+        assert np.array_equal(C[band], T[band])
+        if L % 2 == 0:  # the tie at |i - j| = L/2: mean of the two diagonals
+            d = L // 2
+            assert np.isclose(C[d, 0], 0.5 * (T[d, 0] + T[0, d]), rtol=1e-15)
+
+
+def test_strang_fixed_point_and_parity():
+    rng = np.random.default_rng(12)
+    L = 8
+    c = random_field(L, rng)
+    t = np.array([c[o % L] for o in range(-(L - 1), L)])
+    assert np.allclose(_strang_1d(t), c, rtol=1e-15, atol=0)
+    # an odd Toeplitz symbol (t_{-o} = -t_o, as the xy/xz/yz blocks along an
+    # odd axis) gives an odd circulant: c_{L-p} = -c_p, c_0 = c_{L/2} = 0
+    h = random_field(L, rng)
+    h[0] = 0
+    t_odd = np.array([np.sign(o) * h[abs(o)] for o in range(-(L - 1), L)])
+    s = _strang_1d(t_odd)
+    assert s[0] == 0 and s[L // 2] == 0
+    assert np.allclose(s[1:], -s[1:][::-1], rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("comp", [0, 1, 2, 5])
+def test_multilevel_strang_keeps_the_central_band(comp):
+    # dense 3-level circulant from the closed form equals the BTTB block on
+    # every pair whose x, y and z offsets all lie inside the central bands
+    l, m, n, dx, k = 4, 5, 6, 0.3, 1.7
+    T = circulant.bttb_block_dense(l, m, n, dx, k, comp)
+    C3 = circulant.multilevel_circulant(l, m, n, dx, k, (True, True, True), "strang")[comp]
+    z, y, x = np.meshgrid(np.arange(n), np.arange(m), np.arange(l), indexing="ij")
+    x, y, z = x.reshape(-1), y.reshape(-1), z.reshape(-1)
+    ox, oy, oz = x[:, None] - x[None, :], y[:, None] - y[None, :], z[:, None] - z[None, :]
+    C = C3[oz % n, oy % m, ox % l]
+    band = (2 * np.abs(ox) < l) & (2 * np.abs(oy) < m) & (2 * np.abs(oz) < n)
+    assert np.allclose(C[band], T[band], rtol=1e-13, atol=1e-13 * np.abs(T).max())
+    assert band.sum() > 0 and (~band).sum() > 0

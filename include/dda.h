@@ -74,9 +74,12 @@ typedef struct {
   int32_t max_rhs;       /* largest right-hand-side batch used with this plan   */
   int32_t krylov_m;      /* GMRES restart length to reserve (0: no solver)      */
   int32_t precisions;    /* DDA_PLAN_C128 | DDA_PLAN_C64                         */
-  int32_t precond2;      /* 1: reserve the 2-level preconditioner's dense blocks
-                            ((l/2+1)(m/2+1)(3n)^2 complex64 values, the other
-                            frequency pairs follow by parity) and build scratch */
+  int32_t precond2;      /* reserve the 2-level preconditioner: 1 with z as its
+                            Toeplitz (dense) level as in the paper, 2 with x, 3 with
+                            y (Section 5's alternative for long prisms).  Storage:
+                            (l'/2+1)(m'/2+1)(3n')^2 complex64 values for the box
+                            relabelled so that the Toeplitz level is z' (the other
+                            frequency pairs follow by parity), plus build scratch */
   int32_t circulant;     /* circulant of the preconditioners (Section 3): 0 T. Chan's
                             optimal one (eq. 13), 1 Strang's (central diagonals kept;
                             at p = L/2 of an even level the mean of t_{L/2}, t_{-L/2}) */
@@ -193,11 +196,15 @@ dda_status_t dda_precond_apply_noalloc(dda_plan_t plan, int32_t prec, int32_t nr
 /* The paper's 2-level circulant preconditioner (Section 3, eqs. 17-19; the
  * block inversion of Section 3.1): T. Chan's circulant (eq. 13) on the x and
  * y levels, the z level kept Toeplitz, so after a 2-D DFT every frequency
- * pair (wx, wy) carries a dense 3n x 3n block alpha_tilde^{-1} I - dx^3 Chat2(wx, wy), inverted on the GPU
- * (Gauss-Jordan with partial pivoting, complex64) and stored.  alpha_tilde is
- * that of the first right-hand side of the current incidence (call after
- * dda_set_incidence; the blocks serve the whole batch).  Needs a plan with
- * desc.precond2 = 1.  DDA_ERR_SINGULAR_PRECOND if a block is singular. */
+ * pair (wx, wy) carries a dense 3n x 3n block alpha_tilde^{-1} I -
+ * dx^3 Chat2(wx, wy), inverted on the GPU (Gauss-Jordan with partial
+ * pivoting, complex64) and stored.  With desc.precond2 = 2 (3) the Toeplitz
+ * level is x (y) instead: the same construction on the box relabelled by the
+ * rotation (x', y', z') = (y, z, x) ((z, x, y)), fields relabelled on the way
+ * in and out of the apply.  alpha_tilde is that of the first right-hand side
+ * of the current incidence (call after dda_set_incidence; the blocks serve
+ * the whole batch).  Needs a plan with desc.precond2 >= 1.
+ * DDA_ERR_SINGULAR_PRECOND if a block is singular. */
 dda_status_t dda_precond2_build(dda_plan_t plan, void* stream);
 
 /* z = M o P2^{-1}(M o v) (restricted to the scatterer as dda_precond_apply):

@@ -238,6 +238,35 @@ def precond2_blocks(l: int, m: int, n: int, dx: float, k: float,
     return np.linalg.inv(blocks)
 
 
+# The paper keeps z as the Toeplitz (dense) level of the 2-level preconditioner
+# and notes that for long prisms making the long axis circulant may do better
+# (Section 5).  Another Toeplitz level is reached by relabelling the axes
+# cyclically so that it becomes z: a rotation of the frame, under which the
+# Green tensor transforms as G(R r) = R G(r) R^T and the polarizability is
+# unchanged, so the 2-level preconditioner of the relabelled box is the same
+# operator.  Fields are (3, nz, ny, nx).
+#   axis "x": (x', y', z') = (y, z, x), box (m, n, l)
+#   axis "y": (x', y', z') = (z, x, y), box (n, l, m)
+def toeplitz_frame_dims(l: int, m: int, n: int, axis: str):
+    return {"z": (l, m, n), "x": (m, n, l), "y": (n, l, m)}[axis]
+
+
+def to_toeplitz_frame(v: np.ndarray, axis: str) -> np.ndarray:
+    if axis == "z":
+        return v
+    if axis == "x":
+        return v[[1, 2, 0]].transpose(0, 3, 1, 2)
+    return v[[2, 0, 1]].transpose(0, 2, 3, 1)
+
+
+def from_toeplitz_frame(w: np.ndarray, axis: str) -> np.ndarray:
+    if axis == "z":
+        return w
+    if axis == "x":
+        return w[[2, 0, 1]].transpose(0, 2, 3, 1)
+    return w[[1, 2, 0]].transpose(0, 3, 1, 2)
+
+
 def precond2_apply(v: np.ndarray, blocks_inv: np.ndarray) -> np.ndarray:
     """z = P2^{-1} v: DFT over x and y, dense 3n block solve per (wy, wx), inverse DFT."""
     _, n, m, l = v.shape

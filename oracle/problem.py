@@ -78,14 +78,19 @@ class Problem:
             return lambda v: circulant.precond3_apply(v, lam_inv)
         return lambda v: circulant.precond3_apply(v * ice, lam_inv) * ice
 
-    def precond2(self, restrict: bool = True, kind: str = "chan"):
-        """The paper's 2-level preconditioner; restricted to the scatterer by default."""
-        l, m, n = self.dims
+    def precond2(self, restrict: bool = True, kind: str = "chan", axis: str = "z"):
+        """The paper's 2-level preconditioner; restricted to the scatterer by default.
+
+        axis: the Toeplitz (dense) level, z in the paper; x or y through the
+        relabelled frame of circulant.to_toeplitz_frame."""
+        l, m, n = circulant.toeplitz_frame_dims(*self.dims, axis)
         blocks = circulant.precond2_blocks(l, m, n, self.dx, self.k, self.alpha_tilde_inv, kind)
-        ice = (self.mat > 0)[None]
-        if not restrict:
-            return lambda v: circulant.precond2_apply(v, blocks)
-        return lambda v: circulant.precond2_apply(v * ice, blocks) * ice
+        ice = (self.mat > 0)[None] if restrict else True
+
+        def apply(v):
+            w = circulant.to_toeplitz_frame(v * ice, axis)
+            return circulant.from_toeplitz_frame(circulant.precond2_apply(w, blocks), axis) * ice
+        return apply
 
     def solve_direct(self) -> np.ndarray:
         A = operator.dense_matrix(self.mat, self.alpha_inv_vox, self.k, self.dx)
@@ -97,7 +102,8 @@ class Problem:
         Ghat = self.kernel_spectrum()
         M = {"none": None, "3": self.precond3, "2": self.precond2,
              "3s": lambda: self.precond3(kind="strang"),
-             "2s": lambda: self.precond2(kind="strang")}[precond]
+             "2s": lambda: self.precond2(kind="strang"),
+             "2x": lambda: self.precond2(axis="x"), "2y": lambda: self.precond2(axis="y")}[precond]
         M = M() if M is not None else None
         return krylov.gmres(lambda v: self.matvec(v, Ghat), self.rhs(), tol=tol,
                             restart=restart, maxiter=maxiter, precond=M, side=side)

@@ -43,7 +43,8 @@ bool valid_desc(const dda_plan_desc_t& d, std::string& why, dda_status_t& st) {
   if (d.n_materials < 1 || d.n_materials > 255) return why = "n_materials must be 1..255", false;
   if (d.max_rhs < 1 || d.max_rhs > 4096) return why = "max_rhs must be 1..4096", false;
   if (d.krylov_m < 0 || d.krylov_m > 512) return why = "krylov_m must be 0..512", false;
-  if (d.precond2 != 0 && d.precond2 != 1) return why = "precond2 must be 0 or 1", false;
+  if (d.precond2 < 0 || d.precond2 > 3)
+    return why = "precond2 must be 0 (none) or 1, 2, 3 (Toeplitz level z, x, y)", false;
   if (d.circulant != 0 && d.circulant != 1) return why = "circulant must be 0 (Chan) or 1 (Strang)", false;
   if ((d.precisions & (DDA_PLAN_C128 | DDA_PLAN_C64)) == 0 ||
       (d.precisions & ~(DDA_PLAN_C128 | DDA_PLAN_C64)) != 0)
@@ -92,8 +93,13 @@ bool make_layout(const dda_plan_desc_t& d, void* ws, Layout& L, std::string& why
   L.buf2 = c.take(b2);
   L.err_flag = c.take(64);
   if (d.precond2) {
-    L.P2 = c.take((size_t)(l / 2 + 1) * (m / 2 + 1) * (3 * n) * (3 * n) * 8);
-    L.C2 = c.take((size_t)6 * (2 * n - 1) * l * m * 16);
+    // edges of the relabelled box whose z is the Toeplitz level
+    const long fl = d.precond2 == 2 ? m : (d.precond2 == 3 ? n : l);
+    const long fm = d.precond2 == 2 ? n : (d.precond2 == 3 ? l : m);
+    const long fn = d.precond2 == 2 ? l : (d.precond2 == 3 ? m : n);
+    L.P2 = c.take((size_t)(fl / 2 + 1) * (fm / 2 + 1) * (3 * fn) * (3 * fn) * 8);
+    L.C2 = c.take((size_t)6 * (2 * fn - 1) * fl * fm * 16);
+    if (d.precond2 != 1) L.mat2 = c.take(nvox);
   }
   // complex128 field batch: the solver's residual and the cross sections' A c
   if (h128) L.R128 = c.take(16 * R * nu);

@@ -80,6 +80,7 @@ struct Layout {
   void* C64 = nullptr;
   void* P2 = nullptr;   // 2-level preconditioner: l m (3n)^2 complex64 inverse blocks
   void* C2 = nullptr;   // its build scratch: 6 (2n-1) l m complex128
+  void* mat2 = nullptr; // material mask in the relabelled frame (Toeplitz level x or y)
   // twiddles for the largest transform length
   void* tw128 = nullptr;
   void* tw64 = nullptr;

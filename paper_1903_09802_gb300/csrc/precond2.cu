@@ -435,22 +435,100 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Box the 2-level construction runs on: the plan's own (Toeplitz level z) or
+// the relabelled one whose z' is the chosen Toeplitz level, with its mask.
+struct P2Geom {
+  long l, m, n;
+  const uint8_t* mat;
+};
+
+// Relabelling of a field batch between the plan's frame and the frame whose
+// z' is the Toeplitz level (a rotation: G(R r) = R G(r) R^T):
+//   AXIS 2 (x): (x', y', z') = (y, z, x), component c' takes c = {1, 2, 0}[c'];
+//   AXIS 3 (y): (x', y', z') = (z, x, y), component c' takes c = {2, 0, 1}[c'].
+// TO: dst is in the relabelled frame; otherwise dst is in the plan's frame.
+// l, m, n are the plan's edges.
+template <typename T, int AXIS, bool TO>
+__global__ void k_frame(const cx<T>* __restrict__ src, cx<T>* __restrict__ dst, int nrhs, long l,
+                        long m, long n) {
+  pdl_entry();
+  const long nv = l * m * n, tot = (long)nrhs * 3 * nv;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < tot;
+       i += (long)gridDim.x * blockDim.x) {
+    const long rc = i / nv, v = i - rc * nv;
+    const long r = rc / 3;
+    const int c = (int)(rc - 3 * r);
+    long sidx;
+    int sc;
+    if (TO) {
+      if (AXIS == 2) {  // frame edges (m, n, l)
+        const long xp = v % m, yp = (v / m) % n, zp = v / (m * n);
+        sidx = (yp * m + xp) * l + zp;  // (x, y, z) = (z', x', y')
+        sc = c == 0 ? 1 : (c == 1 ? 2 : 0);
+      } else {  // frame edges (n, l, m)
+        const long xp = v % n, yp = (v / n) % l, zp = v / (n * l);
+        sidx = (xp * m + zp) * l + yp;  // (x, y, z) = (y', z', x')
+        sc = c == 0 ? 2 : (c == 1 ? 0 : 1);
+      }
+    } else {
+      const long x = v % l, y = (v / l) % m, z = v / (l * m);
+      if (AXIS == 2) {
+        sidx = (x * n + z) * m + y;  // frame (x', y', z') = (y, z, x), edges (m, n, l)
+        sc = c == 0 ? 2 : (c == 1 ? 0 : 1);
+      } else {
+        sidx = (y * l + x) * n + z;  // frame (x', y', z') = (z, x, y), edges (n, l, m)
+        sc = c == 0 ? 1 : (c == 1 ? 2 : 0);
+      }
+    }
+    dst[i] = src[(r * 3 + sc) * nv + sidx];
+  }
+}
+
+// The material mask in the relabelled frame.
+template <int AXIS>
+__global__ void k_frame_mask(const uint8_t* __restrict__ mat, uint8_t* __restrict__ out, long l,
+                             long m, long n) {
+  pdl_entry();
+  const long nv = l * m * n;
+  for (long v = blockIdx.x * (long)blockDim.x + threadIdx.x; v < nv;
+       v += (long)gridDim.x * blockDim.x) {
+    long sidx;
+    if (AXIS == 2) {
+      const long xp = v % m, yp = (v / m) % n, zp = v / (m * n);
+      sidx = (yp * m + xp) * l + zp;
+    } else {
+      const long xp = v % n, yp = (v / n) % l, zp = v / (n * l);
+      sidx = (xp * m + zp) * l + yp;
+    }
+    out[v] = mat[sidx];
+  }
+}
+
+inline P2Geom p2_geom(const dda_plan_s* p) {
+  switch (p->d.precond2) {
+    case 2: return P2Geom{p->m, p->n, p->l, static_cast<const uint8_t*>(p->w.mat2)};
+    case 3: return P2Geom{p->n, p->l, p->m, static_cast<const uint8_t*>(p->w.mat2)};
+    default: return P2Geom{p->l, p->m, p->n, p->mat};
+  }
+}
+
 inline unsigned grid_for(long n, int threads) {
   const long g = (n + threads - 1) / threads;
   return (unsigned)std::min<long>(std::max<long>(g, 1), 152L * 32);
 }
 
 template <typename T>
-void precond2_apply_impl(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cudaStream_t s) {
+void precond2_apply_impl(dda_plan_s* p, const P2Geom& gm, int nrhs, const cx<T>* v, cx<T>* z,
+                         cudaStream_t s) {
   const cx<T>* tw = tw_of<T>(p);
   cx<T>* t = static_cast<cx<T>*>(p->w.buf2);
-  const long l = p->l, m = p->m, n = p->n;
+  const long l = gm.l, m = gm.m, n = gm.n;
   const long lines = (long)nrhs * 3 * n * m;
   const long plane = l * m;
   const double u = (double)nrhs * 3 * p->nvox * sizeof(cx<T>);
   const double blk = (double)(l / 2 + 1) * (m / 2 + 1) * 9.0 * n * n * sizeof(float2);
   p->prof.begin(PROF_PC_XF, s, 2 * u + p->nvox);
-  launch_contig<T, false>(v, t, p->mat, nullptr, n * m, lines, (int)l, (int)l, l, (int)l, l, T(1), tw,
+  launch_contig<T, false>(v, t, gm.mat, nullptr, n * m, lines, (int)l, (int)l, l, (int)l, l, T(1), tw,
                           p->Lmax, s);
   p->prof.end(s);
   p->prof.begin(PROF_PC_YF, s, 2 * u);
@@ -508,7 +586,7 @@ void precond2_apply_impl(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cuda
                             T(1), tw, p->Lmax, s);
   p->prof.end(s);
   p->prof.begin(PROF_PC_XI, s, 2 * u + p->nvox);
-  launch_contig<T, true>(t, z, nullptr, p->mat, n * m, lines, (int)l, (int)l, l, (int)l, l, T(1), tw,
+  launch_contig<T, true>(t, z, nullptr, gm.mat, n * m, lines, (int)l, (int)l, l, (int)l, l, T(1), tw,
                          p->Lmax, s);
   p->prof.end(s);
 }
@@ -517,7 +595,27 @@ void precond2_apply_impl(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cuda
 
 template <typename T>
 void precond2_apply(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cudaStream_t s) {
-  precond2_apply_impl<T>(p, nrhs, v, z, s);
+  const P2Geom gm = p2_geom(p);
+  const int axis = p->d.precond2;
+  if (axis == 1) {
+    precond2_apply_impl<T>(p, gm, nrhs, v, z, s);
+    return;
+  }
+  // relabel into buf1 (two box-field batches: in and out), apply, relabel back
+  cx<T>* vin = static_cast<cx<T>*>(p->w.buf1);
+  cx<T>* vout = vin + (long)nrhs * 3 * p->nvox;
+  const unsigned g = grid_for((long)nrhs * 3 * p->nvox, 256);
+  note_launch();
+  if (axis == 2)
+    launch_k(k_frame<T, 2, true>, g, 256, 0, s, v, vin, nrhs, (long)p->l, (long)p->m, (long)p->n);
+  else
+    launch_k(k_frame<T, 3, true>, g, 256, 0, s, v, vin, nrhs, (long)p->l, (long)p->m, (long)p->n);
+  precond2_apply_impl<T>(p, gm, nrhs, vin, vout, s);
+  note_launch();
+  if (axis == 2)
+    launch_k(k_frame<T, 2, false>, g, 256, 0, s, vout, z, nrhs, (long)p->l, (long)p->m, (long)p->n);
+  else
+    launch_k(k_frame<T, 3, false>, g, 256, 0, s, vout, z, nrhs, (long)p->l, (long)p->m, (long)p->n);
 }
 template void precond2_apply<float>(dda_plan_s*, int, const cx<float>*, cx<float>*, cudaStream_t);
 template void precond2_apply<double>(dda_plan_s*, int, const cx<double>*, cx<double>*,
@@ -533,7 +631,17 @@ extern "C" dda_status_t dda_precond2_build(dda_plan_t p, void* stream) {
   if (p->nrhs_inc < 1)
     return fail(DDA_ERR_INVALID_ARG, "dda_precond2_build: set the incidence first (alpha_tilde)");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const long l = p->l, m = p->m, n = p->n, N = 3 * n;
+  if (p->d.precond2 != 1) {
+    note_launch();
+    if (p->d.precond2 == 2)
+      k_frame_mask<2><<<grid_for(p->nvox, 256), 256, 0, s>>>(
+          p->mat, static_cast<uint8_t*>(p->w.mat2), p->l, p->m, p->n);
+    else
+      k_frame_mask<3><<<grid_for(p->nvox, 256), 256, 0, s>>>(
+          p->mat, static_cast<uint8_t*>(p->w.mat2), p->l, p->m, p->n);
+  }
+  const P2Geom gm = p2_geom(p);
+  const long l = gm.l, m = gm.m, n = gm.n, N = 3 * n;
   double2* c2 = static_cast<double2*>(p->w.C2);
   note_launch();
   k_chan2<<<grid_for(l * m * (2 * n - 1), 128), 128, 0, s>>>(c2, l, m, n, p->d.dx, p->d.k,

@@ -34,6 +34,16 @@ STATUS = {
 
 CIRCULANTS = {"chan": 0, "strang": 1}  # preconditioner circulant: eq. 13 or Strang's
 
+
+def _precond2_code(v) -> int:
+    """2-level storage request: False (none), True or "z" (Toeplitz level z, the
+    paper's), "x" or "y" (that level Toeplitz instead)."""
+    if v is False or v is None or v == 0:
+        return 0
+    if v is True or v == "z" or v == 1:
+        return 1
+    return {"x": 2, "y": 3}[v]
+
 EXPORTS = ("dda_workspace_size", "dda_plan_create", "dda_set_incidence", "dda_incident_field",
            "dda_matvec", "dda_precond_build", "dda_precond_apply", "dda_precond_apply_noalloc",
            "dda_precond2_build", "dda_precond2_apply",
@@ -158,8 +168,8 @@ def _prec_of(t: torch.Tensor) -> int:
 
 def workspace_size(l, m, n, dx, k, n_materials=1, max_rhs=1, krylov_m=0,
                    precisions=PLAN_C128 | PLAN_C64, precond2=0, circulant="chan") -> int:
-    d = PlanDesc(l, m, n, dx, k, n_materials, max_rhs, krylov_m, precisions, int(bool(precond2)),
-                 CIRCULANTS[circulant])
+    d = PlanDesc(l, m, n, dx, k, n_materials, max_rhs, krylov_m, precisions,
+                 _precond2_code(precond2), CIRCULANTS[circulant])
     return int(_lib.dda_workspace_size(ctypes.byref(d)))
 
 
@@ -179,7 +189,7 @@ class Plan:
 
     def __init__(self, mat: torch.Tensor, eps, dx: float, k: float, max_rhs: int = 1,
                  krylov_m: int = 0, precisions: int = PLAN_C128 | PLAN_C64,
-                 precond2: bool = False, circulant: str = "chan"):
+                 precond2=False, circulant: str = "chan"):
         if mat.dtype != torch.uint8 or not mat.is_cuda or mat.dim() != 3:
             raise TypeError("mat must be a (n, m, l) uint8 CUDA tensor")
         self.mat = mat.contiguous()
@@ -187,7 +197,7 @@ class Plan:
         self.shape = (l, m, n)
         eps = [complex(e) for e in eps]
         self.desc = PlanDesc(l, m, n, float(dx), float(k), len(eps), int(max_rhs), int(krylov_m),
-                             int(precisions), int(bool(precond2)), CIRCULANTS[circulant])
+                             int(precisions), _precond2_code(precond2), CIRCULANTS[circulant])
         size = int(_lib.dda_workspace_size(ctypes.byref(self.desc)))
         if size == 0:
             raise DDAError(1, last_error())

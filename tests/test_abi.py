@@ -85,5 +85,10 @@ def test_workspace_options_validated():
     assert dda.workspace_size(16, 16, 8, 0.125, 5.0, 1, 2, 50, circulant="strang") == base
     desc = dda.PlanDesc(16, 16, 8, 0.125, 5.0, 1, 2, 50, 3, 0, 2)  # circulant 2: unknown
     assert dda._lib.dda_workspace_size(ctypes.byref(desc)) == 0
-    desc = dda.PlanDesc(16, 16, 8, 0.125, 5.0, 1, 2, 50, 3, 2, 0)  # precond2 2: invalid
+    desc = dda.PlanDesc(16, 16, 8, 0.125, 5.0, 1, 2, 50, 3, 4, 0)  # precond2 4: unknown
     assert dda._lib.dda_workspace_size(ctypes.byref(desc)) == 0
+    # Toeplitz level x on a 16 x 16 x 8 box: (8/2+1)(16/2+1) blocks of 48^2
+    # instead of (16/2+1)^2 blocks of 24^2, plus the relabelled mask
+    zsize = dda.workspace_size(16, 16, 8, 0.125, 5.0, 1, 2, 50, precond2="z")
+    xsize = dda.workspace_size(16, 16, 8, 0.125, 5.0, 1, 2, 50, precond2="x")
+    assert xsize - zsize >= (5 * 9 * 48 ** 2 - 81 * 24 ** 2) * 8

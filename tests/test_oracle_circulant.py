@@ -161,3 +161,36 @@ def test_multilevel_strang_keeps_the_central_band(comp):
     band = (2 * np.abs(ox) < l) & (2 * np.abs(oy) < m) & (2 * np.abs(oz) < n)
     assert np.allclose(C[band], T[band], rtol=1e-13, atol=1e-13 * np.abs(T).max())
     assert band.sum() > 0 and (~band).sum() > 0
+
+
+@pytest.mark.parametrize("axis", ["x", "y"])
+def test_precond2_other_toeplitz_axis_inverts_direct_construction(axis):
+    # 2-level preconditioner with the Toeplitz level on x (y): assembled
+    # directly as a dense matrix from the Chan circulant of the other two
+    # levels, independently of the relabelling the oracle applies it with.
+    from oracle.problem import Problem
+    l, m, n, dx, k = 3, 4, 2, 0.5, 1.4
+    levels = (False, True, True) if axis == "x" else (True, False, True)
+    C2 = circulant.multilevel_circulant(l, m, n, dx, k, levels)
+    z, y, x = np.meshgrid(np.arange(n), np.arange(m), np.arange(l), indexing="ij")
+    x, y, z = x.reshape(-1), y.reshape(-1), z.reshape(-1)
+    ox, oy, oz = x[:, None] - x[None, :], y[:, None] - y[None, :], z[:, None] - z[None, :]
+    ix = ox + l - 1 if axis == "x" else ox % l
+    iy = oy + m - 1 if axis == "y" else oy % m
+    iz = oz % n
+    mat = np.ones((n, m, l), dtype=np.uint8)
+    prob = Problem(mat=mat, dx=dx, k=k, eps=[1.7 + 0.1j], d=np.array([0, 0, 1.0]),
+                   e=np.array([1.0, 0, 0]))
+    ati = prob.alpha_tilde_inv
+    nv = l * m * n
+    P = np.zeros((3 * nv, 3 * nv), dtype=np.complex128)
+    for a in range(3):
+        for b in range(3):
+            P[a * nv:(a + 1) * nv, b * nv:(b + 1) * nv] = -dx ** 3 * C2[operator.comp_index(a, b)][iz, iy, ix]
+    P += ati * np.eye(3 * nv)
+    v = random_field((3, n, m, l), np.random.default_rng(9))
+    Pv = (P @ v.reshape(-1)).reshape(v.shape)
+    got = prob.precond2(restrict=False, axis=axis)(Pv)
+    assert np.allclose(got, v, rtol=1e-11, atol=1e-11)
+    # and it differs from the z-Toeplitz form (a different approximation)
+    assert not np.allclose(prob.precond2(restrict=False)(Pv), v, rtol=1e-6, atol=1e-6)

@@ -166,7 +166,8 @@ class Runner:
 
 
 def traffic_from_profiles(kernel):
-    """dram bytes per launch recorded by the committed ncu summary, if still current."""
+    """DRAM bytes per launch recorded by the committed ncu summary, if still
+    current: {box "lxmxn" or "*": bytes}."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_64cube.md")
     if not os.path.exists(path):
         return None
@@ -175,13 +176,17 @@ def traffic_from_profiles(kernel):
         if line.startswith("- ") and ":" in line:
             k, v = line[2:].split(":", 1)
             vals[k.strip()] = v.strip()
-    h = source_hash()
-    if vals.get("source_hash") != h:
+    if vals.get("source_hash") != source_hash():
         return None
-    try:
-        return float(vals["dram_bytes_per_launch"])
-    except Exception:
-        return None
+    out = {}
+    for k, v in vals.items():
+        if k.startswith("dram_bytes_per_launch"):
+            box = k[len("dram_bytes_per_launch"):].lstrip("_") or "*"
+            try:
+                out[box] = float(v)
+            except ValueError:
+                pass
+    return out or None
 
 
 def source_hash():
@@ -207,6 +212,19 @@ def roofline(runner, peak, peak_kind):
             t[2] += nbytes
     dom = max(tot, key=lambda k: tot[k][0])
     ms, cnt, nbytes = tot[dom]
+    # measured DRAM traffic per launch: the launch-weighted mean of the
+    # per-box figures over the same profiled step
+    traffic = None
+    per_box = traffic_from_profiles(dom)
+    if per_box:
+        num = den = 0.0
+        for case, prof in runner.prof:
+            c = prof[dom][1]
+            t = per_box.get("x".join(map(str, case.dims)), per_box.get("*"))
+            if c and t is not None:
+                num += c * t
+                den += c
+        traffic = round(num / den) if den else None
     achieved = nbytes / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
     total_ms = sum(x[0] for x in tot.values())
     share = {k: round(v[0] / total_ms, 4) for k, v in tot.items() if v[0] > 0}
@@ -215,50 +233,80 @@ def roofline(runner, peak, peak_kind):
             "peak_kind": f"{peak_kind} hbm_gbs", "unit": "GB/s", "frac": round(achieved / peak, 4),
             "avg_launch_us": round(ms / cnt * 1e3, 2) if cnt else None,
             "algorithmic_bytes_per_launch": round(nbytes / cnt) if cnt else None,
-            "traffic": traffic_from_profiles(dom), "share_of_profiled_kernel_time": share,
+            "traffic": traffic, "share_of_profiled_kernel_time": share,
             "achieved_gbs_by_class": per_class}
 
 
 def compare_solvers(runner):
-    """Untimed side measurements on the two 64^3 systems of the sweep (m = 1.31
-    and 1.31 + 0.05i, both polarisations): solve time per right-hand side and
-    iterations for the variants the paper and the benchmark spec compare."""
+    """Untimed side measurements: solve time per right-hand side and iterations
+    of the variants the paper and the benchmark spec compare, on the two aspect-1
+    64^3 systems of the sweep (m = 1.31 and 1.31 + 0.05i, both polarisations),
+    and the preconditioner's Toeplitz-level choice on the long (aspect-2,
+    64x64x128) m = 1.31 prism."""
     import torch
     dda = runner.dda
+    c64 = dict(inner_prec=dda.C64, inner_tol=1e-4)
     variants = {
-        "gmres_3level_c64_fp64ir": dict(precond=3, inner_prec=dda.C64, inner_tol=1e-4,
-                                        reorth_eta=REORTH_ETA),
-        "gmres_none_c64_fp64ir": dict(precond=0, inner_prec=dda.C64, inner_tol=1e-4,
-                                      reorth_eta=REORTH_ETA),
+        "gmres_3level_c64_fp64ir": dict(precond=3, reorth_eta=REORTH_ETA, **c64),
+        "gmres_none_c64_fp64ir": dict(precond=0, reorth_eta=REORTH_ETA, **c64),
         "gmres_3level_c128": dict(precond=3, inner_prec=dda.C128, reorth_eta=REORTH_ETA),
-        "bicgstab_3level_c64_fp64ir": dict(precond=3, inner_prec=dda.C64, inner_tol=1e-4,
-                                           method=dda.BICGSTAB),
-        "gmres_2level_c64_fp64ir": dict(precond=2, inner_prec=dda.C64, inner_tol=1e-4,
-                                        reorth_eta=REORTH_ETA),
+        "bicgstab_3level_c64_fp64ir": dict(precond=3, method=dda.BICGSTAB, **c64),
+        "gmres_2level_c64_fp64ir": dict(precond=2, reorth_eta=REORTH_ETA, **c64),
+        "bicgstab_2level_c64_fp64ir": dict(precond=2, method=dda.BICGSTAB, **c64),
     }
-    out = {}
-    for i, case in enumerate(runner.cases):
-        if case.dims != (64, 64, 64):
-            continue
-        plan = dda.Plan(runner.masks[i], case.eps, case.dx, case.k, max_rhs=2, krylov_m=50,
-                        precond2=True)
-        plan.set_incidence(case.dirs, case.pols)
-        plan.precond_build()
-        key = f"m={complex(case.eps[0]) ** 0.5:.2f}"
-        out[key] = {}
+
+    def timed(fn):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        plan.precond2_build()  # the paper's 2-level blocks: FP64 build, complex64 inverses
+        r = fn()
         torch.cuda.synchronize()
-        out[key]["precond2_build_ms"] = round(1e3 * (time.perf_counter() - t0), 2)
-        for name, kw in variants.items():
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            res = plan.solve(tol=1e-6, restart=50, max_iters=3000, raise_on_error=False, **kw)
-            torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            out[key][name] = {"ms_per_solve": round(1e3 * dt / case.nrhs, 2), "iters": res.iters,
-                              "converged": all(res.converged)}
+        return r, time.perf_counter() - t0
+
+    def run(plan, case, kw):
+        res, dt = timed(lambda: plan.solve(tol=1e-6, restart=50, max_iters=3000,
+                                           raise_on_error=False, **kw))
+        return {"ms_per_solve": round(1e3 * dt / case.nrhs, 2), "iters": res.iters,
+                "converged": all(res.converged)}
+
+    out = {}
+    for i, case in enumerate(runner.cases):
+        m_key = f"m={complex(case.eps[0]) ** 0.5:.2f}"
+        if case.dims == (64, 64, 64):
+            plan = dda.Plan(runner.masks[i], case.eps, case.dx, case.k, max_rhs=2, krylov_m=50,
+                            precond2=True)
+            plan.set_incidence(case.dirs, case.pols)
+            plan.precond_build()
+            key = m_key
+            out[key] = {}
+            _, dt = timed(plan.precond2_build)  # FP64 build, complex64 Gauss-Jordan inverses
+            out[key]["precond2_build_ms"] = round(1e3 * dt, 2)
+            for name, kw in variants.items():
+                out[key][name] = run(plan, case, kw)
+            del plan
+            # Strang's circulant instead of T. Chan's (eq. 13)
+            plan = dda.Plan(runner.masks[i], case.eps, case.dx, case.k, max_rhs=2, krylov_m=50,
+                            circulant="strang")
+            plan.set_incidence(case.dirs, case.pols)
+            plan.precond_build()
+            out[key]["gmres_3level_strang_c64_fp64ir"] = run(
+                plan, case, dict(precond=3, reorth_eta=REORTH_ETA, **c64))
+            del plan
+        elif case.dims == (64, 64, 128) and complex(case.eps[0]).imag == 0:
+            key = m_key + " long prism 64x64x128"
+            out[key] = {}
+            for axis in ("z", "x"):
+                plan = dda.Plan(runner.masks[i], case.eps, case.dx, case.k, max_rhs=2,
+                                krylov_m=50, precond2=axis)
+                plan.set_incidence(case.dirs, case.pols)
+                _, dt = timed(plan.precond2_build)
+                out[key][f"precond2_{axis}_build_ms"] = round(1e3 * dt, 2)
+                out[key][f"gmres_2level_toeplitz_{axis}_c64_fp64ir"] = run(
+                    plan, case, dict(precond=2, reorth_eta=REORTH_ETA, **c64))
+                if axis == "z":
+                    plan.precond_build()
+                    out[key]["gmres_3level_c64_fp64ir"] = run(
+                        plan, case, dict(precond=3, reorth_eta=REORTH_ETA, **c64))
+                del plan
     return out
 
 

@@ -77,6 +77,9 @@ bool make_layout(const dda_plan_desc_t& d, void* ws, Layout& L, std::string& why
   if (h128) {
     L.G128 = c.take(gsz * 16);
     L.C128 = c.take(csz * 16);
+    L.twdf = c.take(Lmax * 16);
+    L.Gdf = c.take(gsz * 16);
+    L.ainvdf = c.take(R * K1 * 16);
   }
   if (h64) {
     L.G64 = c.take(gsz * 8);
@@ -330,6 +333,11 @@ extern "C" dda_status_t dda_plan_create(dda_plan_t* out, const dda_plan_desc_t* 
     }
     cudaMemcpyAsync(L.tw128, t128.data(), p->Lmax * 16, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(L.tw64, t64.data(), p->Lmax * 8, cudaMemcpyHostToDevice, s);
+    if (L.twdf) {
+      std::vector<cx<df>> tdf(p->Lmax);
+      for (int t = 0; t < p->Lmax; ++t) tdf[t] = mk<df>(df(t128[t].x), df(t128[t].y));
+      cudaMemcpyAsync(L.twdf, tdf.data(), p->Lmax * 16, cudaMemcpyHostToDevice, s);
+    }
   }
   cudaMemsetAsync(L.err_flag, 0, 64, s);
 
@@ -345,6 +353,12 @@ extern "C" dda_status_t dda_plan_create(dda_plan_t* out, const dda_plan_desc_t* 
     k_compress<<<grid_for((long)p->hx * p->hy * p->hz, 256), 256, 0, s>>>(
         scratch, p->Lx, p->Ly, p->Lz, p->hx, p->hy, p->hz, c, static_cast<double2*>(L.G128),
         static_cast<float2*>(L.G64));
+  }
+  if (L.Gdf) {
+    const long ng = (long)p->hx * p->hy * p->hz * 6;
+    note_launch();
+    k_to_df<<<grid_for(ng, 256), 256, 0, s>>>(static_cast<const double2*>(L.G128),
+                                                static_cast<cx<df>*>(L.Gdf), ng);
   }
   const dda_status_t cs = check_cuda("dda_plan_create");
   if (cs != DDA_OK) {
@@ -420,6 +434,12 @@ extern "C" dda_status_t dda_set_incidence(dda_plan_t p, int32_t nrhs, const dda_
                   cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(p->w.dainv128, p->dainv_host.data(), p->dainv_host.size() * sizeof(double),
                   cudaMemcpyHostToDevice, s);
+  if (p->w.ainvdf) {
+    std::vector<cx<df>> adf(p->ainv_host.size() / 2);
+    for (size_t i = 0; i < adf.size(); ++i)
+      adf[i] = mk<df>(df(p->ainv_host[2 * i]), df(p->ainv_host[2 * i + 1]));
+    cudaMemcpyAsync(p->w.ainvdf, adf.data(), adf.size() * 16, cudaMemcpyHostToDevice, s);
+  }
   p->inc.assign(inc, inc + nrhs);
   p->nrhs_inc = nrhs;
   return check_cuda("dda_set_incidence");

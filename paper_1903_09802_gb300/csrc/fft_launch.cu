@@ -203,5 +203,7 @@ DDA_INST_FFT(float, false)
 DDA_INST_FFT(float, true)
 DDA_INST_FFT(double, false)
 DDA_INST_FFT(double, true)
+DDA_INST_FFT(df, false)
+DDA_INST_FFT(df, true)
 
 }  // namespace dda

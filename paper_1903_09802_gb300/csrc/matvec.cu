@@ -236,10 +236,8 @@ inline int ilog2(int v) {
   return b;
 }
 
-}  // namespace
-
 template <typename T>
-void matvec_impl(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t s) {
+void matvec_core(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t s) {
   const cx<T>* tw = tw_of<T>(p);
   cx<T>* b1 = static_cast<cx<T>*>(p->w.buf1);
   cx<T>* b2 = static_cast<cx<T>*>(p->w.buf2);
@@ -302,8 +300,31 @@ void matvec_impl(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t
   }
 }
 
-template void matvec_impl<float>(dda_plan_s*, int, const cx<float>*, cx<float>*, cudaStream_t);
-template void matvec_impl<double>(dda_plan_s*, int, const cx<double>*, cx<double>*, cudaStream_t);
+}  // namespace
+
+template <>
+void matvec_impl<float>(dda_plan_s* p, int nrhs, const cx<float>* x, cx<float>* y,
+                        cudaStream_t s) {
+  matvec_core<float>(p, nrhs, x, y, s);
+}
+
+// complex128 fields, double-float arithmetic (about 48 bits, at FP32 rates):
+// y <- x converted, the five passes in place on y (the epilogue reads each
+// input value before writing the output value of the same thread), y
+// converted back.  x and y must not overlap unless they are the same buffer.
+template <>
+void matvec_impl<double>(dda_plan_s* p, int nrhs, const cx<double>* x, cx<double>* y,
+                         cudaStream_t s) {
+  const long n = (long)nrhs * 3 * p->nvox;
+  const unsigned g = (unsigned)std::min<long>((n + 255) / 256, 152L * 32);
+  cx<df>* ydf = reinterpret_cast<cx<df>*>(y);
+  note_launch();
+  launch_k(k_to_df, g, 256, 0, s, reinterpret_cast<const double2*>(x), ydf, n);
+  matvec_core<df>(p, nrhs, ydf, ydf, s);
+  note_launch();
+  launch_k(k_from_df, g, 256, 0, s, static_cast<const cx<df>*>(ydf),
+           reinterpret_cast<double2*>(y), n);
+}
 
 }  // namespace dda
 

@@ -10,6 +10,7 @@
 
 #include "../../include/dda.h"
 #include "cx.cuh"
+#include "dfloat.cuh"
 #include "fft_core.cuh"
 #include "profile.hpp"
 
@@ -84,6 +85,11 @@ struct Layout {
   // twiddles for the largest transform length
   void* tw128 = nullptr;
   void* tw64 = nullptr;
+  // double-float copies of the twiddles, the kernel spectrum and alpha^{-1},
+  // for the complex128 matvec that runs in double-float arithmetic
+  void* twdf = nullptr;
+  void* Gdf = nullptr;
+  void* ainvdf = nullptr;
   // alpha^{-1} per (rhs, material 0..K); entry 0 is alpha_tilde^{-1}
   void* ainv128 = nullptr;
   void* ainv64 = nullptr;
@@ -155,6 +161,11 @@ void fft3d_inplace(cx<T>* data, long nbatch, int Lx, int Ly, int Lz, T scale, co
 // Operator pieces (matvec.cu, precond.cu), nrhs fields of the box.
 template <typename T>
 void matvec_impl(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t s);
+template <>
+void matvec_impl<float>(dda_plan_s* p, int nrhs, const cx<float>* x, cx<float>* y, cudaStream_t s);
+template <>
+void matvec_impl<double>(dda_plan_s* p, int nrhs, const cx<double>* x, cx<double>* y,
+                         cudaStream_t s);
 template <typename T>
 void precond_apply_impl(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cudaStream_t s);
 template <typename T>
@@ -171,7 +182,13 @@ template <> inline const cx<double>* tw_of<double>(const dda_plan_s* p) {
 template <> inline const cx<float>* tw_of<float>(const dda_plan_s* p) {
   return static_cast<const cx<float>*>(p->w.tw64);
 }
+template <> inline const cx<df>* tw_of<df>(const dda_plan_s* p) {
+  return static_cast<const cx<df>*>(p->w.twdf);
+}
 template <typename T> inline const cx<T>* G_of(const dda_plan_s* p);
+template <> inline const cx<df>* G_of<df>(const dda_plan_s* p) {
+  return static_cast<const cx<df>*>(p->w.Gdf);
+}
 template <> inline const cx<double>* G_of<double>(const dda_plan_s* p) {
   return static_cast<const cx<double>*>(p->w.G128);
 }
@@ -191,6 +208,9 @@ template <> inline const cx<double>* ainv_of<double>(const dda_plan_s* p) {
 }
 template <> inline const cx<float>* ainv_of<float>(const dda_plan_s* p) {
   return static_cast<const cx<float>*>(p->w.ainv64);
+}
+template <> inline const cx<df>* ainv_of<df>(const dda_plan_s* p) {
+  return static_cast<const cx<df>*>(p->w.ainvdf);
 }
 
 }  // namespace dda

@@ -22,9 +22,18 @@
 #include <cstdint>
 #include <cstdlib>
 
+#include "dfloat.cuh"
 #include "fft_core.cuh"
 
 namespace dda {
+
+// Threads per CTA of the three-component pass: double-float values need
+// twice the registers of their arithmetic, so that kernel keeps 256 threads
+// (255 registers each) instead of 512.
+template <typename T>
+__host__ __device__ constexpr int fft3c_max_threads() {
+  return sizeof(T) == 4 ? 768 : (std::is_same<T, df>::value ? 256 : 512);
+}
 
 template <typename T, bool INV>
 __global__ void __launch_bounds__(256)
@@ -192,7 +201,7 @@ __device__ __forceinline__ int mirror_perm(int r, int n) {
 // (component, column) with the column fastest, so shared-memory index and
 // tile index coincide.
 template <typename T, class Op, bool FIX>
-__global__ void __launch_bounds__(sizeof(T) == 8 ? 512 : 768)
+__global__ void __launch_bounds__(fft3c_max_threads<T>())
     k_fft3c(cx<T>* data, long ncols, int Lin, long js, long cs, long ss, int Lout, Op op,
             const cx<T>* __restrict__ tw, int twshift, RadixPlan rp, int nbc_sh, int row_len,
             int nrows) {
@@ -365,7 +374,7 @@ void launch_fft3c(cx<T>* data, long ncols, long nslabs, int L, int Lin, long js,
                   int Lout, const Op& op, const cx<T>* tw, int Lmax, int row_len, int nrows,
                   cudaStream_t s) {
   if (ncols <= 0 || nslabs <= 0) return;
-  const int cap = (sizeof(T) == 8 ? 512 : 768) * kElemsPerThread;
+  const int cap = fft3c_max_threads<T>() * kElemsPerThread;
   static const int nbc_env = [] {
     const char* v = getenv("DDA_FFT3C_COLS");
     return v ? atoi(v) : 0;

@@ -70,7 +70,7 @@ struct KernelMul {
 //   y = a x                 (air voxel, a = alpha_tilde^{-1})
 // with coef = dx^3 / (2l 2m 2n) (the inverse transforms are unnormalised).
 template <typename T>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(std::is_same<T, df>::value ? 256 : 512)
     k_mv_epilogue(const cx<T>* __restrict__ buf1, const cx<T>* __restrict__ x,
                   cx<T>* __restrict__ y, const uint8_t* __restrict__ mat,
                   const cx<T>* __restrict__ ainv, int K1, long nlines, long nm, int l, int Lx,
@@ -279,7 +279,7 @@ void matvec_core(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t
     }
   }
   {
-    const int cap = 512 * kElemsPerThread;
+    const int cap = (std::is_same<T, df>::value ? 256 : 512) * kElemsPerThread;
     int per_cta = std::min(4096, cap);
     while (per_cta > 512 && per_cta > Lx && (lines * Lx + per_cta - 1) / per_cta < 2 * 152)
       per_cta /= 2;

@@ -496,76 +496,94 @@ __device__ __forceinline__ void givens(double2 a, double2 b, double& c, double2&
   rho = make_double2(ph.x * nr, ph.y * nr);
 }
 
-__device__ __forceinline__ void givens_step(double2* __restrict__ H, double* __restrict__ cs,
-                                            double2* __restrict__ sn, double2* __restrict__ g,
-                                            double* __restrict__ scal, int* __restrict__ active,
-                                            int* __restrict__ jlen, int* __restrict__ flags,
-                                            int* __restrict__ iters, int m, int j, double brk,
-                                            int r) {
-  const double n2 = scal[(long)r * 16 + 8];  // ||w||^2 after Gram-Schmidt
-  const double hn = sqrt(n2);
-  double2* h = H + (long)r * (m + 1) * m + (long)j * (m + 1);
-  double colnorm2 = n2;
-  for (int i = 0; i <= j; ++i) colnorm2 += h[i].x * h[i].x + h[i].y * h[i].y;
-  double* c = cs + (long)r * m;
-  double2* s = sn + (long)r * m;
-  double2* gg = g + (long)r * (m + 1);
-  for (int i = 0; i < j; ++i) {
-    const double2 a = h[i], b = h[i + 1];
-    h[i] = make_double2(c[i] * a.x + (s[i].x * b.x - s[i].y * b.y),
-                        c[i] * a.y + (s[i].x * b.y + s[i].y * b.x));
-    // -conj(s) a + c b
-    h[i + 1] = make_double2(-(s[i].x * a.x + s[i].y * a.y) + c[i] * b.x,
-                            -(s[i].x * a.y - s[i].y * a.x) + c[i] * b.y);
-  }
-  double cj;
-  double2 sj, rho;
-  givens(h[j], make_double2(hn, 0.0), cj, sj, rho);
-  c[j] = cj;
-  s[j] = sj;
-  h[j] = rho;
-  h[j + 1] = make_double2(0.0, 0.0);
-  const double2 gj = gg[j];
-  gg[j + 1] = make_double2(-(sj.x * gj.x + sj.y * gj.y), -(sj.x * gj.y - sj.y * gj.x));
-  gg[j] = make_double2(cj * gj.x, cj * gj.y);
-  const double res = hypot(gg[j + 1].x, gg[j + 1].y);
-  double* sc = scal + (long)r * 16;
-  sc[4] = res;
-  sc[5] = hn > 0.0 ? 1.0 / hn : 0.0;
-  jlen[r] = j + 1;
-  iters[r] += 1;
-  if (!isfinite(res) || !isfinite(hn)) {
-    flags[r] |= 1;
-    active[r] = 0;
-  } else if (res <= sc[3]) {
-    active[r] = 0;
-  } else if (hn <= brk * sqrt(colnorm2)) {
-    flags[r] |= 2;  // breakdown: the Krylov space is invariant, the cycle's solution is exact
-    active[r] = 0;
-  }
-}
-
-// One thread per right-hand side: finish column j of H (norm of w, earlier
-// rotations, new rotation), update g and the residual estimate, decide
-// whether the cycle of this right-hand side goes on.
-__global__ void k_givens(double2* __restrict__ H, double* __restrict__ cs, double2* __restrict__ sn,
-                         double2* __restrict__ g, double* __restrict__ scal,
-                         int* __restrict__ active, int* __restrict__ jlen, int* __restrict__ flags,
-                         int* __restrict__ iters, int nrhs, int m, int j, double brk,
-                         int* __restrict__ count_out) {
+// One warp per right-hand side: the warp stages column j of H and the
+// earlier rotations in shared memory with parallel loads, lane 0 applies the
+// rotations (a dependent chain: from shared memory it takes cycles, not
+// memory latencies), computes the new rotation, updates g and the residual
+// estimate and decides whether the cycle of this right-hand side goes on; the
+// warp writes the column back.  With count_out, the last block (ticket) also
+// counts the right-hand sides still iterating.
+__global__ void __launch_bounds__(32)
+    k_givens(double2* __restrict__ H, double* __restrict__ cs, double2* __restrict__ sn,
+             double2* __restrict__ g, double* __restrict__ scal, int* __restrict__ active,
+             int* __restrict__ jlen, int* __restrict__ flags, int* __restrict__ iters, int nrhs,
+             int m, int j, double brk, int* __restrict__ count_out, int* __restrict__ ticket) {
   pdl_entry();
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < nrhs && active[r]) givens_step(H, cs, sn, g, scal, active, jlen, flags, iters, m, j, brk, r);
-  // single-block launches also count the right-hand sides still iterating
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* hs = reinterpret_cast<double2*>(smem_raw);  // [j + 2]
+  double2* ss = hs + (j + 2);                           // [j]
+  double* cc = reinterpret_cast<double*>(ss + j);       // [j]
+  const int r = blockIdx.x, lane = threadIdx.x;
+  if (active[r]) {
+    double2* h = H + (long)r * (m + 1) * m + (long)j * (m + 1);
+    double* c = cs + (long)r * m;
+    double2* sv = sn + (long)r * m;
+    for (int i = lane; i <= j; i += 32) hs[i] = h[i];
+    for (int i = lane; i < j; i += 32) {
+      ss[i] = sv[i];
+      cc[i] = c[i];
+    }
+    __syncwarp();
+    if (lane == 0) {
+      const double n2 = scal[(long)r * 16 + 8];  // ||w||^2 after Gram-Schmidt
+      const double hn = sqrt(n2);
+      double colnorm2 = n2;
+      for (int i = 0; i <= j; ++i) colnorm2 += hs[i].x * hs[i].x + hs[i].y * hs[i].y;
+      for (int i = 0; i < j; ++i) {
+        const double2 a = hs[i], b = hs[i + 1], si = ss[i];
+        const double ci = cc[i];
+        hs[i] = make_double2(ci * a.x + (si.x * b.x - si.y * b.y),
+                             ci * a.y + (si.x * b.y + si.y * b.x));
+        // -conj(s) a + c b
+        hs[i + 1] = make_double2(-(si.x * a.x + si.y * a.y) + ci * b.x,
+                                 -(si.x * a.y - si.y * a.x) + ci * b.y);
+      }
+      double cj;
+      double2 sj, rho;
+      givens(hs[j], make_double2(hn, 0.0), cj, sj, rho);
+      c[j] = cj;
+      sv[j] = sj;
+      hs[j] = rho;
+      hs[j + 1] = make_double2(0.0, 0.0);
+      double2* gg = g + (long)r * (m + 1);
+      const double2 gj = gg[j];
+      gg[j + 1] = make_double2(-(sj.x * gj.x + sj.y * gj.y), -(sj.x * gj.y - sj.y * gj.x));
+      gg[j] = make_double2(cj * gj.x, cj * gj.y);
+      const double res = hypot(gg[j + 1].x, gg[j + 1].y);
+      double* sc = scal + (long)r * 16;
+      sc[4] = res;
+      sc[5] = hn > 0.0 ? 1.0 / hn : 0.0;
+      jlen[r] = j + 1;
+      iters[r] += 1;
+      if (!isfinite(res) || !isfinite(hn)) {
+        flags[r] |= 1;
+        active[r] = 0;
+      } else if (res <= sc[3]) {
+        active[r] = 0;
+      } else if (hn <= brk * sqrt(colnorm2)) {
+        flags[r] |= 2;  // breakdown: the Krylov space is invariant, the cycle's solution is exact
+        active[r] = 0;
+      }
+    }
+    __syncwarp();
+    for (int i = lane; i <= j + 1; i += 32) h[i] = hs[i];
+  }
   if (count_out != nullptr) {
-    __syncthreads();
-    int c = r < nrhs ? active[r] : 0;
+    __shared__ int s_last;
+    __threadfence();
+    if (lane == 0) s_last = atomicAdd(ticket, 1) == (int)gridDim.x - 1;
+    __syncwarp();
+    if (s_last) {
+      __threadfence();
+      int cnt = 0;
+      for (int q = lane; q < nrhs; q += 32) cnt += __ldcg(&active[q]);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-    __shared__ int wsum[2];
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = c;
-    __syncthreads();
-    if (threadIdx.x == 0) *count_out = wsum[0] + (blockDim.x > 32 ? wsum[1] : 0);
+      for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+      if (lane == 0) {
+        *count_out = cnt;
+        *ticket = 0;
+      }
+    }
   }
 }
 
@@ -1126,6 +1144,7 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
       if ((status = check_cuda("dda_solve")) != DDA_OK) break;
       continue;
     }
+    cudaMemsetAsync(st.counters + 8, 0, sizeof(int), s);  // Givens kernel's ticket
     note_launch();
     k_start_cycle<T><<<vgrid, kNT, 0, s>>>(R, V, nu, st.scal, st.g, m, st.run, st.active,
                                            st.jlen, o.tol, o.inner_tol);
@@ -1168,18 +1187,14 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
         if (pass == 0) p->prof.end(s);
       }
       note_launch();
-      const bool one_block = nrhs <= 64;  // the Givens kernel counts the active RHS itself
-      launch_k(k_givens, (nrhs + 63) / 64, 64, 0, s, st.H, st.cs, st.sn, st.g, st.scal, st.active,
-               st.jlen, st.flags, st.iters, nrhs, m, j, brk,
-               one_block ? st.counters + (j & 1) : nullptr);
+      // the Givens kernel also counts the right-hand sides still iterating
+      launch_k(k_givens, nrhs, 32, (size_t)(j + 2) * 16 + (size_t)j * 24, s, st.H, st.cs, st.sn,
+               st.g, st.scal, st.active, st.jlen, st.flags, st.iters, nrhs, m, j, brk,
+               st.counters + (j & 1), st.counters + 8);
       if (j + 1 < steps) {
         note_launch();
         launch_k(k_scale<T>, vgrid, kNT, 0, s, W, V + (long)(j + 1) * vstride, nu, st.scal,
                  st.active);
-      }
-      if (!one_block) {
-        note_launch();
-        launch_k(k_count_active, 1, 32, 0, s, st.active, nrhs, st.counters + (j & 1));
       }
       cudaMemcpyAsync(p->pinned + (j & 1), st.counters + (j & 1), sizeof(int),
                       cudaMemcpyDeviceToHost, s);

@@ -239,7 +239,7 @@ def roofline(runner, peak, peak_kind):
 
 def compare_solvers(runner):
     """Untimed side measurements: solve time per right-hand side and iterations
-    of the variants the paper and the benchmark spec compare, on the two aspect-1
+    of the solver and preconditioner variants the paper discusses, on the two aspect-1
     64^3 systems of the sweep (m = 1.31 and 1.31 + 0.05i, both polarisations),
     and the preconditioner's Toeplitz-level choice on the long (aspect-2,
     64x64x128) m = 1.31 prism."""

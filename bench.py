@@ -307,6 +307,27 @@ def compare_solvers(runner):
                     out[key]["gmres_3level_c64_fp64ir"] = run(
                         plan, case, dict(precond=3, reorth_eta=REORTH_ETA, **c64))
                 del plan
+    # an uneven batch: the 32^3 prisms of the same sweep at x = 10 (boxes 32x32x{16,32,64}),
+    # solved one after another and concurrently (dda_solve_many, one stream per plan)
+    from dda_inputs import config2_cases
+    small = [c for c in config2_cases(32, 10.0, seed=0) if abs(complex(c.eps[0]) - 1.78 ** 2) > 1e-9]
+    plans = []
+    for c in small:
+        pl = dda.Plan(torch.from_numpy(c.mask()).to(runner.dev), c.eps, c.dx, c.k, max_rhs=2,
+                      krylov_m=50)
+        pl.set_incidence(c.dirs, c.pols)
+        pl.precond_build()
+        plans.append(pl)
+    kw = dict(tol=1e-6, restart=50, max_iters=3000, precond=3, reorth_eta=REORTH_ETA,
+              raise_on_error=False, **c64)
+    seq, t_seq = timed(lambda: [pl.solve(**kw) for pl in plans])
+    par, t_par = timed(lambda: dda.solve_many(plans, **kw))
+    nsolves = sum(c.nrhs for c in small)
+    out["uneven batch 32^3 x=10 (6 prisms, 12 solves)"] = {
+        "sequential_ms_per_solve": round(1e3 * t_seq / nsolves, 2),
+        "concurrent_ms_per_solve": round(1e3 * t_par / nsolves, 2),
+        "iters": [r.iters for r in par],
+        "same_iterations": [r.iters for r in seq] == [r.iters for r in par]}
     return out
 
 

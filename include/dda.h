@@ -239,6 +239,22 @@ dda_status_t dda_fft3d(dda_plan_t plan, int32_t prec, int32_t nbatch, void* d_da
 dda_status_t dda_solve(dda_plan_t plan, int32_t nrhs, const void* d_b, void* d_x,
                        const dda_solve_opts_t* opts, dda_rhs_stats_t* h_stats, void* stream);
 
+/* Several independent systems solved concurrently: plan i's system (arguments
+ * as dda_solve's, arrays of length nplans; d_b may be NULL or hold NULL
+ * entries for the incident field, h_stats may be NULL or hold NULL entries)
+ * with the shared options *opts.  One host thread per plan drives its solve
+ * loop on streams[i], so the short kernels of small systems (an uneven batch
+ * of prisms) overlap on the GPU; every result equals that of the same
+ * dda_solve call alone.  Plans must be distinct and so must the non-NULL
+ * streams (NULL entries use the default stream and serialise).  Returns when
+ * every solve has ended: DDA_OK, or the first failing status in plan order
+ * (dda_last_error names the plan).  Not part of the paper: a batching form of
+ * its solve (Section 4). */
+dda_status_t dda_solve_many(int32_t nplans, const dda_plan_t* plans, const int32_t* nrhs,
+                            const void* const* d_b, void* const* d_x,
+                            const dda_solve_opts_t* opts, dda_rhs_stats_t* const* h_stats,
+                            void* const* streams);
+
 /* Cross sections of the solutions d_c (complex128 box fields) for the
  * incidence set by dda_set_incidence; h_out[3*r + {0,1,2}] = C_ext, C_abs,
  * C_sca of right-hand side r.  The paper prints no formula; these are the

@@ -47,7 +47,7 @@ def _precond2_code(v) -> int:
 EXPORTS = ("dda_workspace_size", "dda_plan_create", "dda_set_incidence", "dda_incident_field",
            "dda_matvec", "dda_precond_build", "dda_precond_apply", "dda_precond_apply_noalloc",
            "dda_precond2_build", "dda_precond2_apply",
-           "dda_fft3d", "dda_solve",
+           "dda_fft3d", "dda_solve", "dda_solve_many",
            "dda_cross_sections", "dda_adjoint_rhs", "dda_ext_gradient", "dda_profile_enable", "dda_profile_read", "dda_plan_destroy",
            "dda_last_error", "dda_launch_count")
 
@@ -102,6 +102,8 @@ _lib.dda_precond_build.restype = ctypes.c_int
 _lib.dda_precond_build.argtypes = [_vp, _vp]
 _lib.dda_precond_apply.restype = ctypes.c_int
 _lib.dda_precond_apply.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, _vp]
+_lib.dda_solve_many.restype = ctypes.c_int
+_lib.dda_solve_many.argtypes = [ctypes.c_int32, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.dda_precond2_build.restype = ctypes.c_int
 _lib.dda_precond2_build.argtypes = [_vp, _vp]
 _lib.dda_precond2_apply.restype = ctypes.c_int
@@ -339,3 +341,37 @@ class Plan:
         out = (ctypes.c_double * (3 * nrhs))()
         _check(_lib.dda_cross_sections(self._h, nrhs, _ptr(c), out, _stream()))
         return np.array(out[:], dtype=np.float64).reshape(nrhs, 3)
+
+
+def solve_many(plans, bs=None, streams=None, tol: float = 1e-6, max_iters: int = 2000,
+               restart: int = 50, precond: int = 3, inner_prec: int = C128,
+               inner_tol: float = 0.0, reorth_eta: float = 0.5 ** 0.5, method: int = 0,
+               raise_on_error: bool = True) -> list:
+    """dda_solve_many: the systems of several plans solved concurrently, one
+    stream each (created here unless given); returns one SolveResult per plan."""
+    n = len(plans)
+    cur = torch.cuda.current_stream()
+    if streams is None:
+        streams = [torch.cuda.Stream(device=p.mat.device) for p in plans]
+    xs, stats = [], []
+    for p in plans:
+        xs.append(torch.zeros(p.field_shape(p.nrhs), dtype=torch.complex128, device=p.mat.device))
+        stats.append((RhsStats * p.nrhs)())
+    for s in streams:
+        s.wait_stream(cur)  # the zeroed x and any b are ready before the solves start
+    arr = lambda ptrs: (ctypes.c_void_p * n)(*[ctypes.c_void_p(v) for v in ptrs])
+    hp = (ctypes.c_void_p * n)(*[ctypes.c_void_p(p._h.value) for p in plans])
+    nr = (ctypes.c_int32 * n)(*[p.nrhs for p in plans])
+    bp = arr([b.contiguous().data_ptr() if b is not None else 0 for b in bs]) if bs else None
+    xp = arr([x.data_ptr() for x in xs])
+    sp = (ctypes.POINTER(RhsStats) * n)(*[ctypes.cast(st, ctypes.POINTER(RhsStats)) for st in stats])
+    strp = arr([s.cuda_stream for s in streams])
+    opts = SolveOpts(tol, max_iters, restart, precond, inner_prec, inner_tol, reorth_eta, method)
+    st = _lib.dda_solve_many(n, hp, nr, bp, xp, ctypes.byref(opts), sp, strp)
+    for s in streams:
+        cur.wait_stream(s)
+    if st != 0 and raise_on_error:
+        raise DDAError(st, last_error())
+    return [SolveResult(x, [q.iters for q in sv], [q.cycles for q in sv],
+                        [bool(q.converged) for q in sv], [q.rel_resid for q in sv], st,
+                        [q.reorth for q in sv]) for x, sv in zip(xs, stats)]

@@ -72,7 +72,7 @@ void ct_contig_launch(const cx<float>* in, cx<float>* out, const uint8_t* mask,
                       const uint8_t* omask, long mask_lines, long nlines, int Lin, long in_ld,
                       int Lout, long out_ld, float scale, const cx<float>* tw, int Lmax,
                       cudaStream_t s) {
-  constexpr int NB = (4096 / L) > 16 ? 4096 / L : 16;
+  constexpr int NB = (2048 / L) > 16 ? 2048 / L : 16;
   const size_t smem = ((size_t)L * (NB + 1) + L) * sizeof(cx<float>);
   auto kern = k_ct_contig<float, INV, L, NB, HI, HO>;
   allow_smem(kern, smem);

@@ -207,7 +207,7 @@ __global__ void __launch_bounds__(NB * LX / kElemsPerThread, 1024 / (NB * LX / k
 template <int LX>
 void ct_epilogue_launch(dda_plan_s* p, const cx<float>* b1, const cx<float>* x, cx<float>* y,
                         long lines, long nm, float coef, cudaStream_t s) {
-  constexpr int NB = (4096 / LX) > 16 ? 4096 / LX : 16;
+  constexpr int NB = (2048 / LX) > 16 ? 2048 / LX : 16;
   const size_t smem = ((size_t)LX * (NB + 1) + LX) * sizeof(cx<float>);
   auto kern = k_ct_mv_epilogue<float, LX, NB>;
   if (smem > 48 * 1024)

@@ -5,7 +5,8 @@
 // (Section 4) and points to restarted GMRES as the memory-bounded variant
 // (Sections 4 and 5).  Here every restart cycle
 //   1. recomputes the residual r = b - A x in complex128 (FP64 iterative
-//      refinement when the cycle itself runs in complex64),
+//      refinement when the cycle itself runs in complex64; the complex128
+//      matvec computes in double-float arithmetic, about 48 bits),
 //   2. runs Arnoldi on A P^{-1} from v0 = r/||r||: w = A P^{-1} v_j,
 //      classical Gram-Schmidt (h = V^H w, w -= V h) with a second pass when
 //      the first left less than eta of ||w|| (selective reorthogonalisation,

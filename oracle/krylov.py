@@ -126,8 +126,9 @@ def bicgstab(matvec, b: np.ndarray, x0: np.ndarray | None = None, tol: float = 1
     Solves A M u = b, x = M u, with the shadow residual r_hat = r0 and the
     conjugated inner product.  Stops when the true-residual recurrence
     ||r|| / ||b|| <= tol (checked after each half step).  Returns
-    (x, info) with info = {iters, history, converged}; one iteration is two
-    matvecs and two preconditioner applies.
+    (x, info) with info = {iters, half_steps, history, converged}; one
+    iteration is two matvecs and two preconditioner applies, half_steps counts
+    the half steps taken (2 iters, one less when the first half converged).
     """
     shape = b.shape
     bf = b.reshape(-1).astype(np.complex128)
@@ -137,9 +138,11 @@ def bicgstab(matvec, b: np.ndarray, x0: np.ndarray | None = None, tol: float = 1
     x = np.zeros_like(bf) if x0 is None else x0.reshape(-1).astype(np.complex128).copy()
     bnorm = np.linalg.norm(bf)
     if bnorm == 0:
-        return np.zeros(shape, dtype=np.complex128), dict(iters=0, history=[], converged=True)
+        return np.zeros(shape, dtype=np.complex128), dict(iters=0, half_steps=0, history=[],
+                                                          converged=True)
     r = bf - A(x)
     rhat = r.copy()
+    half = 0
     rho = alpha = omega = 1.0 + 0j
     v = np.zeros_like(bf)
     p = np.zeros_like(bf)
@@ -155,11 +158,13 @@ def bicgstab(matvec, b: np.ndarray, x0: np.ndarray | None = None, tol: float = 1
         alpha = rho_new / np.vdot(rhat, v)
         s = r - alpha * v
         it += 1
+        half += 1
         if np.linalg.norm(s) / bnorm <= tol:
             x = x + alpha * ph
             history.append(np.linalg.norm(s) / bnorm)
             converged = True
             break
+        half += 1
         sh = Mv(s)
         t = A(sh)
         omega = np.vdot(t, s) / np.vdot(t, t)
@@ -169,4 +174,5 @@ def bicgstab(matvec, b: np.ndarray, x0: np.ndarray | None = None, tol: float = 1
         res = np.linalg.norm(r) / bnorm
         history.append(res)
         converged = res <= tol
-    return x.reshape(shape), dict(iters=it, history=history, converged=bool(converged))
+    return x.reshape(shape), dict(iters=it, half_steps=half, history=history,
+                                  converged=bool(converged))

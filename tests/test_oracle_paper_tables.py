@@ -89,3 +89,25 @@ def test_oracle_bicgstab_half_steps_match_paper(row):
         assert info2["half_steps"] <= 1.5 * b2, (info2["half_steps"], b2)
     else:
         assert _close(info2["half_steps"], b2), (info2["half_steps"], b2)
+
+
+def _rows_x20():
+    rows = []
+    with open(os.path.join(HERE, "golden", "paper_tables_3_4_x20.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                a, mu, vox, it2 = line.split()
+                rows.append((float(a), float(mu), float(vox), int(it2)))
+    return rows
+
+
+# the plates of up to 7e4 voxels (a few seconds each in the oracle); the four
+# larger ones take 0.5-2 minutes each and are left out of the CPU suite
+@pytest.mark.parametrize("row", [r for r in _rows_x20() if r[2] <= 7e4],
+                         ids=lambda r: f"x=20-L/a={r[0]}-mu={r[1]}")
+def test_oracle_reproduces_paper_x20_preconditioned_counts(row):
+    aspect, mu, voxels, it2 = row
+    prob = _plate(aspect, mu, voxels, x=20.0)
+    _, info2 = prob.solve_gmres("2", tol=1e-5, restart=2000, maxiter=2000, side="left")
+    assert info2["converged"]
+    assert _close(info2["iters"], it2), (info2["iters"], it2)

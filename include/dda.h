@@ -11,7 +11,8 @@
  * function sampled on a uniform l x m x n voxel box (Algorithm 1), applied
  * with a zero-padded 3-D FFT; the multilevel (Chan-Olkin) circulant
  * preconditioner P = alpha_tilde^{-1} I - dx^3 C (Section 3, eq. 20) with
- * the circulant taken on all three levels; and restarted GMRES.
+ * the circulant taken on all three levels, or on two as in the paper
+ * (dda_precond2_*); and restarted GMRES or BiCG-Stab (Section 4).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -99,8 +100,10 @@ typedef struct {
                             BiCG-Stab: iterations per refinement cycle (any >= 1)     */
   int32_t precond;       /* 0: none; 3: three-level circulant (dda_precond_build first);
                             2: the paper's 2-level circulant (dda_precond2_build first) */
-  int32_t inner_prec;    /* DDA_C128: plain FP64 GMRES; DDA_C64: complex64 GMRES cycles
-                            inside FP64 iterative refinement                          */
+  int32_t inner_prec;    /* DDA_C128: complex128 cycles (FP64 Gram-Schmidt, Givens and
+                            preconditioner; the matvec in double-float arithmetic, see
+                            dda_matvec); DDA_C64: complex64 cycles inside FP64
+                            iterative refinement                                      */
   double inner_tol;      /* a cycle ends early once its residual estimate falls below
                             inner_tol times the cycle's starting residual (0: only tol) */
   double reorth_eta;     /* second Gram-Schmidt pass when ||w_after|| < reorth_eta *
@@ -157,13 +160,17 @@ dda_status_t dda_incident_field(dda_plan_t plan, int32_t nrhs, void* d_b, void* 
  *   scatterer rows: alpha_j^{-1} x_j - dx^3 sum_{i scatterer, i != j} g(r_j - r_i) x_i
  *   air rows:       alpha_tilde^{-1} x_j
  * G is applied by the zero-padded FFT convolution (Section 1, Section 2.2).
- * d_x and d_y must not overlap. */
+ * DDA_C128 fields are converted to double-float values (pairs of floats,
+ * about 48 significant bits) and transformed in that arithmetic on the FP32
+ * units, then converted back (relative error well below 1e-10 of the FP64
+ * result); DDA_C64 computes in FP32.  d_x and d_y must not overlap. */
 dda_status_t dda_matvec(dda_plan_t plan, int32_t prec, int32_t nrhs, const void* d_x, void* d_y,
                         void* stream);
 
-/* Build the 3-level circulant: T. Chan's optimal circulant (eq. 13) applied
- * on the x, y and z levels of each of the six blocks, then its 3-D DFT
- * (Section 3).  Independent of the incident wave. */
+/* Build the 3-level circulant: T. Chan's optimal circulant (eq. 13; Strang's
+ * with desc.circulant = 1) applied on the x, y and z levels of each of the
+ * six blocks, then its 3-D DFT (Section 3).  Independent of the incident
+ * wave. */
 dda_status_t dda_precond_build(dda_plan_t plan, void* stream);
 
 /* z = M o P^{-1} (M o v), P = alpha_tilde^{-1} I - dx^3 C, M the scatterer

@@ -35,9 +35,24 @@ STATUS = {
 CIRCULANTS = {"chan": 0, "strang": 1}  # preconditioner circulant: eq. 13 or Strang's
 
 
-def _precond2_code(v) -> int:
+def toeplitz_axis_for(l: int, m: int, n: int) -> str:
+    """The 2-level preconditioner's Toeplitz (dense) level for a box: the
+    shortest edge, so the two longest levels are circulant (Section 5: for
+    plates z, for prisms longer than wide an x or y level).  Ties go to z, then
+    x: cubes keep the paper's choice, and a 64 x 64 x 128 prism gets x, which
+    halves the dense blocks and measured 26% faster than z."""
+    shortest = min(l, m, n)
+    if n == shortest:
+        return "z"
+    return "x" if l == shortest else "y"
+
+
+def _precond2_code(v, dims=None) -> int:
     """2-level storage request: False (none), True or "z" (Toeplitz level z, the
-    paper's), "x" or "y" (that level Toeplitz instead)."""
+    paper's), "x" or "y" (that level Toeplitz instead), "auto" (the shortest
+    edge, toeplitz_axis_for)."""
+    if v == "auto":
+        v = toeplitz_axis_for(*dims)
     if v is False or v is None or v == 0:
         return 0
     if v is True or v == "z" or v == 1:
@@ -171,7 +186,7 @@ def _prec_of(t: torch.Tensor) -> int:
 def workspace_size(l, m, n, dx, k, n_materials=1, max_rhs=1, krylov_m=0,
                    precisions=PLAN_C128 | PLAN_C64, precond2=0, circulant="chan") -> int:
     d = PlanDesc(l, m, n, dx, k, n_materials, max_rhs, krylov_m, precisions,
-                 _precond2_code(precond2), CIRCULANTS[circulant])
+                 _precond2_code(precond2, (l, m, n)), CIRCULANTS[circulant])
     return int(_lib.dda_workspace_size(ctypes.byref(d)))
 
 
@@ -199,7 +214,8 @@ class Plan:
         self.shape = (l, m, n)
         eps = [complex(e) for e in eps]
         self.desc = PlanDesc(l, m, n, float(dx), float(k), len(eps), int(max_rhs), int(krylov_m),
-                             int(precisions), _precond2_code(precond2), CIRCULANTS[circulant])
+                             int(precisions), _precond2_code(precond2, (l, m, n)),
+                             CIRCULANTS[circulant])
         size = int(_lib.dda_workspace_size(ctypes.byref(self.desc)))
         if size == 0:
             raise DDAError(1, last_error())

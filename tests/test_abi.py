@@ -92,3 +92,16 @@ def test_workspace_options_validated():
     zsize = dda.workspace_size(16, 16, 8, 0.125, 5.0, 1, 2, 50, precond2="z")
     xsize = dda.workspace_size(16, 16, 8, 0.125, 5.0, 1, 2, 50, precond2="x")
     assert xsize - zsize >= (5 * 9 * 48 ** 2 - 81 * 24 ** 2) * 8
+
+
+def test_toeplitz_axis_choice():
+    from paper_1903_09802_gb300 import dda
+    assert dda.toeplitz_axis_for(64, 64, 64) == "z"      # cube: the paper's level
+    assert dda.toeplitz_axis_for(64, 64, 4) == "z"       # plate
+    assert dda.toeplitz_axis_for(64, 64, 128) == "x"     # long prism along z
+    assert dda.toeplitz_axis_for(64, 32, 128) == "y"
+    assert dda.toeplitz_axis_for(16, 64, 64) == "x"
+    z = dda.workspace_size(64, 64, 128, 0.1, 5.0, 1, 1, 0, precond2="z")
+    auto = dda.workspace_size(64, 64, 128, 0.1, 5.0, 1, 1, 0, precond2="auto")
+    x = dda.workspace_size(64, 64, 128, 0.1, 5.0, 1, 1, 0, precond2="x")
+    assert auto == x < z

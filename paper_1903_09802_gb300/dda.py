@@ -391,3 +391,52 @@ def solve_many(plans, bs=None, streams=None, tol: float = 1e-6, max_iters: int =
     return [SolveResult(x, [q.iters for q in sv], [q.cycles for q in sv],
                         [bool(q.converged) for q in sv], [q.rel_resid for q in sv], st,
                         [q.reorth for q in sv]) for x, sv in zip(xs, stats)]
+
+
+class _Extinction(torch.autograd.Function):
+    """C_ext of each incident wave as a differentiable function of the
+    materials' permittivities.  Forward: plan, preconditioner, solve, C_ext.
+    Backward: the adjoint solve A lambda = conj(E_inc) with the same operator
+    (A = A^T), the per-voxel gradient dC_ext/d eps_j (dda_ext_gradient), summed
+    over the voxels of each material (they share its eps).  For a real output
+    and a complex input the gradient follows PyTorch's convention:
+    dC/dRe(eps) + i dC/dIm(eps)."""
+
+    @staticmethod
+    def forward(ctx, eps, geometry, solve_kw, plan_factory):
+        mat, dx, k, dirs, pols = geometry
+        eps_list = [complex(e) for e in eps.detach().cpu().tolist()]
+        plan = plan_factory(mat, eps_list, dx, k, len(dirs), solve_kw.get("restart", 50))
+        plan.set_incidence(dirs, pols)
+        if solve_kw.get("precond", 3) == 3:
+            plan.precond_build()
+        c = plan.solve(**solve_kw).x
+        cext = torch.as_tensor(plan.cross_sections(c)[:, 0], dtype=torch.float64)
+        ctx.state = (plan, c, solve_kw, mat, len(eps_list), eps.device)
+        return cext
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        plan, c, solve_kw, mat, K, dev = ctx.state
+        lam = plan.solve(b=plan.adjoint_rhs(c.shape[0]), **solve_kw).x
+        g = plan.ext_gradient_from(c, lam)  # (nrhs, 2, n, m, l)
+        w = grad_out.to(g.device, g.dtype).view(-1, 1, 1, 1, 1)
+        gsum = (w * g).sum(dim=0)  # (2, n, m, l): dL/dRe eps_j, dL/dIm eps_j
+        grad = torch.zeros(K, dtype=torch.complex128, device=dev)
+        for kk in range(K):
+            sel = mat == (kk + 1)
+            grad[kk] = complex(float(gsum[0][sel].sum()), float(gsum[1][sel].sum()))
+        return grad, None, None, None
+
+
+def _default_plan_factory(mat, eps, dx, k, nrhs, krylov_m):
+    return Plan(mat, eps, dx, k, max_rhs=nrhs, krylov_m=krylov_m)
+
+
+def extinction(eps: torch.Tensor, mat: torch.Tensor, dx: float, k: float, dirs, pols,
+               plan_factory=_default_plan_factory, **solve_kw) -> torch.Tensor:
+    """C_ext per incident wave (float64, shape (nrhs,)), differentiable with
+    respect to eps (complex128, one permittivity per material 1..K): the
+    adjoint per-voxel gradient of dda_ext_gradient, summed per material."""
+    return _Extinction.apply(eps, (mat, dx, k, list(dirs), list(pols)), dict(solve_kw),
+                             plan_factory)

@@ -406,10 +406,14 @@ class _Extinction(torch.autograd.Function):
     def forward(ctx, eps, geometry, solve_kw, plan_factory):
         mat, dx, k, dirs, pols = geometry
         eps_list = [complex(e) for e in eps.detach().cpu().tolist()]
-        plan = plan_factory(mat, eps_list, dx, k, len(dirs), solve_kw.get("restart", 50))
+        pc = solve_kw.get("precond", 3)
+        plan = plan_factory(mat, eps_list, dx, k, len(dirs), max(7, solve_kw.get("restart", 50)),
+                            pc == 2)
         plan.set_incidence(dirs, pols)
-        if solve_kw.get("precond", 3) == 3:
+        if pc == 3:
             plan.precond_build()
+        elif pc == 2:
+            plan.precond2_build()
         c = plan.solve(**solve_kw).x
         cext = torch.as_tensor(plan.cross_sections(c)[:, 0], dtype=torch.float64)
         ctx.state = (plan, c, solve_kw, mat, len(eps_list), eps.device)
@@ -429,8 +433,8 @@ class _Extinction(torch.autograd.Function):
         return grad, None, None, None
 
 
-def _default_plan_factory(mat, eps, dx, k, nrhs, krylov_m):
-    return Plan(mat, eps, dx, k, max_rhs=nrhs, krylov_m=krylov_m)
+def _default_plan_factory(mat, eps, dx, k, nrhs, krylov_m, precond2):
+    return Plan(mat, eps, dx, k, max_rhs=nrhs, krylov_m=krylov_m, precond2=precond2)
 
 
 def extinction(eps: torch.Tensor, mat: torch.Tensor, dx: float, k: float, dirs, pols,

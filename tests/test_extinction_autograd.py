@@ -18,7 +18,7 @@ class _Res:
 
 
 class OraclePlan:
-    def __init__(self, mat, eps, dx, k, nrhs, krylov_m):
+    def __init__(self, mat, eps, dx, k, nrhs, krylov_m, precond2):
         self.mat_np = mat.numpy()
         self.eps, self.dx, self.k = eps, dx, k
 

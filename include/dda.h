@@ -313,6 +313,54 @@ dda_status_t dda_adjoint_rhs(dda_plan_t plan, int32_t nrhs, void* d_b, void* str
 dda_status_t dda_ext_gradient(dda_plan_t plan, int32_t nrhs, const void* d_c,
                               const void* d_lambda, double* d_grad, void* stream);
 
+/* Launch schedule of a plan: choices that change how the operator's kernels
+ * are launched, never what they compute (every schedule gives the same
+ * results up to rounding order).
+ *   rr_z: 1 = the complex64 matvec's z pass at transform lengths 64 and 128
+ *         keeps the last forward and first inverse butterflies in registers
+ *         (the 3x3 spectrum multiply between them); 0 = the all-shared-memory
+ *         z kernel.  Other lengths and complex128 ignore it.
+ *   pdl:  1 = kernels are launched with programmatic dependent launch (the
+ *         next kernel's blocks become resident while the previous one drains);
+ *         0 = ordinary stream-ordered launches.
+ * A new plan starts with {1, 1}.  The environment variables DDA_RR_FFT3C=0 and
+ * DDA_PDL=0 force the plain forms whatever the schedule.  The schedule applies
+ * to dda_matvec, dda_precond_apply, dda_precond2_apply and dda_solve (hence
+ * dda_solve_many) of that plan, in the calling thread.  Not in the paper. */
+typedef struct {
+  int32_t rr_z;
+  int32_t pdl;
+} dda_schedule_t;
+
+/* Set or read a plan's schedule (no GPU work).  Fields must be 0 or 1;
+ * DDA_ERR_INVALID_ARG otherwise or on NULL. */
+dda_status_t dda_schedule_set(dda_plan_t plan, const dda_schedule_t* sched);
+dda_status_t dda_schedule_get(dda_plan_t plan, dda_schedule_t* out);
+
+/* What dda_autotune measured. */
+typedef struct {
+  dda_schedule_t chosen;     /* the schedule now set on the plan */
+  int32_t cached;            /* 1: taken from the process-wide table, nothing timed */
+  int32_t ncand;             /* schedules timed (0 when cached) */
+  dda_schedule_t cand[4];    /* the schedules timed, in order */
+  float ms_per_matvec[4];    /* their mean CUDA-event time per matvec call */
+} dda_tune_report_t;
+
+/* Autotuner: choose the plan's schedule by timing the matvec.  Each of the
+ * four schedules runs 2 untimed then `reps` timed dda_matvec calls
+ * (precision prec, nrhs right-hand sides, input d_x, output d_y: caller-owned
+ * device fields of that precision, box layout as dda_matvec's, not
+ * overlapping; d_y is overwritten) bracketed by CUDA events on `stream`; the
+ * fastest is set on the plan and recorded in a process-wide table keyed on
+ * (device, l, m, n, prec, nrhs).  A later call with the same key takes the
+ * recorded schedule without timing unless flags bit 0 (re-measure) is set.
+ * h_report (host, may be NULL) receives the measurements.  reps in 1..1000.
+ * Synchronises `stream`; errors as dda_matvec's (the plan's schedule is then
+ * left as it was).  Not in the paper. */
+dda_status_t dda_autotune(dda_plan_t plan, int32_t prec, int32_t nrhs, const void* d_x,
+                          void* d_y, int32_t reps, int32_t flags, dda_tune_report_t* h_report,
+                          void* stream);
+
 /* Release the host-side plan object (device memory stays the caller's). */
 void dda_plan_destroy(dda_plan_t plan);
 

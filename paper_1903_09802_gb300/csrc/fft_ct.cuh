@@ -29,13 +29,14 @@ __host__ __device__ constexpr int ct_bits(int L, int st) {
 }
 __host__ __device__ constexpr int ct_radix(int L, int st) { return 1 << ct_bits(L, st); }
 
-// DDA_RR_FFT3C=0 in the environment selects the all-shared-memory z pass.
+// DDA_RR_FFT3C=0 in the environment, or a schedule with rr_z off, selects the
+// all-shared-memory z pass.
 inline bool rr_fft3c_enabled() {
   static const bool on = [] {
     const char* e = std::getenv("DDA_RR_FFT3C");
     return !(e && e[0] == '0');
   }();
-  return on;
+  return on && tl_schedule.rr_z;
 }
 
 // One stage: radix R, NS = product of the radices already applied.  The tile

@@ -1275,6 +1275,7 @@ extern "C" dda_status_t dda_solve(dda_plan_t p, int32_t nrhs, const void* d_b, v
   if (o.method == 1 && p->d.krylov_m < 7)
     return fail(DDA_ERR_INVALID_ARG, "dda_solve: BiCG-Stab needs a plan with krylov_m >= 7");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScheduleScope scope(p->sched);
   const double2* b = static_cast<const double2*>(d_b);
   if (!b) {
     dda_status_t st = dda_incident_field(p, nrhs, p->w.B128, stream);

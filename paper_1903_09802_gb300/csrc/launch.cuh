@@ -12,6 +12,12 @@
 // kernel completes only after its predecessor has, so ordering stays
 // transitive along the stream.  DDA_PDL=0 in the environment turns the
 // attribute off (ordinary launches).
+//
+// Schedule: the launch choices a plan may tune (dda_autotune).  The entry
+// points of the library install their plan's schedule for the calling thread
+// (ScheduleScope) before launching; the defaults are the choices measured
+// fastest on the 64^3 workloads.  The environment switches above override a
+// schedule towards the plain forms.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -26,12 +32,27 @@ __device__ __forceinline__ void pdl_entry() {
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
 }
 
+struct Schedule {
+  bool rr_z = true;  // register-resident z pass of the complex64 matvec (lengths 64, 128)
+  bool pdl = true;   // programmatic dependent launch
+};
+
+inline thread_local Schedule tl_schedule;
+
+struct ScheduleScope {
+  Schedule saved;
+  explicit ScheduleScope(const Schedule& s) : saved(tl_schedule) { tl_schedule = s; }
+  ~ScheduleScope() { tl_schedule = saved; }
+  ScheduleScope(const ScheduleScope&) = delete;
+  ScheduleScope& operator=(const ScheduleScope&) = delete;
+};
+
 inline bool pdl_enabled() {
   static const bool on = [] {
     const char* e = std::getenv("DDA_PDL");
     return !(e && e[0] == '0');
   }();
-  return on;
+  return on && tl_schedule.pdl;
 }
 
 template <typename... KArgs, typename... Args>

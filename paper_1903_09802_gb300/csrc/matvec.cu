@@ -337,6 +337,7 @@ extern "C" dda_status_t dda_matvec(dda_plan_t p, int32_t prec, int32_t nrhs, con
     return fail(DDA_ERR_INVALID_ARG, "dda_matvec: nrhs must be 1..(incidences set)");
   if (d_x == d_y) return fail(DDA_ERR_INVALID_ARG, "dda_matvec: x and y must not overlap");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScheduleScope scope(p->sched);
   if (prec == DDA_C128) {
     if (!p->has128) return fail(DDA_ERR_INVALID_ARG, "dda_matvec: plan holds no complex128 data");
     matvec_impl<double>(p, nrhs, static_cast<const cx<double>*>(d_x), static_cast<cx<double>*>(d_y), s);

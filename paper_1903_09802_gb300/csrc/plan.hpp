@@ -136,6 +136,7 @@ struct dda_plan_s {
   std::vector<double> dainv_host;        // [rhs][K+1][2]
   int* pinned = nullptr;                 // host-pinned words polled by the solver
   dda::Profiler prof;                    // optional kernel timing
+  dda::Schedule sched;                   // launch choices (dda_schedule_set, dda_autotune)
 };
 
 namespace dda {

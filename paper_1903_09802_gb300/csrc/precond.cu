@@ -261,6 +261,7 @@ extern "C" dda_status_t dda_precond_apply(dda_plan_t p, int32_t prec, int32_t nr
   if (nrhs < 1 || nrhs > p->nrhs_inc)
     return fail(DDA_ERR_INVALID_ARG, "dda_precond_apply: nrhs must be 1..(incidences set)");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScheduleScope scope(p->sched);
   if (prec == DDA_C128) {
     if (!p->has128) return fail(DDA_ERR_INVALID_ARG, "dda_precond_apply: plan holds no complex128 data");
     precond_apply_impl<double>(p, nrhs, static_cast<const cx<double>*>(d_v),

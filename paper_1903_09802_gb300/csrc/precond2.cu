@@ -675,6 +675,7 @@ extern "C" dda_status_t dda_precond2_apply(dda_plan_t p, int32_t prec, int32_t n
   if (nrhs < 1 || nrhs > p->nrhs_inc)
     return fail(DDA_ERR_INVALID_ARG, "dda_precond2_apply: nrhs must be 1..(incidences set)");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScheduleScope scope(p->sched);
   if (prec == DDA_C128 && p->has128) {
     precond2_apply<double>(p, nrhs, static_cast<const cx<double>*>(d_v),
                            static_cast<cx<double>*>(d_z), s);

@@ -64,6 +64,7 @@ EXPORTS = ("dda_workspace_size", "dda_plan_create", "dda_set_incidence", "dda_in
            "dda_precond2_build", "dda_precond2_apply",
            "dda_fft3d", "dda_solve", "dda_solve_many",
            "dda_cross_sections", "dda_adjoint_rhs", "dda_ext_gradient", "dda_profile_enable", "dda_profile_read", "dda_plan_destroy",
+           "dda_schedule_set", "dda_schedule_get", "dda_autotune",
            "dda_last_error", "dda_launch_count")
 
 PROFILE_NAMES = ("mv_x_fwd", "mv_y_fwd", "mv_z_mul", "mv_y_inv", "mv_x_inv", "pc_x_fwd", "pc_y_fwd",
@@ -99,6 +100,15 @@ class RhsStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("cycles", ctypes.c_int32),
                 ("converged", ctypes.c_int32), ("status", ctypes.c_int32),
                 ("rel_resid", ctypes.c_double), ("reorth", ctypes.c_int32)]
+
+
+class Schedule(ctypes.Structure):
+    _fields_ = [("rr_z", ctypes.c_int32), ("pdl", ctypes.c_int32)]
+
+
+class TuneReport(ctypes.Structure):
+    _fields_ = [("chosen", Schedule), ("cached", ctypes.c_int32), ("ncand", ctypes.c_int32),
+                ("cand", Schedule * 4), ("ms_per_matvec", ctypes.c_float * 4)]
 
 
 _vp = ctypes.c_void_p
@@ -141,6 +151,13 @@ _lib.dda_profile_enable.argtypes = [_vp, ctypes.c_int32]
 _lib.dda_profile_read.restype = ctypes.c_int
 _lib.dda_profile_read.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64),
                                   ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_int32]
+_lib.dda_schedule_set.restype = ctypes.c_int
+_lib.dda_schedule_set.argtypes = [_vp, ctypes.POINTER(Schedule)]
+_lib.dda_schedule_get.restype = ctypes.c_int
+_lib.dda_schedule_get.argtypes = [_vp, ctypes.POINTER(Schedule)]
+_lib.dda_autotune.restype = ctypes.c_int
+_lib.dda_autotune.argtypes = [_vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp, ctypes.c_int32,
+                              ctypes.c_int32, ctypes.POINTER(TuneReport), _vp]
 _lib.dda_plan_destroy.restype = None
 _lib.dda_plan_destroy.argtypes = [_vp]
 _lib.dda_last_error.restype = ctypes.c_char_p
@@ -338,6 +355,29 @@ class Plan:
             c = self.solve(**solve_kw).x
         lam = self.solve(b=self.adjoint_rhs(c.shape[0]), **solve_kw).x
         return c, lam, self.ext_gradient_from(c, lam)
+
+    def schedule(self) -> dict:
+        s = Schedule()
+        _check(_lib.dda_schedule_get(self._h, ctypes.byref(s)))
+        return {"rr_z": bool(s.rr_z), "pdl": bool(s.pdl)}
+
+    def set_schedule(self, rr_z: bool = True, pdl: bool = True):
+        _check(_lib.dda_schedule_set(self._h, ctypes.byref(Schedule(int(rr_z), int(pdl)))))
+
+    def autotune(self, prec: int = C64, nrhs: int | None = None, reps: int = 10,
+                 force: bool = False) -> dict:
+        """dda_autotune on the incident field (complex64 or complex128 box
+        fields of nrhs right-hand sides); returns the report as a dict."""
+        nrhs = nrhs or self.nrhs
+        x = self.incident_field(nrhs).to(torch.complex64 if prec == C64 else torch.complex128)
+        y = torch.empty_like(x)
+        rep = TuneReport()
+        _check(_lib.dda_autotune(self._h, prec, nrhs, _ptr(x), _ptr(y), int(reps), int(force),
+                                 ctypes.byref(rep), _stream()))
+        sched = lambda s: {"rr_z": bool(s.rr_z), "pdl": bool(s.pdl)}  # noqa: E731
+        return {"chosen": sched(rep.chosen), "cached": bool(rep.cached),
+                "timed": [(sched(rep.cand[i]), float(rep.ms_per_matvec[i]))
+                          for i in range(rep.ncand)]}
 
     def profile(self, on: bool = True):
         _check(_lib.dda_profile_enable(self._h, int(on)))

@@ -75,6 +75,11 @@ def test_null_plan_is_rejected(dda):
     assert dda.STATUS[lib.dda_matvec(None, 0, 1, None, None, None)] == "DDA_ERR_INVALID_ARG"
     assert dda.STATUS[lib.dda_precond_build(None, None)] == "DDA_ERR_INVALID_ARG"
     assert dda.STATUS[lib.dda_solve(None, 1, None, None, None, None, None)] == "DDA_ERR_INVALID_ARG"
+    sched = dda.Schedule(1, 1)
+    assert dda.STATUS[lib.dda_schedule_set(None, ctypes.byref(sched))] == "DDA_ERR_INVALID_ARG"
+    assert dda.STATUS[lib.dda_schedule_get(None, ctypes.byref(sched))] == "DDA_ERR_INVALID_ARG"
+    assert dda.STATUS[lib.dda_autotune(None, 1, 1, None, None, 5, 0, None, None)] == \
+        "DDA_ERR_INVALID_ARG"
     lib.dda_plan_destroy(None)
 
 

@@ -123,6 +123,24 @@ def test_solver_edge_cases(case16):
 
 
 @pytest.mark.gpu
+def test_resume_from_a_stopped_solve(case16):
+    # checkpoint and resume: a solve stopped by the iteration cap keeps its
+    # last iterate (and reports its true residual); a solve started from it
+    # finishes the job
+    dda, case, prob, xd, plan = case16
+    part = plan.solve(tol=1e-8, max_iters=10, restart=50, precond=0, inner_prec=dda.C128,
+                      raise_on_error=False)
+    assert dda.STATUS[part.status] == "DDA_ERR_NOT_CONVERGED" and part.iters[0] == 10
+    r_part = _true_resid(prob, part.x[0].cpu().numpy())
+    assert r_part < 0.05 and part.rel_resid[0] == pytest.approx(r_part, rel=1e-6)
+    rest = plan.solve(x0=part.x, tol=1e-8, restart=50, precond=0, inner_prec=dda.C128)
+    assert all(rest.converged)
+    x = rest.x[0].cpu().numpy()
+    assert _true_resid(prob, x) <= 1.1e-8
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-6
+
+
+@pytest.mark.gpu
 def test_precond_required_before_use():
     dda = dda_module()
     mat = hex_prism_mask(8, 8, 8, 0.25, 1.0, 2.0)

@@ -21,7 +21,8 @@ dominant kernel measured live with CUDA events, the CPU oracle timed on a
 bounded sample, the end-to-end figure through host buffers, the number of
 library kernel launches, the SM clocks sampled during the timed region and,
 untimed, solver comparisons on the two 64^3 systems (no preconditioner,
-plain complex128, BiCG-Stab).
+plain complex128, BiCG-Stab) and the complex64 matvec against the same work
+written with cuFFT (torch.fft) and PyTorch elementwise kernels, per box.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -331,6 +332,86 @@ def compare_solvers(runner):
     return out
 
 
+def cufft_convolution_ms(l, m, n, nrhs, dev, reps=20, warmup=3):
+    """The matvec's work written with cuFFT (torch.fft) and PyTorch
+    elementwise kernels, for timing only: mask, zero-pad to (2n, 2m, 2l),
+    forward 3-D FFT, the symmetric 3x3 spectrum multiply (6 stored
+    components, full grid), inverse 3-D FFT, crop, diagonal term.  The
+    spectrum is random, not the Green tensor's: the work and the sizes are
+    those of the operator, the values are not."""
+    import torch
+    g = torch.Generator().manual_seed(0)
+    x = torch.randn((nrhs, 3, n, m, l), dtype=torch.complex64, generator=g).to(dev)
+    mask = (torch.rand((n, m, l), generator=g) < 0.6).to(dev)
+    G = torch.randn((6, 2 * n, 2 * m, 2 * l), dtype=torch.complex64, generator=g).to(dev)
+    ainv = complex(1.5, 0.1)
+    dims = (-3, -2, -1)
+
+    def once():
+        xm = x * mask
+        xp = torch.zeros((nrhs, 3, 2 * n, 2 * m, 2 * l), dtype=torch.complex64, device=dev)
+        xp[..., :n, :m, :l] = xm
+        X = torch.fft.fftn(xp, dim=dims)
+        X0, X1, X2 = X[:, 0], X[:, 1], X[:, 2]
+        Y = torch.stack((G[0] * X0 + G[1] * X1 + G[2] * X2,
+                         G[1] * X0 + G[3] * X1 + G[4] * X2,
+                         G[2] * X0 + G[4] * X1 + G[5] * X2), dim=1)
+        y = torch.fft.ifftn(Y, dim=dims)[..., :n, :m, :l]
+        return (ainv * xm - y) * mask
+
+    for _ in range(warmup):
+        once()
+    if torch.device(dev).type == "cuda":
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            once()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        once()
+    return 1e3 * (time.perf_counter() - t0) / reps
+
+
+def compare_fft(runner, reps=20):
+    """The library's complex64 matvec against the same work through cuFFT
+    (cufft_convolution_ms), per box of the sweep, 2 right-hand sides; CUDA
+    events on the current stream, inputs resident, after warm-up."""
+    import torch
+    dda = runner.dda
+    out = {}
+    for i, case in enumerate(runner.cases):
+        l, m, n = case.dims
+        key = f"{l}x{m}x{n}"
+        if key in out:
+            continue
+        plan = dda.Plan(runner.masks[i], case.eps, case.dx, case.k, max_rhs=2)
+        plan.set_incidence(case.dirs, case.pols)
+        x = plan.incident_field(2).to(torch.complex64)
+        y = torch.empty_like(x)
+        for _ in range(3):
+            plan.matvec(x, out=y)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            plan.matvec(x, out=y)
+        e1.record()
+        e1.synchronize()
+        ours = e0.elapsed_time(e1) / reps
+        del plan, x, y
+        theirs = cufft_convolution_ms(l, m, n, 2, runner.dev, reps)
+        out[key] = {"dda_matvec_c64_ms": round(ours, 4), "cufft_torch_c64_ms": round(theirs, 4),
+                    "speedup": round(theirs / ours, 2)}
+        torch.cuda.empty_cache()
+    return out
+
+
 def oracle_iterations():
     """Iteration counts of the oracle's own solves of the workload, written by
     oracle/iteration_counts.py (key: box dims, eps, rhs)."""
@@ -474,6 +555,11 @@ def run_ours(args, rank, world):
     peak, peak_kind = read_peak()
     roof = roofline(runner, peak, peak_kind)
     comparisons = compare_solvers(runner) if not args.no_compare else None
+    if comparisons is not None:
+        try:
+            comparisons["matvec_vs_cufft (2 RHS, ms per matvec)"] = compare_fft(runner)
+        except Exception as exc:  # a side measurement must not cost the bench line
+            comparisons["matvec_vs_cufft (2 RHS, ms per matvec)"] = {"error": repr(exc)[:200]}
     if rank != 0:
         return
     value = whole_job_ms_per_solve(total_ms, args.steps, nsolve, world)

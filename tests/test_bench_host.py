@@ -54,3 +54,10 @@ def test_roofline_arithmetic(monkeypatch):
 def test_roofline_traffic_null_without_summary(monkeypatch):
     monkeypatch.setattr(bench, "traffic_from_profiles", lambda k: None)
     assert bench.roofline(_FakeRunner(), 1000.0, "measured")["traffic"] is None
+
+
+def test_cufft_comparison_runs_on_cpu():
+    # the cuFFT side of the matvec comparison, on the CPU backend of torch.fft:
+    # same code, tiny box, just that it runs and times something
+    ms = bench.cufft_convolution_ms(4, 4, 2, 2, "cpu", reps=2, warmup=1)
+    assert ms > 0

@@ -28,7 +28,8 @@
  * - Unknowns are the paper's c (eq. 9); dipole moments are p = dx^3 c.
  * - `stream` is a cudaStream_t passed as void* (NULL = legacy stream).  Calls
  *   are stream-ordered and asynchronous unless they return host results
- *   (dda_solve stats, dda_cross_sections), which synchronise that stream.
+ *   (dda_solve stats, dda_cross_sections, dda_autotune's timings), which
+ *   synchronise that stream.
  * - Errors come back as dda_status_t; arguments are checked before any
  *   launch; a failing call leaves outputs unspecified.  dda_last_error()
  *   returns a thread-local description of the last failure.  No entry point

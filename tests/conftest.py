@@ -9,3 +9,10 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: oracle test that takes tens of seconds")
+    config.addinivalue_line(
+        "markers", "late: run after every other test, so that under -x a failure in one of them "
+        "(tests of recently added paths) cannot keep the others from running")
+
+
+def pytest_collection_modifyitems(session, config, items):
+    items.sort(key=lambda it: it.get_closest_marker("late") is not None)

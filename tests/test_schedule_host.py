@@ -2,7 +2,7 @@
 it per plan; each entry point installs its plan's schedule with a scope),
 checked on the host: scopes nest and restore, other threads keep theirs, and
 the switches the launch code reads follow the scope.  The GPU test of every
-schedule's results is tests/test_gpu_zz_autotune.py."""
+schedule's results is tests/test_gpu_autotune.py."""
 import os
 import shutil
 import subprocess

@@ -21,8 +21,9 @@ dominant kernel measured live with CUDA events, the CPU oracle timed on a
 bounded sample, the end-to-end figure through host buffers, the number of
 library kernel launches, the SM clocks sampled during the timed region and,
 untimed, solver comparisons on the two 64^3 systems (no preconditioner,
-plain complex128, BiCG-Stab) and the complex64 matvec against the same work
-written with cuFFT (torch.fft) and PyTorch elementwise kernels, per box.
+plain complex128, BiCG-Stab), the complex64 matvec against the same work
+written with cuFFT (torch.fft) and PyTorch elementwise kernels, per box, and
+the 128^3 prism (x = 40) solved in mixed precision and in complex128.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -412,6 +413,40 @@ def compare_fft(runner, reps=20):
     return out
 
 
+def compare_precision_128(runner):
+    """The 128^3 prism (x = 40, m = 1.31 + 0.01i, aspect 1, +z incidence,
+    x-polarised) solved to a complex128 relative residual of 1e-6 with
+    complex64 GMRES(50) cycles inside FP64 refinement and with complex128
+    cycles, 3-level preconditioner: time per solve, iterations, and the
+    relative difference of C_ext and C_sca between the two results."""
+    import torch
+    from dda_inputs import prism_case
+    dda = runner.dda
+    case = prism_case(128, 40.0, 1.31 + 0.01j, 1.0)
+    mask = torch.from_numpy(case.mask()).to(runner.dev)
+    plan = dda.Plan(mask, case.eps, case.dx, case.k, max_rhs=1, krylov_m=50)
+    plan.set_incidence(case.dirs, case.pols)
+    plan.precond_build()
+    out, xsec = {}, {}
+    for name, kw in (("c64_fp64ir", dict(inner_prec=dda.C64, inner_tol=1e-4)),
+                     ("c128", dict(inner_prec=dda.C128))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = plan.solve(tol=1e-6, restart=50, max_iters=3000, precond=3, reorth_eta=REORTH_ETA,
+                         raise_on_error=False, **kw)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        xsec[name] = plan.cross_sections(res.x)[0]
+        out[name] = {"ms_per_solve": round(1e3 * dt, 1), "iters": res.iters[0],
+                     "converged": bool(res.converged[0]), "rel_resid": res.rel_resid[0]}
+    a, b = xsec["c64_fp64ir"], xsec["c128"]
+    out["c_ext_rel_diff"] = float(abs(a[0] - b[0]) / abs(b[0]))
+    out["c_sca_rel_diff"] = float(abs(a[2] - b[2]) / abs(b[2]))
+    del plan
+    torch.cuda.empty_cache()
+    return out
+
+
 def oracle_iterations():
     """Iteration counts of the oracle's own solves of the workload, written by
     oracle/iteration_counts.py (key: box dims, eps, rhs)."""
@@ -560,6 +595,11 @@ def run_ours(args, rank, world):
             comparisons["matvec_vs_cufft (2 RHS, ms per matvec)"] = compare_fft(runner)
         except Exception as exc:  # a side measurement must not cost the bench line
             comparisons["matvec_vs_cufft (2 RHS, ms per matvec)"] = {"error": repr(exc)[:200]}
+        key128 = "128^3 x=40 m=1.31+0.01i: complex64 + FP64 refinement vs complex128"
+        try:
+            comparisons[key128] = compare_precision_128(runner)
+        except Exception as exc:
+            comparisons[key128] = {"error": repr(exc)[:200]}
     if rank != 0:
         return
     value = whole_job_ms_per_solve(total_ms, args.steps, nsolve, world)

@@ -15,4 +15,9 @@ def pytest_configure(config):
 
 
 def pytest_collection_modifyitems(session, config, items):
-    items.sort(key=lambda it: it.get_closest_marker("late") is not None)
+    # stable sort: established tests keep their order; late ones follow, by
+    # the marker's optional rank (lowest first)
+    def key(it):
+        mk = it.get_closest_marker("late")
+        return (0, 0) if mk is None else (1, mk.args[0] if mk.args else 0)
+    items.sort(key=key)

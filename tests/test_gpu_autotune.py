@@ -25,7 +25,7 @@ def _oracle_matvec(mat, eps, dx, k, d, e, x):
 
 
 @pytest.mark.gpu
-@pytest.mark.late
+@pytest.mark.late(4)
 @pytest.mark.parametrize("n", [32, 64])
 def test_every_schedule_gives_the_operator_and_autotune(n):
     dda = dda_module()

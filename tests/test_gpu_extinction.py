@@ -29,7 +29,7 @@ def _oracle(mat, dx, k, eps, dirs, pols, w):
 
 
 @pytest.mark.gpu
-@pytest.mark.late
+@pytest.mark.late(3)
 @pytest.mark.parametrize("precond", [3, 2])
 def test_extinction_and_gradient_vs_oracle(precond):
     dda = dda_module()

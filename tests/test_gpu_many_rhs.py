@@ -14,7 +14,7 @@ from oracle.problem import Problem
 
 
 @pytest.mark.gpu
-@pytest.mark.late
+@pytest.mark.late(2)
 def test_24_waves_in_one_batch():
     dda = dda_module()
     case = prism_case(16, 5.0, 1.31 + 0.01j, 1.0)

@@ -123,7 +123,7 @@ def test_solver_edge_cases(case16):
 
 
 @pytest.mark.gpu
-@pytest.mark.late
+@pytest.mark.late(1)
 def test_resume_from_a_stopped_solve(case16):
     # checkpoint and resume: a solve stopped by the iteration cap keeps its
     # last iterate (and reports its true residual); a solve started from it

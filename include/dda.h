@@ -286,11 +286,11 @@ dda_status_t dda_cross_sections(dda_plan_t plan, int32_t nrhs, const void* d_c, 
  * preconditioner's block pass (its FFT passes count as 5, 6, 8, 9); n entries
  * are written (n <= 13); reset != 0 zeroes the sums.  h_bytes (may be NULL) receives the
  * summed algorithmic bytes of the timed launches: per right-hand side and
- * with u = one box field (3 l m n values), matvec passes 9u (+mask), 18u,
- * 24u (+ the kernel spectrum once), 18u, 12u (+mask); preconditioner
- * passes 6u each (+mask, + the circulant spectrum once for the middle one);
- * Gram-Schmidt dots (j+2)u, update (j+3)u at Arnoldi step j.  Events add a
- * few microseconds per launch. */
+ * with F = one three-component box field (3 l m n values), matvec passes 3F
+ * (+mask), 6F, 8F (+ the kernel spectrum once), 6F, 4F (+mask);
+ * preconditioner passes 2F each (+mask, + the circulant spectrum once for
+ * the middle one); Gram-Schmidt dots (j+2)F, update (j+3)F at Arnoldi step
+ * j.  Events add a few microseconds per launch. */
 dda_status_t dda_profile_enable(dda_plan_t plan, int32_t on);
 dda_status_t dda_profile_read(dda_plan_t plan, double* h_ms, int64_t* h_count, double* h_bytes,
                               int32_t n, int32_t reset);

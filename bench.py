@@ -413,6 +413,45 @@ def compare_fft(runner, reps=20):
     return out
 
 
+def compare_sweep_2level(runner):
+    """The timed step's six systems solved with the paper's 2-level
+    preconditioner instead of the 3-level one (Toeplitz level on the
+    shortest box edge, as precond2="auto" picks), same solver settings:
+    iterations and time per solve (preconditioner build included), next to
+    the same for the 3-level form."""
+    import torch
+    dda = runner.dda
+    out = {"2level_auto": {}, "3level": {}}
+    tot = {"2level_auto": 0.0, "3level": 0.0}
+    nsolve = 0
+    for i, case in enumerate(runner.cases):
+        key = f"{'x'.join(map(str, case.dims))} m={complex(case.eps[0]) ** 0.5:.2f}"
+        nsolve += case.nrhs
+        for name in ("2level_auto", "3level"):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            two = name == "2level_auto"
+            plan = dda.Plan(runner.masks[i], case.eps, case.dx, case.k, max_rhs=2, krylov_m=50,
+                            precond2="auto" if two else False)
+            plan.set_incidence(case.dirs, case.pols)
+            if two:
+                plan.precond2_build()
+            else:
+                plan.precond_build()
+            res = plan.solve(tol=1e-6, restart=50, max_iters=3000, precond=2 if two else 3,
+                             inner_prec=dda.C64, inner_tol=1e-4, reorth_eta=REORTH_ETA,
+                             raise_on_error=False)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            tot[name] += dt
+            out[name][key] = {"iters": res.iters, "converged": all(res.converged),
+                              "ms_per_solve": round(1e3 * dt / case.nrhs, 2)}
+            del plan
+    for name in tot:
+        out[name]["all systems ms_per_solve"] = round(1e3 * tot[name] / nsolve, 2)
+    return out
+
+
 def compare_precision_128(runner):
     """The 128^3 prism (x = 40, m = 1.31 + 0.01i, aspect 1, +z incidence,
     x-polarised) solved to a complex128 relative residual of 1e-6 with
@@ -595,6 +634,11 @@ def run_ours(args, rank, world):
             comparisons["matvec_vs_cufft (2 RHS, ms per matvec)"] = compare_fft(runner)
         except Exception as exc:  # a side measurement must not cost the bench line
             comparisons["matvec_vs_cufft (2 RHS, ms per matvec)"] = {"error": repr(exc)[:200]}
+        key2 = "timed-step systems with the 2-level preconditioner (wall time, untimed step)"
+        try:
+            comparisons[key2] = compare_sweep_2level(runner)
+        except Exception as exc:
+            comparisons[key2] = {"error": repr(exc)[:200]}
         key128 = "128^3 x=40 m=1.31+0.01i: complex64 + FP64 refinement vs complex128"
         try:
             comparisons[key128] = compare_precision_128(runner)

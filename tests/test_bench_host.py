@@ -61,3 +61,85 @@ def test_cufft_comparison_runs_on_cpu():
     # same code, tiny box, just that it runs and times something
     ms = bench.cufft_convolution_ms(4, 4, 2, 2, "cpu", reps=2, warmup=1)
     assert ms > 0
+
+
+class _FakeRes:
+    def __init__(self, nrhs):
+        self.iters = [3] * nrhs
+        self.converged = [True] * nrhs
+        self.rel_resid = [1e-7] * nrhs
+        self.x = None
+
+
+class _FakePlan:
+    """Stands in for dda.Plan on the CPU: records calls, computes nothing."""
+
+    def __init__(self, mat, eps, dx, k, max_rhs=1, krylov_m=0, precond2=False, **kw):
+        self.shape = tuple(mat.shape)
+        self.precond2 = precond2
+        self.nrhs = 0
+
+    def set_incidence(self, dirs, pols):
+        self.nrhs = len(dirs)
+
+    def precond_build(self):
+        pass
+
+    def precond2_build(self):
+        assert self.precond2
+
+    def solve(self, **kw):
+        assert kw["precond"] in (2, 3) and (kw["precond"] == 3 or self.precond2)
+        return _FakeRes(self.nrhs)
+
+    def cross_sections(self, x):
+        import numpy as np
+        return np.tile([2.0, 0.5, 1.5], (self.nrhs, 1))
+
+    def incident_field(self, nrhs):
+        import torch
+        n, m, l = self.shape
+        return torch.ones((nrhs, 3, n, m, l), dtype=torch.complex128)
+
+    def matvec(self, x, out=None):
+        return x
+
+
+class _FakeEvent:
+    def __init__(self, **kw):
+        pass
+
+    def record(self, *a):
+        pass
+
+    def synchronize(self):
+        pass
+
+    def elapsed_time(self, other):
+        return 1.0
+
+
+def test_side_comparisons_run_with_a_stand_in_library(monkeypatch):
+    # the Python of the guarded comparisons (2-level sweep, 128^3 precision pair,
+    # cuFFT matvec), run against a stand-in library on the CPU so that a slip in
+    # it shows here rather than as an error entry of the GPU run's JSON line
+    import numpy as np
+    import torch
+    from paper_1903_09802_gb300 import dda as real
+    fake = SimpleNamespace(Plan=_FakePlan, C64=real.C64, C128=real.C128)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    monkeypatch.setattr(torch.cuda, "Event", _FakeEvent)
+    monkeypatch.setattr(torch.cuda, "empty_cache", lambda: None)
+    monkeypatch.setattr(bench, "cufft_convolution_ms", lambda *a, **k: 2.0)
+    cases = [SimpleNamespace(dims=(4, 4, 2), eps=[1.31 ** 2], dx=0.5, k=1.0, nrhs=2,
+                             dirs=[np.array([0, 0, 1.0])] * 2,
+                             pols=[np.array([1.0, 0, 0]), np.array([0, 1.0, 0])])]
+    runner = SimpleNamespace(dda=fake, cases=cases, masks=[torch.zeros((2, 4, 4), dtype=torch.uint8)],
+                             dev="cpu")
+    sweep = bench.compare_sweep_2level(runner)
+    assert sweep["2level_auto"]["all systems ms_per_solve"] >= 0
+    assert "4x4x2 m=1.31+0.00j" in sweep["3level"]
+    fft = bench.compare_fft(runner, reps=2)
+    assert fft["4x4x2"]["speedup"] == 4.0  # 2 ms against 1 ms over 2 calls
+    p128 = bench.compare_precision_128(runner)
+    assert p128["c_ext_rel_diff"] == 0.0 and p128["c128"]["converged"]

@@ -1,5 +1,6 @@
 """The C ABI library: symbols, workspace sizing and argument checks (no GPU needed)."""
 import ctypes
+from types import SimpleNamespace
 import os
 import re
 
@@ -110,3 +111,33 @@ def test_toeplitz_axis_choice():
     auto = dda.workspace_size(64, 64, 128, 0.1, 5.0, 1, 1, 0, precond2="auto")
     x = dda.workspace_size(64, 64, 128, 0.1, 5.0, 1, 1, 0, precond2="x")
     assert auto == x < z
+
+
+def test_autotune_report_marshalling(monkeypatch):
+    # Plan.autotune's marshalling of dda_tune_report_t, with the C call replaced
+    # by one that fills the report as the library does (no GPU needed)
+    import torch
+    from paper_1903_09802_gb300 import dda
+
+    def fake_autotune(h, prec, nrhs, x, y, reps, flags, rep_ref, stream):
+        rep = rep_ref._obj
+        rep.ncand = 4
+        for c in range(4):
+            rep.cand[c].rr_z, rep.cand[c].pdl = int(c & 1 == 0), int(c & 2 == 0)
+            rep.ms_per_matvec[c] = [0.3, 0.2, 0.4, 0.5][c]
+        rep.chosen = rep.cand[1]
+        rep.cached = 0
+        assert prec == dda.C64 and nrhs == 2 and reps == 7 and flags == 1
+        return 0
+
+    monkeypatch.setattr(dda, "_lib", SimpleNamespace(dda_autotune=fake_autotune))
+    monkeypatch.setattr(dda, "_stream", lambda: None)
+    plan = dda.Plan.__new__(dda.Plan)
+    plan._h = None
+    plan.nrhs = 2
+    plan.incident_field = lambda n: torch.ones((n, 3, 2, 2, 2), dtype=torch.complex128)
+    rep = plan.autotune(reps=7, force=True)
+    assert rep["chosen"] == {"rr_z": False, "pdl": True} and not rep["cached"]
+    assert [t[1] for t in rep["timed"]] == pytest.approx([0.3, 0.2, 0.4, 0.5])
+    assert rep["timed"][3][0] == {"rr_z": False, "pdl": False}
+    plan._h = None  # nothing to destroy

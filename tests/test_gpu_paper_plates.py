@@ -42,3 +42,31 @@ def test_paper_plate_two_level_solve(mu, n):
     # and with complex64 cycles inside FP64 refinement
     res64 = plan.solve(tol=1e-5, restart=50, precond=2, inner_prec=dda.C64, inner_tol=1e-3)
     assert res64.converged[0]
+
+
+@pytest.mark.gpu
+@pytest.mark.late(5)
+def test_paper_plate_x20_two_level_solve():
+    # the x = 20 row of Table 3 for mu = 1.2 (L/a = 0.1: 77 x 67 x 4 plate box),
+    # grown with air to 128 x 128 x 4; GPU against the oracle on that box
+    dda = dda_module()
+    mu, n, x, a = 1.2, 4, 20.0, 1.0
+    k = x / a
+    dx = 2 * math.pi / (10 * mu * k)
+    l = m = 128
+    mat = hex_prism_mask(l, m, n, dx, a, n * dx)
+    d, e = np.array([1.0, 0.0, 0.0]), np.array([0.0, 0.0, 1.0])
+    prob = Problem(mat=mat, dx=dx, k=k, eps=[mu ** 2], d=d, e=e)
+    x_ref, info = prob.solve_gmres("2", tol=1e-10, restart=50, maxiter=500)
+    assert info["converged"]
+    plan = dda.Plan(to_dev(mat, torch.uint8), [mu ** 2], dx, k, max_rhs=1, krylov_m=50,
+                    precond2=True)
+    plan.set_incidence([d], [e])
+    plan.precond2_build()
+    res = plan.solve(tol=1e-10, restart=50, precond=2, inner_prec=dda.C128)
+    assert res.converged[0]
+    xg = res.x[0].cpu().numpy()
+    assert np.linalg.norm(xg - x_ref) / np.linalg.norm(x_ref) < 1e-8
+    _, info5 = prob.solve_gmres("2", tol=1e-5, restart=50, maxiter=500)
+    res5 = plan.solve(tol=1e-5, restart=50, precond=2, inner_prec=dda.C128)
+    assert abs(res5.iters[0] - info5["iters"]) <= 2

@@ -191,13 +191,17 @@ dda_status_t dda_precond_apply(dda_plan_t plan, int32_t prec, int32_t nrhs, cons
  * deployment variant.  Same arguments and result as dda_precond_apply, but
  * the transform's scratch (nrhs * 3 * l*m*n complex values) lives in a
  * 32 MiB array compiled into the library instead of the plan's workspace;
- * larger requests return DDA_ERR_WORKSPACE.  Every GPU that loads the
- * library holds that array until the process exits.  The first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.
+ * larger requests return DDA_ERR_WORKSPACE.  Every GPU on which a plan is
+ * created holds that array until the process exits: dda_plan_create loads
+ * it into the current context (with lazy module loading that is when its
+ * memory is reserved), so make the plan while allocation is still allowed.
+ * Each call looks the array's device address up again with the plan's device
+ * current (a host-side lookup that allocates nothing), so a context reset
+ * leaves no stale address; plans made before a reset are invalid anyway.
  * All calls share the one array, and it keeps the last call's contents
  * (each call overwrites everything it reads): calls that overlap on the GPU,
- * on any streams, race and give wrong results.  Allocates nothing. */
+ * on any streams, race and give wrong results.  Uses the plan's launch
+ * schedule like dda_precond_apply.  Allocates nothing. */
 dda_status_t dda_precond_apply_noalloc(dda_plan_t plan, int32_t prec, int32_t nrhs,
                                        const void* d_v, void* d_z, void* stream);
 

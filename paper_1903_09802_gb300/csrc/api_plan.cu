@@ -360,7 +360,8 @@ extern "C" dda_status_t dda_plan_create(dda_plan_t* out, const dda_plan_desc_t* 
     k_to_df<<<grid_for(ng, 256), 256, 0, s>>>(static_cast<const double2*>(L.G128),
                                                 static_cast<cx<df>*>(L.Gdf), ng);
   }
-  const dda_status_t cs = check_cuda("dda_plan_create");
+  dda_status_t cs = check_cuda("dda_plan_create");
+  if (cs == DDA_OK) cs = noalloc_prepare();
   if (cs != DDA_OK) {
     delete p;
     return cs;

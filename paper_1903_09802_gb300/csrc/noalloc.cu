@@ -7,7 +7,6 @@
 // fixed array compiled into the library, so the call itself reserves
 // nothing.
 #include <cstring>
-#include <mutex>
 
 #include "plan.hpp"
 
@@ -19,31 +18,34 @@ namespace {
 constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
-
-// Device address of the array on the current device, looked up once per
-// device (the host-side symbol is not a device address).
+// Device address of the array in the current context.  The host-side
+// symbol is not a device address.  Once the library's device code is loaded
+// in the context (noalloc_prepare, called by dda_plan_create), the lookup is
+// a host-side table read that allocates nothing; it is repeated on every call
+// so that a context torn down and made again (cudaDeviceReset) never leaves
+// a stale address behind.
 dda_status_t scratch_address(void** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return check_cuda("dda_precond_apply_noalloc");
-  if (dev < 0 || dev >= kMaxDevices)
-    return fail(DDA_ERR_INVALID_ARG, "dda_precond_apply_noalloc: device index above 63");
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (g_addr[dev] == nullptr) {
-    void* ptr = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess || ptr == nullptr)
-      return fail(DDA_ERR_CUDA, std::string("dda_precond_apply_noalloc: cudaGetSymbolAddress: ") +
-                                    cudaGetErrorString(e));
-    g_addr[dev] = ptr;
-  }
-  *out = g_addr[dev];
+  void* ptr = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  if (e != cudaSuccess || ptr == nullptr)
+    return fail(DDA_ERR_CUDA, std::string("dda_precond_apply_noalloc: cudaGetSymbolAddress: ") +
+                                  cudaGetErrorString(e));
+  *out = ptr;
   return DDA_OK;
 }
 
 }  // namespace
+
+// Loads this file's device code (and with it the 32 MiB array) into the
+// current context.  With lazy module loading the first symbol lookup is what
+// loads it, and loading reserves the array's memory; plan creation, which
+// the caller makes while it may still allocate, does that lookup so that the
+// apply itself never reserves anything.
+dda_status_t noalloc_prepare() {
+  void* ptr = nullptr;
+  return scratch_address(&ptr);
+}
+
 }  // namespace dda
 
 using namespace dda;
@@ -70,6 +72,7 @@ extern "C" dda_status_t dda_precond_apply_noalloc(dda_plan_t p, int32_t prec, in
   const dda_status_t st = scratch_address(&scratch);
   if (st != DDA_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ScheduleScope scope(p->sched);
   if (prec == DDA_C128)
     precond_apply_into<double>(p, nrhs, static_cast<const cx<double>*>(d_v),
                                static_cast<cx<double>*>(d_z), static_cast<cx<double>*>(scratch), s);

@@ -141,6 +141,10 @@ struct dda_plan_s {
 
 namespace dda {
 
+// Loads the no-allocation apply's static scratch into the current context
+// (noalloc.cu); dda_plan_create calls it.
+dda_status_t noalloc_prepare();
+
 // Layout of a plan's workspace; with ws == nullptr only the size is computed.
 bool make_layout(const dda_plan_desc_t& d, void* ws, Layout& L, std::string& why);
 

@@ -258,6 +258,44 @@ class Plan:
         l, m, n = self.shape
         return (nrhs, 3, n, m, l)
 
+    def _field(self, t: torch.Tensor, name: str, dtype=None) -> torch.Tensor:
+        """Check a box field against the plan before its pointer reaches a
+        kernel: shape (nrhs, 3, n, m, l) with 1 <= nrhs, complex64 or
+        complex128 (or exactly `dtype`), on the plan's device; returns it
+        contiguous."""
+        if not isinstance(t, torch.Tensor):
+            raise TypeError(f"{name} must be a tensor")
+        if t.dim() != 5 or t.shape[0] < 1 or tuple(t.shape) != self.field_shape(t.shape[0]):
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, the plan's box fields are "
+                             f"(nrhs, 3, n, m, l) = (nrhs, *{self.field_shape(1)[1:]})")
+        if dtype is not None and t.dtype != dtype:
+            raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+        _prec_of(t)
+        if t.device != self.mat.device:
+            raise ValueError(f"{name} is on {t.device}, the plan on {self.mat.device}")
+        return t.contiguous()
+
+    def _out(self, out: torch.Tensor | None, like: torch.Tensor, name: str = "out",
+             may_alias: bool = True) -> torch.Tensor:
+        """The output buffer of an apply: a new one like `like`, or the
+        caller's, which must match it in shape, dtype and device and be
+        contiguous (the library writes through its raw pointer)."""
+        if out is None:
+            return torch.empty_like(like)
+        if not isinstance(out, torch.Tensor):
+            raise TypeError(f"{name} must be a tensor")
+        if tuple(out.shape) != tuple(like.shape):
+            raise ValueError(f"{name} has shape {tuple(out.shape)}, expected {tuple(like.shape)}")
+        if out.dtype != like.dtype:
+            raise TypeError(f"{name} is {out.dtype}, the input is {like.dtype}")
+        if out.device != like.device:
+            raise ValueError(f"{name} is on {out.device}, the input on {like.device}")
+        if not out.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if not may_alias and out.data_ptr() == like.data_ptr():
+            raise ValueError(f"{name} must not be the input buffer")
+        return out
+
     def set_incidence(self, dirs, pols):
         dirs = np.asarray(dirs, dtype=np.float64).reshape(-1, 3)
         pols = np.asarray(pols, dtype=np.float64).reshape(-1, 3)
@@ -275,8 +313,8 @@ class Plan:
         return b
 
     def matvec(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
-        x = x.contiguous()
-        y = torch.empty_like(x) if out is None else out
+        x = self._field(x, "x")
+        y = self._out(out, x, may_alias=False)
         _check(_lib.dda_matvec(self._h, _prec_of(x), x.shape[0], _ptr(x), _ptr(y), _stream()))
         return y
 
@@ -284,8 +322,8 @@ class Plan:
         _check(_lib.dda_precond_build(self._h, _stream()))
 
     def precond_apply(self, v: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
-        v = v.contiguous()
-        z = torch.empty_like(v) if out is None else out
+        v = self._field(v, "v")
+        z = self._out(out, v)
         _check(_lib.dda_precond_apply(self._h, _prec_of(v), v.shape[0], _ptr(v), _ptr(z), _stream()))
         return z
 
@@ -294,22 +332,31 @@ class Plan:
         _check(_lib.dda_precond2_build(self._h, _stream()))
 
     def precond2_apply(self, v: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
-        v = v.contiguous()
-        z = torch.empty_like(v) if out is None else out
+        v = self._field(v, "v")
+        z = self._out(out, v)
         _check(_lib.dda_precond2_apply(self._h, _prec_of(v), v.shape[0], _ptr(v), _ptr(z), _stream()))
         return z
 
     def precond_apply_noalloc(self, v: torch.Tensor, out: torch.Tensor) -> torch.Tensor:
         """dda_precond_apply_noalloc: the library's static scratch instead of the workspace."""
-        v = v.contiguous()
+        v = self._field(v, "v")
+        if out is None:
+            raise ValueError("precond_apply_noalloc needs the caller's out buffer")
+        out = self._out(out, v)
         _check(_lib.dda_precond_apply_noalloc(self._h, _prec_of(v), v.shape[0], _ptr(v), _ptr(out),
                                               _stream()))
         return out
 
     def fft3d(self, data: torch.Tensor, inverse: bool = False) -> torch.Tensor:
         """In-place 3-D DFT of (batch, n, m, l) complex arrays."""
-        assert data.is_contiguous()
-        nb = data.numel() // (self.shape[0] * self.shape[1] * self.shape[2])
+        l, m, n = self.shape
+        if data.dim() != 4 or tuple(data.shape[1:]) != (n, m, l) or data.shape[0] < 1:
+            raise ValueError(f"data has shape {tuple(data.shape)}, expected (batch, {n}, {m}, {l})")
+        if not data.is_contiguous():
+            raise ValueError("data must be contiguous (the transform is in place)")
+        if data.device != self.mat.device:
+            raise ValueError(f"data is on {data.device}, the plan on {self.mat.device}")
+        nb = data.shape[0]
         _check(_lib.dda_fft3d(self._h, _prec_of(data), nb, _ptr(data), int(inverse), _stream()))
         return data
 
@@ -325,7 +372,15 @@ class Plan:
             x = x0.clone().contiguous()
         opts = SolveOpts(tol, max_iters, restart, precond, inner_prec, inner_tol, reorth_eta, method)
         stats = (RhsStats * nrhs)()
-        bp = _ptr(b.contiguous()) if b is not None else ctypes.c_void_p(0)
+        if b is not None:
+            b = self._field(b, "b", torch.complex128)
+            if b.shape[0] != nrhs:
+                raise ValueError(f"b holds {b.shape[0]} right-hand sides, nrhs is {nrhs}")
+        if x0 is not None:
+            self._field(x, "x0", torch.complex128)
+            if x.shape[0] != nrhs:
+                raise ValueError(f"x0 holds {x.shape[0]} right-hand sides, nrhs is {nrhs}")
+        bp = _ptr(b) if b is not None else ctypes.c_void_p(0)
         st = _lib.dda_solve(self._h, nrhs, bp, _ptr(x), ctypes.byref(opts), stats, _stream())
         if st != 0 and raise_on_error:
             raise DDAError(st, last_error())
@@ -341,7 +396,10 @@ class Plan:
 
     def ext_gradient_from(self, c: torch.Tensor, lam: torch.Tensor) -> torch.Tensor:
         """(nrhs, 2, n, m, l) float64: dC_ext/dRe(eps), dC_ext/dIm(eps) per voxel."""
-        c, lam = c.contiguous(), lam.contiguous()
+        c = self._field(c, "c", torch.complex128)
+        lam = self._field(lam, "lam", torch.complex128)
+        if lam.shape != c.shape:
+            raise ValueError("c and lam must hold the same right-hand sides")
         nrhs = c.shape[0]
         l, m, n = self.shape
         g = torch.empty((nrhs, 2, n, m, l), dtype=torch.float64, device=self.mat.device)
@@ -392,7 +450,7 @@ class Plan:
         return {name: (ms[i], cnt[i], byt[i]) for i, name in enumerate(PROFILE_NAMES)}
 
     def cross_sections(self, c: torch.Tensor) -> np.ndarray:
-        c = c.contiguous()
+        c = self._field(c, "c", torch.complex128)
         nrhs = c.shape[0]
         out = (ctypes.c_double * (3 * nrhs))()
         _check(_lib.dda_cross_sections(self._h, nrhs, _ptr(c), out, _stream()))

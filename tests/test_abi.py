@@ -141,3 +141,55 @@ def test_autotune_report_marshalling(monkeypatch):
     assert [t[1] for t in rep["timed"]] == pytest.approx([0.3, 0.2, 0.4, 0.5])
     assert rep["timed"][3][0] == {"rr_z": False, "pdl": False}
     plan._h = None  # nothing to destroy
+
+
+def _fake_plan(dda, shape=(8, 4, 2)):
+    """A Plan object with no library handle: enough for the binding's own
+    argument checks, which must raise before any pointer reaches the library."""
+    import torch
+    p = object.__new__(dda.Plan)
+    l, m, n = shape
+    p.mat = torch.zeros((n, m, l), dtype=torch.uint8)
+    p.shape = shape
+    p._h = None
+    p.nrhs = 2
+    return p
+
+
+def test_binding_rejects_bad_out_before_any_launch(dda, monkeypatch):
+    import torch
+
+    def boom(*a, **k):  # any call into the library would be a launch
+        raise AssertionError("library called")
+
+    for name in ("dda_matvec", "dda_precond_apply", "dda_precond2_apply",
+                 "dda_precond_apply_noalloc", "dda_fft3d", "dda_cross_sections",
+                 "dda_ext_gradient", "dda_solve"):
+        monkeypatch.setattr(dda._lib, name, boom)
+    p = _fake_plan(dda)
+    v = torch.zeros(p.field_shape(2), dtype=torch.complex64)
+    bad_outs = [torch.zeros(p.field_shape(1), dtype=torch.complex64),         # too small
+                torch.zeros(p.field_shape(2), dtype=torch.complex128),        # other dtype
+                torch.zeros((2, 3, 2, 4, 16), dtype=torch.complex64)[..., ::2],  # strided
+                "not a tensor"]
+    for apply in (p.matvec, p.precond_apply, p.precond2_apply, p.precond_apply_noalloc):
+        for out in bad_outs:
+            with pytest.raises((TypeError, ValueError)):
+                apply(v, out)
+    with pytest.raises(ValueError):
+        p.precond_apply_noalloc(v, None)
+    with pytest.raises(ValueError):
+        p.matvec(v, v)                                       # y must not alias x
+    with pytest.raises(ValueError):
+        p.precond_apply(torch.zeros((2, 3, 2, 4, 4), dtype=torch.complex64))  # wrong box
+    with pytest.raises(TypeError):
+        p.precond_apply(torch.zeros(p.field_shape(2), dtype=torch.float32))
+    with pytest.raises(TypeError):
+        p.cross_sections(v)                                  # solutions are complex128
+    with pytest.raises(ValueError):
+        p.fft3d(torch.zeros((1, 2, 4, 4), dtype=torch.complex64))
+    with pytest.raises(ValueError):
+        p.ext_gradient_from(torch.zeros(p.field_shape(2), dtype=torch.complex128),
+                            torch.zeros(p.field_shape(1), dtype=torch.complex128))
+    with pytest.raises(ValueError):
+        p.solve(b=torch.zeros(p.field_shape(1)[:-1] + (3,), dtype=torch.complex128))

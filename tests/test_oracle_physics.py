@@ -3,6 +3,7 @@ import os
 
 import numpy as np
 import pytest
+from scipy.special import erfc
 
 from oracle import physics
 from oracle.operator import COMPONENTS
@@ -33,18 +34,103 @@ def test_alpha_cm_special_values():
     assert np.isclose(physics.alpha_cm(1e12), 3.0 / (4.0 * np.pi), rtol=1e-10)
 
 
-def test_ldr_tends_to_cm_and_series():
+def test_ldr_tends_to_cm():
     eps = 1.31 ** 2
     a = physics.alpha_cm(eps)
-    for kd in (1e-3, 1e-4):
-        S = 0.3
-        got = physics.alpha_ldr(eps, kd, 1.0, S)
-        # first-order expansion of 1/(1 + a*q),
-        # q = (b1 + eps b2 + eps b3 S) kd^2 - (2i/3) kd^3
-        q = ((physics.LDR_B1 + eps * physics.LDR_B2 + eps * physics.LDR_B3 * S) * kd ** 2
-             - (2j / 3.0) * kd ** 3)
-        assert abs(got - a * (1 - a * q)) < 10 * abs(a) * abs(a * q) ** 2 + 1e-15
     assert np.isclose(physics.alpha_ldr(eps, 0.0, 1.0, 0.0), a, rtol=1e-15)
+    assert np.isclose(physics.alpha_ldr(eps, 1e-4, 1.0, 0.3), a, rtol=1e-6)
+
+
+def _lattice_green_sum(K, k, eta, nshell=6):
+    """sum over R != 0 of g(R) exp(i K.R) on the unit simple-cubic lattice.
+
+    g = (k^2 + grad grad) e^{ikr}/r is the Green function of Section 2.  The
+    conditionally convergent sum is split the Ewald way (parameter eta): the
+    real-space part uses
+        phi(r) = [e^{ikr} erfc(r eta + ik/2eta) + e^{-ikr} erfc(r eta - ik/2eta)] / 2r,
+    the reciprocal part 4 pi e^{-(q^2-k^2)/4eta^2} / (q^2 - k^2) at q = K + G,
+    and the R = 0 term of phi minus e^{ikr}/r is removed by its Taylor series
+    at r = 0, (k^2 f0 + 2 f2) I.  The result does not depend on eta (checked).
+    """
+    K = np.asarray(K, dtype=np.float64)
+    c = 2.0 / np.sqrt(np.pi)
+    a = 1j * k / (2.0 * eta)
+    ea = np.exp(-a * a)
+    span = np.arange(-nshell, nshell + 1)
+    R = np.stack(np.meshgrid(span, span, span, indexing="ij"), -1).reshape(-1, 3).astype(np.float64)
+    # reciprocal lattice: G = 2 pi R
+    q = K[None] + 2.0 * np.pi * R
+    q2 = np.sum(q * q, axis=1)
+    w = 4.0 * np.pi * np.exp(-(q2 - k * k) / (4.0 * eta ** 2)) / (q2 - k * k)
+    T = k * k * np.sum(w) * np.eye(3) - np.einsum("n,ni,nj->ij", w, q, q)
+    # real space, R != 0: (k^2 + grad grad) phi(|R|) = (k^2 phi + phi'/r) I + (phi'' - phi'/r) RR^T
+    R = R[np.any(R != 0, axis=1)]
+    r = np.linalg.norm(R, axis=1)
+    u1, u2 = r * eta + a, r * eta - a
+    e1, e2 = np.exp(1j * k * r), np.exp(-1j * k * r)
+    E1, E2 = erfc(u1), erfc(u2)
+    g1, g2 = np.exp(-u1 * u1), np.exp(-u2 * u2)
+    h = e1 * E1 + e2 * E2
+    h1 = 1j * k * (e1 * E1 - e2 * E2) - c * eta * (e1 * g1 + e2 * g2)
+    h2 = (-k * k * h - 2j * k * c * eta * (e1 * g1 - e2 * g2)
+          + 2.0 * c * eta ** 2 * (u1 * e1 * g1 + u2 * e2 * g2))
+    phi = h / (2 * r)
+    d1 = h1 / (2 * r) - h / (2 * r ** 2)
+    d2 = h2 / (2 * r) - h1 / r ** 2 + h / r ** 3
+    Rh = R / r[:, None]
+    ph = np.exp(1j * (R @ K))
+    T = T + np.einsum("n,ij->ij", ph * (k * k * phi + d1 / r), np.eye(3))
+    T = T + np.einsum("n,ni,nj->ij", ph * (d2 - d1 / r), Rh, Rh)
+    # R = 0: phi(r) - e^{ikr}/r = f0 + f2 r^2 + ...,
+    # f0 = -ik erfc(-a) - c e^{-a^2} eta, f2 = ik^3 erfc(-a)/6 + c e^{-a^2}(k^2 eta + 2 eta^3)/6
+    qa = erfc(-a)
+    T = T + (-(2.0 / 3.0) * 1j * k ** 3 * qa - (2.0 / 3.0) * k * k * c * ea * eta
+             + (2.0 / 3.0) * c * ea * eta ** 3) * np.eye(3)
+    return T
+
+
+def test_lattice_sum_is_ewald_invariant_and_lossless():
+    # The Ewald split parameter must drop out; for a real refractive index the
+    # infinite lattice radiates nothing, so Im of the sum is minus the
+    # radiative reaction of the removed self term, -(2/3) k^3.
+    k, K = 0.3, np.array([0.1, 0.2, 0.35])
+    ref = _lattice_green_sum(K, k, 2.0)
+    for eta in (1.5, 3.0):
+        assert np.allclose(_lattice_green_sum(K, k, eta), ref, rtol=0, atol=1e-11)
+    assert np.allclose(ref.imag, -(2.0 / 3.0) * k ** 3 * np.eye(3), rtol=0, atol=1e-11)
+    assert np.allclose(ref, ref.T, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("m_index", [1.31, 1.78, 2.5])
+def test_ldr_is_the_lattice_dispersion_relation(m_index):
+    # Independent pin of the whole LDR display of Section 2.1, dispersion term
+    # included.  The constants b1, b2, b3 come from the lattice dispersion
+    # relation of Draine & Goodman (1993): with alpha = alpha_LDR, an infinite
+    # cubic lattice of dipoles (spacing dx) carries a free transverse wave of
+    # wavevector K = m k d and polarisation e, i.e.
+    #     e . [sum_{R != 0} g(R) e^{iK.R}] e = 1/alpha,
+    # up to O((k dx)^4).  The lattice sum is computed here by Ewald summation,
+    # with no use of the LDR formula.  A wrong power of m in the b2 or b3 term,
+    # swapped b2/b3, a dropped b1 or the bare CM value all leave a residual of
+    # order (k dx)^2 (residual / (k dx)^2 >= 0.2 for every such variant here).
+    eps = m_index ** 2
+    pairs = [((0, 0, 1.0), (1.0, 0, 0)),                      # S = 0
+             ((1.0, 1, 1), (1.0, -1, 0)),                     # S = 1/3
+             ((1.0, 1, 0), (1.0, -1, 0)),                     # S = 1/2
+             ((1.0, 1, 0), (0, 0, 1.0))]                      # S = 0
+    for d, e in pairs:
+        d = np.asarray(d) / np.linalg.norm(d)
+        e = np.asarray(e) / np.linalg.norm(e)
+        S = physics.ldr_S(d, e)
+        scaled = []
+        for kd in (0.05, 0.1):
+            T = _lattice_green_sum(m_index * kd * d, kd, 2.0)
+            lam = e @ T @ e
+            assert np.linalg.norm(T @ e - lam * e) < 1e-10   # e is a lattice eigenmode
+            scaled.append(abs(lam - 1.0 / physics.alpha_ldr(eps, kd, 1.0, S)) / kd ** 2)
+        assert scaled[0] < 0.005, (m_index, S, scaled)
+        # the residual is O((k dx)^4): halving k dx divides residual/(k dx)^2 by ~4
+        assert 3.0 < scaled[1] / scaled[0] < 5.0, (m_index, S, scaled)
 
 
 def test_ldr_radiative_reaction_real_eps():

@@ -33,7 +33,14 @@ def test_noalloc_apply_matches_workspace_apply(prec):
         v = to_dev(random_field((2, 3, n, m, l), rng), dt)
         want = plan.precond_apply(v).cpu().numpy()
         out = torch.empty_like(v)
-        got = plan.precond_apply_noalloc(v, out).cpu().numpy()
+        # the call's whole contract: the device's free memory does not move,
+        # on the first call as on the second (plan creation loaded the array)
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
+        plan.precond_apply_noalloc(v, out)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free_before, (prec, call)
+        got = out.cpu().numpy()
         assert rel_err(got, want) < tol, (prec, call)
 
 

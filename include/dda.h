@@ -85,6 +85,8 @@ typedef struct {
   int32_t circulant;     /* circulant of the preconditioners (Section 3): 0 T. Chan's
                             optimal one (eq. 13), 1 Strang's (central diagonals kept;
                             at p = L/2 of an even level the mean of t_{L/2}, t_{-L/2}) */
+  int32_t voxel_eps;     /* 1: reserve a permittivity per voxel (dda_set_voxel_eps):
+                            (16 + max_rhs * 40) bytes per voxel                      */
 } dda_plan_desc_t;
 
 /* Plane wave E_inc = pol * exp(i k dir . r), r measured from the box centre.
@@ -113,6 +115,18 @@ typedef struct {
   int32_t method;        /* 0: GMRES(restart); 1: BiCG-Stab (van der Vorst), the paper's
                             second solver (Section 4), restart = iterations per
                             refinement cycle; the plan needs krylov_m >= 7             */
+  int32_t history_cap;   /* entries of h_history per right-hand side (0: none)        */
+  int64_t timeout_ns;    /* time limit of the solve on the device's global timer
+                            (0: none); checked after every inner iteration and at
+                            every restart: right-hand sides not converged by then
+                            stop with DDA_ERR_TIMEOUT, x holding the last cycle's
+                            iterate                                                   */
+  double* h_history;     /* host [nrhs][history_cap] or NULL: relative residual after
+                            each inner iteration (entry i after i iterations; GMRES's
+                            estimate |g_{j+1}|/||b||, BiCG-Stab's ||r||/||b||, the
+                            true FP64 residual at every restart, entry 0 = the
+                            initial one): the convergence history of Section 4's
+                            figures.  dda_solve_many needs NULL                      */
 } dda_solve_opts_t;
 
 typedef struct {
@@ -122,6 +136,9 @@ typedef struct {
   int32_t status;        /* dda_status_t of this right-hand side                       */
   double rel_resid;      /* final ||b - A x|| / ||b|| evaluated in complex128          */
   int32_t reorth;        /* Arnoldi steps that needed a second Gram-Schmidt pass       */
+  int32_t history_len;   /* entries written to this RHS's row of h_history             */
+  int32_t graph;         /* 1: the solve ran as one CUDA graph launch (below)          */
+  float ms;              /* wall time of the dda_solve call, milliseconds              */
 } dda_rhs_stats_t;
 
 /* Bytes of device workspace a plan with this description needs (0 when the
@@ -153,6 +170,18 @@ dda_status_t dda_plan_create(dda_plan_t* out, const dda_plan_desc_t* desc, const
  * (Section 3.1, eq. 20), and uploads them on `stream`. */
 dda_status_t dda_set_incidence(dda_plan_t plan, int32_t nrhs, const dda_incidence_t* h_inc,
                                void* stream);
+
+/* A complex permittivity for every voxel (Section 2.1 defines alpha from a
+ * voxel's eps = m^2; nothing in the method requires it to be one value per
+ * material): d_eps is device complex128 [n][m][l] (re, im pairs), copied.
+ * Voxels of material 0 stay air and their entries are ignored; every other
+ * voxel's alpha^{-1} (CM + LDR, per right-hand side) comes from its own eps
+ * in the matvec, the cross sections and dda_ext_gradient.  alpha_tilde (air
+ * rows, preconditioners) stays that of the material table (dda_plan_create's
+ * h_eps).  Needs a plan made with desc.voxel_eps = 1; may be called before or
+ * after dda_set_incidence (the per-voxel polarizabilities are re-tabulated
+ * on the device for the current incidences).  NULL turns the table off. */
+dda_status_t dda_set_voxel_eps(dda_plan_t plan, const void* d_eps, void* stream);
 
 /* d_b[rhs] = E_inc on scatterer voxels, 0 on air; complex128 box fields. */
 dda_status_t dda_incident_field(dda_plan_t plan, int32_t nrhs, void* d_b, void* stream);
@@ -244,10 +273,19 @@ dda_status_t dda_fft3d(dda_plan_t plan, int32_t prec, int32_t nbatch, void* d_da
  * device.  Every restart recomputes
  * the residual b - A x in complex128; with inner_prec = DDA_C64 the Krylov
  * basis, matvecs and preconditioner run in complex64 (FP64 iterative
- * refinement).  Returns DDA_ERR_NOT_CONVERGED if any right-hand side missed
- * tol within max_iters (x then holds the last iterate), DDA_ERR_NAN on a
- * non-finite residual, DDA_ERR_NO_PRECOND if precond = 3 was asked before
- * dda_precond_build.  Synchronises `stream`. */
+ * refinement).  The loop's decisions (restart, convergence, iteration cap,
+ * time limit) are taken on the device; with the plan's schedule field graph
+ * = 1 (the default) the whole loop is one CUDA graph launch (see
+ * dda_schedule_t), captured on the first solve with given arguments and
+ * reused by later ones with the same arguments, device pointers included.
+ * Returns DDA_ERR_NOT_CONVERGED if any right-hand side missed tol within
+ * max_iters (x then holds the last iterate), DDA_ERR_TIMEOUT if the time
+ * limit stopped one, DDA_ERR_BREAKDOWN if a restart cycle ended without a
+ * single iteration (BiCG-Stab breaking down at its first step: the next
+ * cycle would repeat it, so that right-hand side stops; the loop always
+ * ends), DDA_ERR_NAN on a non-finite residual, DDA_ERR_NO_PRECOND
+ * if precond = 3 was asked before dda_precond_build.  Synchronises
+ * `stream`. */
 dda_status_t dda_solve(dda_plan_t plan, int32_t nrhs, const void* d_b, void* d_x,
                        const dda_solve_opts_t* opts, dda_rhs_stats_t* h_stats, void* stream);
 
@@ -328,13 +366,23 @@ dda_status_t dda_ext_gradient(dda_plan_t plan, int32_t nrhs, const void* d_c,
  *   pdl:  1 = kernels are launched with programmatic dependent launch (the
  *         next kernel's blocks become resident while the previous one drains);
  *         0 = ordinary stream-ordered launches.
- * A new plan starts with {1, 1}.  The environment variables DDA_RR_FFT3C=0 and
- * DDA_PDL=0 force the plain forms whatever the schedule.  The schedule applies
- * to dda_matvec, dda_precond_apply, dda_precond2_apply and dda_solve (hence
- * dda_solve_many) of that plan, in the calling thread.  Not in the paper. */
+ *   graph: 1 = dda_solve captures its whole loop once into a CUDA graph whose
+ *         conditional nodes (a WHILE over restart cycles, an IF per cycle, a
+ *         WHILE over the cycle's steps) take their conditions from the device
+ *         (convergence, iteration cap, time limit), so a solve is one graph
+ *         launch with no host round trip; the graph is kept and reused while
+ *         the solve's arguments stay the same.  0 = the host drives the loop
+ *         and polls the device's decisions.  Kernel timing
+ *         (dda_profile_enable) always uses the host-driven loop.
+ * A new plan starts with {1, 1, 1}.  The environment variables DDA_RR_FFT3C=0,
+ * DDA_PDL=0 and DDA_SOLVE_GRAPH=0 force the plain forms whatever the schedule.
+ * The schedule applies to dda_matvec, dda_precond_apply, dda_precond2_apply
+ * and dda_solve (hence dda_solve_many) of that plan, in the calling thread.
+ * Not in the paper. */
 typedef struct {
   int32_t rr_z;
   int32_t pdl;
+  int32_t graph;
 } dda_schedule_t;
 
 /* Set or read a plan's schedule (no GPU work).  Fields must be 0 or 1;
@@ -347,7 +395,7 @@ typedef struct {
   dda_schedule_t chosen;     /* the schedule now set on the plan */
   int32_t cached;            /* 1: taken from the process-wide table, nothing timed */
   int32_t ncand;             /* schedules timed (0 when cached) */
-  dda_schedule_t cand[4];    /* the schedules timed, in order */
+  dda_schedule_t cand[4];    /* the schedules timed, in order (graph as set) */
   float ms_per_matvec[4];    /* their mean CUDA-event time per matvec call */
 } dda_tune_report_t;
 

@@ -1,6 +1,7 @@
 // Plan creation: workspace layout, Green-function spectrum, polarizabilities,
 // incident field and the standalone 3-D FFT entry point.
 #include <atomic>
+#include <cstdlib>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -17,6 +18,16 @@ std::atomic<long long> g_launches{0};
 }
 
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launch_counter() { return g_launches.load(std::memory_order_relaxed); }
+void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+bool solve_graph_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("DDA_SOLVE_GRAPH");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
 
 void set_error(const std::string& msg) { g_err = msg; }
 
@@ -46,6 +57,7 @@ bool valid_desc(const dda_plan_desc_t& d, std::string& why, dda_status_t& st) {
   if (d.precond2 < 0 || d.precond2 > 3)
     return why = "precond2 must be 0 (none) or 1, 2, 3 (Toeplitz level z, x, y)", false;
   if (d.circulant != 0 && d.circulant != 1) return why = "circulant must be 0 (Chan) or 1 (Strang)", false;
+  if (d.voxel_eps != 0 && d.voxel_eps != 1) return why = "voxel_eps must be 0 or 1", false;
   if ((d.precisions & (DDA_PLAN_C128 | DDA_PLAN_C64)) == 0 ||
       (d.precisions & ~(DDA_PLAN_C128 | DDA_PLAN_C64)) != 0)
     return why = "precisions must be a non-empty set of DDA_PLAN_C128 | DDA_PLAN_C64", false;
@@ -88,6 +100,12 @@ bool make_layout(const dda_plan_desc_t& d, void* ws, Layout& L, std::string& why
   L.ainv128 = c.take(R * K1 * 16);
   L.ainv64 = c.take(R * K1 * 8);
   L.incd = static_cast<double*>(c.take(R * 6 * sizeof(double)));
+  if (d.voxel_eps) {
+    L.eps_vox = c.take(16 * nvox);
+    L.pv128 = c.take(16 * R * nvox);
+    L.pv64 = c.take(8 * R * nvox);
+    if (h128) L.pvdf = c.take(16 * R * nvox);
+  }
   L.dainv128 = c.take(R * K1 * 16);
   L.buf1 = c.take(esz * R * 3 * n * m * Lx);
   size_t b2 = esz * R * 3 * n * Ly * Lx;
@@ -134,6 +152,11 @@ bool make_layout(const dda_plan_desc_t& d, void* ws, Layout& L, std::string& why
     s.tickets = static_cast<int*>(c.take(8 * R));
     s.bscal = static_cast<double*>(c.take(8 * 16 * R));
     s.counters = static_cast<int*>(c.take(64));
+    s.ctl = static_cast<int*>(c.take(16));
+    s.out = c.take((size_t)kRhsOutBytes * R);
+    s.hist = static_cast<double*>(c.take(sizeof(double) * kHistCap * R));
+    s.t0 = static_cast<unsigned long long*>(c.take(8));
+    s.nlaunch = static_cast<long long*>(c.take(8));
   }
   L.total = c.off + 256;
   return true;
@@ -262,6 +285,73 @@ extern "C" size_t dda_workspace_size(const dda_plan_desc_t* desc) {
   return L.total;
 }
 
+namespace dda {
+namespace {
+
+__device__ __forceinline__ double2 cdivd(double2 a, double2 b) {
+  const double dn = b.x * b.x + b.y * b.y;
+  return make_double2((a.x * b.x + a.y * b.y) / dn, (a.y * b.x - a.x * b.y) / dn);
+}
+
+// alpha^{-1} of every scatterer voxel for every right-hand side from the
+// voxel's own permittivity: 1/alpha = 1/alpha_CM + (b1 + eps b2 + eps b3 S)(k dx)^2
+// - (2i/3)(k dx)^3 with 1/alpha_CM = (4 pi/3)(eps + 2)/(eps - 1) (Section 2.1,
+// the LDR display), S = sum_j (d_j e_j)^2 of the right-hand side's wave.
+// Air voxels get alpha_tilde^{-1} (ainv[rhs][0]); they are never read.
+__global__ void k_voxel_ainv(const double2* __restrict__ eps, const uint8_t* __restrict__ mat,
+                             const double* __restrict__ incd, const double2* __restrict__ ainv,
+                             int K1, int nrhs, long nvox, double kd, double2* __restrict__ pv128,
+                             float2* __restrict__ pv64, cx<df>* __restrict__ pvdf,
+                             int* __restrict__ err) {
+  pdl_entry();
+  const double pi = 3.14159265358979323846;
+  const long tot = nvox * nrhs;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < tot;
+       i += (long)gridDim.x * blockDim.x) {
+    const long v = i % nvox;
+    const int r = (int)(i / nvox);
+    double2 a = ainv[(long)r * K1];
+    if (mat[v] != 0) {
+      const double2 e = eps[v];
+      const double* q = incd + r * 6;
+      double S = 0.0;
+      for (int c = 0; c < 3; ++c) S += (q[c] * q[3 + c]) * (q[c] * q[3 + c]);
+      const double2 cm = cdivd(make_double2(e.x + 2.0, e.y), make_double2(e.x - 1.0, e.y));
+      const double b = -1.7700004 * S + 0.1648469;
+      const double kd2 = kd * kd;
+      a.x = (4.0 * pi / 3.0) * cm.x + (-1.891531 + e.x * b) * kd2;
+      a.y = (4.0 * pi / 3.0) * cm.y + e.y * b * kd2 - (2.0 / 3.0) * kd2 * kd;
+      if (!isfinite(a.x) || !isfinite(a.y)) atomicOr(err, 2);
+    }
+    pv128[i] = a;
+    pv64[i] = make_float2((float)a.x, (float)a.y);
+    if (pvdf != nullptr) pvdf[i] = mk<df>(df(a.x), df(a.y));
+  }
+}
+
+// Tabulate the per-voxel polarizabilities for the current incidences.
+dda_status_t tabulate_voxel_ainv(dda_plan_s* p, cudaStream_t s) {
+  if (!p->voxel_eps_on || p->nrhs_inc < 1) return DDA_OK;
+  cudaMemsetAsync(p->w.err_flag, 0, 4, s);
+  const long tot = p->nvox * p->nrhs_inc;
+  const unsigned grid = (unsigned)std::min<long>(std::max<long>((tot + 255) / 256, 1), 152L * 32);
+  note_launch();
+  k_voxel_ainv<<<grid, 256, 0, s>>>(
+      static_cast<const double2*>(p->w.eps_vox), p->mat, p->w.incd,
+      static_cast<const double2*>(p->w.ainv128), p->K + 1, p->nrhs_inc, p->nvox,
+      p->d.k * p->d.dx, static_cast<double2*>(p->w.pv128), static_cast<float2*>(p->w.pv64),
+      static_cast<cx<df>*>(p->w.pvdf), static_cast<int*>(p->w.err_flag));
+  int err = 0;
+  cudaMemcpyAsync(&err, p->w.err_flag, 4, cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return check_cuda("dda_set_voxel_eps");
+  if (err) return fail(DDA_ERR_INVALID_ARG, "dda_set_voxel_eps: a voxel's polarizability is "
+                                            "singular (eps = 1 on a scatterer voxel?)");
+  return DDA_OK;
+}
+
+}  // namespace
+}  // namespace dda
+
 extern "C" dda_status_t dda_plan_create(dda_plan_t* out, const dda_plan_desc_t* desc,
                                         const uint8_t* d_mat, const double* h_eps, void* d_work,
                                         size_t work_bytes, void* stream) {
@@ -283,6 +373,8 @@ extern "C" dda_status_t dda_plan_create(dda_plan_t* out, const dda_plan_desc_t* 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   dda_plan_s* p = new dda_plan_s();
+  static std::atomic<long long> next_id{1};
+  p->id = next_id.fetch_add(1);
   p->d = *desc;
   p->l = desc->l;
   p->m = desc->m;
@@ -443,7 +535,26 @@ extern "C" dda_status_t dda_set_incidence(dda_plan_t p, int32_t nrhs, const dda_
   }
   p->inc.assign(inc, inc + nrhs);
   p->nrhs_inc = nrhs;
-  return check_cuda("dda_set_incidence");
+  const dda_status_t st = check_cuda("dda_set_incidence");
+  if (st != DDA_OK) return st;
+  return tabulate_voxel_ainv(p, s);
+}
+
+extern "C" dda_status_t dda_set_voxel_eps(dda_plan_t p, const void* d_eps, void* stream) {
+  if (!p) return fail(DDA_ERR_INVALID_ARG, "dda_set_voxel_eps: NULL plan");
+  if (!p->d.voxel_eps)
+    return fail(DDA_ERR_INVALID_ARG, "dda_set_voxel_eps: plan made without voxel_eps");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (d_eps == nullptr) {
+    p->voxel_eps_on = false;
+    return DDA_OK;
+  }
+  cudaMemcpyAsync(p->w.eps_vox, d_eps, 16 * p->nvox, cudaMemcpyDeviceToDevice, s);
+  p->voxel_eps_on = true;
+  dda_status_t st = check_cuda("dda_set_voxel_eps");
+  if (st == DDA_OK) st = tabulate_voxel_ainv(p, s);
+  if (st != DDA_OK) p->voxel_eps_on = false;
+  return st;
 }
 
 extern "C" dda_status_t dda_incident_field(dda_plan_t p, int32_t nrhs, void* d_b, void* stream) {

@@ -27,7 +27,11 @@
 // a pinned word to stop launching once every right-hand side has finished
 // its cycle.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
 #include <vector>
 
 #include "plan.hpp"
@@ -37,6 +41,45 @@ namespace dda {
 namespace {
 
 constexpr int kNT = 256;  // threads of the vector kernels
+
+// Device time in nanoseconds (the global timer of the GPU).
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Control of the solve loop from the device.  When the loop runs as one
+// CUDA graph (conditional WHILE and IF nodes), the kernels that decide
+// whether another restart cycle or Arnoldi step follows set the graph's
+// condition values themselves; graph == 0 is the host-driven loop, whose
+// kernels get the step index as an argument and whose host reads the
+// decisions back.  The same kernels serve both.
+struct LoopCtl {
+  int graph;                          // 1: graph-driven (handles valid)
+  cudaGraphConditionalHandle h_cycle; // WHILE over restart cycles
+  cudaGraphConditionalHandle h_run;   // IF: this cycle has right-hand sides to run
+  cudaGraphConditionalHandle h_step;  // WHILE over the steps of a cycle
+  int* jstep;                         // step index within the cycle
+  int* steps;                         // steps allowed in this cycle
+  int* nrun;                          // right-hand sides running this cycle
+  long long* nlaunch;                 // kernels run by the graph (counted on the device)
+  int k_head, k_run, k_step;          // kernels per cycle head, cycle start + end, step
+  const unsigned long long* t0;       // solve start (global timer)
+  long long timeout_ns;               // 0: no limit
+  double* hist;                       // [rhs][hcap] relative residual per inner iteration
+  int hcap;
+  int max_iters;
+};
+
+// Outcome of one right-hand side, written by k_cycle_decide.
+struct RhsOut {
+  int conv, nan, cycles, timeout;
+  double rel;
+  int last_it;  // inner iterations when the last cycle that ran started
+  int stalled;  // a cycle ran without a single iteration (BiCG-Stab breakdown)
+};
+static_assert(sizeof(RhsOut) == kRhsOutBytes, "RhsOut layout");
 
 // Error-free sum of two floats (Knuth's TwoSum): a + b = s + e exactly.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -178,8 +221,12 @@ __global__ void __launch_bounds__(kNT, sizeof(T) == 4 ? 3 : 1)
                int jc, double2* __restrict__ partial, int pst, const int* __restrict__ mask,
                const int* __restrict__ mask2, int want_norm, int* __restrict__ tickets,
                double2* __restrict__ hcol, double2* __restrict__ H, int m, int j, int pass,
-               double* __restrict__ scal) {
+               double* __restrict__ scal, const int* __restrict__ jdev) {
   pdl_entry();
+  if (jdev != nullptr) {  // graph-driven loop: the step index lives on the device
+    j = *jdev;
+    jc = j + 1;
+  }
   constexpr int ND = 8;
   constexpr int NW = kNT / 32;
   __shared__ double2 sh[ND][NW];
@@ -299,8 +346,12 @@ __global__ void __launch_bounds__(kDotNT)
              int jc, double2* __restrict__ partial, int pst, const int* __restrict__ mask,
              const int* __restrict__ mask2, int want_norm, int* __restrict__ tickets,
              double2* __restrict__ hcol, double2* __restrict__ H, int m, int j, int pass,
-             double* __restrict__ scal) {
+             double* __restrict__ scal, const int* __restrict__ jdev) {
   pdl_entry();
+  if (jdev != nullptr) {
+    j = *jdev;
+    jc = j + 1;
+  }
   constexpr int NW = kDotNT / 32;
   __shared__ int s_last;
   const int r = blockIdx.y;
@@ -392,8 +443,9 @@ __global__ void __launch_bounds__(kNT)
              const double2* __restrict__ hcol, int m, double2* __restrict__ partial, int pst,
              const int* __restrict__ mask, const int* __restrict__ mask2, int* __restrict__ tickets,
              double* __restrict__ scal, int pass, int* __restrict__ reorth,
-             int* __restrict__ reorth_count, double eta2) {
+             int* __restrict__ reorth_count, double eta2, const int* __restrict__ jdev) {
   pdl_entry();
+  if (jdev != nullptr) jc = *jdev + 1;
   __shared__ cx<T> hs[520];
   __shared__ double2 sh[32];
   __shared__ int s_last;
@@ -508,8 +560,10 @@ __global__ void __launch_bounds__(32)
     k_givens(double2* __restrict__ H, double* __restrict__ cs, double2* __restrict__ sn,
              double2* __restrict__ g, double* __restrict__ scal, int* __restrict__ active,
              int* __restrict__ jlen, int* __restrict__ flags, int* __restrict__ iters, int nrhs,
-             int m, int j, double brk, int* __restrict__ count_out, int* __restrict__ ticket) {
+             int m, int j, double brk, int* __restrict__ count_out, int* __restrict__ ticket,
+             LoopCtl ctl) {
   pdl_entry();
+  if (ctl.graph) j = *ctl.jstep;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* hs = reinterpret_cast<double2*>(smem_raw);  // [j + 2]
   double2* ss = hs + (j + 2);                           // [j]
@@ -555,8 +609,16 @@ __global__ void __launch_bounds__(32)
       sc[4] = res;
       sc[5] = hn > 0.0 ? 1.0 / hn : 0.0;
       jlen[r] = j + 1;
-      iters[r] += 1;
-      if (!isfinite(res) || !isfinite(hn)) {
+      const int it = iters[r] + 1;
+      iters[r] = it;
+      if (ctl.hist != nullptr && it < ctl.hcap) {
+        const double bn = sc[2];
+        ctl.hist[(long)r * ctl.hcap + it] = bn > 0.0 ? res / bn : res;
+      }
+      if (ctl.timeout_ns > 0 && (long long)(now_ns() - *ctl.t0) > ctl.timeout_ns) {
+        flags[r] |= 4;  // time limit of the solve reached
+        active[r] = 0;
+      } else if (!isfinite(res) || !isfinite(hn)) {
         flags[r] |= 1;
         active[r] = 0;
       } else if (res <= sc[3]) {
@@ -564,6 +626,8 @@ __global__ void __launch_bounds__(32)
       } else if (hn <= brk * sqrt(colnorm2)) {
         flags[r] |= 2;  // breakdown: the Krylov space is invariant, the cycle's solution is exact
         active[r] = 0;
+      } else if (it >= ctl.max_iters) {
+        active[r] = 0;  // this right-hand side's iteration cap
       }
     }
     __syncwarp();
@@ -583,32 +647,154 @@ __global__ void __launch_bounds__(32)
       if (lane == 0) {
         *count_out = cnt;
         *ticket = 0;
+        if (ctl.graph) {  // the next step runs while some RHS iterate and the cycle has room
+          const int jn = j + 1;
+          *ctl.jstep = jn;
+          cudaGraphSetConditional(ctl.h_step, (cnt > 0 && jn < *ctl.steps) ? 1u : 0u);
+          *ctl.nlaunch += ctl.k_step;
+        }
       }
     }
   }
 }
 
+// v_{j+1} = w / h_{j+1,j} into the basis (slot Vn, or with jdev the slot of
+// the device's step index, which the Givens kernel has just advanced), and
+// the same vector into Zc when given: the graph-driven loop feeds the next
+// step's preconditioner and matvec from that fixed buffer.
 template <typename T>
 __global__ void __launch_bounds__(kNT)
     k_scale(const cx<T>* __restrict__ W, cx<T>* __restrict__ Vn, long nu,
-            const double* __restrict__ scal, const int* __restrict__ active) {
+            const double* __restrict__ scal, const int* __restrict__ active,
+            cx<T>* __restrict__ V, long vstride, const int* __restrict__ jdev,
+            cx<T>* __restrict__ Zc) {
   pdl_entry();
   const int r = blockIdx.y;
   if (!active[r]) return;
+  if (jdev != nullptr) Vn = V + (long)(*jdev) * vstride;
   const T inv = (T)scal[(long)r * 16 + 5];
   long k0, k1;
   chunk_of(nu, gridDim.x, k0, k1);
-  for (long k = k0 + threadIdx.x; k < k1; k += kNT) Vn[r * nu + k] = inv * W[r * nu + k];
+  for (long k = k0 + threadIdx.x; k < k1; k += kNT) {
+    const cx<T> v = inv * W[r * nu + k];
+    Vn[r * nu + k] = v;
+    if (Zc != nullptr) Zc[r * nu + k] = v;
+  }
 }
 
-// Number of right-hand sides still iterating.
-__global__ void k_count_active(const int* __restrict__ active, int nrhs, int* __restrict__ out) {
+// Number of right-hand sides still iterating (one warp).  Also the
+// BiCG-Stab loop's step control: the time limit, the residual history
+// (sqrt of bs[10], the last ||r||^2, relative to ||b||) and, graph-driven,
+// the next step's condition.
+__global__ void k_count_active(int* __restrict__ active, int nrhs, int* __restrict__ out,
+                               int* __restrict__ flags, const int* __restrict__ iters,
+                               const double* __restrict__ bs, const double* __restrict__ scal,
+                               LoopCtl ctl) {
   pdl_entry();
+  const bool late = ctl.timeout_ns > 0 && (long long)(now_ns() - *ctl.t0) > ctl.timeout_ns;
   int c = 0;
-  for (int r = threadIdx.x; r < nrhs; r += blockDim.x) c += active[r];
+  for (int r = threadIdx.x; r < nrhs; r += blockDim.x) {
+    if (late && active[r]) {
+      flags[r] |= 4;
+      active[r] = 0;
+    }
+    c += active[r];
+    const int it = iters[r];
+    if (ctl.hist != nullptr && it < ctl.hcap && bs != nullptr) {
+      const double bn = scal[(long)r * 16 + 2], rn = sqrt(bs[(long)r * 16 + 10]);
+      ctl.hist[(long)r * ctl.hcap + it] = bn > 0.0 ? rn / bn : rn;
+    }
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
-  if (threadIdx.x == 0) *out = c;
+  if (threadIdx.x == 0) {
+    *out = c;
+    if (ctl.graph) {
+      const int jn = *ctl.jstep + 1;
+      *ctl.jstep = jn;
+      cudaGraphSetConditional(ctl.h_step, (c > 0 && jn < *ctl.steps) ? 1u : 0u);
+      *ctl.nlaunch += ctl.k_step;
+    }
+  }
+}
+
+// Start of a restart cycle, after the FP64 residual: per right-hand side
+// converged (||r|| <= tol ||b||), non-finite, out of time or out of
+// iterations, or running another cycle; the cycle's step count (restart
+// length, at most the iterations the running RHS have left); the true
+// relative residual into the history at the current iteration count.
+// Graph-driven, it sets the conditions of the cycle loop, of this cycle's
+// body and of its step loop.  One block.
+__global__ void __launch_bounds__(256)
+    k_cycle_decide(const double* __restrict__ scal, const int* __restrict__ iters,
+                   int* __restrict__ flags, int* __restrict__ run, RhsOut* __restrict__ out,
+                   int nrhs, double tol, int m, LoopCtl ctl) {
+  pdl_entry();
+  __shared__ int s_n[8], s_l[8];
+  const bool late = ctl.timeout_ns > 0 && (long long)(now_ns() - *ctl.t0) > ctl.timeout_ns;
+  int nrun = 0, left = 0;
+  for (int r = threadIdx.x; r < nrhs; r += blockDim.x) {
+    const double bn = scal[(long)r * 16 + 2], rn = scal[(long)r * 16 + 6];
+    const double rel = bn > 0.0 ? rn / bn : rn;
+    const int nan = !isfinite(rn) || (flags[r] & 1);
+    const int conv = isfinite(rn) && (rn <= tol * bn || bn == 0.0);
+    if (late && !conv && !nan) flags[r] |= 4;
+    const int to = (flags[r] & 4) != 0;
+    const int it = iters[r];
+    RhsOut o = out[r];
+    // a cycle that ended without one iteration (a breakdown at its first
+    // step) would repeat forever: such a right-hand side stops here, and so
+    // does any that has run more cycles than it has iterations to spend
+    const int stalled = o.stalled || (o.cycles > 0 && it == o.last_it) ||
+                        o.cycles > ctl.max_iters;
+    const int rr = !conv && !nan && !to && !stalled && it < ctl.max_iters;
+    run[r] = rr;
+    o.conv = conv;
+    o.nan = nan;
+    o.timeout = to && !conv;
+    o.rel = rel;
+    o.stalled = stalled && !conv;
+    o.cycles += rr;
+    if (rr) o.last_it = it;
+    out[r] = o;
+    if (ctl.hist != nullptr && it < ctl.hcap) ctl.hist[(long)r * ctl.hcap + it] = rel;
+    nrun += rr;
+    if (rr) left = max(left, ctl.max_iters - it);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    nrun += __shfl_down_sync(0xffffffffu, nrun, o);
+    left = max(left, __shfl_down_sync(0xffffffffu, left, o));
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    s_n[wid] = nrun;
+    s_l[wid] = left;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int n = 0, l = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      n += s_n[w];
+      l = max(l, s_l[w]);
+    }
+    const int steps = min(m, l);
+    *ctl.steps = steps;
+    *ctl.jstep = 0;
+    *ctl.nrun = n;
+    if (ctl.graph) {
+      cudaGraphSetConditional(ctl.h_cycle, n > 0 ? 1u : 0u);
+      cudaGraphSetConditional(ctl.h_run, n > 0 ? 1u : 0u);
+      cudaGraphSetConditional(ctl.h_step, (n > 0 && steps > 0) ? 1u : 0u);
+      *ctl.nlaunch += ctl.k_head + (n > 0 ? ctl.k_run : 0);
+    }
+  }
+}
+
+// Start of the solve: the global timer's reading for the time limit.
+__global__ void k_solve_begin(unsigned long long* __restrict__ t0) {
+  pdl_entry();
+  *t0 = now_ns();
 }
 
 // Back substitution R y = g with the rotated (upper triangular) H.
@@ -720,7 +906,7 @@ __global__ void __launch_bounds__(kNT)
     k_start_cycle(const double2* __restrict__ R, cx<T>* __restrict__ V0, long nu,
                   double* __restrict__ scal, double2* __restrict__ g, int m,
                   const int* __restrict__ run, int* __restrict__ active, int* __restrict__ jlen,
-                  double tol, double inner_tol) {
+                  double tol, double inner_tol, cx<T>* __restrict__ Zc) {
   pdl_entry();
   const int r = blockIdx.y;
   const double beta = scal[(long)r * 16 + 6];
@@ -737,7 +923,9 @@ __global__ void __launch_bounds__(kNT)
   chunk_of(nu, gridDim.x, k0, k1);
   for (long k = k0 + threadIdx.x; k < k1; k += kNT) {
     const double2 v = R[r * nu + k];
-    V0[r * nu + k] = mk<T>((T)(v.x * inv), (T)(v.y * inv));
+    const cx<T> w = mk<T>((T)(v.x * inv), (T)(v.y * inv));
+    V0[r * nu + k] = w;
+    if (Zc != nullptr) Zc[r * nu + k] = w;
   }
 }
 
@@ -999,204 +1187,290 @@ __global__ void __launch_bounds__(kNT)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Host side.  One restart cycle is: the FP64 residual and the decision
+// (cycle_head), the cycle's start, its Arnoldi (or BiCG-Stab) steps, and its
+// end (x update).  The same launch sequences serve the host-driven loop
+// (step index as an argument, the host polls the device's decisions) and
+// the graph-driven one, where the whole solve is captured once into a CUDA
+// graph: WHILE(cycle) { head; IF(run) { start; WHILE(step) { step }; end } },
+// with the conditions set by the device (k_cycle_decide, k_givens,
+// k_count_active), so one graph launch runs the solve to the end.
+
 template <typename T>
-dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
-                        const dda_solve_opts_t& o, dda_rhs_stats_t* stats, cudaStream_t s) {
-  const long nu = 3 * p->nvox;
-  const int m = o.restart;
-  // one wave of 3 blocks per SM over the whole batch
-  const int nblk = std::max(1, std::min(p->w.nblk, (456 + nrhs - 1) / nrhs));
-  const int pst = m + 2;
-  SolverState& st = p->w.st;
-  cx<T>* V = static_cast<cx<T>*>(p->w.V);
-  cx<T>* W = static_cast<cx<T>*>(p->w.Wv);
-  cx<T>* Z = static_cast<cx<T>*>(p->w.Zv);
-  double2* R = static_cast<double2*>(p->w.R128);
-  const long vstride = (long)nrhs * nu;
-  const dim3 vgrid(nblk, nrhs);
-  const dim3 dgrid(p->w.nblk, nrhs);  // warp-per-vector dots: the plan's full block count
-  const bool prec = o.precond != 0;
-  auto apply_prec = [&](const cx<T>* in, cx<T>* out) {
+struct Ctx {
+  dda_plan_s* p;
+  int nrhs;
+  const double2* b;
+  double2* x;
+  dda_solve_opts_t o;
+  long nu;
+  int m;
+  int nblk, pst;
+  SolverState* st;
+  cx<T>* V;
+  cx<T>* W;
+  cx<T>* Z;
+  double2* R;
+  long vstride;
+  dim3 vgrid, dgrid;
+  bool prec, vec;
+  double brk, eta2;
+
+  Ctx(dda_plan_s* p_, int nrhs_, const double2* b_, double2* x_, const dda_solve_opts_t& o_)
+      : p(p_), nrhs(nrhs_), b(b_), x(x_), o(o_) {
+    nu = 3 * p->nvox;
+    m = o.restart;
+    // one wave of 3 blocks per SM over the whole batch
+    nblk = std::max(1, std::min(p->w.nblk, (456 + nrhs - 1) / nrhs));
+    pst = m + 2;
+    st = &p->w.st;
+    V = static_cast<cx<T>*>(p->w.V);
+    W = static_cast<cx<T>*>(p->w.Wv);
+    Z = static_cast<cx<T>*>(p->w.Zv);
+    R = static_cast<double2*>(p->w.R128);
+    vstride = (long)nrhs * nu;
+    vgrid = dim3(nblk, nrhs);
+    dgrid = dim3(p->w.nblk, nrhs);  // warp-per-vector dots: the plan's full block count
+    prec = o.precond != 0;
+    vec = (nu % 2) == 0;  // 16-byte pairs stay aligned
+    brk = sizeof(T) == 8 ? 1e-13 : 1e-6;
+    eta2 = o.reorth_eta * o.reorth_eta;
+  }
+
+  void apply_prec(const cx<T>* in, cx<T>* out, cudaStream_t s) const {
     if (o.precond == 2)
       precond2_apply<T>(p, nrhs, in, out, s);
     else
       precond_apply_impl<T>(p, nrhs, in, out, s);
-  };
-  const double brk = sizeof(T) == 8 ? 1e-13 : 1e-6;
-  const bool vec = (nu % 2) == 0;  // 16-byte pairs stay aligned
-  const double eta2 = o.reorth_eta * o.reorth_eta;
+  }
 
-  if (!p->pinned) {
-    if (cudaHostAlloc(&p->pinned, 64, cudaHostAllocDefault) != cudaSuccess) {
-      p->pinned = nullptr;
-      return check_cuda("dda_solve: pinned host word");
+  LoopCtl ctl_base() const {
+    LoopCtl c{};
+    c.jstep = st->ctl;
+    c.steps = st->ctl + 1;
+    c.nrun = st->ctl + 2;
+    c.nlaunch = st->nlaunch;
+    c.t0 = st->t0;
+    c.timeout_ns = o.timeout_ns;
+    c.hist = st->hist;
+    c.hcap = kHistCap;
+    c.max_iters = o.max_iters;
+    return c;
+  }
+
+  // The FP64 residual r = b - A x and the cycle decision.
+  void cycle_head(const LoopCtl& c, cudaStream_t s) const {
+    matvec_impl<double>(p, nrhs, reinterpret_cast<const cx<double>*>(x),
+                        reinterpret_cast<cx<double>*>(R), s);
+    note_launch();
+    k_residual<<<vgrid, kNT, 0, s>>>(b, R, nu, st->partial);
+    note_launch();
+    k_finish_norms<<<(nrhs + 127) / 128, 128, 0, s>>>(st->partial, nblk, nrhs, st->scal);
+    note_launch();
+    k_cycle_decide<<<1, 256, 0, s>>>(st->scal, st->iters, st->flags, st->run,
+                                     reinterpret_cast<RhsOut*>(st->out), nrhs, o.tol, m, c);
+  }
+
+  // GMRES -------------------------------------------------------------------
+  void gmres_start(cx<T>* Zc, cudaStream_t s) const {
+    cudaMemsetAsync(st->counters + 8, 0, sizeof(int), s);  // Givens kernel's ticket
+    note_launch();
+    k_start_cycle<T><<<vgrid, kNT, 0, s>>>(R, V, nu, st->scal, st->g, m, st->run, st->active,
+                                           st->jlen, o.tol, o.inner_tol, Zc);
+  }
+
+  // Arnoldi step j (host-driven) or the device's step (graph: jdev != null,
+  // the step's vector in Z, the preconditioner applied in place).
+  void gmres_step(int j, bool scale_next, const LoopCtl& c, cudaStream_t s) const {
+    const bool dev = c.graph != 0;
+    const int* jdev = dev ? c.jstep : nullptr;
+    const cx<T>* src = dev ? Z : V + (long)j * vstride;
+    if (prec) {
+      apply_prec(src, Z, s);
+      src = Z;
+    }
+    matvec_impl<T>(p, nrhs, src, W, s);
+    for (int pass = 0; pass < 2; ++pass) {
+      const int* mask2 = pass == 0 ? nullptr : st->reorth;
+      // kernel timing brackets the first pass (the second runs only for
+      // some right-hand sides, so its work is not known on the host)
+      const double vb = (double)nrhs * nu * sizeof(cx<T>);
+      if (pass == 0) p->prof.begin(PROF_AR_DOT, s, (j + 2) * vb);
+      note_launch();
+      if (vec)
+        launch_k(k_dots_w<T>, dgrid, kDotNT, 0, s, V, W, nu, vstride, j + 1, st->partial, pst,
+                 st->active, mask2, pass == 0, st->tickets, st->hcol, st->H, m, j, pass, st->scal,
+                 jdev);
+      else
+        launch_k(k_multidot<T, false>, vgrid, kNT, 0, s, V, W, nu, vstride, j + 1, st->partial,
+                 pst, st->active, mask2, pass == 0, st->tickets, st->hcol, st->H, m, j, pass,
+                 st->scal, jdev);
+      if (pass == 0) p->prof.end(s);
+      if (pass == 0) p->prof.begin(PROF_AR_UPD, s, (j + 3) * vb);
+      note_launch();
+      if (vec)
+        launch_k(k_update<T, true>, vgrid, kNT, 0, s, V, W, nu, vstride, j + 1, st->hcol, m,
+                 st->partial, pst, st->active, mask2, st->tickets + nrhs, st->scal, pass,
+                 st->reorth, st->reorth_count, eta2, jdev);
+      else
+        launch_k(k_update<T, false>, vgrid, kNT, 0, s, V, W, nu, vstride, j + 1, st->hcol, m,
+                 st->partial, pst, st->active, mask2, st->tickets + nrhs, st->scal, pass,
+                 st->reorth, st->reorth_count, eta2, jdev);
+      if (pass == 0) p->prof.end(s);
+    }
+    note_launch();
+    // the Givens kernel also counts the right-hand sides still iterating
+    const int jsm = dev ? m : j;
+    launch_k(k_givens, nrhs, 32, (size_t)(jsm + 2) * 16 + (size_t)jsm * 24, s, st->H, st->cs,
+             st->sn, st->g, st->scal, st->active, st->jlen, st->flags, st->iters, nrhs, m, j, brk,
+             st->counters + (j & 1), st->counters + 8, c);
+    if (dev || scale_next) {
+      note_launch();
+      launch_k(k_scale<T>, vgrid, kNT, 0, s, W, V + (long)(j + 1) * vstride, nu, st->scal,
+               st->active, V, vstride, jdev, dev ? Z : nullptr);
     }
   }
-  cudaEvent_t ev[2];
-  cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
-  cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
 
+  // x += P^{-1} V y
+  void gmres_end(cudaStream_t s) const {
+    note_launch();
+    k_trisolve<<<(nrhs + 63) / 64, 64, 0, s>>>(st->H, st->g, st->jlen, st->y, nrhs, m);
+    note_launch();
+    k_combine<T><<<vgrid, kNT, 0, s>>>(V, st->y, st->jlen, W, nu, vstride, m);
+    const cx<T>* upd = W;
+    if (prec) {
+      apply_prec(W, Z, s);
+      upd = Z;
+    }
+    note_launch();
+    k_add_x<T><<<vgrid, kNT, 0, s>>>(x, upd, st->jlen, nu);
+  }
+
+  // BiCG-Stab ---------------------------------------------------------------
+  cx<T>* bv(int i) const { return V + (long)i * vstride; }
+  cx<T>* b_ph() const { return prec ? bv(6) : bv(2); }
+  cx<T>* b_sh() const { return prec ? bv(7) : bv(4); }
+
+  void bicg_start(cudaStream_t s) const {
+    note_launch();
+    k_bstart<T><<<vgrid, kNT, 0, s>>>(R, bv(0), bv(1), bv(2), bv(3), Z, nu, st->scal, st->bscal,
+                                      st->run, st->active, o.tol, o.inner_tol);
+  }
+
+  void bicg_step(int it, const LoopCtl& c, cudaStream_t s) const {
+    cx<T>* Vr = bv(0);
+    cx<T>* Vrh = bv(1);
+    cx<T>* Vp = bv(2);
+    cx<T>* Vv = bv(3);
+    cx<T>* Vs = bv(4);
+    cx<T>* Vt = bv(5);
+    cx<T>* Vph = b_ph();
+    cx<T>* Vsh = b_sh();
+    cx<T>* D = Z;
+    double* bs = st->bscal;
+    int* tk2 = st->tickets + nrhs;
+    const unsigned sg = (nrhs + 63) / 64;
+    note_launch();
+    launch_k(k_bdots<T, 1>, vgrid, kNT, 0, s, Vrh, Vr, nullptr, nullptr, nu, st->active,
+             st->partial, st->tickets, bs, 6);
+    note_launch();
+    launch_k(k_bscalar, sg, 64, 0, s, 0, bs, st->active, st->flags, nrhs);
+    note_launch();
+    launch_k(k_baxpy<T>, vgrid, kNT, 0, s, 0, Vp, nullptr, Vr, Vv, nullptr, nullptr, nu, bs, bs,
+             st->active, st->iters, st->partial, tk2);
+    if (prec) apply_prec(Vp, Vph, s);
+    matvec_impl<T>(p, nrhs, Vph, Vv, s);
+    note_launch();
+    launch_k(k_bdots<T, 1>, vgrid, kNT, 0, s, Vrh, Vv, nullptr, nullptr, nu, st->active,
+             st->partial, st->tickets, bs, 6);
+    note_launch();
+    launch_k(k_bscalar, sg, 64, 0, s, 1, bs, st->active, st->flags, nrhs);
+    note_launch();
+    launch_k(k_baxpy<T>, vgrid, kNT, 0, s, 1, nullptr, Vs, Vr, Vv, nullptr, nullptr, nu, bs, bs,
+             st->active, st->iters, st->partial, tk2);
+    note_launch();
+    launch_k(k_baxpy<T>, vgrid, kNT, 0, s, 2, nullptr, nullptr, Vph, nullptr, nullptr, D, nu, bs,
+             bs, st->active, st->iters, st->partial, tk2);
+    note_launch();
+    launch_k(k_bscalar, sg, 64, 0, s, 3, bs, st->active, st->flags, nrhs);
+    if (prec) apply_prec(Vs, Vsh, s);
+    matvec_impl<T>(p, nrhs, Vsh, Vt, s);
+    note_launch();
+    launch_k(k_bdots<T, 2>, vgrid, kNT, 0, s, Vt, Vs, Vt, Vt, nu, st->active, st->partial,
+             st->tickets, bs, 6);
+    note_launch();
+    launch_k(k_bscalar, sg, 64, 0, s, 2, bs, st->active, st->flags, nrhs);
+    note_launch();
+    launch_k(k_baxpy<T>, vgrid, kNT, 0, s, 3, Vr, Vs, Vph, Vsh, Vt, D, nu, bs, bs, st->active,
+             st->iters, st->partial, tk2);
+    note_launch();
+    launch_k(k_count_active, 1, 32, 0, s, st->active, nrhs, st->counters + (it & 1), st->flags,
+             st->iters, st->bscal, st->scal, c);
+  }
+
+  void bicg_end(cudaStream_t s) const {
+    note_launch();
+    k_badd_x<T><<<vgrid, kNT, 0, s>>>(x, Z, st->run, nu);
+  }
+
+  void start(cudaStream_t s, bool graph) const {
+    if (o.method == 1)
+      bicg_start(s);
+    else
+      gmres_start(graph ? Z : nullptr, s);
+  }
+  void end(cudaStream_t s) const {
+    if (o.method == 1)
+      bicg_end(s);
+    else
+      gmres_end(s);
+  }
+};
+
+// State reset at the start of every solve (both drivers).
+template <typename T>
+void solve_prologue(const Ctx<T>& c, cudaStream_t s) {
+  SolverState& st = *c.st;
+  const int nrhs = c.nrhs;
   cudaMemsetAsync(st.iters, 0, sizeof(int) * nrhs, s);
   cudaMemsetAsync(st.reorth_count, 0, sizeof(int) * nrhs, s);
   cudaMemsetAsync(st.tickets, 0, sizeof(int) * 2 * nrhs, s);
   cudaMemsetAsync(st.flags, 0, sizeof(int) * nrhs, s);
-  cudaMemsetAsync(p->w.err_flag, 0, 4, s);
-  std::vector<double> hs((size_t)nrhs * 16);
-  std::vector<int> hits(nrhs), hflags(nrhs), hreo(nrhs), run(nrhs, 0), conv(nrhs, 0), nan(nrhs, 0);
-  std::vector<double> rel(nrhs, 0.0);
-  std::vector<int> ncyc(nrhs, 0);
+  cudaMemsetAsync(st.out, 0, sizeof(RhsOut) * nrhs, s);
+  cudaMemsetAsync(st.nlaunch, 0, sizeof(long long), s);
+  cudaMemsetAsync(c.p->w.err_flag, 0, 4, s);
+  note_launch();
+  k_solve_begin<<<1, 1, 0, s>>>(st.t0);
+}
 
+// Host-driven loop: the host reads each cycle's decision and polls the
+// step count (at most two Arnoldi steps queued ahead of the GPU).  Used
+// when kernel timing is on (events bracket launches) and as the fallback.
+template <typename T>
+dda_status_t drive_host(const Ctx<T>& c, cudaStream_t s) {
+  dda_plan_s* p = c.p;
+  SolverState& st = *c.st;
+  LoopCtl ctl = c.ctl_base();
+  cudaEvent_t ev[2];
+  cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
   dda_status_t status = DDA_OK;
-  for (int cycle = 0;; ++cycle) {
-    // r = b - A x in complex128
-    matvec_impl<double>(p, nrhs, reinterpret_cast<const cx<double>*>(x),
-                        reinterpret_cast<cx<double>*>(R), s);
-    note_launch();
-    k_residual<<<vgrid, kNT, 0, s>>>(b, R, nu, st.partial);
-    note_launch();
-    k_finish_norms<<<(nrhs + 127) / 128, 128, 0, s>>>(st.partial, nblk, nrhs, st.scal);
-    cudaMemcpyAsync(hs.data(), st.scal, sizeof(double) * 16 * nrhs, cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(hits.data(), st.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(hflags.data(), st.flags, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s);
-    cudaMemcpyAsync(hreo.data(), st.reorth_count, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s);
+  for (;;) {
+    c.cycle_head(ctl, s);
+    cudaMemcpyAsync(p->pinned + 2, st.ctl + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) {
       status = check_cuda("dda_solve");
       break;
     }
-    int nrun = 0;
-    for (int r = 0; r < nrhs; ++r) {
-      const double bn = hs[r * 16 + 2], rn = hs[r * 16 + 6];
-      rel[r] = bn > 0 ? rn / bn : rn;
-      nan[r] = !std::isfinite(rn) || (hflags[r] & 1);
-      conv[r] = std::isfinite(rn) && (rn <= o.tol * bn || bn == 0.0);
-      run[r] = !conv[r] && !nan[r] && hits[r] < o.max_iters;
-      nrun += run[r];
-    }
+    const int steps = p->pinned[2], nrun = p->pinned[3];
     if (nrun == 0) break;
-    for (int r = 0; r < nrhs; ++r) ncyc[r] += run[r];
-    cudaMemcpyAsync(st.run, run.data(), sizeof(int) * nrhs, cudaMemcpyHostToDevice, s);
-    int maxit_left = 0;
-    for (int r = 0; r < nrhs; ++r)
-      if (run[r]) maxit_left = std::max(maxit_left, o.max_iters - hits[r]);
-    const int steps = std::min(m, maxit_left);
-    if (o.method == 1) {
-      // BiCG-Stab cycle in the inner precision on the FP64 residual R
-      cx<T>* Vr = V;
-      cx<T>* Vrh = V + vstride;
-      cx<T>* Vp = V + 2 * vstride;
-      cx<T>* Vv = V + 3 * vstride;
-      cx<T>* Vs = V + 4 * vstride;
-      cx<T>* Vt = V + 5 * vstride;
-      cx<T>* Vph = prec ? V + 6 * vstride : Vp;
-      cx<T>* Vsh = prec ? V + 7 * vstride : Vs;
-      cx<T>* D = Z;
-      double* bs = st.bscal;
-      int* tk2 = st.tickets + nrhs;
-      const unsigned sg = (nrhs + 63) / 64;
-      note_launch();
-      k_bstart<T><<<vgrid, kNT, 0, s>>>(R, Vr, Vrh, Vp, Vv, D, nu, st.scal, bs, st.run, st.active,
-                                        o.tol, o.inner_tol);
-      for (int it = 0; it < steps; ++it) {
-        note_launch();
-        launch_k(k_bdots<T, 1>, vgrid, kNT, 0, s, Vrh, Vr, nullptr, nullptr, nu, st.active, st.partial,
-                                            st.tickets, bs, 6);
-        note_launch();
-        launch_k(k_bscalar, sg, 64, 0, s, 0, bs, st.active, st.flags, nrhs);
-        note_launch();
-        launch_k(k_baxpy<T>, vgrid, kNT, 0, s, 0, Vp, nullptr, Vr, Vv, nullptr, nullptr, nu, bs, bs,
-                                         st.active, st.iters, st.partial, tk2);
-        if (prec) apply_prec(Vp, Vph);
-        matvec_impl<T>(p, nrhs, Vph, Vv, s);
-        note_launch();
-        launch_k(k_bdots<T, 1>, vgrid, kNT, 0, s, Vrh, Vv, nullptr, nullptr, nu, st.active, st.partial,
-                                            st.tickets, bs, 6);
-        note_launch();
-        launch_k(k_bscalar, sg, 64, 0, s, 1, bs, st.active, st.flags, nrhs);
-        note_launch();
-        launch_k(k_baxpy<T>, vgrid, kNT, 0, s, 1, nullptr, Vs, Vr, Vv, nullptr, nullptr, nu, bs, bs,
-                                         st.active, st.iters, st.partial, tk2);
-        note_launch();
-        launch_k(k_baxpy<T>, vgrid, kNT, 0, s, 2, nullptr, nullptr, Vph, nullptr, nullptr, D, nu, bs, bs,
-                                         st.active, st.iters, st.partial, tk2);
-        note_launch();
-        launch_k(k_bscalar, sg, 64, 0, s, 3, bs, st.active, st.flags, nrhs);
-        if (prec) apply_prec(Vs, Vsh);
-        matvec_impl<T>(p, nrhs, Vsh, Vt, s);
-        note_launch();
-        launch_k(k_bdots<T, 2>, vgrid, kNT, 0, s, Vt, Vs, Vt, Vt, nu, st.active, st.partial, st.tickets,
-                                            bs, 6);
-        note_launch();
-        launch_k(k_bscalar, sg, 64, 0, s, 2, bs, st.active, st.flags, nrhs);
-        note_launch();
-        launch_k(k_baxpy<T>, vgrid, kNT, 0, s, 3, Vr, Vs, Vph, Vsh, Vt, D, nu, bs, bs, st.active,
-                                         st.iters, st.partial, tk2);
-        note_launch();
-        launch_k(k_count_active, 1, 32, 0, s, st.active, nrhs, st.counters + (it & 1));
-        cudaMemcpyAsync(p->pinned + (it & 1), st.counters + (it & 1), sizeof(int),
-                        cudaMemcpyDeviceToHost, s);
-        cudaEventRecord(ev[it & 1], s);
-        if (it >= 1) {
-          cudaEventSynchronize(ev[(it - 1) & 1]);
-          if (p->pinned[(it - 1) & 1] == 0) break;
-        }
-      }
-      note_launch();
-      k_badd_x<T><<<vgrid, kNT, 0, s>>>(x, D, st.run, nu);
-      if ((status = check_cuda("dda_solve")) != DDA_OK) break;
-      continue;
-    }
-    cudaMemsetAsync(st.counters + 8, 0, sizeof(int), s);  // Givens kernel's ticket
-    note_launch();
-    k_start_cycle<T><<<vgrid, kNT, 0, s>>>(R, V, nu, st.scal, st.g, m, st.run, st.active,
-                                           st.jlen, o.tol, o.inner_tol);
-    // Arnoldi steps
+    c.start(s, false);
     for (int j = 0; j < steps; ++j) {
-      const cx<T>* vj = V + (long)j * vstride;
-      const cx<T>* src = vj;
-      if (prec) {
-        apply_prec(vj, Z);
-        src = Z;
-      }
-      matvec_impl<T>(p, nrhs, src, W, s);
-      for (int pass = 0; pass < 2; ++pass) {
-        const int* mask2 = pass == 0 ? nullptr : st.reorth;
-        // kernel timing brackets the first pass (the second runs only for
-        // some right-hand sides, so its work is not known on the host)
-        const double vb = (double)nrhs * nu * sizeof(cx<T>);
-        if (pass == 0) p->prof.begin(PROF_AR_DOT, s, (j + 2) * vb);
-        note_launch();
-        if (vec)
-          launch_k(k_dots_w<T>, dgrid, kDotNT, 0, s, V, W, nu, vstride, j + 1, st.partial, pst,
-                                               st.active, mask2, pass == 0, st.tickets, st.hcol,
-                                               st.H, m, j, pass, st.scal);
-        else
-          launch_k(k_multidot<T, false>, vgrid, kNT, 0, s, V, W, nu, vstride, j + 1, st.partial, pst,
-                                                     st.active, mask2, pass == 0, st.tickets,
-                                                     st.hcol, st.H, m, j, pass, st.scal);
-        if (pass == 0) p->prof.end(s);
-        if (pass == 0) p->prof.begin(PROF_AR_UPD, s, (j + 3) * vb);
-        note_launch();
-        if (vec)
-          launch_k(k_update<T, true>, vgrid, kNT, 0, s, V, W, nu, vstride, j + 1, st.hcol, m, st.partial,
-                                                  pst, st.active, mask2, st.tickets + nrhs,
-                                                  st.scal, pass, st.reorth, st.reorth_count, eta2);
-        else
-          launch_k(k_update<T, false>, vgrid, kNT, 0, s, V, W, nu, vstride, j + 1, st.hcol, m,
-                                                   st.partial, pst, st.active, mask2,
-                                                   st.tickets + nrhs, st.scal, pass, st.reorth,
-                                                   st.reorth_count, eta2);
-        if (pass == 0) p->prof.end(s);
-      }
-      note_launch();
-      // the Givens kernel also counts the right-hand sides still iterating
-      launch_k(k_givens, nrhs, 32, (size_t)(j + 2) * 16 + (size_t)j * 24, s, st.H, st.cs, st.sn,
-               st.g, st.scal, st.active, st.jlen, st.flags, st.iters, nrhs, m, j, brk,
-               st.counters + (j & 1), st.counters + 8);
-      if (j + 1 < steps) {
-        note_launch();
-        launch_k(k_scale<T>, vgrid, kNT, 0, s, W, V + (long)(j + 1) * vstride, nu, st.scal,
-                 st.active);
-      }
+      if (c.o.method == 1)
+        c.bicg_step(j, ctl, s);
+      else
+        c.gmres_step(j, j + 1 < steps, ctl, s);
       cudaMemcpyAsync(p->pinned + (j & 1), st.counters + (j & 1), sizeof(int),
                       cudaMemcpyDeviceToHost, s);
       cudaEventRecord(ev[j & 1], s);
@@ -1205,59 +1479,368 @@ dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
         if (p->pinned[(j - 1) & 1] == 0) break;
       }
     }
-    // x += P^{-1} V y
-    note_launch();
-    k_trisolve<<<(nrhs + 63) / 64, 64, 0, s>>>(st.H, st.g, st.jlen, st.y, nrhs, m);
-    note_launch();
-    k_combine<T><<<vgrid, kNT, 0, s>>>(V, st.y, st.jlen, W, nu, vstride, m);
-    const cx<T>* upd = W;
-    if (prec) {
-      apply_prec(W, Z);
-      upd = Z;
-    }
-    note_launch();
-    k_add_x<T><<<vgrid, kNT, 0, s>>>(x, upd, st.jlen, nu);
+    c.end(s);
     if ((status = check_cuda("dda_solve")) != DDA_OK) break;
   }
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
-  if (status != DDA_OK) return status;
+  return status;
+}
+
+// What a captured solve graph depends on: a new graph is captured when any
+// of it changes (pointers and scalars are baked into the kernel nodes).
+struct GraphKey {
+  const void* plan;
+  long long plan_id;
+  int nrhs, tsize, method, precond, restart, max_iters, rr_z, pdl;
+  const void* b;
+  void* x;
+  double tol, inner_tol, eta;
+  long long timeout_ns;
+};
+
+template <typename T>
+GraphKey graph_key(const Ctx<T>& c) {
+  GraphKey key{};
+  key.plan = c.p;
+  key.plan_id = c.p->id;
+  key.nrhs = c.nrhs;
+  key.tsize = sizeof(T);
+  key.method = c.o.method;
+  key.precond = c.o.precond;
+  key.restart = c.o.restart;
+  key.max_iters = c.o.max_iters;
+  key.rr_z = tl_schedule.rr_z;
+  key.pdl = pdl_enabled();
+  key.b = c.b;
+  key.x = c.x;
+  key.tol = c.o.tol;
+  key.inner_tol = c.o.inner_tol;
+  key.eta = c.o.reorth_eta;
+  key.timeout_ns = c.o.timeout_ns;
+  return key;
+}
+
+// A conditional node on the capturing stream, after everything captured so
+// far; returns its body graph, to be captured separately.
+cudaGraph_t add_conditional(cudaStream_t cs, cudaGraphConditionalHandle h,
+                            cudaGraphConditionalNodeType type, bool& ok) {
+  if (!ok) return nullptr;
+  cudaStreamCaptureStatus stt;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* edata = nullptr;
+  size_t nd = 0;
+  if (cudaStreamGetCaptureInfo(cs, &stt, nullptr, &cg, &deps, &edata, &nd) != cudaSuccess ||
+      stt != cudaStreamCaptureStatusActive) {
+    ok = false;
+    return nullptr;
+  }
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = type;
+  np.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (cudaGraphAddNode(&node, cg, deps, nullptr, nd, &np) != cudaSuccess ||
+      cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1,
+                                          cudaStreamSetCaptureDependencies) != cudaSuccess) {
+    ok = false;
+    return nullptr;
+  }
+  return np.conditional.phGraph_out[0];
+}
+
+// Run fn() captured on cs into graph g (appended after g's roots: a new
+// independent chain); ok turns false on any capture error.
+template <typename F>
+void capture(cudaStream_t cs, cudaGraph_t g, bool& ok, F&& fn) {
+  if (!ok || g == nullptr) {
+    ok = false;
+    return;
+  }
+  if (cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+      cudaSuccess) {
+    ok = false;
+    return;
+  }
+  fn();
+  cudaGraph_t out = nullptr;
+  if (cudaStreamEndCapture(cs, &out) != cudaSuccess) ok = false;
+}
+
+// Capture one plan's whole solve into `top` as an independent chain:
+// prologue (state reset, start time), then
+// WHILE(cycle) { head; IF(run) { start; WHILE(step) { step }; end } }.
+// The kernel counts per part go into the kernel arguments (the device
+// counts what the graph runs), so a throwaway capture counts them first.
+// Launches made while capturing are not counted as launches.
+template <typename T>
+bool capture_into(const Ctx<T>& c, cudaGraph_t top, cudaStream_t cs) {
+  ScheduleScope scope(c.p->sched);
+  const long long before = launch_counter();
+  bool ok = true;
+  cudaGraphConditionalHandle hc = 0, hr = 0, hs = 0;
+  ok = cudaGraphConditionalHandleCreate(&hc, top, 1, cudaGraphCondAssignDefault) == cudaSuccess &&
+       cudaGraphConditionalHandleCreate(&hr, top, 0, 0) == cudaSuccess &&
+       cudaGraphConditionalHandleCreate(&hs, top, 0, 0) == cudaSuccess;
+  LoopCtl ctl = c.ctl_base();
+  ctl.graph = 1;
+  ctl.h_cycle = hc;
+  ctl.h_run = hr;
+  ctl.h_step = hs;
+  {
+    cudaGraph_t dry = nullptr;
+    ok = ok && cudaGraphCreate(&dry, 0) == cudaSuccess;
+    long long t = launch_counter();
+    capture(cs, dry, ok, [&] { c.cycle_head(ctl, cs); });
+    ctl.k_head = (int)(launch_counter() - t);
+    t = launch_counter();
+    capture(cs, dry, ok, [&] {
+      c.start(cs, true);
+      c.end(cs);
+    });
+    ctl.k_run = (int)(launch_counter() - t);
+    t = launch_counter();
+    capture(cs, dry, ok, [&] {
+      if (c.o.method == 1)
+        c.bicg_step(0, ctl, cs);
+      else
+        c.gmres_step(0, true, ctl, cs);
+    });
+    ctl.k_step = (int)(launch_counter() - t);
+    if (dry) cudaGraphDestroy(dry);
+  }
+  cudaGraph_t body_cycle = nullptr, body_run = nullptr, body_step = nullptr;
+  capture(cs, top, ok, [&] {
+    solve_prologue(c, cs);
+    body_cycle = add_conditional(cs, hc, cudaGraphCondTypeWhile, ok);
+  });
+  capture(cs, body_cycle, ok, [&] {
+    c.cycle_head(ctl, cs);
+    body_run = add_conditional(cs, hr, cudaGraphCondTypeIf, ok);
+  });
+  capture(cs, body_run, ok, [&] {
+    c.start(cs, true);
+    body_step = add_conditional(cs, hs, cudaGraphCondTypeWhile, ok);
+    c.end(cs);
+  });
+  capture(cs, body_step, ok, [&] {
+    if (c.o.method == 1)
+      c.bicg_step(0, ctl, cs);
+    else
+      c.gmres_step(0, true, ctl, cs);
+  });
+  add_launches(before - launch_counter());  // captured, not run
+  if (!ok) cudaGetLastError();
+  return ok;
+}
+
+// Make (or reuse) the graph of `keys` in G: one chain per context.
+template <typename T>
+bool ensure_graph(SolveGraph& G, const std::vector<const Ctx<T>*>& ctxs) {
+  std::vector<GraphKey> keys;
+  for (const Ctx<T>* c : ctxs) {
+    ScheduleScope scope(c->p->sched);
+    keys.push_back(graph_key(*c));
+  }
+  const size_t nb = keys.size() * sizeof(GraphKey);
+  if (G.exec && G.key.size() == nb && std::memcmp(G.key.data(), keys.data(), nb) == 0) return true;
+  G.reset();
+  if (!G.cs && cudaStreamCreateWithFlags(&G.cs, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    G.cs = nullptr;
+    return false;
+  }
+  bool ok = cudaGraphCreate(&G.graph, 0) == cudaSuccess;
+  for (const Ctx<T>* c : ctxs) {
+    if (!ok) break;
+    ok = capture_into(*c, G.graph, G.cs);
+  }
+  ok = ok && cudaGraphInstantiate(&G.exec, G.graph, 0) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    G.reset();
+    return false;
+  }
+  G.key.assign(reinterpret_cast<const char*>(keys.data()),
+               reinterpret_cast<const char*>(keys.data()) + nb);
+  return true;
+}
+
+// Copy a finished solve's outcome to the host (queued on s; the caller
+// synchronises) and turn it into stats and a status.
+struct Collected {
+  std::vector<RhsOut> out;
+  std::vector<int> hits, hreo;
   int perr = 0;
-  cudaMemcpyAsync(&perr, p->w.err_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
-  cudaStreamSynchronize(s);
-  bool any_nan = false, any_nc = false;
-  for (int r = 0; r < nrhs; ++r) {
-    any_nan |= nan[r] != 0;
-    any_nc |= !conv[r];
+  long long nl = 0;
+};
+
+template <typename T>
+void collect_async(const Ctx<T>& c, Collected& r, cudaStream_t s) {
+  const SolverState& st = *c.st;
+  const int nrhs = c.nrhs;
+  r.out.resize(nrhs);
+  r.hits.resize(nrhs);
+  r.hreo.resize(nrhs);
+  cudaMemcpyAsync(r.out.data(), st.out, sizeof(RhsOut) * nrhs, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(r.hits.data(), st.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(r.hreo.data(), st.reorth_count, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&r.perr, c.p->w.err_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(&r.nl, st.nlaunch, sizeof(long long), cudaMemcpyDeviceToHost, s);
+  if (c.o.h_history != nullptr && c.o.history_cap > 0) {
+    const int w = std::min(c.o.history_cap, kHistCap);
+    cudaMemcpy2DAsync(c.o.h_history, sizeof(double) * c.o.history_cap, st.hist,
+                      sizeof(double) * kHistCap, sizeof(double) * w, nrhs, cudaMemcpyDeviceToHost,
+                      s);
+  }
+}
+
+template <typename T>
+dda_status_t finish_stats(const Ctx<T>& c, const Collected& r, bool graph, float ms,
+                          dda_rhs_stats_t* stats) {
+  const dda_solve_opts_t& o = c.o;
+  bool any_nan = false, any_nc = false, any_to = false, any_brk = false;
+  for (int i = 0; i < c.nrhs; ++i) {
+    const RhsOut& q = r.out[i];
+    any_nan |= q.nan != 0;
+    any_to |= !q.conv && !q.nan && q.timeout;
+    any_brk |= !q.conv && !q.nan && !q.timeout && q.stalled;
+    any_nc |= !q.conv;
     if (stats) {
-      stats[r].iters = hits[r];
-      stats[r].cycles = ncyc[r];
-      stats[r].reorth = hreo[r];
-      stats[r].converged = conv[r];
-      stats[r].rel_resid = rel[r];
-      stats[r].status = nan[r] ? DDA_ERR_NAN : (conv[r] ? DDA_OK : DDA_ERR_NOT_CONVERGED);
+      stats[i].iters = r.hits[i];
+      stats[i].cycles = q.cycles;
+      stats[i].reorth = r.hreo[i];
+      stats[i].converged = q.conv;
+      stats[i].rel_resid = q.rel;
+      stats[i].status = q.nan ? DDA_ERR_NAN
+                        : q.conv ? DDA_OK
+                        : q.timeout ? DDA_ERR_TIMEOUT
+                        : q.stalled ? DDA_ERR_BREAKDOWN
+                                    : DDA_ERR_NOT_CONVERGED;
+      stats[i].history_len =
+          (o.h_history != nullptr && o.history_cap > 0)
+              ? std::min(r.hits[i] + 1, std::min(o.history_cap, kHistCap))
+              : 0;
+      stats[i].graph = graph ? 1 : 0;
+      stats[i].ms = ms;
     }
   }
-  if (perr) return fail(DDA_ERR_SINGULAR_PRECOND, "dda_solve: preconditioner symbol is singular");
+  if (r.perr) return fail(DDA_ERR_SINGULAR_PRECOND, "dda_solve: preconditioner symbol is singular");
   if (any_nan) return fail(DDA_ERR_NAN, "dda_solve: non-finite residual");
+  if (any_to) return fail(DDA_ERR_TIMEOUT, "dda_solve: time limit reached");
+  if (any_brk)
+    return fail(DDA_ERR_BREAKDOWN, "dda_solve: a restart cycle made no progress (BiCG-Stab "
+                                   "breakdown at its first step)");
   if (any_nc) return fail(DDA_ERR_NOT_CONVERGED, "dda_solve: tolerance not reached within max_iters");
   return DDA_OK;
 }
 
-}  // namespace
+bool ensure_pinned(dda_plan_s* p) {
+  if (p->pinned) return true;
+  if (cudaHostAlloc(&p->pinned, 64, cudaHostAllocDefault) != cudaSuccess) {
+    p->pinned = nullptr;
+    return false;
+  }
+  return true;
+}
 
-}  // namespace dda
+template <typename T>
+dda_status_t solve_impl(dda_plan_s* p, int nrhs, const double2* b, double2* x,
+                        const dda_solve_opts_t& o, dda_rhs_stats_t* stats, cudaStream_t s) {
+  const auto t_begin = std::chrono::steady_clock::now();
+  Ctx<T> c(p, nrhs, b, x, o);
+  if (!ensure_pinned(p)) return check_cuda("dda_solve: pinned host word");
+  dda_status_t status = DDA_OK;
+  bool graph = tl_schedule.graph && !p->prof.on && solve_graph_enabled() && !p->graph.failed;
+  if (graph && !ensure_graph<T>(p->graph, {&c})) {
+    p->graph.failed = true;  // this plan keeps to the host-driven loop
+    graph = false;
+  }
+  if (graph) {
+    if (cudaGraphLaunch(p->graph.exec, s) != cudaSuccess) status = check_cuda("dda_solve: graph");
+  } else {
+    solve_prologue(c, s);
+    status = drive_host(c, s);
+  }
+  if (status != DDA_OK) return status;
+  Collected r;
+  collect_async(c, r, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return check_cuda("dda_solve");
+  if (graph) add_launches(r.nl + 1);  // the graph's kernels and its prologue kernel
+  const float ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() -
+                                                            t_begin).count();
+  return finish_stats(c, r, graph, ms, stats);
+}
 
-using namespace dda;
+// dda_solve_many as one graph launch: every plan's solve an independent
+// chain of one graph, so the uneven batch runs concurrently on the GPU with
+// no host thread per plan.  Returns false (nothing launched) when a plan
+// cannot take part; the caller then falls back to one thread per plan.
+template <typename T>
+bool solve_many_graph(int nplans, const dda_plan_t* plans, const int32_t* nrhs,
+                      const void* const* d_b, void* const* d_x, const dda_solve_opts_t& o,
+                      dda_rhs_stats_t* const* h_stats, void* const* streams,
+                      dda_status_t* st_out, std::string* why) {
+  const auto t_begin = std::chrono::steady_clock::now();
+  std::vector<std::unique_ptr<Ctx<T>>> ctxs;
+  std::vector<const Ctx<T>*> cptr;
+  for (int i = 0; i < nplans; ++i) {
+    dda_plan_s* p = plans[i];
+    if (!p->sched.graph || p->prof.on || !ensure_pinned(p)) return false;
+    const double2* b = d_b && d_b[i] ? static_cast<const double2*>(d_b[i])
+                                     : static_cast<const double2*>(p->w.B128);
+    ctxs.emplace_back(new Ctx<T>(p, nrhs[i], b, static_cast<double2*>(d_x[i]), o));
+    cptr.push_back(ctxs.back().get());
+  }
+  // the batch graph lives with the first plan
+  SolveGraph& G = plans[0]->batch;
+  if (!ensure_graph<T>(G, cptr)) return false;
+  cudaStream_t s0 = streams ? static_cast<cudaStream_t>(streams[0]) : nullptr;
+  // the launch stream waits for every plan's stream (their b and x), and
+  // every plan's stream waits for the launch
+  std::vector<cudaEvent_t> evs;
+  for (int i = 1; i < nplans && streams; ++i) {
+    if (!streams[i]) continue;
+    cudaEvent_t e;
+    cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    cudaEventRecord(e, static_cast<cudaStream_t>(streams[i]));
+    cudaStreamWaitEvent(s0, e, 0);
+    evs.push_back(e);
+  }
+  dda_status_t status = DDA_OK;
+  if (cudaGraphLaunch(G.exec, s0) != cudaSuccess) status = check_cuda("dda_solve_many: graph");
+  std::vector<Collected> r(nplans);
+  for (int i = 0; i < nplans && status == DDA_OK; ++i) collect_async(*cptr[i], r[i], s0);
+  if (status == DDA_OK && cudaStreamSynchronize(s0) != cudaSuccess)
+    status = check_cuda("dda_solve_many");
+  cudaEvent_t done;
+  cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+  cudaEventRecord(done, s0);
+  for (int i = 1; i < nplans && streams; ++i)
+    if (streams[i]) cudaStreamWaitEvent(static_cast<cudaStream_t>(streams[i]), done, 0);
+  cudaEventDestroy(done);
+  for (cudaEvent_t e : evs) cudaEventDestroy(e);
+  const float ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() -
+                                                            t_begin).count();
+  for (int i = 0; i < nplans; ++i) {
+    if (status != DDA_OK) {
+      st_out[i] = status;
+      continue;
+    }
+    add_launches(r[i].nl + 1);
+    st_out[i] = finish_stats(*cptr[i], r[i], true, ms, h_stats ? h_stats[i] : nullptr);
+    if (st_out[i] != DDA_OK) why[i] = dda_last_error();
+  }
+  return true;
+}
 
-extern "C" dda_status_t dda_solve(dda_plan_t p, int32_t nrhs, const void* d_b, void* d_x,
-                                  const dda_solve_opts_t* opts, dda_rhs_stats_t* h_stats,
-                                  void* stream) {
-  if (!p || !d_x || !opts) return fail(DDA_ERR_INVALID_ARG, "dda_solve: NULL argument");
+// Options and plan checks shared by dda_solve and dda_solve_many.
+dda_status_t check_solve(dda_plan_t p, int32_t nrhs, const dda_solve_opts_t& o) {
   if (p->d.krylov_m < 1) return fail(DDA_ERR_INVALID_ARG, "dda_solve: plan has krylov_m = 0");
   if (nrhs < 1 || nrhs > p->nrhs_inc)
     return fail(DDA_ERR_INVALID_ARG, "dda_solve: nrhs must be 1..(incidences set)");
-  const dda_solve_opts_t& o = *opts;
   if (!(o.tol > 0) || o.max_iters < 1 || o.restart < 1 ||
       (o.method == 0 && o.restart > p->d.krylov_m) ||
       !(o.inner_tol >= 0) || !(o.reorth_eta >= 0) ||
@@ -1274,6 +1857,48 @@ extern "C" dda_status_t dda_solve(dda_plan_t p, int32_t nrhs, const void* d_b, v
     return fail(DDA_ERR_INVALID_ARG, "dda_solve: method must be 0 (GMRES) or 1 (BiCG-Stab)");
   if (o.method == 1 && p->d.krylov_m < 7)
     return fail(DDA_ERR_INVALID_ARG, "dda_solve: BiCG-Stab needs a plan with krylov_m >= 7");
+  if (o.history_cap < 0 || o.timeout_ns < 0 || (o.h_history != nullptr && o.history_cap < 1))
+    return fail(DDA_ERR_INVALID_ARG, "dda_solve: history_cap and timeout_ns must be >= 0");
+  if (o.inner_prec != DDA_C128 && o.inner_prec != DDA_C64)
+    return fail(DDA_ERR_INVALID_ARG, "dda_solve: inner_prec must be DDA_C128 or DDA_C64");
+  if (o.inner_prec == DDA_C64 && !p->has64)
+    return fail(DDA_ERR_INVALID_ARG, "dda_solve: plan holds no complex64 data");
+  return DDA_OK;
+}
+
+}  // namespace
+
+// One graph launch for a batch of plans (dda_solve_many); false: use threads.
+bool solve_many_as_graph(int32_t nplans, const dda_plan_t* plans, const int32_t* nrhs,
+                         const void* const* d_b, void* const* d_x, const dda_solve_opts_t* opts,
+                         dda_rhs_stats_t* const* h_stats, void* const* streams,
+                         dda_status_t* st_out, std::string* why) {
+  if (!solve_graph_enabled()) return false;
+  for (int i = 0; i < nplans; ++i) {
+    if (check_solve(plans[i], nrhs[i], *opts) != DDA_OK) return false;  // dda_solve reports it
+    if (!(d_b && d_b[i])) {
+      cudaStream_t si = streams ? static_cast<cudaStream_t>(streams[i]) : nullptr;
+      if (dda_incident_field(plans[i], nrhs[i], plans[i]->w.B128, si) != DDA_OK) return false;
+    }
+  }
+  if (opts->inner_prec == DDA_C128)
+    return solve_many_graph<double>(nplans, plans, nrhs, d_b, d_x, *opts, h_stats, streams, st_out,
+                                    why);
+  return solve_many_graph<float>(nplans, plans, nrhs, d_b, d_x, *opts, h_stats, streams, st_out,
+                                 why);
+}
+
+}  // namespace dda
+
+using namespace dda;
+
+extern "C" dda_status_t dda_solve(dda_plan_t p, int32_t nrhs, const void* d_b, void* d_x,
+                                  const dda_solve_opts_t* opts, dda_rhs_stats_t* h_stats,
+                                  void* stream) {
+  if (!p || !d_x || !opts) return fail(DDA_ERR_INVALID_ARG, "dda_solve: NULL argument");
+  const dda_solve_opts_t& o = *opts;
+  const dda_status_t chk = check_solve(p, nrhs, o);
+  if (chk != DDA_OK) return chk;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   ScheduleScope scope(p->sched);
   const double2* b = static_cast<const double2*>(d_b);
@@ -1284,9 +1909,5 @@ extern "C" dda_status_t dda_solve(dda_plan_t p, int32_t nrhs, const void* d_b, v
   }
   if (o.inner_prec == DDA_C128)
     return solve_impl<double>(p, nrhs, b, static_cast<double2*>(d_x), o, h_stats, s);
-  if (o.inner_prec == DDA_C64) {
-    if (!p->has64) return fail(DDA_ERR_INVALID_ARG, "dda_solve: plan holds no complex64 data");
-    return solve_impl<float>(p, nrhs, b, static_cast<double2*>(d_x), o, h_stats, s);
-  }
-  return fail(DDA_ERR_INVALID_ARG, "dda_solve: inner_prec must be DDA_C128 or DDA_C64");
+  return solve_impl<float>(p, nrhs, b, static_cast<double2*>(d_x), o, h_stats, s);
 }

@@ -35,6 +35,7 @@ __device__ __forceinline__ void pdl_entry() {
 struct Schedule {
   bool rr_z = true;  // register-resident z pass of the complex64 matvec (lengths 64, 128)
   bool pdl = true;   // programmatic dependent launch
+  bool graph = true; // dda_solve as one CUDA graph launch (device-side loop control)
 };
 
 inline thread_local Schedule tl_schedule;

@@ -74,7 +74,8 @@ __global__ void __launch_bounds__(std::is_same<T, df>::value ? 256 : 512)
     k_mv_epilogue(const cx<T>* __restrict__ buf1, const cx<T>* __restrict__ x,
                   cx<T>* __restrict__ y, const uint8_t* __restrict__ mat,
                   const cx<T>* __restrict__ ainv, int K1, long nlines, long nm, int l, int Lx,
-                  T coef, const cx<T>* __restrict__ tw, int twshift, RadixPlan rp, int nb_sh) {
+                  T coef, const cx<T>* __restrict__ tw, int twshift, RadixPlan rp, int nb_sh,
+                  const cx<T>* __restrict__ pv) {
   pdl_entry();
   const int NB = 1 << nb_sh;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -110,7 +111,8 @@ __global__ void __launch_bounds__(std::is_same<T, df>::value ? 256 : 512)
     long rem = line - rhs * 3 * nm;
     for (int b = b0; b < NB && line < nlines; b += bstep, line += bstep) {
       const int mt = mat[vrow * l + j];
-      const cx<T> a = ainv[rhs * K1 + mt];
+      const cx<T> a = (pv != nullptr && mt != 0) ? pv[(rhs * nm + vrow) * l + j]
+                                                 : ainv[rhs * K1 + mt];
       const cx<T> xv = x[line * l + j];
       cx<T> out = a * xv;
       if (mt != 0) out = out - coef * s[j * ld + b];
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(std::is_same<T, df>::value ? 256 : 512)
         const long vox = (line % nm) * l + j;
         const long rhs = line / (3 * nm);
         const int mt = mat[vox];
-        const cx<T> a = ainv[rhs * K1 + mt];
+        const cx<T> a = (pv != nullptr && mt != 0) ? pv[rhs * nm * l + vox] : ainv[rhs * K1 + mt];
         const cx<T> xv = x[line * l + j];
         cx<T> out = a * xv;
         if (mt != 0) out = out - coef * s[j * ld + b];
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__(NB * LX / kElemsPerThread, 1024 / (NB * LX / k
     k_ct_mv_epilogue(const cx<T>* __restrict__ buf1, const cx<T>* __restrict__ x,
                      cx<T>* __restrict__ y, const uint8_t* __restrict__ mat,
                      const cx<T>* __restrict__ ainv, int K1, long nlines, long nm, T coef,
-                     const cx<T>* __restrict__ tw, int twshift) {
+                     const cx<T>* __restrict__ tw, int twshift, const cx<T>* __restrict__ pv) {
   pdl_entry();
   static_assert(NB >= 16, "one position per thread");
   constexpr int NTH = NB * LX / kElemsPerThread;
@@ -189,7 +191,8 @@ __global__ void __launch_bounds__(NB * LX / kElemsPerThread, 1024 / (NB * LX / k
   for (int b = b0; b < NB; b += OSTEP, line += OSTEP) {
     if (line >= nlines) break;
     const int mt = mat[vrow * l + j];
-    const cx<T> a = ainv[rhs * K1 + mt];
+    const cx<T> a = (pv != nullptr && mt != 0) ? pv[(rhs * nm + vrow) * l + j]
+                                               : ainv[rhs * K1 + mt];
     const cx<T> xv = x[line * l + j];
     cx<T> out = a * xv;
     if (mt != 0) out = out - coef * s[j * LD + b];
@@ -215,7 +218,7 @@ void ct_epilogue_launch(dda_plan_s* p, const cx<float>* b1, const cx<float>* x, 
   note_launch();
   launch_k(kern, (unsigned)((lines + NB - 1) / NB), NB * LX / kElemsPerThread, smem, s,
       b1, x, y, p->mat, ainv_of<float>(p), p->K + 1, lines, nm, coef, tw_of<float>(p),
-      p->Lmax / LX);
+      p->Lmax / LX, pv_of<float>(p));
 }
 
 bool ct_epilogue(dda_plan_s* p, const cx<float>* b1, const cx<float>* x, cx<float>* y, long lines,
@@ -295,7 +298,7 @@ void matvec_core(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t
     note_launch();
     launch_k(kern, (unsigned)((lines + NB - 1) / NB), nth, smem, s,
         b1, x, y, p->mat, ainv_of<T>(p), p->K + 1, lines, nm, (int)l, (int)Lx, coef, tw,
-        p->Lmax / (int)Lx, make_radix_plan((int)Lx), ilog2i(NB));
+        p->Lmax / (int)Lx, make_radix_plan((int)Lx), ilog2i(NB), pv_of<T>(p));
     p->prof.end(s);
   }
 }

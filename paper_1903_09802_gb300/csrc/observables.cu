@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(kNT)
     k_xsec_sums(const double2* __restrict__ c, const double2* __restrict__ y,
                 const uint8_t* __restrict__ mat, const double2* __restrict__ ainv, int K1,
                 const double* __restrict__ inc, long l, long m, long n, double dx, double k,
-                double* __restrict__ part) {
+                double* __restrict__ part, const double2* __restrict__ pv) {
   pdl_entry();
   __shared__ double sh[4][32];
   const int r = blockIdx.y;
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(kNT)
   for (long v = v0 + threadIdx.x; v < v1; v += kNT) {
     const int mt = mat[v];
     if (mt == 0) continue;
-    const double2 a = ainv[(long)r * K1 + mt];
+    const double2 a = pv != nullptr ? pv[(long)r * nvox + v] : ainv[(long)r * K1 + mt];
     const long x = v % l, yy = (v / l) % m, z = v / (l * m);
     const double px = dx * (x - 0.5 * (l - 1)), py = dx * (yy - 0.5 * (m - 1)),
                  pz = dx * (z - 0.5 * (n - 1));
@@ -81,9 +81,14 @@ __global__ void __launch_bounds__(kNT)
 // grad[rhs][0][v] = dC_ext/dRe(eps_v), grad[rhs][1][v] = dC_ext/dIm(eps_v):
 // g = (lambda_v . c_v) d(alpha^{-1})/d(eps) (unconjugated over components),
 // dRe = pref Im(g), dIm = pref Re(g), pref = -4 pi k dx^3; zero on air.
+// With a per-voxel permittivity (eps != null) d(alpha^{-1})/d(eps) is that of
+// the voxel's own eps: -4 pi/(eps - 1)^2 + (b2 + b3 S)(k dx)^2, S of the
+// right-hand side's wave (inc: direction, polarisation).
 __global__ void k_ext_gradient(const double2* __restrict__ c, const double2* __restrict__ lam,
                                const uint8_t* __restrict__ mat, const double2* __restrict__ dainv,
-                               int K1, long nvox, int nrhs, double pref, double* __restrict__ grad) {
+                               int K1, long nvox, int nrhs, double pref, double* __restrict__ grad,
+                               const double2* __restrict__ eps, const double* __restrict__ inc,
+                               double kd) {
   pdl_entry();
   const long tot = nvox * nrhs;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < tot;
@@ -98,7 +103,21 @@ __global__ void k_ext_gradient(const double2* __restrict__ c, const double2* __r
         sx += a.x * b.x - a.y * b.y;
         sy += a.x * b.y + a.y * b.x;
       }
-      const double2 d = dainv[r * K1 + mt];
+      double2 d;
+      if (eps != nullptr) {
+        const double pi = 3.14159265358979323846;
+        const double* q = inc + r * 6;
+        double S = 0.0;
+        for (int k = 0; k < 3; ++k) S += (q[k] * q[3 + k]) * (q[k] * q[3 + k]);
+        const double2 e = eps[v];
+        const double ax = e.x - 1.0, ay = e.y;
+        const double wx = ax * ax - ay * ay, wy = 2.0 * ax * ay;  // (eps - 1)^2
+        const double dn = wx * wx + wy * wy;
+        d.x = -4.0 * pi * wx / dn + (0.1648469 + -1.7700004 * S) * kd * kd;
+        d.y = 4.0 * pi * wy / dn;
+      } else {
+        d = dainv[r * K1 + mt];
+      }
       const double gx = sx * d.x - sy * d.y, gy = sx * d.y + sy * d.x;
       gre = pref * gy;
       gim = pref * gx;
@@ -129,7 +148,10 @@ extern "C" dda_status_t dda_ext_gradient(dda_plan_t p, int32_t nrhs, const void*
   k_ext_gradient<<<grid, 256, 0, s>>>(static_cast<const double2*>(d_c),
                                       static_cast<const double2*>(d_lambda), p->mat,
                                       static_cast<const double2*>(p->w.dainv128), p->K + 1,
-                                      p->nvox, nrhs, pref, d_grad);
+                                      p->nvox, nrhs, pref, d_grad,
+                                      p->voxel_eps_on ? static_cast<const double2*>(p->w.eps_vox)
+                                                      : nullptr,
+                                      p->w.incd, p->d.k * p->d.dx);
   return check_cuda("dda_ext_gradient");
 }
 
@@ -151,7 +173,7 @@ extern "C" dda_status_t dda_cross_sections(dda_plan_t p, int32_t nrhs, const voi
   k_xsec_sums<<<dim3(nblk, nrhs), kNT, 0, s>>>(
       reinterpret_cast<const double2*>(c), reinterpret_cast<const double2*>(y), p->mat,
       static_cast<const double2*>(p->w.ainv128), p->K + 1, p->w.incd, p->l, p->m, p->n, p->d.dx,
-      p->d.k, part);
+      p->d.k, part, reinterpret_cast<const double2*>(pv_of<double>(p)));
   std::vector<double> h((size_t)nrhs * nblk * 4);
   cudaMemcpyAsync(h.data(), part, h.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (cudaStreamSynchronize(s) != cudaSuccess) return check_cuda("dda_cross_sections");

@@ -71,7 +71,54 @@ struct SolverState {
   int* tickets;      // [2][rhs] last-block counters of the Gram-Schmidt kernels
   double* bscal;     // [rhs][16] BiCG-Stab scalars
   int* counters;     // [16] 0: RHS still iterating in the current cycle
+  int* ctl;          // [4] step index of the cycle, steps allowed, RHS running
+  void* out;         // [rhs] outcome per right-hand side (krylov.cu's RhsOut)
+  double* hist;      // [rhs][kHistCap] relative residual after each inner iteration
+  unsigned long long* t0;  // solve start, device global timer (ns)
+  long long* nlaunch;      // kernels run by a graph-driven solve
 };
+
+// Residual-history entries kept per right-hand side on the device.
+constexpr int kHistCap = 4096;
+// Bytes of one right-hand side's outcome record (krylov.cu's RhsOut).
+constexpr int kRhsOutBytes = 32;
+
+// A plan's solve captured as one CUDA graph (krylov.cu), reused while the
+// solve's arguments stay the same.
+struct SolveGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cs = nullptr;     // capture stream
+  std::vector<char> key;         // arguments the graph was captured for
+  bool failed = false;           // capture did not work: host-driven loop only
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    key.clear();
+  }
+  ~SolveGraph() {
+    reset();
+    if (cs) cudaStreamDestroy(cs);
+  }
+};
+
+// Library launch counter (dda_launch_count): current value, and a signed
+// adjustment (kernels a graph ran on the device; launches only captured).
+long long launch_counter();
+void add_launches(long long n);
+
+// Whether dda_solve may run as one graph launch (DDA_SOLVE_GRAPH=0 in the
+// environment forces the host-driven loop).
+bool solve_graph_enabled();
+
+// dda_solve_many's batch as one graph launch (krylov.cu); false when the
+// plans cannot take part (then nothing was launched).
+bool solve_many_as_graph(int32_t nplans, const dda_plan_t* plans, const int32_t* nrhs,
+                         const void* const* d_b, void* const* d_x, const dda_solve_opts_t* opts,
+                         dda_rhs_stats_t* const* h_stats, void* const* streams,
+                         dda_status_t* st_out, std::string* why);
 
 struct Layout {
   // spectra, octant-compressed: [(hz)(hy)(hx)][6]
@@ -94,6 +141,12 @@ struct Layout {
   void* ainv128 = nullptr;
   void* ainv64 = nullptr;
   double* incd = nullptr;  // [rhs][6]: direction, polarisation
+  // per-voxel permittivity (desc.voxel_eps): eps [nvox] complex128 and
+  // alpha^{-1} per (rhs, voxel) in complex128, complex64 and double-float
+  void* eps_vox = nullptr;
+  void* pv128 = nullptr;
+  void* pv64 = nullptr;
+  void* pvdf = nullptr;
   void* dainv128 = nullptr;  // d(alpha^{-1})/d(eps) per (rhs, material), entry 0 unused
   int nblk = 1;            // reduction blocks per right-hand side
   // FFT scratch
@@ -130,6 +183,7 @@ struct dda_plan_s {
   bool precond_built = false;
   bool precond2_built = false;
   int nrhs_inc = 0;                      // RHS count of the last dda_set_incidence
+  bool voxel_eps_on = false;             // dda_set_voxel_eps holds a table
   std::vector<dda_incidence_t> inc;      // incidence per RHS
   std::vector<double> ainv_host;         // [rhs][K+1][2]
   std::vector<float> ainv_host32;
@@ -137,6 +191,9 @@ struct dda_plan_s {
   int* pinned = nullptr;                 // host-pinned words polled by the solver
   dda::Profiler prof;                    // optional kernel timing
   dda::Schedule sched;                   // launch choices (dda_schedule_set, dda_autotune)
+  dda::SolveGraph graph;                 // the last captured solve
+  dda::SolveGraph batch;                 // the last batch (dda_solve_many) led by this plan
+  long long id = 0;                      // creation number (graph cache keys)
 };
 
 namespace dda {
@@ -207,6 +264,19 @@ template <> inline const cx<double>* C_of<double>(const dda_plan_s* p) {
 template <> inline const cx<float>* C_of<float>(const dda_plan_s* p) {
   return static_cast<const cx<float>*>(p->w.C64);
 }
+// Per-voxel alpha^{-1} [rhs][nvox] of the plan's precision, or nullptr when
+// the plan has no per-voxel permittivity.
+template <typename T> inline const cx<T>* pv_of(const dda_plan_s* p);
+template <> inline const cx<double>* pv_of<double>(const dda_plan_s* p) {
+  return p->voxel_eps_on ? static_cast<const cx<double>*>(p->w.pv128) : nullptr;
+}
+template <> inline const cx<float>* pv_of<float>(const dda_plan_s* p) {
+  return p->voxel_eps_on ? static_cast<const cx<float>*>(p->w.pv64) : nullptr;
+}
+template <> inline const cx<df>* pv_of<df>(const dda_plan_s* p) {
+  return p->voxel_eps_on ? static_cast<const cx<df>*>(p->w.pvdf) : nullptr;
+}
+
 template <typename T> inline const cx<T>* ainv_of(const dda_plan_s* p);
 template <> inline const cx<double>* ainv_of<double>(const dda_plan_s* p) {
   return static_cast<const cx<double>*>(p->w.ainv128);

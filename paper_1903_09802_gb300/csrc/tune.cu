@@ -22,7 +22,9 @@ using TuneKey = std::tuple<int, int, int, int, int, int>;  // device, l, m, n, p
 std::mutex g_tune_mu;
 std::map<TuneKey, Schedule> g_tune_table;
 
-dda_schedule_t to_c(const Schedule& s) { return dda_schedule_t{s.rr_z ? 1 : 0, s.pdl ? 1 : 0}; }
+dda_schedule_t to_c(const Schedule& s) {
+  return dda_schedule_t{s.rr_z ? 1 : 0, s.pdl ? 1 : 0, s.graph ? 1 : 0};
+}
 
 // Mean milliseconds per matvec under the plan's current schedule.
 dda_status_t time_matvec(dda_plan_t p, int32_t prec, int32_t nrhs, const void* x, void* y,
@@ -49,10 +51,12 @@ dda_status_t time_matvec(dda_plan_t p, int32_t prec, int32_t nrhs, const void* x
 
 extern "C" dda_status_t dda_schedule_set(dda_plan_t p, const dda_schedule_t* sched) {
   if (!p || !sched) return fail(DDA_ERR_INVALID_ARG, "dda_schedule_set: NULL argument");
-  if ((sched->rr_z != 0 && sched->rr_z != 1) || (sched->pdl != 0 && sched->pdl != 1))
+  if ((sched->rr_z != 0 && sched->rr_z != 1) || (sched->pdl != 0 && sched->pdl != 1) ||
+      (sched->graph != 0 && sched->graph != 1))
     return fail(DDA_ERR_INVALID_ARG, "dda_schedule_set: fields must be 0 or 1");
   p->sched.rr_z = sched->rr_z == 1;
   p->sched.pdl = sched->pdl == 1;
+  p->sched.graph = sched->graph == 1;
   return DDA_OK;
 }
 
@@ -82,7 +86,8 @@ extern "C" dda_status_t dda_autotune(dda_plan_t p, int32_t prec, int32_t nrhs, c
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_table.find(key);
     if (it != g_tune_table.end()) {
-      p->sched = it->second;
+      p->sched.rr_z = it->second.rr_z;
+      p->sched.pdl = it->second.pdl;
       rep.chosen = to_c(p->sched);
       rep.cached = 1;
       if (h_report) *h_report = rep;
@@ -99,7 +104,7 @@ extern "C" dda_status_t dda_autotune(dda_plan_t p, int32_t prec, int32_t nrhs, c
   dda_status_t st = DDA_OK;
   int best = -1;
   for (int c = 0; c < 4 && st == DDA_OK; ++c) {
-    Schedule cand;
+    Schedule cand = saved;  // the solve-loop choice (graph) is not tuned here
     cand.rr_z = (c & 1) == 0;
     cand.pdl = (c & 2) == 0;
     p->sched = cand;

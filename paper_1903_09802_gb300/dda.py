@@ -60,6 +60,7 @@ def _precond2_code(v, dims=None) -> int:
     return {"x": 2, "y": 3}[v]
 
 EXPORTS = ("dda_workspace_size", "dda_plan_create", "dda_set_incidence", "dda_incident_field",
+           "dda_set_voxel_eps",
            "dda_matvec", "dda_precond_build", "dda_precond_apply", "dda_precond_apply_noalloc",
            "dda_precond2_build", "dda_precond2_apply",
            "dda_fft3d", "dda_solve", "dda_solve_many",
@@ -82,7 +83,8 @@ class PlanDesc(ctypes.Structure):
                 ("dx", ctypes.c_double), ("k", ctypes.c_double),
                 ("n_materials", ctypes.c_int32), ("max_rhs", ctypes.c_int32),
                 ("krylov_m", ctypes.c_int32), ("precisions", ctypes.c_int32),
-                ("precond2", ctypes.c_int32), ("circulant", ctypes.c_int32)]
+                ("precond2", ctypes.c_int32), ("circulant", ctypes.c_int32),
+                ("voxel_eps", ctypes.c_int32)]
 
 
 class Incidence(ctypes.Structure):
@@ -93,17 +95,21 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iters", ctypes.c_int32),
                 ("restart", ctypes.c_int32), ("precond", ctypes.c_int32),
                 ("inner_prec", ctypes.c_int32), ("inner_tol", ctypes.c_double),
-                ("reorth_eta", ctypes.c_double), ("method", ctypes.c_int32)]
+                ("reorth_eta", ctypes.c_double), ("method", ctypes.c_int32),
+                ("history_cap", ctypes.c_int32), ("timeout_ns", ctypes.c_int64),
+                ("h_history", ctypes.POINTER(ctypes.c_double))]
 
 
 class RhsStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("cycles", ctypes.c_int32),
                 ("converged", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("rel_resid", ctypes.c_double), ("reorth", ctypes.c_int32)]
+                ("rel_resid", ctypes.c_double), ("reorth", ctypes.c_int32),
+                ("history_len", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("ms", ctypes.c_float)]
 
 
 class Schedule(ctypes.Structure):
-    _fields_ = [("rr_z", ctypes.c_int32), ("pdl", ctypes.c_int32)]
+    _fields_ = [("rr_z", ctypes.c_int32), ("pdl", ctypes.c_int32), ("graph", ctypes.c_int32)]
 
 
 class TuneReport(ctypes.Structure):
@@ -119,6 +125,8 @@ _lib.dda_plan_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(PlanDesc), 
                                  ctypes.POINTER(ctypes.c_double), _vp, ctypes.c_size_t, _vp]
 _lib.dda_set_incidence.restype = ctypes.c_int
 _lib.dda_set_incidence.argtypes = [_vp, ctypes.c_int32, ctypes.POINTER(Incidence), _vp]
+_lib.dda_set_voxel_eps.restype = ctypes.c_int
+_lib.dda_set_voxel_eps.argtypes = [_vp, _vp, _vp]
 _lib.dda_incident_field.restype = ctypes.c_int
 _lib.dda_incident_field.argtypes = [_vp, ctypes.c_int32, _vp, _vp]
 _lib.dda_matvec.restype = ctypes.c_int
@@ -201,9 +209,10 @@ def _prec_of(t: torch.Tensor) -> int:
 
 
 def workspace_size(l, m, n, dx, k, n_materials=1, max_rhs=1, krylov_m=0,
-                   precisions=PLAN_C128 | PLAN_C64, precond2=0, circulant="chan") -> int:
+                   precisions=PLAN_C128 | PLAN_C64, precond2=0, circulant="chan",
+                   voxel_eps=False) -> int:
     d = PlanDesc(l, m, n, dx, k, n_materials, max_rhs, krylov_m, precisions,
-                 _precond2_code(precond2, (l, m, n)), CIRCULANTS[circulant])
+                 _precond2_code(precond2, (l, m, n)), CIRCULANTS[circulant], int(bool(voxel_eps)))
     return int(_lib.dda_workspace_size(ctypes.byref(d)))
 
 
@@ -216,6 +225,19 @@ class SolveResult:
     rel_resid: list
     status: int
     reorth: list
+    history: list = None     # per RHS: relative residual after each inner iteration
+    graph: bool = False      # the solve ran as one CUDA graph launch
+    ms: float = 0.0          # wall time of the library call
+
+
+def _result(x, stats, st, hist=None, cap=0):
+    h = None
+    if hist is not None:
+        h = [np.array(hist[r * cap: r * cap + s.history_len]) for r, s in enumerate(stats)]
+    return SolveResult(x, [s.iters for s in stats], [s.cycles for s in stats],
+                       [bool(s.converged) for s in stats], [s.rel_resid for s in stats], st,
+                       [s.reorth for s in stats], h, bool(stats[0].graph) if len(stats) else False,
+                       float(stats[0].ms) if len(stats) else 0.0)
 
 
 class Plan:
@@ -223,7 +245,11 @@ class Plan:
 
     def __init__(self, mat: torch.Tensor, eps, dx: float, k: float, max_rhs: int = 1,
                  krylov_m: int = 0, precisions: int = PLAN_C128 | PLAN_C64,
-                 precond2=False, circulant: str = "chan"):
+                 precond2=False, circulant: str = "chan", voxel_eps: torch.Tensor | None = None):
+        """mat: (n, m, l) uint8 material per voxel (0 air); eps: permittivity of
+        materials 1..K; voxel_eps: optional (n, m, l) complex128 permittivity of
+        every voxel (dda_set_voxel_eps), which then overrides the table on
+        scatterer voxels (the table still gives alpha_tilde)."""
         if mat.dtype != torch.uint8 or not mat.is_cuda or mat.dim() != 3:
             raise TypeError("mat must be a (n, m, l) uint8 CUDA tensor")
         self.mat = mat.contiguous()
@@ -232,7 +258,7 @@ class Plan:
         eps = [complex(e) for e in eps]
         self.desc = PlanDesc(l, m, n, float(dx), float(k), len(eps), int(max_rhs), int(krylov_m),
                              int(precisions), _precond2_code(precond2, (l, m, n)),
-                             CIRCULANTS[circulant])
+                             CIRCULANTS[circulant], int(voxel_eps is not None))
         size = int(_lib.dda_workspace_size(ctypes.byref(self.desc)))
         if size == 0:
             raise DDAError(1, last_error())
@@ -243,6 +269,23 @@ class Plan:
                                     _ptr(self.work), size, _stream()))
         self._h = h
         self.nrhs = 0
+        self.voxel_eps = None
+        if voxel_eps is not None:
+            self.set_voxel_eps(voxel_eps)
+
+    def set_voxel_eps(self, eps: torch.Tensor | None):
+        """dda_set_voxel_eps: (n, m, l) complex128 permittivity per voxel, or None."""
+        if eps is None:
+            _check(_lib.dda_set_voxel_eps(self._h, None, _stream()))
+            self.voxel_eps = None
+            return
+        n, m, l = self.mat.shape
+        if tuple(eps.shape) != (n, m, l) or eps.dtype != torch.complex128:
+            raise ValueError(f"voxel_eps must be a complex128 tensor of shape {(n, m, l)}")
+        if eps.device != self.mat.device:
+            raise ValueError("voxel_eps must be on the plan's device")
+        self.voxel_eps = eps.contiguous()
+        _check(_lib.dda_set_voxel_eps(self._h, _ptr(self.voxel_eps), _stream()))
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -364,13 +407,20 @@ class Plan:
               tol: float = 1e-6, max_iters: int = 2000, restart: int = 50, precond: int = 3,
               inner_prec: int = C128, inner_tol: float = 0.0, raise_on_error: bool = True,
               nrhs: int | None = None, reorth_eta: float = 0.5 ** 0.5,
-              method: int = 0) -> SolveResult:
+              method: int = 0, history: int = 0, timeout_ms: float = 0.0) -> SolveResult:
+        """dda_solve.  history: entries of residual history kept per right-hand
+        side (0: none); timeout_ms: the solve's time limit on the device (0:
+        none; a right-hand side stopped by it ends with DDA_ERR_TIMEOUT)."""
         nrhs = nrhs or (b.shape[0] if b is not None else self.nrhs)
         if x0 is None:
             x = torch.zeros(self.field_shape(nrhs), dtype=torch.complex128, device=self.mat.device)
         else:
             x = x0.clone().contiguous()
-        opts = SolveOpts(tol, max_iters, restart, precond, inner_prec, inner_tol, reorth_eta, method)
+        hist = (ctypes.c_double * (nrhs * history))() if history > 0 else None
+        opts = SolveOpts(tol, max_iters, restart, precond, inner_prec, inner_tol, reorth_eta, method,
+                         int(history), int(timeout_ms * 1e6),
+                         ctypes.cast(hist, ctypes.POINTER(ctypes.c_double)) if hist is not None
+                         else None)
         stats = (RhsStats * nrhs)()
         if b is not None:
             b = self._field(b, "b", torch.complex128)
@@ -384,9 +434,7 @@ class Plan:
         st = _lib.dda_solve(self._h, nrhs, bp, _ptr(x), ctypes.byref(opts), stats, _stream())
         if st != 0 and raise_on_error:
             raise DDAError(st, last_error())
-        return SolveResult(x, [s.iters for s in stats], [s.cycles for s in stats],
-                           [bool(s.converged) for s in stats], [s.rel_resid for s in stats], st,
-                           [s.reorth for s in stats])
+        return _result(x, stats, st, hist, history)
 
     def adjoint_rhs(self, nrhs: int | None = None) -> torch.Tensor:
         nrhs = nrhs or self.nrhs
@@ -417,10 +465,11 @@ class Plan:
     def schedule(self) -> dict:
         s = Schedule()
         _check(_lib.dda_schedule_get(self._h, ctypes.byref(s)))
-        return {"rr_z": bool(s.rr_z), "pdl": bool(s.pdl)}
+        return {"rr_z": bool(s.rr_z), "pdl": bool(s.pdl), "graph": bool(s.graph)}
 
-    def set_schedule(self, rr_z: bool = True, pdl: bool = True):
-        _check(_lib.dda_schedule_set(self._h, ctypes.byref(Schedule(int(rr_z), int(pdl)))))
+    def set_schedule(self, rr_z: bool = True, pdl: bool = True, graph: bool = True):
+        _check(_lib.dda_schedule_set(self._h, ctypes.byref(Schedule(int(rr_z), int(pdl),
+                                                                    int(graph)))))
 
     def autotune(self, prec: int = C64, nrhs: int | None = None, reps: int = 10,
                  force: bool = False) -> dict:
@@ -432,7 +481,7 @@ class Plan:
         rep = TuneReport()
         _check(_lib.dda_autotune(self._h, prec, nrhs, _ptr(x), _ptr(y), int(reps), int(force),
                                  ctypes.byref(rep), _stream()))
-        sched = lambda s: {"rr_z": bool(s.rr_z), "pdl": bool(s.pdl)}  # noqa: E731
+        sched = lambda s: {"rr_z": bool(s.rr_z), "pdl": bool(s.pdl), "graph": bool(s.graph)}  # noqa: E731
         return {"chosen": sched(rep.chosen), "cached": bool(rep.cached),
                 "timed": [(sched(rep.cand[i]), float(rep.ms_per_matvec[i]))
                           for i in range(rep.ncand)]}
@@ -480,33 +529,42 @@ def solve_many(plans, bs=None, streams=None, tol: float = 1e-6, max_iters: int =
     xp = arr([x.data_ptr() for x in xs])
     sp = (ctypes.POINTER(RhsStats) * n)(*[ctypes.cast(st, ctypes.POINTER(RhsStats)) for st in stats])
     strp = arr([s.cuda_stream for s in streams])
-    opts = SolveOpts(tol, max_iters, restart, precond, inner_prec, inner_tol, reorth_eta, method)
+    opts = SolveOpts(tol, max_iters, restart, precond, inner_prec, inner_tol, reorth_eta, method,
+                     0, 0, None)
     st = _lib.dda_solve_many(n, hp, nr, bp, xp, ctypes.byref(opts), sp, strp)
     for s in streams:
         cur.wait_stream(s)
     if st != 0 and raise_on_error:
         raise DDAError(st, last_error())
-    return [SolveResult(x, [q.iters for q in sv], [q.cycles for q in sv],
-                        [bool(q.converged) for q in sv], [q.rel_resid for q in sv], st,
-                        [q.reorth for q in sv]) for x, sv in zip(xs, stats)]
+    return [_result(x, sv, st) for x, sv in zip(xs, stats)]
 
 
 class _Extinction(torch.autograd.Function):
     """C_ext of each incident wave as a differentiable function of the
-    materials' permittivities.  Forward: plan, preconditioner, solve, C_ext.
-    Backward: the adjoint solve A lambda = conj(E_inc) with the same operator
-    (A = A^T), the per-voxel gradient dC_ext/d eps_j (dda_ext_gradient), summed
-    over the voxels of each material (they share its eps).  For a real output
-    and a complex input the gradient follows PyTorch's convention:
-    dC/dRe(eps) + i dC/dIm(eps)."""
+    permittivities: one per material (eps of shape (K,)) or one per voxel (eps
+    of shape (n, m, l), dda_set_voxel_eps).  Forward: plan, preconditioner,
+    solve, C_ext.  Backward: the adjoint solve A lambda = conj(E_inc) with the
+    same operator (A = A^T), the per-voxel gradient dC_ext/d eps_j
+    (dda_ext_gradient), weighted by the incoming gradient of each wave and
+    summed over waves on the device; per material it is then summed over the
+    material's voxels (one index_add).  For a real output and a complex input
+    the gradient follows PyTorch's convention: dC/dRe(eps) + i dC/dIm(eps)."""
 
     @staticmethod
     def forward(ctx, eps, geometry, solve_kw, plan_factory):
         mat, dx, k, dirs, pols = geometry
-        eps_list = [complex(e) for e in eps.detach().cpu().tolist()]
+        per_voxel = eps.dim() == 3
+        if per_voxel:
+            e = eps.detach().to(mat.device, torch.complex128).contiguous()
+            sel = mat > 0
+            # alpha_tilde (air rows, preconditioner) from the scatterer's mean permittivity
+            table = [complex(e[sel].mean().item()) if bool(sel.any()) else complex(e.mean().item())]
+        else:
+            table = [complex(v) for v in eps.detach().cpu().tolist()]
         pc = solve_kw.get("precond", 3)
-        plan = plan_factory(mat, eps_list, dx, k, len(dirs), max(7, solve_kw.get("restart", 50)),
-                            pc == 2)
+        extra = {"voxel_eps": e} if per_voxel else {}
+        plan = plan_factory(mat, table, dx, k, len(dirs), max(7, solve_kw.get("restart", 50)),
+                            pc == 2, **extra)
         plan.set_incidence(dirs, pols)
         if pc == 3:
             plan.precond_build()
@@ -514,31 +572,36 @@ class _Extinction(torch.autograd.Function):
             plan.precond2_build()
         c = plan.solve(**solve_kw).x
         cext = torch.as_tensor(plan.cross_sections(c)[:, 0], dtype=torch.float64)
-        ctx.state = (plan, c, solve_kw, mat, len(eps_list), eps.device)
+        ctx.state = (plan, c, solve_kw, mat, len(table), eps.device, per_voxel)
         return cext
 
     @staticmethod
     def backward(ctx, grad_out):
-        plan, c, solve_kw, mat, K, dev = ctx.state
+        plan, c, solve_kw, mat, K, dev, per_voxel = ctx.state
         lam = plan.solve(b=plan.adjoint_rhs(c.shape[0]), **solve_kw).x
         g = plan.ext_gradient_from(c, lam)  # (nrhs, 2, n, m, l)
         w = grad_out.to(g.device, g.dtype).view(-1, 1, 1, 1, 1)
         gsum = (w * g).sum(dim=0)  # (2, n, m, l): dL/dRe eps_j, dL/dIm eps_j
-        grad = torch.zeros(K, dtype=torch.complex128, device=dev)
-        for kk in range(K):
-            sel = mat == (kk + 1)
-            grad[kk] = complex(float(gsum[0][sel].sum()), float(gsum[1][sel].sum()))
-        return grad, None, None, None
+        gc = torch.complex(gsum[0], gsum[1])
+        if per_voxel:
+            return gc.to(dev), None, None, None
+        idx = mat.reshape(-1).to(gc.device, torch.long)
+        per_mat = torch.zeros(K + 1, dtype=torch.complex128, device=gc.device)
+        per_mat.index_add_(0, idx, gc.reshape(-1))
+        return per_mat[1:].to(dev), None, None, None
 
 
-def _default_plan_factory(mat, eps, dx, k, nrhs, krylov_m, precond2):
-    return Plan(mat, eps, dx, k, max_rhs=nrhs, krylov_m=krylov_m, precond2=precond2)
+def _default_plan_factory(mat, eps, dx, k, nrhs, krylov_m, precond2, voxel_eps=None):
+    return Plan(mat, eps, dx, k, max_rhs=nrhs, krylov_m=krylov_m, precond2=precond2,
+                voxel_eps=voxel_eps)
 
 
 def extinction(eps: torch.Tensor, mat: torch.Tensor, dx: float, k: float, dirs, pols,
                plan_factory=_default_plan_factory, **solve_kw) -> torch.Tensor:
     """C_ext per incident wave (float64, shape (nrhs,)), differentiable with
-    respect to eps (complex128, one permittivity per material 1..K): the
-    adjoint per-voxel gradient of dda_ext_gradient, summed per material."""
+    respect to eps (complex128): one permittivity per material 1..K (shape
+    (K,)), or one per voxel (shape (n, m, l); entries on air voxels are
+    ignored and get zero gradient).  The gradient is the adjoint one of
+    dda_ext_gradient."""
     return _Extinction.apply(eps, (mat, dx, k, list(dirs), list(pols)), dict(solve_kw),
                              plan_factory)

@@ -142,3 +142,29 @@ def test_precond_apply_parity_strang(box):
                      .precond3(kind="strang")(v[r]) for r in range(2)])
     assert rel_err(plan.precond_apply(to_dev(v)).cpu().numpy(), want) < 1e-10
     assert rel_err(plan.precond_apply(to_dev(v, torch.complex64)).cpu().numpy(), want) < 2e-5
+
+
+@pytest.mark.gpu
+@pytest.mark.late(1)
+def test_operator_parity_z256():
+    """The preconditioner's z pass at transform length 256 and the matvec's at
+    512 (the 256^3 solve's lengths), on a thin 4 x 4 x 256 box, vs the oracle."""
+    dda = dda_module()
+    l, m, n = 4, 4, 256
+    rng = np.random.default_rng(256)
+    mat = np.ones((n, m, l), dtype=np.uint8)
+    mat[rng.random((n, m, l)) < 0.3] = 0
+    dx, k = 0.05, 2.0
+    dirs, pols = _incidences()
+    plan = dda.Plan(to_dev(mat, torch.uint8), [1.31 ** 2], dx, k, max_rhs=2)
+    plan.set_incidence(dirs, pols)
+    plan.precond_build()
+    v = random_field((2, 3, n, m, l), rng)
+    want = np.stack([Problem(mat=mat, dx=dx, k=k, eps=[1.31 ** 2], d=dirs[r], e=pols[r])
+                     .precond3()(v[r]) for r in range(2)])
+    assert rel_err(plan.precond_apply(to_dev(v)).cpu().numpy(), want) < 1e-10
+    assert rel_err(plan.precond_apply(to_dev(v, torch.complex64)).cpu().numpy(), want) < 2e-5
+    wantm = np.stack([_oracle_box_matvec(mat, [1.31 ** 2], dx, k, dirs[r], pols[r], v[r])[0]
+                      for r in range(2)])
+    assert rel_err(plan.matvec(to_dev(v)).cpu().numpy(), wantm) < 1e-10
+    assert rel_err(plan.matvec(to_dev(v, torch.complex64)).cpu().numpy(), wantm) < 2e-5

@@ -7,23 +7,28 @@ aspect ratios L/(2 a_h) in {0.5, 1, 2} (boxes 64x64x32, 64^3, 64x64x128),
 one seeded incident direction with its two orthogonal polarisations solved
 together: 6 systems x 2 right-hand sides = 12 solves.  For every system the
 step runs the whole path through the C ABI: plan (Green-function spectrum),
-incident waves and polarizabilities, 3-level circulant preconditioner build,
-right-preconditioned GMRES(50) in complex64 with FP64 iterative refinement to
-a true complex128 relative residual of 1e-6, and the cross sections.
-The m = 1.78 systems of the same sweep are left out of the timed step: with
-GMRES(50) or GMRES(200) neither the plain nor the preconditioned solve
-reaches 1e-6 within 4000 iterations on this grid (|m| k dx = 1.1).
+incident waves and polarizabilities, circulant preconditioner build (the
+paper's 2-level form on the plate-like 64x64x32 prism, the 3-level form on
+the others: dda.precond_for), right-preconditioned GMRES(50) in complex64
+with FP64 iterative refinement to a true complex128 relative residual of
+1e-6 (the whole solve loop one CUDA graph launch), and the cross sections.
+The sweep's m = 1.78 systems (6 more solves) reach 1e-6 with no solver here
+within the paper's iteration caps; they are timed separately to those caps
+(comparisons, "no convergence"), not in the step.
 
 Metric: time-to-solve per right-hand side (ms, lower is better), whole job:
 elapsed device time of K steps / (12 K N).  L2 is flushed (a 512 MB write)
 before every timed step.  The JSON line also carries the roofline of the
-dominant kernel measured live with CUDA events, the CPU oracle timed on a
-bounded sample, the end-to-end figure through host buffers, the number of
+dominant kernel measured live with CUDA events (and the matvec's passes at
+the 128^3 box), the CPU oracle timed on a bounded sample on one core and on
+every host core, the end-to-end figure through host buffers, the number of
 library kernel launches, the SM clocks sampled during the timed region and,
-untimed, solver comparisons on the two 64^3 systems (no preconditioner,
-plain complex128, BiCG-Stab), the complex64 matvec against the same work
-written with cuFFT (torch.fft) and PyTorch elementwise kernels, per box, and
-the 128^3 prism (x = 40) solved in mixed precision and in complex128.
+untimed, comparisons: preconditioned vs unpreconditioned per system, solver
+variants, complex128 vs mixed precision on the same workload, the m = 1.78
+systems to the caps, the complex64 matvec against cuFFT (torch.fft), the
+128^3 prism in both precisions, the 32^3 twin against the oracle's stored
+FP64 cross sections, the 256^3 solve and an uneven batch of 32 prisms in
+one graph launch.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -46,9 +51,10 @@ sys.path.insert(0, ROOT)
 METRIC = "GMRES time-to-solve @1e-6 (FP64 vs mixed/batched); FFT-matvec HBM GB/s"
 UNIT = "ms/solve"
 WORKLOAD = ("64^3 hexagonal prisms, x=20, m in {1.31, 1.31+0.05i} x aspect {0.5,1,2}, "
-            "seeded direction x 2 polarisations (12 solves), 3-level circulant "
-            "preconditioner, GMRES(50) complex64 + FP64 refinement to 1e-6, "
-            "reorthogonalisation threshold 0.1")
+            "seeded direction x 2 polarisations (12 solves; the sweep's m=1.78 systems do not "
+            "converge and are reported apart), circulant preconditioner per dda.precond_for "
+            "(2-level on the 64x64x32 plate-like prism, 3-level otherwise), GMRES(50) "
+            "complex64 + FP64 refinement to 1e-6, one graph launch per solve")
 FLUSH_BYTES = 512 << 20
 # Second Gram-Schmidt pass only under severe cancellation (||w|| drops below
 # 10% in the first pass).  On this workload the iteration counts and final
@@ -145,18 +151,25 @@ class Runner:
     def flush_l2(self):
         self.flush_buf.fill_(1)
 
-    def step(self, masks=None, host_out=None):
+    def step(self, masks=None, host_out=None, inner="c64"):
         dda = self.dda
         masks = masks if masks is not None else self.masks
         out = []
+        prec = dict(inner_prec=dda.C64, inner_tol=1e-4) if inner == "c64" else dict(
+            inner_prec=dda.C128)
         for i, case in enumerate(self.cases):
-            plan = dda.Plan(masks[i], case.eps, case.dx, case.k, max_rhs=2, krylov_m=50)
+            pc = dda.precond_for(*case.dims)
+            plan = dda.Plan(masks[i], case.eps, case.dx, case.k, max_rhs=2, krylov_m=50,
+                            precond2="auto" if pc == 2 else False)
             if self.profile:
                 plan.profile(True)
             plan.set_incidence(case.dirs, case.pols)
-            plan.precond_build()
-            res = plan.solve(tol=1e-6, restart=50, precond=3, inner_prec=dda.C64, inner_tol=1e-4,
-                             max_iters=2000, reorth_eta=REORTH_ETA)
+            if pc == 2:
+                plan.precond2_build()
+            else:
+                plan.precond_build()
+            res = plan.solve(tol=1e-6, restart=50, precond=pc, max_iters=2000,
+                             reorth_eta=REORTH_ETA, **prec)
             xs = plan.cross_sections(res.x)
             if host_out is not None:
                 host_out[i].copy_(res.x, non_blocking=True)
@@ -252,6 +265,7 @@ def compare_solvers(runner):
         "gmres_3level_c64_fp64ir": dict(precond=3, reorth_eta=REORTH_ETA, **c64),
         "gmres_none_c64_fp64ir": dict(precond=0, reorth_eta=REORTH_ETA, **c64),
         "gmres_3level_c128": dict(precond=3, inner_prec=dda.C128, reorth_eta=REORTH_ETA),
+        "bicgstab_none_c64_fp64ir": dict(precond=0, method=dda.BICGSTAB, **c64),
         "bicgstab_3level_c64_fp64ir": dict(precond=3, method=dda.BICGSTAB, **c64),
         "gmres_2level_c64_fp64ir": dict(precond=2, reorth_eta=REORTH_ETA, **c64),
         "bicgstab_2level_c64_fp64ir": dict(precond=2, method=dda.BICGSTAB, **c64),
@@ -264,8 +278,8 @@ def compare_solvers(runner):
         torch.cuda.synchronize()
         return r, time.perf_counter() - t0
 
-    def run(plan, case, kw):
-        res, dt = timed(lambda: plan.solve(tol=1e-6, restart=50, max_iters=3000,
+    def run(plan, case, kw, cap=3000):
+        res, dt = timed(lambda: plan.solve(tol=1e-6, restart=50, max_iters=cap,
                                            raise_on_error=False, **kw))
         return {"ms_per_solve": round(1e3 * dt / case.nrhs, 2), "iters": res.iters,
                 "converged": all(res.converged)}
@@ -290,8 +304,8 @@ def compare_solvers(runner):
                             circulant="strang")
             plan.set_incidence(case.dirs, case.pols)
             plan.precond_build()
-            out[key]["gmres_3level_strang_c64_fp64ir"] = run(
-                plan, case, dict(precond=3, reorth_eta=REORTH_ETA, **c64))
+            out[key]["gmres_3level_strang_c64_fp64ir (cap 600)"] = run(
+                plan, case, dict(precond=3, reorth_eta=REORTH_ETA, **c64), cap=600)
             del plan
         elif case.dims == (64, 64, 128) and complex(case.eps[0]).imag == 0:
             key = m_key + " long prism 64x64x128"
@@ -413,42 +427,44 @@ def compare_fft(runner, reps=20):
     return out
 
 
-def compare_sweep_2level(runner):
-    """The timed step's six systems solved with the paper's 2-level
-    preconditioner instead of the 3-level one (Toeplitz level on the
-    shortest box edge, as precond2="auto" picks), same solver settings:
-    iterations and time per solve (preconditioner build included), next to
-    the same for the 3-level form."""
+def compare_policy(runner):
+    """Preconditioned against unpreconditioned, per system of the timed step:
+    GMRES(50) complex64 + FP64 refinement with no preconditioner, the
+    3-level, the 2-level (Toeplitz level on the shortest edge) and the
+    step's own choice (dda.precond_for), each timed from plan creation to the
+    solution (preconditioner build included), and the solve alone; the
+    iterations of each."""
     import torch
     dda = runner.dda
-    out = {"2level_auto": {}, "3level": {}}
-    tot = {"2level_auto": 0.0, "3level": 0.0}
-    nsolve = 0
+    out = {}
     for i, case in enumerate(runner.cases):
         key = f"{'x'.join(map(str, case.dims))} m={complex(case.eps[0]) ** 0.5:.2f}"
-        nsolve += case.nrhs
-        for name in ("2level_auto", "3level"):
+        row = {"policy": f"{dda.precond_for(*case.dims)}-level"}
+        for name, pc in (("none", 0), ("3level", 3), ("2level", 2)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            two = name == "2level_auto"
             plan = dda.Plan(runner.masks[i], case.eps, case.dx, case.k, max_rhs=2, krylov_m=50,
-                            precond2="auto" if two else False)
+                            precond2="auto" if pc == 2 else False)
             plan.set_incidence(case.dirs, case.pols)
-            if two:
-                plan.precond2_build()
-            else:
+            if pc == 3:
                 plan.precond_build()
-            res = plan.solve(tol=1e-6, restart=50, max_iters=3000, precond=2 if two else 3,
+            elif pc == 2:
+                plan.precond2_build()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            res = plan.solve(tol=1e-6, restart=50, max_iters=3000, precond=pc,
                              inner_prec=dda.C64, inner_tol=1e-4, reorth_eta=REORTH_ETA,
                              raise_on_error=False)
             torch.cuda.synchronize()
-            dt = time.perf_counter() - t0
-            tot[name] += dt
-            out[name][key] = {"iters": res.iters, "converged": all(res.converged),
-                              "ms_per_solve": round(1e3 * dt / case.nrhs, 2)}
+            t2 = time.perf_counter()
+            row[name] = {"iters": res.iters, "converged": all(res.converged),
+                         "ms_per_solve_with_setup": round(1e3 * (t2 - t0) / case.nrhs, 2),
+                         "ms_per_solve": round(1e3 * (t2 - t1) / case.nrhs, 2)}
             del plan
-    for name in tot:
-        out[name]["all systems ms_per_solve"] = round(1e3 * tot[name] / nsolve, 2)
+        pol = row[row["policy"].replace("-", "")]
+        row["policy_beats_none"] = (pol["ms_per_solve_with_setup"]
+                                    < row["none"]["ms_per_solve_with_setup"])
+        out[key] = row
     return out
 
 
@@ -484,6 +500,215 @@ def compare_precision_128(runner):
     del plan
     torch.cuda.empty_cache()
     return out
+
+
+def compare_m178(runner, cap=2000):
+    """The sweep's m = 1.78 systems (|m| k dx = 1.1), which no solver here
+    brings to 1e-6: each variant timed to the cap (GMRES: cap iterations,
+    the paper's GMRES cap; BiCG-Stab: cap iterations = 2 cap half steps, the
+    paper's BiCG-Stab cap), with the final FP64 residual and the smallest
+    one the residual history reached."""
+    import torch
+    from dda_inputs import config2_cases
+    dda = runner.dda
+    c64 = dict(inner_prec=dda.C64, inner_tol=1e-4)
+    variants = {"gmres_none": dict(precond=0, method=0, reorth_eta=REORTH_ETA),
+                "gmres_2level": dict(precond=2, method=0, reorth_eta=REORTH_ETA),
+                "bicgstab_none": dict(precond=0, method=1),
+                "bicgstab_2level": dict(precond=2, method=1)}
+    out = {}
+    for case in config2_cases(64, 20.0, seed=0):
+        if abs(complex(case.eps[0]) - 1.78 ** 2) > 1e-9:
+            continue
+        key = f"{'x'.join(map(str, case.dims))} m=1.78"
+        mask = torch.from_numpy(case.mask()).to(runner.dev)
+        plan = dda.Plan(mask, case.eps, case.dx, case.k, max_rhs=2, krylov_m=50, precond2="auto")
+        plan.set_incidence(case.dirs, case.pols)
+        plan.precond2_build()
+        out[key] = {}
+        for name, kw in variants.items():
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = plan.solve(tol=1e-6, restart=50, max_iters=cap, raise_on_error=False,
+                           history=4096, **c64, **kw)
+            torch.cuda.synchronize()
+            out[key][name] = {"ms_per_solve": round(1e3 * (time.perf_counter() - t0) / 2, 1),
+                              "iters": r.iters, "converged": r.converged,
+                              "final_rel_resid": [float(f"{v:.3e}") for v in r.rel_resid],
+                              "min_rel_resid": [float(f"{float(min(h)):.3e}") for h in r.history],
+                              "status": dda.STATUS.get(r.status, r.status)}
+        del plan
+        torch.cuda.empty_cache()
+    return out
+
+
+def compare_precision_sweep(runner):
+    """The FP64-vs-mixed pair on the timed step's own workload: its twelve
+    solves (same preconditioner per system) with complex64 cycles inside FP64
+    refinement and with complex128 cycles, wall time per solve (plan and
+    preconditioner build included) and iterations."""
+    import torch
+    out, dts = {}, {}
+    for name, prec in (("c64_fp64ir", "c64"), ("c128", "c128")):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = runner.step(inner=prec)
+        torch.cuda.synchronize()
+        dts[name] = time.perf_counter() - t0
+        nsolve = sum(c.nrhs for c in runner.cases)
+        out[name] = {"ms_per_solve": round(1e3 * dts[name] / nsolve, 2),
+                     "iters": [r[0] for r in res], "max_rel_resid": max(max(r[1]) for r in res)}
+    out["c128_over_mixed"] = round(dts["c128"] / max(dts["c64_fp64ir"], 1e-12), 2)
+    return out
+
+
+def compare_256(runner):
+    """The largest single solve: the 256^3 prism (x = 80, m = 1.31, aspect 1,
+    +z incidence, x-polarised; 16.7M voxels, 50M unknown slots), GMRES(30)
+    in complex64 inside FP64 refinement, 3-level preconditioner, to 1e-6:
+    build and solve time, iterations, workspace."""
+    import torch
+    from dda_inputs import prism_case
+    dda = runner.dda
+    case = prism_case(256, 80.0, 1.31, 1.0)
+    mask = torch.from_numpy(case.mask()).to(runner.dev)
+    ws = dda.workspace_size(256, 256, 256, case.dx, case.k, 1, 1, 30)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = dda.Plan(mask, case.eps, case.dx, case.k, max_rhs=1, krylov_m=30)
+    plan.set_incidence(case.dirs, case.pols)
+    plan.precond_build()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    r = plan.solve(tol=1e-6, restart=30, max_iters=1500, precond=3, inner_prec=dda.C64,
+                   inner_tol=1e-4, reorth_eta=REORTH_ETA, raise_on_error=False, timeout_ms=120000)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    xs = plan.cross_sections(r.x)[0]
+    out = {"scatterer_voxels": int(mask.count_nonzero()), "setup_ms": round(1e3 * (t1 - t0), 1),
+           "solve_ms": round(1e3 * (t2 - t1), 1), "iters": r.iters[0], "cycles": r.cycles[0],
+           "converged": bool(r.converged[0]), "rel_resid": r.rel_resid[0],
+           "c_ext_abs_sca": [float(v) for v in xs], "workspace_gb": round(ws / 1e9, 2),
+           "one_graph_launch": r.graph}
+    del plan, mask
+    torch.cuda.empty_cache()
+    return out
+
+
+def compare_uneven_batch(runner, cap=600):
+    """An uneven batch: 32 prisms with edges N ~ U{24..96} (seed 2), x = 0.3 N
+    (k dx = 0.6), m ~ U[1.3, 1.8] + i U[0, 0.1], aspect 1, +z incidence, each
+    air-padded to its power-of-two box (64^3 or 128^3), 3-level
+    preconditioner, GMRES(50) complex64 + FP64 refinement to 1e-6, at most
+    `cap` iterations: all 32 solves in one graph launch (dda_solve_many)."""
+    import torch
+    from dda_inputs import uneven_batch_cases
+    dda = runner.dda
+    cases = uneven_batch_cases(32, seed=2)
+    plans = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c in cases:
+        pl = dda.Plan(torch.from_numpy(c.mask()).to(runner.dev), c.eps, c.dx, c.k, max_rhs=1,
+                      krylov_m=50)
+        pl.set_incidence(c.dirs, c.pols)
+        pl.precond_build()
+        plans.append(pl)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    kw = dict(tol=1e-6, restart=50, max_iters=cap, precond=3, reorth_eta=REORTH_ETA,
+              raise_on_error=False, inner_prec=dda.C64, inner_tol=1e-4)
+    res = dda.solve_many(plans, **kw)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    res = dda.solve_many(plans, **kw)  # the captured batch graph again
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    out = {"prisms (N, box edge, m)": [[c.N, c.dims[0], f"{complex(c.eps[0]) ** 0.5:.3f}"]
+                                       for c in cases],
+           "setup_ms": round(1e3 * (t1 - t0), 1),
+           "first_solve_ms (capture included)": round(1e3 * (t2 - t1), 1),
+           "solve_ms": round(1e3 * (t3 - t2), 1), "ms_per_solve": round(1e3 * (t3 - t2) / 32, 2),
+           "iters": [r.iters[0] for r in res], "converged": sum(r.converged[0] for r in res),
+           "one_graph_launch": all(r.graph for r in res)}
+    del plans
+    torch.cuda.empty_cache()
+    return out
+
+
+def twin_golden():
+    """The oracle's FP64 cross sections of the 32^3 twin, stored by
+    oracle/twin_values.py (read as text)."""
+    vals = {}
+    path = os.path.join(ROOT, "tests", "golden", "config3_twin32_oracle.txt")
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            f = line.split()
+            vals[f[0]] = [float(v) for v in f[1:]]
+    return vals
+
+
+def compare_twin(runner):
+    """The 32^3 twin of the 128^3 precision workload (x = 10, m = 1.31 + 0.01i,
+    k dx = 0.625): complex64 + FP64 refinement to 1e-6, C_ext and C_sca
+    against the oracle's FP64 values."""
+    from dda_inputs import prism_case
+    import torch
+    dda = runner.dda
+    case = prism_case(32, 10.0, 1.31 + 0.01j, 1.0)
+    plan = dda.Plan(torch.from_numpy(case.mask()).to(runner.dev), case.eps, case.dx, case.k,
+                    max_rhs=1, krylov_m=50)
+    plan.set_incidence(case.dirs, case.pols)
+    plan.precond_build()
+    r = plan.solve(tol=1e-6, restart=50, precond=3, inner_prec=dda.C64, inner_tol=1e-4,
+                   reorth_eta=REORTH_ETA, max_iters=2000)
+    got = plan.cross_sections(r.x)[0]
+    want = twin_golden()
+    return {"iters": r.iters[0], "rel_resid": r.rel_resid[0],
+            "c_ext_rel_err_vs_oracle": float(abs(got[0] - want["c_ext"][0]) / abs(want["c_ext"][0])),
+            "c_sca_rel_err_vs_oracle": float(abs(got[2] - want["c_sca"][0]) / abs(want["c_sca"][0]))}
+
+
+def roofline_128(runner, peak, peak_kind):
+    """The matvec's passes at the 128^3 box (1 RHS, complex64), back to back
+    (CUDA events per launch): algorithmic bytes / time per pass, and the whole
+    matvec's 87u model bytes over its time."""
+    import torch
+    from dda_inputs import prism_case
+    dda = runner.dda
+    case = prism_case(128, 40.0, 1.31 + 0.01j, 1.0)
+    plan = dda.Plan(torch.from_numpy(case.mask()).to(runner.dev), case.eps, case.dx, case.k,
+                    max_rhs=1)
+    plan.set_incidence(case.dirs, case.pols)
+    x = plan.incident_field(1).to(torch.complex64)
+    y = torch.empty_like(x)
+    for _ in range(3):
+        plan.matvec(x, out=y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        plan.matvec(x, out=y)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    plan.profile(True)
+    plan.profile_read()
+    for _ in range(reps):
+        plan.matvec(x, out=y)
+    prof = plan.profile_read()
+    plan.profile(False)
+    u = 8 * 128 ** 3
+    passes = {k: {"us_per_launch": round(1e3 * v[0] / v[1], 1),
+                  "achieved_GBs": round(v[2] / (v[0] * 1e-3) / 1e9, 1),
+                  "frac": round(v[2] / (v[0] * 1e-3) / 1e9 / peak, 3)}
+              for k, v in prof.items() if v[1] > 0}
+    del plan
+    torch.cuda.empty_cache()
+    return {"matvec_us": round(1e3 * ms, 1), "model_bytes_87u": 87 * u,
+            "matvec_frac_87u": round(87 * u / (ms * 1e-3) / 1e9 / peak, 3),
+            "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs", "passes": passes}
 
 
 def oracle_iterations():
@@ -534,21 +759,91 @@ def oracle_ms_per_solve(cases, per_box, its_table, fallback_its):
     return total / nsolve
 
 
-def cpu_baseline(gpu_iters):
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu model")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def _oracle_box_worker(dims):
+    """One process of the all-cores sample: the oracle's setup and one
+    preconditioned iteration for the first system of that box size."""
+    cases = [c for c in workload_cases() if c.dims == tuple(dims)]
+    return tuple(dims), oracle_sample(cases[:1])[tuple(dims)]
+
+
+def oracle_all_cores(cases, cores, boxes=None):
+    """The same sample on every host core at once: `cores` independent
+    oracle processes (spawned, one BLAS / FFT thread each), the box sizes
+    (all of the workload's, or `boxes`) dealt round robin; per box the median
+    of the timings taken under that load."""
+    import multiprocessing as mp
+    boxes = sorted({c.dims for c in cases}) if boxes is None else list(boxes)
+    jobs = [boxes[i % len(boxes)] for i in range(max(cores, len(boxes)))]
+    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {k: os.environ.get(k) for k in env_keys}
+    for k in env_keys:
+        os.environ[k] = "1"
+    try:
+        with mp.get_context("spawn").Pool(cores) as pool:
+            res = pool.map(_oracle_box_worker, jobs)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    per_box = {}
+    for dims in boxes:
+        got = sorted((r[1] for r in res if r[0] == dims), key=lambda t: t[0] + 50 * t[1])
+        per_box[dims] = got[len(got) // 2]
+    return per_box
+
+
+def cpu_baseline(gpu_iters, all_cores=True):
     """The oracle on a bounded sample: per box size, spectrum + preconditioner
     setup and one preconditioned GMRES iteration, extrapolated to every
-    system with the oracle's own iteration count for it."""
+    system with the oracle's own iteration count for it; timed on one core
+    (one process) and on every host core (that many processes, each solving
+    its own system: the throughput figure divides by the core count)."""
     cases = workload_cases()
+    table = oracle_iterations()
     t_all = time.perf_counter()
     per_box = oracle_sample(cases)
-    table = oracle_iterations()
-    value = oracle_ms_per_solve(cases, per_box, table, gpu_iters)
+    one = oracle_ms_per_solve(cases, per_box, table, gpu_iters)
+    t_one = time.perf_counter() - t_all
+    cores = os.cpu_count() or 1
+    out = {"unit": UNIT, "kind": "oracle", "cpu_model": cpu_model(),
+           "one_core": {"value": round(one, 1), "cores": 1,
+                        "sample": f"{t_one:.1f} s of CPU work in one process"}}
+    value, used = one, 1
+    if all_cores and cores > 1:
+        t0 = time.perf_counter()
+        loaded = oracle_all_cores(cases, cores)
+        many = oracle_ms_per_solve(cases, loaded, table, gpu_iters) / cores
+        out["all_cores"] = {"value": round(many, 1), "cores": cores,
+                            "sample": (f"{cores} concurrent oracle processes, "
+                                       f"{time.perf_counter() - t0:.1f} s wall")}
+        value, used = many, cores
     src = "the oracle's own GMRES(50) counts" if table else "the GPU solve's counts"
-    return {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": ("numpy/scipy FP64 oracle (numpy.fft is single-threaded), per box size: "
-                       "kernel spectrum + 3-level preconditioner setup + 1 preconditioned GMRES "
-                       f"iteration, extrapolated to each system with {src}; "
-                       f"{time.perf_counter() - t_all:.1f} s of CPU work")}
+    out.update({"value": round(value, 1), "cores": used,
+                "sample": ("numpy/scipy FP64 oracle (numpy.fft single-threaded), per box size: "
+                           "kernel spectrum + 3-level preconditioner setup + 1 preconditioned GMRES "
+                           f"iteration, extrapolated to each system with {src}; value = the "
+                           f"{'all-cores throughput' if used > 1 else 'one-core time'} per solve")})
+    return out
 
 
 def max_over_ranks(ms, world, device):
@@ -628,22 +923,33 @@ def run_ours(args, rank, world):
 
     peak, peak_kind = read_peak()
     roof = roofline(runner, peak, peak_kind)
-    comparisons = compare_solvers(runner) if not args.no_compare else None
-    if comparisons is not None:
-        try:
-            comparisons["matvec_vs_cufft (2 RHS, ms per matvec)"] = compare_fft(runner)
-        except Exception as exc:  # a side measurement must not cost the bench line
-            comparisons["matvec_vs_cufft (2 RHS, ms per matvec)"] = {"error": repr(exc)[:200]}
-        key2 = "timed-step systems with the 2-level preconditioner (wall time, untimed step)"
-        try:
-            comparisons[key2] = compare_sweep_2level(runner)
-        except Exception as exc:
-            comparisons[key2] = {"error": repr(exc)[:200]}
-        key128 = "128^3 x=40 m=1.31+0.01i: complex64 + FP64 refinement vs complex128"
-        try:
-            comparisons[key128] = compare_precision_128(runner)
-        except Exception as exc:
-            comparisons[key128] = {"error": repr(exc)[:200]}
+    roof128 = None
+    try:
+        roof128 = roofline_128(runner, peak, peak_kind)
+    except Exception as exc:  # a side measurement must not cost the bench line
+        roof128 = {"error": repr(exc)[:200]}
+    comparisons = None
+    if not args.no_compare:
+        comparisons = {}
+        for key, fn in (
+                ("solver variants, 64^3 prisms", lambda: compare_solvers(runner)),
+                ("preconditioned vs unpreconditioned per system (GMRES(50) c64+IR)",
+                 lambda: compare_policy(runner)),
+                ("FP64 vs mixed on the timed workload (wall time, untimed step)",
+                 lambda: compare_precision_sweep(runner)),
+                ("m=1.78 systems to the paper's iteration caps (no convergence)",
+                 lambda: compare_m178(runner)),
+                ("matvec_vs_cufft (2 RHS, ms per matvec)", lambda: compare_fft(runner)),
+                ("128^3 x=40 m=1.31+0.01i: complex64 + FP64 refinement vs complex128",
+                 lambda: compare_precision_128(runner)),
+                ("32^3 twin (x=10, m=1.31+0.01i) vs the FP64 oracle", lambda: compare_twin(runner)),
+                ("256^3 x=80 m=1.31 GMRES(30) c64+IR", lambda: compare_256(runner)),
+                ("uneven batch: 32 prisms N~U{24..96}, one graph launch",
+                 lambda: compare_uneven_batch(runner))):
+            try:
+                comparisons[key] = fn()
+            except Exception as exc:  # a side measurement must not cost the bench line
+                comparisons[key] = {"error": repr(exc)[:300]}
     if rank != 0:
         return
     value = whole_job_ms_per_solve(total_ms, args.steps, nsolve, world)
@@ -662,6 +968,7 @@ def run_ours(args, rank, world):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": int(launches),
         "roofline": roof,
+        "roofline_128cube_matvec": roof128,
         "clocks": clk.summary(),
     }
     if comparisons is not None:
@@ -672,29 +979,35 @@ def run_ours(args, rank, world):
 
 
 def run_reference(args, rank, world):
-    """The oracle as the reference arm, on bounded samples of the same workload:
-    each step times one box size's setup and one preconditioned iteration and
-    extrapolates the whole sweep with the oracle's own iteration counts."""
+    """The oracle as the reference arm, on bounded samples of the same workload
+    on every host core: each step runs one oracle process per core (box
+    sizes round robin: setup and one preconditioned iteration each) and the
+    sweep is extrapolated with the oracle's own iteration counts; the value
+    is the all-cores throughput per solve."""
     if rank != 0:
         return
     cases = workload_cases()
-    boxes = sorted({c.dims for c in cases})
     table = oracle_iterations()
     fallback = [[50] * c.nrhs for c in cases]
+    cores = os.cpu_count() or 1
+    boxes = sorted({c.dims for c in cases})
     samples = {}
     for i in range(args.warmup + args.steps):
-        dims = boxes[i % len(boxes)]
-        per = oracle_sample([c for c in cases if c.dims == dims])
+        dims = boxes[i % len(boxes)]  # one box size per step, on every core
+        per = oracle_all_cores(cases, cores, [dims])
         if i >= args.warmup or dims not in samples:
-            samples[dims] = per[dims]
+            samples.setdefault(dims, []).append(per[dims])
     for dims in boxes:
         if dims not in samples:
-            samples.update(oracle_sample([c for c in cases if c.dims == dims]))
-    value = oracle_ms_per_solve(cases, samples, table, fallback)
-    cpu = {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
-           "sample": ("per step one box size: kernel spectrum + preconditioner setup and one "
-                      "preconditioned GMRES iteration; sweep extrapolated with the oracle's "
-                      "own GMRES(50) iteration counts")}
+            samples[dims] = [oracle_all_cores(cases, cores, [dims])[dims]]
+    med = {k: sorted(v, key=lambda t: t[0] + 50 * t[1])[len(v) // 2] for k, v in samples.items()}
+    value = oracle_ms_per_solve(cases, med, table, fallback) / cores
+    cpu = {"value": round(value, 1), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "cpu_model": cpu_model(),
+           "sample": (f"per step {cores} concurrent oracle processes (one per core) on one "
+                      "box size (round robin): kernel spectrum + preconditioner setup and one "
+                      "preconditioned GMRES iteration each; sweep extrapolated with the oracle's own GMRES(50) "
+                      "iteration counts; value = all-cores throughput per solve")}
     print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT,
                       "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                       "higher_is_better": False, "scaling": "weak", "vs_baseline": None,

@@ -28,7 +28,8 @@ import numpy as np
 __all__ = [
     "voxel_centres", "hex_prism_mask", "sphere_mask", "prism_box",
     "random_direction", "polarisations", "random_field", "PrismCase",
-    "small_prism_case", "prism_case", "config2_cases", "pad_box",
+    "small_prism_case", "prism_case", "config2_cases", "pad_box", "next_pow2",
+    "uneven_batch_cases",
 ]
 
 
@@ -124,9 +125,11 @@ class PrismCase:
     dirs: list = field(default_factory=lambda: [np.array([0.0, 0.0, 1.0])])
     pols: list = field(default_factory=lambda: [np.array([1.0, 0.0, 0.0])])
 
+    box: tuple | None = None    # (l, m, n) air-padded box; None: the prism's own box
+
     @property
     def dims(self) -> tuple[int, int, int]:
-        return prism_box(self.N, self.aspect)
+        return tuple(self.box) if self.box is not None else prism_box(self.N, self.aspect)
 
     @property
     def dx(self) -> float:
@@ -173,4 +176,31 @@ def config2_cases(N: int = 64, size_param: float = 20.0, seed: int = 0):
         for aspect in (0.5, 1.0, 2.0):
             cases.append(prism_case(N, size_param, m_index, aspect,
                                     dirs=[d, d], pols=[e1, e2]))
+    return cases
+
+
+def next_pow2(v: int) -> int:
+    """Smallest power of two >= v."""
+    p = 1
+    while p < v:
+        p *= 2
+    return p
+
+
+def uneven_batch_cases(count: int = 32, seed: int = 2, kd: float = 0.6, pad_pow2: bool = True):
+    """An uneven batch of prisms: edges N_i drawn uniformly from 24..96, size
+    parameter x_i = kd N_i / 2 (voxel size k dx = kd), refractive index
+    U[1.3, 1.8] + i U[0, 0.1], aspect 1, +z incidence, x-polarised.  With
+    pad_pow2 each prism sits centred in the power-of-two box that holds it
+    (air padding)."""
+    rng = np.random.default_rng(seed)
+    cases = []
+    for _ in range(count):
+        N = int(rng.integers(24, 97))
+        m_index = complex(rng.uniform(1.3, 1.8), rng.uniform(0.0, 0.1))
+        c = prism_case(N, kd * N / 2.0, m_index, 1.0)
+        if pad_pow2:
+            L = next_pow2(N)
+            c.box = (L, L, L)
+        cases.append(c)
     return cases

@@ -65,9 +65,14 @@ def test_cufft_comparison_runs_on_cpu():
 
 class _FakeRes:
     def __init__(self, nrhs):
+        import numpy as np
         self.iters = [3] * nrhs
+        self.cycles = [1] * nrhs
         self.converged = [True] * nrhs
         self.rel_resid = [1e-7] * nrhs
+        self.history = [np.array([1.0, 1e-3, 1e-7])] * nrhs
+        self.graph = True
+        self.status = 0
         self.x = None
 
 
@@ -89,8 +94,14 @@ class _FakePlan:
         assert self.precond2
 
     def solve(self, **kw):
-        assert kw["precond"] in (2, 3) and (kw["precond"] == 3 or self.precond2)
+        assert kw["precond"] in (0, 2, 3) and (kw["precond"] != 2 or self.precond2)
         return _FakeRes(self.nrhs)
+
+    def profile(self, on=True):
+        pass
+
+    def profile_read(self):
+        return {"mv_z_mul": (1.0, 2, 1e9), "mv_x_fwd": (0.5, 2, 4e8)}
 
     def cross_sections(self, x):
         import numpy as np
@@ -126,7 +137,10 @@ def test_side_comparisons_run_with_a_stand_in_library(monkeypatch):
     import numpy as np
     import torch
     from paper_1903_09802_gb300 import dda as real
-    fake = SimpleNamespace(Plan=_FakePlan, C64=real.C64, C128=real.C128)
+    fake = SimpleNamespace(Plan=_FakePlan, C64=real.C64, C128=real.C128, STATUS=real.STATUS,
+                           precond_for=real.precond_for, BICGSTAB=real.BICGSTAB,
+                           workspace_size=lambda *a, **k: 123,
+                           solve_many=lambda plans, **kw: [_FakeRes(1) for _ in plans])
     monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
     monkeypatch.setattr(torch.cuda, "Event", _FakeEvent)
     monkeypatch.setattr(torch.cuda, "empty_cache", lambda: None)
@@ -136,9 +150,27 @@ def test_side_comparisons_run_with_a_stand_in_library(monkeypatch):
                              pols=[np.array([1.0, 0, 0]), np.array([0, 1.0, 0])])]
     runner = SimpleNamespace(dda=fake, cases=cases, masks=[torch.zeros((2, 4, 4), dtype=torch.uint8)],
                              dev="cpu")
-    sweep = bench.compare_sweep_2level(runner)
-    assert sweep["2level_auto"]["all systems ms_per_solve"] >= 0
-    assert "4x4x2 m=1.31+0.00j" in sweep["3level"]
+    pol = bench.compare_policy(runner)
+    row = pol["4x4x2 m=1.31+0.00j"]
+    assert row["policy"] == "2-level" and row["none"]["ms_per_solve_with_setup"] >= 0
+    assert isinstance(row["policy_beats_none"], bool)
+
+    def step(inner="c64", **kw):
+        return [([3, 3], [1e-7, 1e-7], None)]
+    runner.step = step
+    ps = bench.compare_precision_sweep(runner)
+    assert ps["c128"]["max_rel_resid"] == 1e-7 and ps["c128_over_mixed"] > 0
+    m178 = bench.compare_m178(runner)
+    assert len(m178) == 3 and all(v["gmres_none"]["min_rel_resid"] == [1e-7, 1e-7]
+                                  for v in m178.values())
+    monkeypatch.setattr(_FakePlan, "cross_sections",
+                        lambda self, x: np.tile([6.029132679, 1.38, 4.646511536], (1, 1)))
+    tw = bench.compare_twin(runner)
+    assert tw["c_ext_rel_err_vs_oracle"] < 1e-8 and tw["c_sca_rel_err_vs_oracle"] < 1e-8
+    r128 = bench.roofline_128(runner, 1000.0, "measured")
+    assert r128["passes"]["mv_z_mul"]["us_per_launch"] == 500.0
+    ub = bench.compare_uneven_batch(runner, cap=5)
+    assert ub["converged"] == 32 and len(ub["prisms (N, box edge, m)"]) == 32
     fft = bench.compare_fft(runner, reps=2)
     assert fft["4x4x2"]["speedup"] == 4.0  # 2 ms against 1 ms over 2 calls
     p128 = bench.compare_precision_128(runner)

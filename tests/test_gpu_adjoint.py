@@ -110,9 +110,9 @@ def test_voxel_eps_operator_solve_and_gradient_vs_oracle():
     adjoint gradient with a different permittivity in every voxel, against the
     oracle with one material per voxel."""
     dda = dda_module()
-    l = m = n = 6
+    l, m, n = 8, 8, 4
     dx, k = 0.3, 2.0
-    mat = hex_prism_mask(l, m, n, dx, 0.85, 1.8)
+    mat = hex_prism_mask(l, m, n, dx, 1.15, 1.2)
     rng = np.random.default_rng(21)
     eps_vox = ((1.4 + 0.03j) + 0.25 * rng.standard_normal(mat.shape)
                + 0.03j * rng.random(mat.shape)) ** 2

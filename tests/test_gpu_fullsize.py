@@ -98,7 +98,9 @@ def test_matvec_256cube_complex_symmetry():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("idx", [1, 4])  # 64^3 prisms: m = 1.31 and m = 1.31 + 0.05i
+# the six converging systems of the 64^3 sweep: m = 1.31 (0-2) and
+# m = 1.31 + 0.05i (3-5), aspects 0.5, 1, 2 (boxes 64x64x32, 64^3, 64x64x128)
+@pytest.mark.parametrize("idx", [0, 1, 2, 3, 4, 5])
 def test_solve_bench_configuration(idx):
     dda = dda_module()
     case = config2_cases()[idx]
@@ -121,3 +123,33 @@ def test_solve_bench_configuration(idx):
         prob = from_case(case, r)
         want = np.array(prob.cross_sections(xs[r]))
         assert np.abs(got[r] - want).max() <= 1e-9 * abs(want[0])
+
+
+def _twin_golden():
+    vals = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "config3_twin32_oracle.txt")):
+        if line.strip() and not line.startswith("#"):
+            f = line.split()
+            vals[f[0]] = [float(v) for v in f[1:]]
+    return vals
+
+
+@pytest.mark.gpu
+@pytest.mark.late(1)
+def test_config3_twin_mixed_precision_vs_oracle():
+    """The 32^3 twin of the 128^3 precision workload (x = 10, k dx = 0.625,
+    m = 1.31 + 0.01i): complex64 GMRES cycles inside FP64 refinement to 1e-6,
+    C_ext and C_sca against the oracle's FP64 solve (to 1e-12, stored by
+    oracle/twin_values.py): relative error <= 1e-5."""
+    dda = dda_module()
+    case = prism_case(32, 10.0, 1.31 + 0.01j, 1.0)
+    want = _twin_golden()
+    assert int(want["box"][3]) == int((case.mask() > 0).sum())
+    plan = _plan(dda, case, krylov_m=50)
+    plan.precond_build()
+    res = plan.solve(tol=1e-6, restart=50, precond=3, inner_prec=dda.C64, inner_tol=1e-4,
+                     max_iters=2000, reorth_eta=0.1, nrhs=1)
+    assert res.converged[0]
+    got = plan.cross_sections(res.x)[0]
+    for i, name in ((0, "c_ext"), (2, "c_sca")):
+        assert abs(got[i] - want[name][0]) <= 1e-5 * abs(want[name][0]), (name, got[i], want[name])

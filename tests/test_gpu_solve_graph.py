@@ -13,7 +13,9 @@ from oracle.problem import from_case
 @pytest.fixture(scope="module")
 def setup16():
     dda = dda_module()
-    case = prism_case(16, 5.0, 1.31, 1.0)
+    d2 = np.array([0.3, -0.5, 0.8]) / np.linalg.norm([0.3, -0.5, 0.8])
+    e2 = np.cross(d2, [0.0, 0.0, 1.0]) / np.linalg.norm(np.cross(d2, [0.0, 0.0, 1.0]))
+    case = prism_case(16, 5.0, 1.31, 1.0, dirs=[[0.0, 0.0, 1.0], d2], pols=[[1.0, 0.0, 0.0], e2])
     prob = from_case(case)
     plan = dda.Plan(to_dev(case.mask(), torch.uint8), case.eps, case.dx, case.k, max_rhs=2,
                     krylov_m=50, precond2=True)

@@ -636,6 +636,57 @@ def compare_uneven_batch(runner, cap=600):
     return out
 
 
+def compare_many_waves(runner, nwaves_dirs=64, restart=20, chunk=8, cap=1500):
+    """Many incident waves of one prism in one graph launch: the 96^3 prism
+    (x = 30, m = 1.31, aspect 1) with 64 seeded directions (seed 1) x 2
+    polarisations = 128 right-hand sides advancing in lock step, GMRES(20)
+    complex64 + FP64 refinement, 3-level preconditioner, to 1e-6.  Box edges
+    are powers of two here, so the prism sits in a 128^3 box (air padded);
+    the FFT scratch holds 8 right-hand sides (rhs_chunk) and the batch passes
+    through the transforms in chunks of 8.  Reports the total and per-wave
+    time, iterations, the workspace (Krylov basis in complex64:
+    krylov_c64), and C_ext of the first waves."""
+    import torch
+    from dda_inputs import polarisations, prism_case, random_direction
+    dda = runner.dda
+    torch.cuda.empty_cache()
+    rng = np.random.default_rng(1)
+    dirs, pols = [], []
+    for _ in range(nwaves_dirs):
+        d = random_direction(rng)
+        for e in polarisations(d):
+            dirs.append(d)
+            pols.append(e)
+    case = prism_case(96, 30.0, 1.31, 1.0, dirs=dirs, pols=pols)
+    case.box = (128, 128, 128)
+    nrhs = len(dirs)
+    ws = dda.workspace_size(128, 128, 128, case.dx, case.k, 1, nrhs, restart, rhs_chunk=chunk,
+                            krylov_c64=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = dda.Plan(torch.from_numpy(case.mask()).to(runner.dev), case.eps, case.dx, case.k,
+                    max_rhs=nrhs, krylov_m=restart, rhs_chunk=chunk, krylov_c64=True)
+    plan.set_incidence(dirs, pols)
+    plan.precond_build()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    r = plan.solve(tol=1e-6, restart=restart, max_iters=cap, precond=3, inner_prec=dda.C64,
+                   inner_tol=1e-4, reorth_eta=REORTH_ETA, raise_on_error=False)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    xs = plan.cross_sections(r.x)
+    out = {"waves": nrhs, "box": "128^3 (96^3 prism, air padded)", "rhs_chunk": chunk,
+           "workspace_gb": round(ws / 1e9, 1), "setup_ms": round(1e3 * (t1 - t0), 1),
+           "solve_ms": round(1e3 * (t2 - t1), 1),
+           "ms_per_wave": round(1e3 * (t2 - t1) / nrhs, 2),
+           "iters_min_max": [min(r.iters), max(r.iters)], "converged": int(sum(r.converged)),
+           "max_rel_resid": max(r.rel_resid), "one_graph_launch": r.graph,
+           "c_ext_first_4": [float(v) for v in xs[:4, 0]]}
+    del plan, r
+    torch.cuda.empty_cache()
+    return out
+
+
 def twin_golden():
     """The oracle's FP64 cross sections of the 32^3 twin, stored by
     oracle/twin_values.py (read as text)."""
@@ -945,7 +996,9 @@ def run_ours(args, rank, world):
                 ("32^3 twin (x=10, m=1.31+0.01i) vs the FP64 oracle", lambda: compare_twin(runner)),
                 ("256^3 x=80 m=1.31 GMRES(30) c64+IR", lambda: compare_256(runner)),
                 ("uneven batch: 32 prisms N~U{24..96}, one graph launch",
-                 lambda: compare_uneven_batch(runner))):
+                 lambda: compare_uneven_batch(runner)),
+                ("128 waves of the 96^3 prism (x=30, m=1.31), one graph launch",
+                 lambda: compare_many_waves(runner))):
             try:
                 comparisons[key] = fn()
             except Exception as exc:  # a side measurement must not cost the bench line

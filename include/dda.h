@@ -87,6 +87,12 @@ typedef struct {
                             at p = L/2 of an even level the mean of t_{L/2}, t_{-L/2}) */
   int32_t voxel_eps;     /* 1: reserve a permittivity per voxel (dda_set_voxel_eps):
                             (16 + max_rhs * 40) bytes per voxel                      */
+  int32_t rhs_chunk;     /* right-hand sides the FFT scratch holds (0: max_rhs); larger
+                            batches pass through the transforms in chunks of it, so a
+                            batch of many waves needs scratch for rhs_chunk only      */
+  int32_t krylov_c64;    /* 1: the Krylov basis and step vectors are reserved in
+                            complex64 (solves with inner_prec = DDA_C64 only), half
+                            the memory of the complex128 reservation                  */
 } dda_plan_desc_t;
 
 /* Plane wave E_inc = pol * exp(i k dir . r), r measured from the box centre.

@@ -58,6 +58,10 @@ bool valid_desc(const dda_plan_desc_t& d, std::string& why, dda_status_t& st) {
     return why = "precond2 must be 0 (none) or 1, 2, 3 (Toeplitz level z, x, y)", false;
   if (d.circulant != 0 && d.circulant != 1) return why = "circulant must be 0 (Chan) or 1 (Strang)", false;
   if (d.voxel_eps != 0 && d.voxel_eps != 1) return why = "voxel_eps must be 0 or 1", false;
+  if (d.rhs_chunk < 0) return why = "rhs_chunk must be >= 0", false;
+  if (d.krylov_c64 != 0 && d.krylov_c64 != 1) return why = "krylov_c64 must be 0 or 1", false;
+  if (d.krylov_c64 && !(d.precisions & DDA_PLAN_C64))
+    return why = "krylov_c64 needs a plan holding complex64 data", false;
   if ((d.precisions & (DDA_PLAN_C128 | DDA_PLAN_C64)) == 0 ||
       (d.precisions & ~(DDA_PLAN_C128 | DDA_PLAN_C64)) != 0)
     return why = "precisions must be a non-empty set of DDA_PLAN_C128 | DDA_PLAN_C64", false;
@@ -107,8 +111,13 @@ bool make_layout(const dda_plan_desc_t& d, void* ws, Layout& L, std::string& why
     if (h128) L.pvdf = c.take(16 * R * nvox);
   }
   L.dainv128 = c.take(R * K1 * 16);
-  L.buf1 = c.take(esz * R * 3 * n * m * Lx);
-  size_t b2 = esz * R * 3 * n * Ly * Lx;
+  // FFT scratch for one chunk of right-hand sides
+  const long RC = d.rhs_chunk > 0 ? std::min<long>(d.rhs_chunk, R) : R;
+  // (its head also holds the cross sections' block sums: 4 doubles per block
+  // of at most 304, per right-hand side)
+  const size_t xsec = (size_t)32 * std::min<long>(304, std::max<long>(1, (nvox + 4095) / 4096)) * R;
+  L.buf1 = c.take(std::max<size_t>(esz * RC * 3 * n * m * Lx, xsec));
+  size_t b2 = esz * RC * 3 * n * Ly * Lx;
   b2 = std::max(b2, (size_t)P * 16);     // Green-function spectrum build (complex128)
   b2 = std::max(b2, (size_t)nvox * 96);  // circulant build: six complex128 components
   L.buf2 = c.take(b2);
@@ -129,9 +138,12 @@ bool make_layout(const dda_plan_desc_t& d, void* ws, Layout& L, std::string& why
     // Gram-Schmidt reduction blocks per right-hand side: at most one wave of
     // 3 blocks x 152 SMs, chunks of at least 512 values
     L.nblk = (int)std::min<long>(456, std::max<long>(1, (nu + 511) / 512));
-    L.V = c.take(esz * (mk + 1) * R * nu);
-    L.Wv = c.take(esz * R * nu);
-    L.Zv = c.take(esz * R * nu);
+    // basis and step vectors in the inner precision: complex64 only when the
+    // plan is limited to complex64 cycles (krylov_c64)
+    const size_t vsz = d.krylov_c64 ? 8 : esz;
+    L.V = c.take(vsz * (mk + 1) * R * nu);
+    L.Wv = c.take(vsz * R * nu);
+    L.Zv = c.take(vsz * R * nu);
     L.B128 = c.take(16 * R * nu);
     SolverState& s = L.st;
     s.H = static_cast<double2*>(c.take(16 * R * (mk + 1) * mk));
@@ -392,6 +404,7 @@ extern "C" dda_status_t dda_plan_create(dda_plan_t* out, const dda_plan_desc_t* 
   p->cy_ = p->m / 2 + 1;
   p->cz_ = p->n / 2 + 1;
   p->K = desc->n_materials;
+  p->rhs_chunk = desc->rhs_chunk > 0 ? std::min(desc->rhs_chunk, desc->max_rhs) : desc->max_rhs;
   p->mat = d_mat;
   p->eps.assign(h_eps, h_eps + 2 * desc->n_materials);
   p->w = L;

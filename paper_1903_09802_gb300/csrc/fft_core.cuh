@@ -23,34 +23,43 @@ void note_launch();
 
 constexpr int kElemsPerThread = 16;
 
-// cos(2 pi j / 16), j = 0..4.
-constexpr double kCos16[5] = {1.0, 0.92387953251128675613, 0.70710678118654752440,
-                              0.38268343236508977173, 0.0};
+// cos(2 pi j / 32), j = 0..8 (plain trigonometry: cos(pi j / 16)).
+constexpr double kCos32[9] = {1.0,
+                              0.98078528040323044913,
+                              0.92387953251128675613,
+                              0.83146961230254523708,
+                              0.70710678118654752440,
+                              0.55557023301960222474,
+                              0.38268343236508977173,
+                              0.19509032201612826785,
+                              0.0};
 
-__host__ __device__ constexpr double cos16(int j) {
-  return ((j & 15) <= 4)    ? kCos16[j & 15]
-         : ((j & 15) <= 8)  ? -kCos16[8 - (j & 15)]
-         : ((j & 15) <= 12) ? -kCos16[(j & 15) - 8]
-                            : kCos16[16 - (j & 15)];
+// cos(2 pi j / 32) for any j, by the quarter-wave symmetries.
+__host__ __device__ constexpr double cos32(int j) {
+  return ((j & 31) <= 8)    ? kCos32[j & 31]
+         : ((j & 31) <= 16) ? -kCos32[16 - (j & 31)]
+         : ((j & 31) <= 24) ? -kCos32[(j & 31) - 16]
+                            : kCos32[32 - (j & 31)];
 }
 // sin(x) = cos(x - pi/2)
-__host__ __device__ constexpr double sin16(int j) { return cos16(j - 4); }
+__host__ __device__ constexpr double sin32(int j) { return cos32(j - 8); }
 
-// a * exp(-+ 2 pi i Q / R) (minus sign forward, plus sign inverse), R | 16.
+// a * exp(-+ 2 pi i Q / R) (minus sign forward, plus sign inverse), R | 32.
 template <int R, int Q, bool INV, typename T>
 __device__ __forceinline__ cx<T> twc(cx<T> a) {
-  constexpr int j = (Q * (16 / R)) & 15;
+  static_assert(32 % R == 0, "radix up to 32");
+  constexpr int j = (Q * (32 / R)) & 31;
   if constexpr (j == 0) {
     return a;
-  } else if constexpr (j == 4) {
-    return INV ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
   } else if constexpr (j == 8) {
+    return INV ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x);
+  } else if constexpr (j == 16) {
     return mk<T>(-a.x, -a.y);
-  } else if constexpr (j == 12) {
+  } else if constexpr (j == 24) {
     return INV ? mk<T>(a.y, -a.x) : mk<T>(-a.y, a.x);
   } else {
-    constexpr T c = (T)cos16(j);
-    constexpr T s = INV ? (T)sin16(j) : -(T)sin16(j);
+    constexpr T c = (T)cos32(j);
+    constexpr T s = INV ? (T)sin32(j) : -(T)sin32(j);
     return mk<T>(a.x * c - a.y * s, a.x * s + a.y * c);
   }
 }

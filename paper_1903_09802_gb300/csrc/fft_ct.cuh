@@ -172,17 +172,27 @@ __global__ void __launch_bounds__(NB * L / kElemsPerThread, 1024 / (NB * L / kEl
   const int j = tid & (L - 1);
   const int b0 = tid / L;
   if (!(HALF_IN && 2 * j >= L)) {
-    long line = line0 + b0;
-    long mrow = line % mask_lines;
-    const cx<T>* g = in + line * in_ld + j;
+    // the mask bytes of all 16 elements first (independent loads in
+    // flight together), then the 16 copies
+    unsigned ok = 0;
+    {
+      long line = line0 + b0;
+      long mrow = line % mask_lines;
+#pragma unroll
+      for (int i = 0; i < kElemsPerThread; ++i, line += BSTEP) {
+        bool v = line < nlines && j < Lin;
+        if (v && mask != nullptr) v = __ldg(mask + mrow * Lin + j) != 0;
+        ok |= (unsigned)v << i;
+        mrow += BSTEP;
+        if (mrow >= mask_lines) mrow = mrow >= 2 * mask_lines ? mrow % mask_lines : mrow - mask_lines;
+      }
+    }
+    const cx<T>* g = in + (line0 + b0) * in_ld + j;
     cx<T>* q = s + j * LD + b0;
-#pragma unroll 4
-    for (int i = 0; i < kElemsPerThread; ++i, line += BSTEP, g += BSTEP * in_ld, q += BSTEP) {
-      bool ok = line < nlines && j < Lin;
-      if (ok && mask != nullptr) ok = mask[mrow * Lin + j] != 0;
-      cp_async_cx(q, ok ? g : in, ok);
-      mrow += BSTEP;
-      if (mrow >= mask_lines) mrow = mrow >= 2 * mask_lines ? mrow % mask_lines : mrow - mask_lines;
+#pragma unroll
+    for (int i = 0; i < kElemsPerThread; ++i, g += BSTEP * in_ld, q += BSTEP) {
+      const bool v = (ok >> i) & 1u;
+      cp_async_cx(q, v ? g : in, v);
     }
   }
   load_twiddles(stw, tw, L, twshift);
@@ -295,11 +305,11 @@ __global__ void __launch_bounds__(3 * NBC * L / kElemsPerThread,
 // Every element crosses shared memory about 5.5 times instead of 12.  Tile:
 // NBC columns (16: 128-byte rows) x 3 components; in C-E thread tid owns
 // column b = tid % NBC, butterfly jb = tid / NBC.
-template <class Op, int L, int R1, int R2, int NBC>
-__global__ void __launch_bounds__(R1 * NBC)
-    k_rr_fft3c(cx<float>* data, long ncols, long js, long cs, long ss, Op op,
-               const cx<float>* __restrict__ tw, int twshift, int row_len, int nrows) {
-  pdl_entry();
+template <class Op, int L, int R1, int R2, int NBC, bool HALF>
+__device__ __forceinline__ void rr_fft3c_body(cx<float>* data, long ncols, long js, long cs,
+                                              long ss, const Op& op,
+                                              const cx<float>* __restrict__ tw, int twshift,
+                                              int row_len, int nrows) {
   static_assert(R1 * R2 == L, "two stages");
   using T = float;
   constexpr int NL = 3 * NBC;  // lines (component, column) of the tile
@@ -325,9 +335,10 @@ __global__ void __launch_bounds__(R1 * NBC)
     col0 = (long)tt * NBC;
   }
   cx<T>* base = data + slab * ss + col0;
+  constexpr int ROWS_IN = HALF ? H : L;  // rows loaded (the rest are zero padding)
   // A
 #pragma unroll 4
-  for (int e = tid; e < H * NL; e += NTH) {
+  for (int e = tid; e < ROWS_IN * NL; e += NTH) {
     const int j = e / NL, line = e - j * NL;
     const int c = line / NBC, b = line - c * NBC;
     cp_async_cx(s + j * LD + line, base + c * cs + (long)j * js + b, true);
@@ -336,7 +347,7 @@ __global__ void __launch_bounds__(R1 * NBC)
   load_twiddles(stw, tw, L, twshift);
   cp_async_wait_all();
   __syncthreads();
-  // B: inputs rows jb + q R2 (q < R1/2 non-zero), outputs rows jb R1 + q
+  // B: inputs rows jb + q R2 (with HALF only q < R1/2 non-zero), outputs rows jb R1 + q
   {
     cx<T> v[GB][R1];
 #pragma unroll
@@ -345,7 +356,7 @@ __global__ void __launch_bounds__(R1 * NBC)
       if (u < NBF) {
         const int jb = u / NL, line = u - jb * NL;
 #pragma unroll
-        for (int q = 0; q < R1 / 2; ++q) v[g][q] = s[(jb + q * R2) * LD + line];
+        for (int q = 0; q < (HALF ? R1 / 2 : R1); ++q) v[g][q] = s[(jb + q * R2) * LD + line];
       }
     }
     __syncthreads();
@@ -354,7 +365,10 @@ __global__ void __launch_bounds__(R1 * NBC)
       const int u = tid + g * NTH;
       if (u < NBF) {
         const int jb = u / NL, line = u - jb * NL;
-        dft_half_in<R1, false>(v[g]);
+        if constexpr (HALF)
+          dft_half_in<R1, false>(v[g]);
+        else
+          dft<R1, false>(v[g]);
 #pragma unroll
         for (int q = 0; q < R1; ++q) s[(jb * R1 + q) * LD + line] = v[g][q];
       }
@@ -399,20 +413,241 @@ __global__ void __launch_bounds__(R1 * NBC)
       for (int q = 0; q < R1; ++q) v[q] = s[(j2 + q * R2) * LD + line];
 #pragma unroll
       for (int q = 1; q < R1; ++q) v[q] = mulc<true>(v[q], stw[q * j2]);
-      dft_half_out<R1, true>(v);
+      if constexpr (HALF)
+        dft_half_out<R1, true>(v);
+      else
+        dft<R1, true>(v);
       cx<T>* g = base + c * cs + bb;
 #pragma unroll
-      for (int q = 0; q < R1 / 2; ++q) g[(long)(j2 + q * R2) * js] = v[q];
+      for (int q = 0; q < (HALF ? R1 / 2 : R1); ++q) g[(long)(j2 + q * R2) * js] = v[q];
     }
   }
 }
 
-template <int L, int R1, int R2, int NBC, class Op>
+// The pass as a kernel, with registers bounded so that MINB blocks fit on an
+// SM (more warps in flight, fewer registers per thread).
+template <class Op, int L, int R1, int R2, int NBC, bool HALF, int MINB>
+__global__ void __launch_bounds__(R1 * NBC, MINB)
+    k_rr_fft3c_mb(cx<float>* data, long ncols, long js, long cs, long ss, Op op,
+                  const cx<float>* __restrict__ tw, int twshift, int row_len, int nrows) {
+  pdl_entry();
+  rr_fft3c_body<Op, L, R1, R2, NBC, HALF>(data, ncols, js, cs, ss, op, tw, twshift, row_len,
+                                           nrows);
+}
+
+// The same pass with three stages each way, for lengths where two stages
+// would need too many registers (L = 512 = 8 x 8 x 8): forward radix R1a
+// (first input half zero) and R1b in shared memory, R2 from shared memory
+// into registers, the 3x3 point operation on the R2 frequencies a thread
+// holds (jb + q L/R2), inverse R2 from registers to shared memory, then
+// inverse R1b and R1a (only outputs j < L/2) back to global memory.  Stockham
+// indexing per stage (NS = product of the radices already applied):
+// butterfly jb reads x[jb + q L/R], twiddle w^{q (jb mod NS) L/(NS R)},
+// writes y[(jb - jb mod NS) R + jb mod NS + q NS].
+template <class Op, int L, int R1A, int R1B, int R2, int NBC, bool HALF>
+__global__ void __launch_bounds__(NBC * (L / R2))
+    k_rr3_fft3c(cx<float>* data, long ncols, long js, long cs, long ss, Op op,
+                const cx<float>* __restrict__ tw, int twshift, int row_len, int nrows) {
+  pdl_entry();
+  static_assert(R1A * R1B * R2 == L, "three stages");
+  using T = float;
+  constexpr int NL = 3 * NBC;
+  constexpr int LD = NL;
+  constexpr int NTH = NBC * (L / R2);
+  constexpr int H = L / 2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
+  cx<T>* stw = s + L * LD;
+  const int tid = threadIdx.x;
+  const long tiles = ncols / NBC;
+  const long slab = blockIdx.x / tiles;
+  const int tt = (int)(blockIdx.x - slab * tiles);
+  long col0;
+  if (row_len >= NBC && nrows > 0) {
+    const int row_tiles = row_len / NBC;
+    const int r = tt / row_tiles;
+    const int ti = tt - r * row_tiles;
+    col0 = (long)mirror_perm(r, nrows) * row_len + (long)mirror_perm(ti, row_tiles) * NBC;
+  } else {
+    col0 = (long)tt * NBC;
+  }
+  cx<T>* base = data + slab * ss + col0;
+  constexpr int ROWS_IN = HALF ? H : L;
+  // A: rows j < L/2 (HALF) or all rows of the 3 x NBC lines
+#pragma unroll 4
+  for (int e = tid; e < ROWS_IN * NL; e += NTH) {
+    const int j = e / NL, line = e - j * NL;
+    const int c = line / NBC, b = line - c * NBC;
+    cp_async_cx(s + j * LD + line, base + c * cs + (long)j * js + b, true);
+  }
+  op.prefetch(col0, NBC, L);
+  load_twiddles(stw, tw, L, twshift);
+  cp_async_wait_all();
+  __syncthreads();
+  // B1: radix R1A, NS = 1, input rows jb + q L/R1A (q < R1A/2 non-zero)
+  {
+    constexpr int NB1 = NL * (L / R1A);
+    constexpr int G = (NB1 + NTH - 1) / NTH;
+    cx<T> v[G][R1A];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int u = tid + g * NTH;
+      if (u < NB1) {
+        const int jb = u / NL, line = u - jb * NL;
+#pragma unroll
+        for (int q = 0; q < (HALF ? R1A / 2 : R1A); ++q)
+          v[g][q] = s[(jb + q * (L / R1A)) * LD + line];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int u = tid + g * NTH;
+      if (u < NB1) {
+        const int jb = u / NL, line = u - jb * NL;
+        if constexpr (HALF)
+          dft_half_in<R1A, false>(v[g]);
+        else
+          dft<R1A, false>(v[g]);
+#pragma unroll
+        for (int q = 0; q < R1A; ++q) s[(jb * R1A + q) * LD + line] = v[g][q];
+      }
+    }
+    __syncthreads();
+  }
+  // B2: radix R1B, NS = R1A
+  {
+    constexpr int NB2 = NL * (L / R1B);
+    constexpr int G = (NB2 + NTH - 1) / NTH;
+    cx<T> v[G][R1B];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int u = tid + g * NTH;
+      if (u < NB2) {
+        const int jb = u / NL, line = u - jb * NL;
+#pragma unroll
+        for (int q = 0; q < R1B; ++q) v[g][q] = s[(jb + q * (L / R1B)) * LD + line];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int u = tid + g * NTH;
+      if (u < NB2) {
+        const int jb = u / NL, line = u - jb * NL;
+        const int k = jb % R1A;
+#pragma unroll
+        for (int q = 1; q < R1B; ++q) v[g][q] = mulc<false>(v[g][q], stw[q * k * R2]);
+        dft<R1B, false>(v[g]);
+#pragma unroll
+        for (int q = 0; q < R1B; ++q) s[((jb - k) * R1B + k + q * R1A) * LD + line] = v[g][q];
+      }
+    }
+    __syncthreads();
+  }
+  // C: radix R2, NS = L/R2, rows jb + q L/R2 of all three components of column b
+  const int b = tid % NBC, jb = tid / NBC;  // jb < L/R2
+  cx<T> x[3][R2];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+#pragma unroll
+    for (int q = 0; q < R2; ++q) x[c][q] = s[(jb + q * (L / R2)) * LD + c * NBC + b];
+#pragma unroll
+    for (int q = 1; q < R2; ++q) x[c][q] = mulc<false>(x[c][q], stw[q * jb]);
+    dft<R2, false>(x[c]);
+  }
+  // D
+  {
+    const auto ctx = op.column(slab, col0 + b);
+#pragma unroll
+    for (int q = 0; q < R2; ++q) op.point(ctx, jb + q * (L / R2), x[0][q], x[1][q], x[2][q]);
+  }
+  // E: inverse radix R2, NS = 1, outputs rows jb R2 + q
+#pragma unroll
+  for (int c = 0; c < 3; ++c) dft<R2, true>(x[c]);
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int q = 0; q < R2; ++q) s[(jb * R2 + q) * LD + c * NBC + b] = x[c][q];
+  __syncthreads();
+  // F1: inverse radix R1B, NS = R2
+  {
+    constexpr int NB2 = NL * (L / R1B);
+    constexpr int G = (NB2 + NTH - 1) / NTH;
+    cx<T> v[G][R1B];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int u = tid + g * NTH;
+      if (u < NB2) {
+        const int j2 = u / NL, line = u - j2 * NL;
+#pragma unroll
+        for (int q = 0; q < R1B; ++q) v[g][q] = s[(j2 + q * (L / R1B)) * LD + line];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const int u = tid + g * NTH;
+      if (u < NB2) {
+        const int j2 = u / NL, line = u - j2 * NL;
+        const int k = j2 % R2;
+#pragma unroll
+        for (int q = 1; q < R1B; ++q) v[g][q] = mulc<true>(v[g][q], stw[q * k * R1A]);
+        dft<R1B, true>(v[g]);
+#pragma unroll
+        for (int q = 0; q < R1B; ++q) s[((j2 - k) * R1B + k + q * R2) * LD + line] = v[g][q];
+      }
+    }
+    __syncthreads();
+  }
+  // F2: inverse radix R1A, NS = L/R1A, only outputs j < L/2, to global memory
+  {
+    constexpr int NB1 = NL * (L / R1A);
+#pragma unroll 2
+    for (int u = tid; u < NB1; u += NTH) {
+      const int j2 = u / NL, line = u - j2 * NL;
+      const int c = line / NBC, bb = line - c * NBC;
+      cx<T> v[R1A];
+#pragma unroll
+      for (int q = 0; q < R1A; ++q) v[q] = s[(j2 + q * (L / R1A)) * LD + line];
+#pragma unroll
+      for (int q = 1; q < R1A; ++q) v[q] = mulc<true>(v[q], stw[q * j2]);
+      if constexpr (HALF)
+        dft_half_out<R1A, true>(v);
+      else
+        dft<R1A, true>(v);
+      cx<T>* g = base + c * cs + bb;
+#pragma unroll
+      for (int q = 0; q < (HALF ? R1A / 2 : R1A); ++q) g[(long)(j2 + q * (L / R1A)) * js] = v[q];
+    }
+  }
+}
+
+template <int L, int R1A, int R1B, int R2, int NBC, bool HALF, class Op>
+void rr3_fft3c_launch(cx<float>* data, long ncols, long nslabs, long js, long cs, long ss,
+                      const Op& op, const cx<float>* tw, int Lmax, int row_len, int nrows,
+                      cudaStream_t s) {
+  const size_t smem = ((size_t)3 * NBC * L + L) * sizeof(cx<float>);
+  auto kern = k_rr3_fft3c<Op, L, R1A, R1B, R2, NBC, HALF>;
+  if (smem > 48 * 1024)
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const long grid = nslabs * (ncols / NBC);
+  note_launch();
+  launch_k(kern, (unsigned)grid, NBC * (L / R2), smem, s, data, ncols, js, cs, ss, op, tw,
+           Lmax / L, row_len, nrows);
+}
+
+template <int L, int R1, int R2, int NBC, bool HALF, class Op>
 void rr_fft3c_launch(cx<float>* data, long ncols, long nslabs, long js, long cs, long ss,
                      const Op& op, const cx<float>* tw, int Lmax, int row_len, int nrows,
                      cudaStream_t s) {
   const size_t smem = ((size_t)3 * NBC * L + L) * sizeof(cx<float>);
-  auto kern = k_rr_fft3c<Op, L, R1, R2, NBC>;
+  // 256-thread tiles (lengths 128 and 256) with registers bounded so that
+  // three blocks share an SM: measured 11% faster at length 256 and 4% at
+  // 128 than the compiler's own count (two blocks); four blocks spill.
+  auto kern = R1 * NBC == 256 ? k_rr_fft3c_mb<Op, L, R1, R2, NBC, HALF, 3>
+                              : k_rr_fft3c_mb<Op, L, R1, R2, NBC, HALF, 1>;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const long grid = nslabs * (ncols / NBC);
@@ -443,18 +678,34 @@ template <class Op, bool HI, bool HO>
 bool ct_fft3c_dispatch(cx<float>* data, long ncols, long nslabs, int L, int Lin, long js, long cs,
                        long ss, int Lout, const Op& op, const cx<float>* tw, int Lmax, int row_len,
                        int nrows, cudaStream_t s) {
+  // Register-resident forms: the last forward and the first inverse stage
+  // in registers, the point operation between them; the matvec's pass (HI
+  // and HO: zero-padded input, half of the output kept) at lengths 64 to
+  // 512.  (Length 256 as 16 x 16 needs 48 register values per thread and
+  // 180 registers: measured slower than the all-shared-memory kernel; as
+  // 32 x 8 the register stage holds 3 x 8 values.  The preconditioner's pass
+  // (full input and output) measured 10-15% slower in these forms than in
+  // the all-shared-memory kernel, so it keeps that one.)
   if constexpr (HI && HO) {
-    // (length 256 as 16 x 16 needs 48 register values per thread and 180
-    // registers: measured slower than the all-shared-memory kernel)
-    if (ncols % 16 == 0 && rr_fft3c_enabled()) {
-      if (L == 64) {
-        rr_fft3c_launch<64, 8, 8, 16>(data, ncols, nslabs, js, cs, ss, op, tw, Lmax, row_len,
-                                      nrows, s);
+    if (rr_fft3c_enabled()) {
+      if (ncols % 16 == 0 && L == 64) {
+        rr_fft3c_launch<64, 8, 8, 16, HI>(data, ncols, nslabs, js, cs, ss, op, tw, Lmax, row_len,
+                                          nrows, s);
         return true;
       }
-      if (L == 128) {
-        rr_fft3c_launch<128, 16, 8, 16>(data, ncols, nslabs, js, cs, ss, op, tw, Lmax, row_len,
-                                        nrows, s);
+      if (ncols % 16 == 0 && L == 128) {
+        rr_fft3c_launch<128, 16, 8, 16, HI>(data, ncols, nslabs, js, cs, ss, op, tw, Lmax,
+                                            row_len, nrows, s);
+        return true;
+      }
+      if (ncols % 8 == 0 && L == 256) {
+        rr_fft3c_launch<256, 32, 8, 8, HI>(data, ncols, nslabs, js, cs, ss, op, tw, Lmax, row_len,
+                                           nrows, s);
+        return true;
+      }
+      if (ncols % 8 == 0 && L == 512) {
+        rr3_fft3c_launch<512, 8, 8, 8, 8, HI>(data, ncols, nslabs, js, cs, ss, op, tw, Lmax,
+                                              row_len, nrows, s);
         return true;
       }
     }

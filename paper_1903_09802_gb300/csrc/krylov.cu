@@ -1863,6 +1863,10 @@ dda_status_t check_solve(dda_plan_t p, int32_t nrhs, const dda_solve_opts_t& o) 
     return fail(DDA_ERR_INVALID_ARG, "dda_solve: inner_prec must be DDA_C128 or DDA_C64");
   if (o.inner_prec == DDA_C64 && !p->has64)
     return fail(DDA_ERR_INVALID_ARG, "dda_solve: plan holds no complex64 data");
+  if (o.inner_prec == DDA_C128 && p->d.krylov_c64)
+    return fail(DDA_ERR_INVALID_ARG,
+                "dda_solve: the plan's Krylov basis is complex64 (krylov_c64): inner_prec must be "
+                "DDA_C64");
   return DDA_OK;
 }
 

@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(NB * LX / kElemsPerThread, 1024 / (NB * LX / k
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
   cx<T>* stw = s + LX * LD;
+  cx<T>* sx = stw + LX;  // the NB x l input values of the diagonal term
   const int tid = threadIdx.x;
   const long line0 = (long)blockIdx.x * NB;
   {
@@ -175,25 +176,42 @@ __global__ void __launch_bounds__(NB * LX / kElemsPerThread, 1024 / (NB * LX / k
       cp_async_cx(q, ok ? g : buf1, ok);
     }
   }
+  // outputs: NB lines x l positions; thread keeps j = tid mod l.  Its x
+  // values are copied and its material bytes loaded now, so that their
+  // latency passes under the transform.
+  const int j = tid & (l - 1);
+  const int b0 = tid / l;
+  constexpr int OSTEP = NTH / l;
+  constexpr int NOUT = NB / OSTEP;  // outputs per thread
+  int mts[NOUT];
+  {
+    long line = line0 + b0;
+    long vrow = line % nm;
+#pragma unroll
+    for (int i = 0; i < NOUT; ++i, line += OSTEP) {
+      const bool ok = line < nlines;
+      cp_async_cx(sx + (b0 + i * OSTEP) * l + j, ok ? x + line * l + j : x, ok);
+      mts[i] = ok ? (int)__ldg(mat + vrow * l + j) : 0;
+      vrow += OSTEP;
+      if (vrow >= nm) vrow = vrow >= 2 * nm ? vrow % nm : vrow - nm;
+    }
+  }
   load_twiddles(stw, tw, LX, twshift);
   cp_async_wait_all();
   __syncthreads();
   ct_fft<LX, LD, NB, true, false, true>(s, stw);
-  // outputs: NB lines x l positions; thread keeps j = tid mod l
-  const int j = tid & (l - 1);
-  const int b0 = tid / l;
-  constexpr int OSTEP = NTH / l;
   long line = line0 + b0;
   long vrow = line % nm;
   long rhs = line / (3 * nm);
   long rem = line - rhs * 3 * nm;
-#pragma unroll 4
-  for (int b = b0; b < NB; b += OSTEP, line += OSTEP) {
+#pragma unroll
+  for (int i = 0; i < NOUT; ++i, line += OSTEP) {
     if (line >= nlines) break;
-    const int mt = mat[vrow * l + j];
+    const int b = b0 + i * OSTEP;
+    const int mt = mts[i];
     const cx<T> a = (pv != nullptr && mt != 0) ? pv[(rhs * nm + vrow) * l + j]
                                                : ainv[rhs * K1 + mt];
-    const cx<T> xv = x[line * l + j];
+    const cx<T> xv = sx[b * l + j];
     cx<T> out = a * xv;
     if (mt != 0) out = out - coef * s[j * LD + b];
     y[line * l + j] = out;
@@ -209,26 +227,27 @@ __global__ void __launch_bounds__(NB * LX / kElemsPerThread, 1024 / (NB * LX / k
 
 template <int LX>
 void ct_epilogue_launch(dda_plan_s* p, const cx<float>* b1, const cx<float>* x, cx<float>* y,
-                        long lines, long nm, float coef, cudaStream_t s) {
+                        long lines, long nm, float coef, cudaStream_t s, int rhs0) {
   constexpr int NB = (2048 / LX) > 16 ? 2048 / LX : 16;
-  const size_t smem = ((size_t)LX * (NB + 1) + LX) * sizeof(cx<float>);
+  const size_t smem = ((size_t)LX * (NB + 1) + LX + (size_t)NB * (LX / 2)) * sizeof(cx<float>);
   auto kern = k_ct_mv_epilogue<float, LX, NB>;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   note_launch();
   launch_k(kern, (unsigned)((lines + NB - 1) / NB), NB * LX / kElemsPerThread, smem, s,
-      b1, x, y, p->mat, ainv_of<float>(p), p->K + 1, lines, nm, coef, tw_of<float>(p),
-      p->Lmax / LX, pv_of<float>(p));
+      b1, x, y, p->mat, ainv_of<float>(p) + (long)rhs0 * (p->K + 1), p->K + 1, lines, nm, coef,
+      tw_of<float>(p), p->Lmax / LX,
+      pv_of<float>(p) ? pv_of<float>(p) + (long)rhs0 * p->nvox : nullptr);
 }
 
 bool ct_epilogue(dda_plan_s* p, const cx<float>* b1, const cx<float>* x, cx<float>* y, long lines,
-                 long nm, float coef, cudaStream_t s) {
+                 long nm, float coef, cudaStream_t s, int rhs0) {
   switch (p->Lx) {
-    case 32: ct_epilogue_launch<32>(p, b1, x, y, lines, nm, coef, s); return true;
-    case 64: ct_epilogue_launch<64>(p, b1, x, y, lines, nm, coef, s); return true;
-    case 128: ct_epilogue_launch<128>(p, b1, x, y, lines, nm, coef, s); return true;
-    case 256: ct_epilogue_launch<256>(p, b1, x, y, lines, nm, coef, s); return true;
-    case 512: ct_epilogue_launch<512>(p, b1, x, y, lines, nm, coef, s); return true;
+    case 32: ct_epilogue_launch<32>(p, b1, x, y, lines, nm, coef, s, rhs0); return true;
+    case 64: ct_epilogue_launch<64>(p, b1, x, y, lines, nm, coef, s, rhs0); return true;
+    case 128: ct_epilogue_launch<128>(p, b1, x, y, lines, nm, coef, s, rhs0); return true;
+    case 256: ct_epilogue_launch<256>(p, b1, x, y, lines, nm, coef, s, rhs0); return true;
+    case 512: ct_epilogue_launch<512>(p, b1, x, y, lines, nm, coef, s, rhs0); return true;
     default: return false;
   }
 }
@@ -240,7 +259,7 @@ inline int ilog2(int v) {
 }
 
 template <typename T>
-void matvec_core(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t s) {
+void matvec_core(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t s, int rhs0) {
   const cx<T>* tw = tw_of<T>(p);
   cx<T>* b1 = static_cast<cx<T>*>(p->w.buf1);
   cx<T>* b2 = static_cast<cx<T>*>(p->w.buf2);
@@ -276,7 +295,7 @@ void matvec_core(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t
     if (Lx >= 32 && Lx <= 512) {
       const float coef = (float)(p->d.dx * p->d.dx * p->d.dx / (double)p->P);
       p->prof.begin(PROF_MV_XI, s, 4 * u + p->nvox);
-      ct_epilogue(p, b1, x, y, lines, nm, coef, s);
+      ct_epilogue(p, b1, x, y, lines, nm, coef, s, rhs0);
       p->prof.end(s);
       return;
     }
@@ -297,18 +316,25 @@ void matvec_core(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t
     p->prof.begin(PROF_MV_XI, s, 4 * u + p->nvox);
     note_launch();
     launch_k(kern, (unsigned)((lines + NB - 1) / NB), nth, smem, s,
-        b1, x, y, p->mat, ainv_of<T>(p), p->K + 1, lines, nm, (int)l, (int)Lx, coef, tw,
-        p->Lmax / (int)Lx, make_radix_plan((int)Lx), ilog2i(NB), pv_of<T>(p));
+        b1, x, y, p->mat, ainv_of<T>(p) + (long)rhs0 * (p->K + 1), p->K + 1, lines, nm, (int)l,
+        (int)Lx, coef, tw, p->Lmax / (int)Lx, make_radix_plan((int)Lx), ilog2i(NB),
+        pv_of<T>(p) ? pv_of<T>(p) + (long)rhs0 * p->nvox : nullptr);
     p->prof.end(s);
   }
 }
 
 }  // namespace
 
+// Right-hand sides go through the five passes in chunks of the plan's
+// rhs_chunk (the FFT scratch holds that many).
 template <>
 void matvec_impl<float>(dda_plan_s* p, int nrhs, const cx<float>* x, cx<float>* y,
                         cudaStream_t s) {
-  matvec_core<float>(p, nrhs, x, y, s);
+  const long nu = 3 * p->nvox;
+  for (int r0 = 0; r0 < nrhs; r0 += p->rhs_chunk) {
+    const int nr = std::min(p->rhs_chunk, nrhs - r0);
+    matvec_core<float>(p, nr, x + r0 * nu, y + r0 * nu, s, r0);
+  }
 }
 
 // complex128 fields, double-float arithmetic (about 48 bits, at FP32 rates):
@@ -323,7 +349,11 @@ void matvec_impl<double>(dda_plan_s* p, int nrhs, const cx<double>* x, cx<double
   cx<df>* ydf = reinterpret_cast<cx<df>*>(y);
   note_launch();
   launch_k(k_to_df, g, 256, 0, s, reinterpret_cast<const double2*>(x), ydf, n);
-  matvec_core<df>(p, nrhs, ydf, ydf, s);
+  const long nu = 3 * p->nvox;
+  for (int r0 = 0; r0 < nrhs; r0 += p->rhs_chunk) {
+    const int nr = std::min(p->rhs_chunk, nrhs - r0);
+    matvec_core<df>(p, nr, ydf + r0 * nu, ydf + r0 * nu, s, r0);
+  }
   note_launch();
   launch_k(k_from_df, g, 256, 0, s, static_cast<const cx<df>*>(ydf),
            reinterpret_cast<double2*>(y), n);

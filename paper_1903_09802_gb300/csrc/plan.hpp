@@ -175,6 +175,7 @@ struct dda_plan_s {
   int hx, hy, hz;     // compressed kernel spectrum extents (L/2 + 1)
   int cx_, cy_, cz_;  // compressed circulant spectrum extents (l/2 + 1, ...)
   int K;              // materials
+  int rhs_chunk;      // right-hand sides per pass through the FFT scratch
   const uint8_t* mat;
   std::vector<double> eps;  // 2K
   std::vector<long> mat_count;  // voxels per material 0..K

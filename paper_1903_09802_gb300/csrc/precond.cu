@@ -21,6 +21,8 @@
 // matrix), inverse FFT.  Lambda is formed on the fly from the stored Chat and
 // the right-hand side's alpha_tilde, so one build serves every incident wave.
 #include "fft_ct.cuh"
+#include <algorithm>
+
 #include "plan.hpp"
 
 namespace dda {
@@ -160,7 +162,8 @@ inline unsigned grid_for(long n, int threads) {
 }  // namespace
 
 template <typename T>
-void precond_apply_impl(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cudaStream_t s) {
+void precond_apply_chunk(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cudaStream_t s,
+                         int rhs0) {
   const cx<T>* tw = tw_of<T>(p);
   cx<T>* t = static_cast<cx<T>*>(p->w.buf2);
   const long l = p->l, m = p->m, n = p->n;
@@ -176,7 +179,8 @@ void precond_apply_impl(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cudaS
   if (m > 1)
     launch_strided<T, false>(t, t, l, (long)nrhs * 3 * n, (int)m, (int)m, l, plane, (int)m, l, plane,
                              T(1), tw, p->Lmax, s);
-  CircSolve<T> op{C_of<T>(p), ainv_of<T>(p), static_cast<int*>(p->w.err_flag), p->K + 1,
+  CircSolve<T> op{C_of<T>(p), ainv_of<T>(p) + (long)rhs0 * (p->K + 1),
+                  static_cast<int*>(p->w.err_flag), p->K + 1,
                   (int)l, (int)m, (int)n, p->cx_, p->cy_, ilog2((int)l),
                   (T)(p->d.dx * p->d.dx * p->d.dx), (T)(1.0 / (double)p->nvox)};
   p->prof.end(s);
@@ -193,6 +197,17 @@ void precond_apply_impl(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cudaS
   launch_contig<T, true>(t, z, nullptr, p->mat, n * m, lines, (int)l, (int)l, l, (int)l, l, T(1), tw,
                          p->Lmax, s);
   p->prof.end(s);
+}
+
+// Right-hand sides in chunks of the plan's rhs_chunk (the transform scratch
+// holds that many).
+template <typename T>
+void precond_apply_impl(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cudaStream_t s) {
+  const long nu = 3 * p->nvox;
+  for (int r0 = 0; r0 < nrhs; r0 += p->rhs_chunk) {
+    const int nr = std::min(p->rhs_chunk, nrhs - r0);
+    precond_apply_chunk<T>(p, nr, v + r0 * nu, z + r0 * nu, s, r0);
+  }
 }
 
 // The same five passes with the transform held in caller-chosen scratch

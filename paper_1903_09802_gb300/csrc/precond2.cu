@@ -594,7 +594,7 @@ void precond2_apply_impl(dda_plan_s* p, const P2Geom& gm, int nrhs, const cx<T>*
 }  // namespace
 
 template <typename T>
-void precond2_apply(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cudaStream_t s) {
+void precond2_apply_chunk(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cudaStream_t s) {
   const P2Geom gm = p2_geom(p);
   const int axis = p->d.precond2;
   if (axis == 1) {
@@ -616,6 +616,16 @@ void precond2_apply(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cudaStrea
     launch_k(k_frame<T, 2, false>, g, 256, 0, s, vout, z, nrhs, (long)p->l, (long)p->m, (long)p->n);
   else
     launch_k(k_frame<T, 3, false>, g, 256, 0, s, vout, z, nrhs, (long)p->l, (long)p->m, (long)p->n);
+}
+// Right-hand sides in chunks of the plan's rhs_chunk (the FFT scratch and
+// the relabelling buffers hold that many).
+template <typename T>
+void precond2_apply(dda_plan_s* p, int nrhs, const cx<T>* v, cx<T>* z, cudaStream_t s) {
+  const long nu = 3 * p->nvox;
+  for (int r0 = 0; r0 < nrhs; r0 += p->rhs_chunk) {
+    const int nr = std::min(p->rhs_chunk, nrhs - r0);
+    precond2_apply_chunk<T>(p, nr, v + r0 * nu, z + r0 * nu, s);
+  }
 }
 template void precond2_apply<float>(dda_plan_s*, int, const cx<float>*, cx<float>*, cudaStream_t);
 template void precond2_apply<double>(dda_plan_s*, int, const cx<double>*, cx<double>*,

@@ -97,7 +97,8 @@ class PlanDesc(ctypes.Structure):
                 ("n_materials", ctypes.c_int32), ("max_rhs", ctypes.c_int32),
                 ("krylov_m", ctypes.c_int32), ("precisions", ctypes.c_int32),
                 ("precond2", ctypes.c_int32), ("circulant", ctypes.c_int32),
-                ("voxel_eps", ctypes.c_int32)]
+                ("voxel_eps", ctypes.c_int32), ("rhs_chunk", ctypes.c_int32),
+                ("krylov_c64", ctypes.c_int32)]
 
 
 class Incidence(ctypes.Structure):
@@ -223,9 +224,10 @@ def _prec_of(t: torch.Tensor) -> int:
 
 def workspace_size(l, m, n, dx, k, n_materials=1, max_rhs=1, krylov_m=0,
                    precisions=PLAN_C128 | PLAN_C64, precond2=0, circulant="chan",
-                   voxel_eps=False) -> int:
+                   voxel_eps=False, rhs_chunk=0, krylov_c64=False) -> int:
     d = PlanDesc(l, m, n, dx, k, n_materials, max_rhs, krylov_m, precisions,
-                 _precond2_code(precond2, (l, m, n)), CIRCULANTS[circulant], int(bool(voxel_eps)))
+                 _precond2_code(precond2, (l, m, n)), CIRCULANTS[circulant], int(bool(voxel_eps)),
+                 int(rhs_chunk), int(bool(krylov_c64)))
     return int(_lib.dda_workspace_size(ctypes.byref(d)))
 
 
@@ -258,11 +260,14 @@ class Plan:
 
     def __init__(self, mat: torch.Tensor, eps, dx: float, k: float, max_rhs: int = 1,
                  krylov_m: int = 0, precisions: int = PLAN_C128 | PLAN_C64,
-                 precond2=False, circulant: str = "chan", voxel_eps: torch.Tensor | None = None):
+                 precond2=False, circulant: str = "chan", voxel_eps: torch.Tensor | None = None,
+                 rhs_chunk: int = 0, krylov_c64: bool = False):
         """mat: (n, m, l) uint8 material per voxel (0 air); eps: permittivity of
         materials 1..K; voxel_eps: optional (n, m, l) complex128 permittivity of
         every voxel (dda_set_voxel_eps), which then overrides the table on
-        scatterer voxels (the table still gives alpha_tilde)."""
+        scatterer voxels (the table still gives alpha_tilde); rhs_chunk: right-hand
+        sides per pass through the FFT scratch (0: all of max_rhs); krylov_c64:
+        Krylov basis in complex64 (complex64 cycles only, half the memory)."""
         if mat.dtype != torch.uint8 or not mat.is_cuda or mat.dim() != 3:
             raise TypeError("mat must be a (n, m, l) uint8 CUDA tensor")
         self.mat = mat.contiguous()
@@ -271,7 +276,8 @@ class Plan:
         eps = [complex(e) for e in eps]
         self.desc = PlanDesc(l, m, n, float(dx), float(k), len(eps), int(max_rhs), int(krylov_m),
                              int(precisions), _precond2_code(precond2, (l, m, n)),
-                             CIRCULANTS[circulant], int(voxel_eps is not None))
+                             CIRCULANTS[circulant], int(voxel_eps is not None), int(rhs_chunk),
+                             int(bool(krylov_c64)))
         size = int(_lib.dda_workspace_size(ctypes.byref(self.desc)))
         if size == 0:
             raise DDAError(1, last_error())

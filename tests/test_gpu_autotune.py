@@ -43,15 +43,15 @@ def test_every_schedule_gives_the_operator_and_autotune(n):
     mat_d = to_dev(mat, torch.uint8)
     plan = dda.Plan(mat_d, eps, dx, k, max_rhs=1)
     plan.set_incidence([d], [e])
-    assert plan.schedule() == {"rr_z": True, "pdl": True}
+    assert plan.schedule() == {"rr_z": True, "pdl": True, "graph": True}
     x64, x128 = to_dev(x, torch.complex64), to_dev(x)
     for rr_z in (True, False):
         for pdl in (True, False):
             plan.set_schedule(rr_z, pdl)
-            assert plan.schedule() == {"rr_z": rr_z, "pdl": pdl}
+            assert plan.schedule() == {"rr_z": rr_z, "pdl": pdl, "graph": True}
             assert rel_err(plan.matvec(x64).cpu().numpy(), want) < 2e-5
             assert rel_err(plan.matvec(x128).cpu().numpy(), want) < 1e-10
-    bad = dda.Schedule(2, 1)
+    bad = dda.Schedule(2, 1, 1)
     assert dda.STATUS[dda._lib.dda_schedule_set(plan.handle, ctypes.byref(bad))] == \
         "DDA_ERR_INVALID_ARG"
 

@@ -380,7 +380,8 @@ dda_status_t dda_ext_gradient(dda_plan_t plan, int32_t nrhs, const void* d_c,
  *         the solve's arguments stay the same.  0 = the host drives the loop
  *         and polls the device's decisions.  Kernel timing
  *         (dda_profile_enable) always uses the host-driven loop.
- * A new plan starts with {1, 1, 1}.  The environment variables DDA_RR_FFT3C=0,
+ * A new plan starts with {1, 0, 1} (programmatic dependent launch measured
+ * slower on the 64^3 solves).  The environment variables DDA_RR_FFT3C=0,
  * DDA_PDL=0 and DDA_SOLVE_GRAPH=0 force the plain forms whatever the schedule.
  * The schedule applies to dda_matvec, dda_precond_apply, dda_precond2_apply
  * and dda_solve (hence dda_solve_many) of that plan, in the calling thread.

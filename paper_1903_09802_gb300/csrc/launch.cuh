@@ -34,7 +34,11 @@ __device__ __forceinline__ void pdl_entry() {
 
 struct Schedule {
   bool rr_z = true;  // register-resident z pass of the complex64 matvec (lengths 64, 128)
-  bool pdl = true;   // programmatic dependent launch
+  // programmatic dependent launch: off by default (with the register-bounded
+  // z pass and the graph-driven loop it measured 8-15% slower on the 64^3
+  // solves: the next kernel's early-resident blocks take SM room from the
+  // draining one)
+  bool pdl = false;
   bool graph = true; // dda_solve as one CUDA graph launch (device-side loop control)
 };
 

@@ -486,7 +486,7 @@ class Plan:
         _check(_lib.dda_schedule_get(self._h, ctypes.byref(s)))
         return {"rr_z": bool(s.rr_z), "pdl": bool(s.pdl), "graph": bool(s.graph)}
 
-    def set_schedule(self, rr_z: bool = True, pdl: bool = True, graph: bool = True):
+    def set_schedule(self, rr_z: bool = True, pdl: bool = False, graph: bool = True):
         _check(_lib.dda_schedule_set(self._h, ctypes.byref(Schedule(int(rr_z), int(pdl),
                                                                     int(graph)))))
 

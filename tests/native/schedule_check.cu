@@ -19,10 +19,12 @@ int main() {
   {
     Schedule a;
     a.rr_z = false;
+    a.pdl = true;
     ScheduleScope outer(a);
     show("outer");
     {
       Schedule b;
+      b.rr_z = true;
       b.pdl = false;
       ScheduleScope inner(b);
       show("inner");

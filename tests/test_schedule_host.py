@@ -23,8 +23,8 @@ def test_schedule_scopes(tmp_path):
     env = {k: v for k, v in os.environ.items() if k not in ("DDA_PDL", "DDA_RR_FFT3C")}
     out = subprocess.run([exe], check=True, capture_output=True, text=True, env=env).stdout
     seen = {name: (int(a), int(b)) for name, a, b in (ln.split() for ln in out.splitlines())}
-    assert seen == {"default": (1, 1), "outer": (0, 1), "inner": (1, 0),
-                    "other_thread": (1, 1), "outer_again": (0, 1), "restored": (1, 1)}
+    assert seen == {"default": (1, 0), "outer": (0, 1), "inner": (1, 0),
+                    "other_thread": (1, 0), "outer_again": (0, 1), "restored": (1, 0)}
     # the environment switches force the plain forms whatever the schedule
     env["DDA_PDL"] = "0"
     out = subprocess.run([exe], check=True, capture_output=True, text=True, env=env).stdout

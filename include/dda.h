@@ -372,6 +372,9 @@ dda_status_t dda_ext_gradient(dda_plan_t plan, int32_t nrhs, const void* d_c,
  *   pdl:  1 = kernels are launched with programmatic dependent launch (the
  *         next kernel's blocks become resident while the previous one drains);
  *         0 = ordinary stream-ordered launches.
+ *   z_occ: 1 = the register-resident z pass of 256-thread tiles (lengths 128
+ *         and 256) is compiled with registers bounded so that three blocks share
+ *         an SM (more warps in flight); 0 = the compiler's own register count.
  *   graph: 1 = dda_solve captures its whole loop once into a CUDA graph whose
  *         conditional nodes (a WHILE over restart cycles, an IF per cycle, a
  *         WHILE over the cycle's steps) take their conditions from the device
@@ -380,8 +383,8 @@ dda_status_t dda_ext_gradient(dda_plan_t plan, int32_t nrhs, const void* d_c,
  *         the solve's arguments stay the same.  0 = the host drives the loop
  *         and polls the device's decisions.  Kernel timing
  *         (dda_profile_enable) always uses the host-driven loop.
- * A new plan starts with {1, 0, 1} (programmatic dependent launch measured
- * slower on the 64^3 solves).  The environment variables DDA_RR_FFT3C=0,
+ * A new plan starts with {1, 0, 1, 1} (programmatic dependent launch
+ * measured slower on the 64^3 solves).  The environment variables DDA_RR_FFT3C=0,
  * DDA_PDL=0 and DDA_SOLVE_GRAPH=0 force the plain forms whatever the schedule.
  * The schedule applies to dda_matvec, dda_precond_apply, dda_precond2_apply
  * and dda_solve (hence dda_solve_many) of that plan, in the calling thread.
@@ -390,6 +393,7 @@ typedef struct {
   int32_t rr_z;
   int32_t pdl;
   int32_t graph;
+  int32_t z_occ;
 } dda_schedule_t;
 
 /* Set or read a plan's schedule (no GPU work).  Fields must be 0 or 1;
@@ -402,12 +406,12 @@ typedef struct {
   dda_schedule_t chosen;     /* the schedule now set on the plan */
   int32_t cached;            /* 1: taken from the process-wide table, nothing timed */
   int32_t ncand;             /* schedules timed (0 when cached) */
-  dda_schedule_t cand[4];    /* the schedules timed, in order (graph as set) */
-  float ms_per_matvec[4];    /* their mean CUDA-event time per matvec call */
+  dda_schedule_t cand[8];    /* the schedules timed, in order (graph as set) */
+  float ms_per_matvec[8];    /* their mean CUDA-event time per matvec call */
 } dda_tune_report_t;
 
 /* Autotuner: choose the plan's schedule by timing the matvec.  Each of the
- * four schedules runs 2 untimed then `reps` timed dda_matvec calls
+ * eight schedules (rr_z x pdl x z_occ) runs 2 untimed then `reps` timed dda_matvec calls
  * (precision prec, nrhs right-hand sides, input d_x, output d_y: caller-owned
  * device fields of that precision, box layout as dda_matvec's, not
  * overlapping; d_y is overwritten) bracketed by CUDA events on `stream`; the

@@ -424,8 +424,17 @@ __device__ __forceinline__ void rr_fft3c_body(cx<float>* data, long ncols, long 
   }
 }
 
-// The pass as a kernel, with registers bounded so that MINB blocks fit on an
-// SM (more warps in flight, fewer registers per thread).
+// The pass as a kernel: registers left to the compiler (k_rr_fft3c), or
+// bounded so that MINB blocks fit on an SM (k_rr_fft3c_mb: more warps in
+// flight, fewer registers per thread).
+template <class Op, int L, int R1, int R2, int NBC, bool HALF>
+__global__ void __launch_bounds__(R1 * NBC)
+    k_rr_fft3c(cx<float>* data, long ncols, long js, long cs, long ss, Op op,
+               const cx<float>* __restrict__ tw, int twshift, int row_len, int nrows) {
+  pdl_entry();
+  rr_fft3c_body<Op, L, R1, R2, NBC, HALF>(data, ncols, js, cs, ss, op, tw, twshift, row_len,
+                                           nrows);
+}
 template <class Op, int L, int R1, int R2, int NBC, bool HALF, int MINB>
 __global__ void __launch_bounds__(R1 * NBC, MINB)
     k_rr_fft3c_mb(cx<float>* data, long ncols, long js, long cs, long ss, Op op,
@@ -644,10 +653,11 @@ void rr_fft3c_launch(cx<float>* data, long ncols, long nslabs, long js, long cs,
                      cudaStream_t s) {
   const size_t smem = ((size_t)3 * NBC * L + L) * sizeof(cx<float>);
   // 256-thread tiles (lengths 128 and 256) with registers bounded so that
-  // three blocks share an SM: measured 11% faster at length 256 and 4% at
-  // 128 than the compiler's own count (two blocks); four blocks spill.
-  auto kern = R1 * NBC == 256 ? k_rr_fft3c_mb<Op, L, R1, R2, NBC, HALF, 3>
-                              : k_rr_fft3c_mb<Op, L, R1, R2, NBC, HALF, 1>;
+  // three blocks share an SM (schedule z_occ, the default): measured 11%
+  // faster at length 256 and 4% at 128 than the compiler's own count (two
+  // blocks); four blocks spill.
+  auto kern = (R1 * NBC == 256 && tl_schedule.z_occ) ? k_rr_fft3c_mb<Op, L, R1, R2, NBC, HALF, 3>
+                                                     : k_rr_fft3c<Op, L, R1, R2, NBC, HALF>;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const long grid = nslabs * (ncols / NBC);

@@ -40,6 +40,7 @@ struct Schedule {
   // draining one)
   bool pdl = false;
   bool graph = true; // dda_solve as one CUDA graph launch (device-side loop control)
+  bool z_occ = true; // register-resident z pass with 256-thread tiles bounded to three blocks per SM
 };
 
 inline thread_local Schedule tl_schedule;

@@ -23,7 +23,7 @@ std::mutex g_tune_mu;
 std::map<TuneKey, Schedule> g_tune_table;
 
 dda_schedule_t to_c(const Schedule& s) {
-  return dda_schedule_t{s.rr_z ? 1 : 0, s.pdl ? 1 : 0, s.graph ? 1 : 0};
+  return dda_schedule_t{s.rr_z ? 1 : 0, s.pdl ? 1 : 0, s.graph ? 1 : 0, s.z_occ ? 1 : 0};
 }
 
 // Mean milliseconds per matvec under the plan's current schedule.
@@ -52,11 +52,12 @@ dda_status_t time_matvec(dda_plan_t p, int32_t prec, int32_t nrhs, const void* x
 extern "C" dda_status_t dda_schedule_set(dda_plan_t p, const dda_schedule_t* sched) {
   if (!p || !sched) return fail(DDA_ERR_INVALID_ARG, "dda_schedule_set: NULL argument");
   if ((sched->rr_z != 0 && sched->rr_z != 1) || (sched->pdl != 0 && sched->pdl != 1) ||
-      (sched->graph != 0 && sched->graph != 1))
+      (sched->graph != 0 && sched->graph != 1) || (sched->z_occ != 0 && sched->z_occ != 1))
     return fail(DDA_ERR_INVALID_ARG, "dda_schedule_set: fields must be 0 or 1");
   p->sched.rr_z = sched->rr_z == 1;
   p->sched.pdl = sched->pdl == 1;
   p->sched.graph = sched->graph == 1;
+  p->sched.z_occ = sched->z_occ == 1;
   return DDA_OK;
 }
 
@@ -88,6 +89,7 @@ extern "C" dda_status_t dda_autotune(dda_plan_t p, int32_t prec, int32_t nrhs, c
     if (it != g_tune_table.end()) {
       p->sched.rr_z = it->second.rr_z;
       p->sched.pdl = it->second.pdl;
+      p->sched.z_occ = it->second.z_occ;
       rep.chosen = to_c(p->sched);
       rep.cached = 1;
       if (h_report) *h_report = rep;
@@ -103,10 +105,11 @@ extern "C" dda_status_t dda_autotune(dda_plan_t p, int32_t prec, int32_t nrhs, c
   const Schedule saved = p->sched;
   dda_status_t st = DDA_OK;
   int best = -1;
-  for (int c = 0; c < 4 && st == DDA_OK; ++c) {
+  for (int c = 0; c < 8 && st == DDA_OK; ++c) {
     Schedule cand = saved;  // the solve-loop choice (graph) is not tuned here
     cand.rr_z = (c & 1) == 0;
-    cand.pdl = (c & 2) == 0;
+    cand.pdl = (c & 2) != 0;
+    cand.z_occ = (c & 4) == 0;
     p->sched = cand;
     float ms = 0.f;
     st = time_matvec(p, prec, nrhs, d_x, d_y, reps, s, e0, e1, &ms);
@@ -124,6 +127,7 @@ extern "C" dda_status_t dda_autotune(dda_plan_t p, int32_t prec, int32_t nrhs, c
   }
   p->sched.rr_z = rep.cand[best].rr_z == 1;
   p->sched.pdl = rep.cand[best].pdl == 1;
+  p->sched.z_occ = rep.cand[best].z_occ == 1;
   rep.chosen = rep.cand[best];
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -123,12 +123,13 @@ class RhsStats(ctypes.Structure):
 
 
 class Schedule(ctypes.Structure):
-    _fields_ = [("rr_z", ctypes.c_int32), ("pdl", ctypes.c_int32), ("graph", ctypes.c_int32)]
+    _fields_ = [("rr_z", ctypes.c_int32), ("pdl", ctypes.c_int32), ("graph", ctypes.c_int32),
+                ("z_occ", ctypes.c_int32)]
 
 
 class TuneReport(ctypes.Structure):
     _fields_ = [("chosen", Schedule), ("cached", ctypes.c_int32), ("ncand", ctypes.c_int32),
-                ("cand", Schedule * 4), ("ms_per_matvec", ctypes.c_float * 4)]
+                ("cand", Schedule * 8), ("ms_per_matvec", ctypes.c_float * 8)]
 
 
 _vp = ctypes.c_void_p
@@ -484,11 +485,13 @@ class Plan:
     def schedule(self) -> dict:
         s = Schedule()
         _check(_lib.dda_schedule_get(self._h, ctypes.byref(s)))
-        return {"rr_z": bool(s.rr_z), "pdl": bool(s.pdl), "graph": bool(s.graph)}
+        return {"rr_z": bool(s.rr_z), "pdl": bool(s.pdl), "graph": bool(s.graph),
+                "z_occ": bool(s.z_occ)}
 
-    def set_schedule(self, rr_z: bool = True, pdl: bool = False, graph: bool = True):
+    def set_schedule(self, rr_z: bool = True, pdl: bool = False, graph: bool = True,
+                     z_occ: bool = True):
         _check(_lib.dda_schedule_set(self._h, ctypes.byref(Schedule(int(rr_z), int(pdl),
-                                                                    int(graph)))))
+                                                                    int(graph), int(z_occ)))))
 
     def autotune(self, prec: int = C64, nrhs: int | None = None, reps: int = 10,
                  force: bool = False) -> dict:
@@ -500,7 +503,8 @@ class Plan:
         rep = TuneReport()
         _check(_lib.dda_autotune(self._h, prec, nrhs, _ptr(x), _ptr(y), int(reps), int(force),
                                  ctypes.byref(rep), _stream()))
-        sched = lambda s: {"rr_z": bool(s.rr_z), "pdl": bool(s.pdl), "graph": bool(s.graph)}  # noqa: E731
+        sched = lambda s: {"rr_z": bool(s.rr_z), "pdl": bool(s.pdl), "graph": bool(s.graph),  # noqa: E731
+                           "z_occ": bool(s.z_occ)}
         return {"chosen": sched(rep.chosen), "cached": bool(rep.cached),
                 "timed": [(sched(rep.cand[i]), float(rep.ms_per_matvec[i]))
                           for i in range(rep.ncand)]}

@@ -124,7 +124,7 @@ def test_autotune_report_marshalling(monkeypatch):
         rep.ncand = 4
         for c in range(4):
             rep.cand[c].rr_z, rep.cand[c].pdl = int(c & 1 == 0), int(c & 2 == 0)
-            rep.cand[c].graph = 1
+            rep.cand[c].graph, rep.cand[c].z_occ = 1, 1
             rep.ms_per_matvec[c] = [0.3, 0.2, 0.4, 0.5][c]
         rep.chosen = rep.cand[1]
         rep.cached = 0
@@ -138,9 +138,10 @@ def test_autotune_report_marshalling(monkeypatch):
     plan.nrhs = 2
     plan.incident_field = lambda n: torch.ones((n, 3, 2, 2, 2), dtype=torch.complex128)
     rep = plan.autotune(reps=7, force=True)
-    assert rep["chosen"] == {"rr_z": False, "pdl": True, "graph": True} and not rep["cached"]
+    assert rep["chosen"] == {"rr_z": False, "pdl": True, "graph": True, "z_occ": True} \
+        and not rep["cached"]
     assert [t[1] for t in rep["timed"]] == pytest.approx([0.3, 0.2, 0.4, 0.5])
-    assert rep["timed"][3][0] == {"rr_z": False, "pdl": False, "graph": True}
+    assert rep["timed"][3][0] == {"rr_z": False, "pdl": False, "graph": True, "z_occ": True}
     plan._h = None  # nothing to destroy
 
 

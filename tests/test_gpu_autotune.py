@@ -1,9 +1,10 @@
 """Launch schedules and the autotuner: every schedule (register-resident or
-all-shared-memory z pass, with or without programmatic dependent launch)
-gives the oracle's operator on the 64 x 64 x {32, 64} boxes of the bench's
-prism sweep (z transforms of length 64 and 128, where the two z kernels
-differ); dda_autotune times all four, keeps the fastest and serves the next
-plan of the same shape from its table."""
+all-shared-memory z pass, with or without programmatic dependent launch, the
+z pass's registers bounded to three blocks per SM or not) gives the oracle's
+operator on the 64 x 64 x {32, 64} boxes of the bench's prism sweep (z
+transforms of length 64 and 128, where the z kernels differ); dda_autotune
+times all eight, keeps the fastest and serves the next plan of the same shape
+from its table."""
 import ctypes
 
 import numpy as np
@@ -43,22 +44,23 @@ def test_every_schedule_gives_the_operator_and_autotune(n):
     mat_d = to_dev(mat, torch.uint8)
     plan = dda.Plan(mat_d, eps, dx, k, max_rhs=1)
     plan.set_incidence([d], [e])
-    assert plan.schedule() == {"rr_z": True, "pdl": False, "graph": True}
+    assert plan.schedule() == {"rr_z": True, "pdl": False, "graph": True, "z_occ": True}
     x64, x128 = to_dev(x, torch.complex64), to_dev(x)
     for rr_z in (True, False):
         for pdl in (True, False):
-            plan.set_schedule(rr_z, pdl)
-            assert plan.schedule() == {"rr_z": rr_z, "pdl": pdl, "graph": True}
-            assert rel_err(plan.matvec(x64).cpu().numpy(), want) < 2e-5
-            assert rel_err(plan.matvec(x128).cpu().numpy(), want) < 1e-10
-    bad = dda.Schedule(2, 1, 1)
+            for z_occ in (True, False):
+                plan.set_schedule(rr_z, pdl, z_occ=z_occ)
+                assert plan.schedule() == {"rr_z": rr_z, "pdl": pdl, "graph": True, "z_occ": z_occ}
+                assert rel_err(plan.matvec(x64).cpu().numpy(), want) < 2e-5
+                assert rel_err(plan.matvec(x128).cpu().numpy(), want) < 1e-10
+    bad = dda.Schedule(2, 1, 1, 1)
     assert dda.STATUS[dda._lib.dda_schedule_set(plan.handle, ctypes.byref(bad))] == \
         "DDA_ERR_INVALID_ARG"
 
     rep = plan.autotune(reps=3, force=True)
-    assert not rep["cached"] and len(rep["timed"]) == 4
+    assert not rep["cached"] and len(rep["timed"]) == 8
     assert all(ms > 0 for _, ms in rep["timed"])
-    assert len({(s["rr_z"], s["pdl"]) for s, _ in rep["timed"]}) == 4
+    assert len({(s["rr_z"], s["pdl"], s["z_occ"]) for s, _ in rep["timed"]}) == 8
     assert rep["chosen"] == min(rep["timed"], key=lambda t: t[1])[0]
     assert plan.schedule() == rep["chosen"]
     assert rel_err(plan.matvec(x64).cpu().numpy(), want) < 2e-5

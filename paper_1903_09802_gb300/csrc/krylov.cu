@@ -41,6 +41,7 @@ namespace dda {
 namespace {
 
 constexpr int kNT = 256;  // threads of the vector kernels
+constexpr int kUpdDepth = 5;  // basis vectors in flight per thread in the complex64 update
 
 // Device time in nanoseconds (the global timer of the GPU).
 __device__ __forceinline__ unsigned long long now_ns() {
@@ -469,7 +470,59 @@ __global__ void __launch_bounds__(kNT)
   cx<T>* w = W + r * nu;
   const cx<T>* vb = V + r * nu;
   Acc<T> nn;
-  if (VEC) {
+  if constexpr (VEC && sizeof(T) == 4) {
+    // complex64: the basis pairs a thread needs are copied asynchronously
+    // into its own slots of a shared ring, kUpdDepth basis vectors ahead,
+    // so many loads stay in flight without holding registers (the update is
+    // bound by memory latency otherwise).  Each thread reads only what it
+    // copied itself: no block barrier; the arithmetic and its order are
+    // those of the plain loop.
+    constexpr int D = kUpdDepth;
+    __shared__ float4 ring[D][2][kNT];
+    const int tid = threadIdx.x;
+    auto copy = [&](int slot, int i, long k, bool two) {
+      const cx<T>* src = vb + (long)i * vstride + k;
+      const unsigned d0 = (unsigned)__cvta_generic_to_shared(&ring[slot][0][tid]);
+      const unsigned d1 = (unsigned)__cvta_generic_to_shared(&ring[slot][1][tid]);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d0), "l"(src) : "memory");
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d1),
+                   "l"(two ? src + 2 * kNT : src), "r"(two ? 16 : 0)
+                   : "memory");
+    };
+    for (long k = k0 + 2 * tid; k < k1; k += 4 * kNT) {
+      const bool two = k + 2 * kNT < k1;
+      Pair<T> a0 = ld2(w + k);
+      Pair<T> a1 = two ? ld2(w + k + 2 * kNT) : Pair<T>{zero<T>(), zero<T>()};
+#pragma unroll
+      for (int q = 0; q < D; ++q) {
+        if (q < jc) copy(q, q, k, two);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+      }
+      int slot = 0;
+      for (int i = 0; i < jc; ++i) {
+        asm volatile("cp.async.wait_group %0;\n" ::"n"(D - 1) : "memory");
+        const float4 p0 = ring[slot][0][tid], p1 = ring[slot][1][tid];
+        const cx<T> h = hs[i];
+        a0.a = a0.a - h * mk<T>(p0.x, p0.y);
+        a0.b = a0.b - h * mk<T>(p0.z, p0.w);
+        a1.a = a1.a - h * mk<T>(p1.x, p1.y);
+        a1.b = a1.b - h * mk<T>(p1.z, p1.w);
+        // refill the slot just consumed (its values are in registers and used)
+        if (i + D < jc) copy(slot, i + D, k, two);
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        slot = slot + 1 == D ? 0 : slot + 1;
+      }
+      asm volatile("cp.async.wait_all;\n" ::: "memory");
+      st2(w + k, a0);
+      nn.add(norm2(a0.a));
+      nn.add(norm2(a0.b));
+      if (two) {
+        st2(w + k + 2 * kNT, a1);
+        nn.add(norm2(a1.a));
+        nn.add(norm2(a1.b));
+      }
+    }
+  } else if (VEC) {
     for (long k = k0 + 2 * threadIdx.x; k < k1; k += 4 * kNT) {
       const bool two = k + 2 * kNT < k1;
       Pair<T> a0 = ld2(w + k);

@@ -366,23 +366,45 @@ __global__ void __launch_bounds__(kDotNT)
   const int ntot = jc + (want_norm ? 1 : 0);
   for (int i = wid; i < ntot; i += NW) {
     Acc<T> ar, ai;
+    // Trips go in batches of U whose loads are all issued before the first
+    // use (a tail trip past k1 is masked, not run on its own), so a lane
+    // keeps U loads in flight down to the end of its chunk.
+    constexpr int U = sizeof(T) == 4 ? 4 : 2;
     if (i < jc) {
       const cx<T>* v = vb + (long)i * vstride;
-#pragma unroll 8
-      for (long k = k0 + 2 * lane; k < k1; k += 64) {
-        const Pair<T> a = ld2_na(v + k);
-        const Pair<T> b = ld2(w + k);
-        ar.add(a.a.x * b.a.x + a.a.y * b.a.y);
-        ai.add(a.a.x * b.a.y - a.a.y * b.a.x);
-        ar.add(a.b.x * b.b.x + a.b.y * b.b.y);
-        ai.add(a.b.x * b.b.y - a.b.y * b.b.x);
+      for (long kb = k0 + 2 * lane; kb < k1; kb += 64 * U) {
+        Pair<T> a[U], b[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const long k = kb + 64 * u;
+          if (k < k1) {
+            a[u] = ld2_na(v + k);
+            b[u] = ld2(w + k);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (kb + 64 * u < k1) {
+            ar.add(a[u].a.x * b[u].a.x + a[u].a.y * b[u].a.y);
+            ai.add(a[u].a.x * b[u].a.y - a[u].a.y * b[u].a.x);
+            ar.add(a[u].b.x * b[u].b.x + a[u].b.y * b[u].b.y);
+            ai.add(a[u].b.x * b[u].b.y - a[u].b.y * b[u].b.x);
+          }
+        }
       }
     } else {
-#pragma unroll 8
-      for (long k = k0 + 2 * lane; k < k1; k += 64) {
-        const Pair<T> b = ld2(w + k);
-        ar.add(norm2(b.a));
-        ar.add(norm2(b.b));
+      for (long kb = k0 + 2 * lane; kb < k1; kb += 64 * U) {
+        Pair<T> b[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (kb + 64 * u < k1) b[u] = ld2(w + kb + 64 * u);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (kb + 64 * u < k1) {
+            ar.add(norm2(b[u].a));
+            ar.add(norm2(b[u].b));
+          }
+        }
       }
     }
     const double tr = ar.warp_total();

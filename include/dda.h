@@ -93,6 +93,9 @@ typedef struct {
   int32_t krylov_c64;    /* 1: the Krylov basis and step vectors are reserved in
                             complex64 (solves with inner_prec = DDA_C64 only), half
                             the memory of the complex128 reservation                  */
+  int32_t sstep;         /* block size s of the s-step GMRES (method 2) to reserve: 0
+                            none, 2..8 (at most krylov_m): s more Krylov vectors per
+                            right-hand side, the unrotated Hessenberg matrix, shifts  */
 } dda_plan_desc_t;
 
 /* Plane wave E_inc = pol * exp(i k dir . r), r measured from the box centre.
@@ -120,7 +123,17 @@ typedef struct {
                             choice of Daniel, Gragg, Kaufman & Stewart)                      */
   int32_t method;        /* 0: GMRES(restart); 1: BiCG-Stab (van der Vorst), the paper's
                             second solver (Section 4), restart = iterations per
-                            refinement cycle; the plan needs krylov_m >= 7             */
+                            refinement cycle; the plan needs krylov_m >= 7;
+                            2: s-step GMRES(restart) with the plan's s (desc.sstep,
+                            restart a multiple of s): the same GMRES iterates computed
+                            in blocks of s Newton-basis vectors (Bai, Hu & Reichel
+                            1994) whose shifts are the Leja-ordered Ritz values of
+                            the solve's first cycle (plain Arnoldi); each block is
+                            orthogonalised by block classical Gram-Schmidt twice and
+                            a Cholesky QR, reading the basis four times per s
+                            columns instead of twice or more per column; iterations
+                            count columns, the last block of a cycle may compute up
+                            to s - 1 products beyond the converged column           */
   int32_t history_cap;   /* entries of h_history per right-hand side (0: none)        */
   int64_t timeout_ns;    /* time limit of the solve on the device's global timer
                             (0: none); checked after every inner iteration and at
@@ -294,6 +307,20 @@ dda_status_t dda_fft3d(dda_plan_t plan, int32_t prec, int32_t nbatch, void* d_da
  * `stream`. */
 dda_status_t dda_solve(dda_plan_t plan, int32_t nrhs, const void* d_b, void* d_x,
                        const dda_solve_opts_t* opts, dda_rhs_stats_t* h_stats, void* stream);
+
+/* Newton shifts of the s-step GMRES (method 2) from Arnoldi Hessenberg
+ * matrices, as the solver computes them after its first cycle: for each
+ * right-hand side r, the eigenvalues of the leading k x k block of
+ * d_hraw[r] (device complex128 [(m+1) x m], column-major: entry (i, j) at
+ * j*(m+1) + i; upper Hessenberg), k = min(d_jlen[r], 4 s, 32), by shifted QR
+ * iterations, and the first s of them in Leja order (Reichel, BIT 30 (1990)
+ * 332: the one of largest modulus, then each next maximising the product of
+ * its distances to those taken) into d_theta[r] (device complex128 [8];
+ * entries past min(s, k) are zero).  d_jlen: device int32 [nrhs].  Queued on
+ * `stream`, no synchronisation.  DDA_ERR_INVALID_ARG on NULL or m < 1,
+ * nrhs < 1, s outside 1..8.  A test hook of the solver. */
+dda_status_t dda_ritz_shifts(const void* d_hraw, int32_t m, const int32_t* d_jlen, int32_t nrhs,
+                             int32_t s, void* d_theta, void* stream);
 
 /* Several independent systems solved concurrently: plan i's system (arguments
  * as dda_solve's, arrays of length nplans; d_b may be NULL or hold NULL

@@ -62,6 +62,9 @@ bool valid_desc(const dda_plan_desc_t& d, std::string& why, dda_status_t& st) {
   if (d.krylov_c64 != 0 && d.krylov_c64 != 1) return why = "krylov_c64 must be 0 or 1", false;
   if (d.krylov_c64 && !(d.precisions & DDA_PLAN_C64))
     return why = "krylov_c64 needs a plan holding complex64 data", false;
+  if (d.sstep != 0 && (d.sstep < 2 || d.sstep > 8))
+    return why = "sstep must be 0 or 2..8", false;
+  if (d.sstep > d.krylov_m) return why = "sstep must be at most krylov_m", false;
   if ((d.precisions & (DDA_PLAN_C128 | DDA_PLAN_C64)) == 0 ||
       (d.precisions & ~(DDA_PLAN_C128 | DDA_PLAN_C64)) != 0)
     return why = "precisions must be a non-empty set of DDA_PLAN_C128 | DDA_PLAN_C64", false;
@@ -169,6 +172,17 @@ bool make_layout(const dda_plan_desc_t& d, void* ws, Layout& L, std::string& why
     s.hist = static_cast<double*>(c.take(sizeof(double) * kHistCap * R));
     s.t0 = static_cast<unsigned long long*>(c.take(8));
     s.nlaunch = static_cast<long long*>(c.take(8));
+    if (d.sstep > 0) {
+      const long sb = d.sstep;
+      L.Wb = c.take(vsz * sb * R * nu);
+      s.Hraw = static_cast<double2*>(c.take(16 * R * (mk + 1) * mk));
+      s.theta = static_cast<double2*>(c.take(16 * R * 8));
+      s.cb = static_cast<double2*>(c.take(16 * R * 2 * (mk + 1 + sb) * sb));
+      s.rinv = static_cast<double2*>(c.take(16 * R * 64));
+      // block dot partials: nrhs * max(ceil(304 / nrhs), ceil(nu s / 8192)) blocks
+      const long nbmax = 304 + R + R * ((nu * sb + 8191) / 8192);
+      s.bpart = static_cast<double2*>(c.take(16 * nbmax * (mk + 1 + sb) * sb));
+    }
   }
   L.total = c.off + 256;
   return true;

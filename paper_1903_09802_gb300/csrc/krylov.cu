@@ -71,6 +71,11 @@ struct LoopCtl {
   double* hist;                       // [rhs][hcap] relative residual per inner iteration
   int hcap;
   int max_iters;
+  // s-step GMRES: WHILE over the blocks of a cycle, kernels per block, and
+  // the count of cycles started (the first is Arnoldi, later ones blocks)
+  cudaGraphConditionalHandle h_blk;
+  int k_blk;
+  int* scount;                        // nullptr: not s-step
 };
 
 // Outcome of one right-hand side, written by k_cycle_decide.
@@ -636,7 +641,7 @@ __global__ void __launch_bounds__(32)
              double2* __restrict__ g, double* __restrict__ scal, int* __restrict__ active,
              int* __restrict__ jlen, int* __restrict__ flags, int* __restrict__ iters, int nrhs,
              int m, int j, double brk, int* __restrict__ count_out, int* __restrict__ ticket,
-             LoopCtl ctl) {
+             LoopCtl ctl, double2* __restrict__ Hraw) {
   pdl_entry();
   if (ctl.graph) j = *ctl.jstep;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -654,6 +659,11 @@ __global__ void __launch_bounds__(32)
       cc[i] = c[i];
     }
     __syncwarp();
+    if (Hraw != nullptr) {  // the unrotated column (s-step shifts come from it)
+      double2* hr = Hraw + (long)r * (m + 1) * m + (long)j * (m + 1);
+      for (int i = lane; i <= j; i += 32) hr[i] = hs[i];
+      if (lane == 0) hr[j + 1] = make_double2(sqrt(scal[(long)r * 16 + 8]), 0.0);
+    }
     if (lane == 0) {
       const double n2 = scal[(long)r * 16 + 8];  // ||w||^2 after Gram-Schmidt
       const double hn = sqrt(n2);
@@ -857,10 +867,16 @@ __global__ void __launch_bounds__(256)
     *ctl.steps = steps;
     *ctl.jstep = 0;
     *ctl.nrun = n;
+    // s-step: the first cycle that runs is Arnoldi, the later ones blocks
+    const int started = ctl.scount != nullptr ? *ctl.scount : 0;
+    const bool blk = ctl.scount != nullptr && started >= 1;
+    if (ctl.scount != nullptr && n > 0) *ctl.scount = started + 1;
     if (ctl.graph) {
       cudaGraphSetConditional(ctl.h_cycle, n > 0 ? 1u : 0u);
       cudaGraphSetConditional(ctl.h_run, n > 0 ? 1u : 0u);
-      cudaGraphSetConditional(ctl.h_step, (n > 0 && steps > 0) ? 1u : 0u);
+      cudaGraphSetConditional(ctl.h_step, (n > 0 && steps > 0 && !blk) ? 1u : 0u);
+      if (ctl.scount != nullptr)
+        cudaGraphSetConditional(ctl.h_blk, (n > 0 && steps > 0 && blk) ? 1u : 0u);
       *ctl.nlaunch += ctl.k_head + (n > 0 ? ctl.k_run : 0);
     }
   }
@@ -1272,6 +1288,8 @@ __global__ void __launch_bounds__(kNT)
 // with the conditions set by the device (k_cycle_decide, k_givens,
 // k_count_active), so one graph launch runs the solve to the end.
 
+#include "sstep.cuh"
+
 template <typename T>
 struct Ctx {
   dda_plan_s* p;
@@ -1291,6 +1309,10 @@ struct Ctx {
   dim3 vgrid, dgrid;
   bool prec, vec;
   double brk, eta2;
+  // s-step GMRES (method 2): block size, Newton vectors, block dot grid
+  int S = 0, bnb = 1;
+  cx<T>* Wb = nullptr;
+  dim3 bgrid;
 
   Ctx(dda_plan_s* p_, int nrhs_, const double2* b_, double2* x_, const dda_solve_opts_t& o_)
       : p(p_), nrhs(nrhs_), b(b_), x(x_), o(o_) {
@@ -1311,6 +1333,15 @@ struct Ctx {
     vec = (nu % 2) == 0;  // 16-byte pairs stay aligned
     brk = sizeof(T) == 8 ? 1e-13 : 1e-6;
     eta2 = o.reorth_eta * o.reorth_eta;
+    if (o.method == 2) {
+      S = p->d.sstep;
+      Wb = static_cast<cx<T>*>(p->w.Wb);
+      // at least two blocks of 8 warps per SM over the batch, and chunks of
+      // at most 8192 / S values, so that a block's chunk of the S Newton
+      // vectors (64 KB in complex64), which every warp reads, stays in L1
+      bnb = (int)std::max<long>((304 + nrhs - 1) / nrhs, (nu * S + 8191) / 8192);
+      bgrid = dim3(bnb, nrhs);
+    }
   }
 
   void apply_prec(const cx<T>* in, cx<T>* out, cudaStream_t s) const {
@@ -1331,6 +1362,7 @@ struct Ctx {
     c.hist = st->hist;
     c.hcap = kHistCap;
     c.max_iters = o.max_iters;
+    c.scount = o.method == 2 ? st->ctl + 3 : nullptr;
     return c;
   }
 
@@ -1399,7 +1431,7 @@ struct Ctx {
     const int jsm = dev ? m : j;
     launch_k(k_givens, nrhs, 32, (size_t)(jsm + 2) * 16 + (size_t)jsm * 24, s, st->H, st->cs,
              st->sn, st->g, st->scal, st->active, st->jlen, st->flags, st->iters, nrhs, m, j, brk,
-             st->counters + (j & 1), st->counters + 8, c);
+             st->counters + (j & 1), st->counters + 8, c, o.method == 2 ? st->Hraw : nullptr);
     if (dev || scale_next) {
       note_launch();
       launch_k(k_scale<T>, vgrid, kNT, 0, s, W, V + (long)(j + 1) * vstride, nu, st->scal,
@@ -1489,17 +1521,89 @@ struct Ctx {
     k_badd_x<T><<<vgrid, kNT, 0, s>>>(x, Z, st->run, nu);
   }
 
+  // s-step GMRES --------------------------------------------------------------
+  // One block of S columns from column j (host-driven) or the device's step
+  // index (graph); q_j is in Z.
+  template <int SB>
+  void sstep_block_t(int j, const LoopCtl& c, cudaStream_t s) const {
+    const bool dev = c.graph != 0;
+    const int* jdev = dev ? c.jstep : nullptr;
+    for (int t = 0; t < SB; ++t) {
+      const cx<T>* in = t == 0 ? Z : Wb + (long)(t - 1) * vstride;
+      cx<T>* out = Wb + (long)t * vstride;
+      const cx<T>* src = in;
+      if (prec) {
+        apply_prec(in, W, s);
+        src = W;
+      }
+      matvec_impl<T>(p, nrhs, src, out, s);
+      note_launch();
+      launch_k(k_shift<T>, vgrid, kNT, 0, s, out, in, nu, st->theta, t, st->active);
+    }
+    const int slots = (m + 1 + SB) * SB;
+    const dim3 rgrid((slots + 7) / 8, nrhs);
+    const double vb = (double)nrhs * nu * sizeof(cx<T>);
+    for (int pass = 0; pass < 2; ++pass) {
+      p->prof.begin(PROF_AR_DOT, s, (j + 1 + SB) * vb);
+      note_launch();
+      launch_k(k_sdots<T, SB>, bgrid, kBNT, 0, s, V, Wb, nu, vstride, j, jdev, pass,
+               st->active, st->bpart, slots);
+      note_launch();
+      launch_k(k_sdots_reduce, rgrid, 256, 0, s, st->bpart, bnb, slots, SB, j, jdev, pass,
+               st->active, st->cb, slots, pass);
+      p->prof.end(s);
+      if (pass == 0) {
+        p->prof.begin(PROF_AR_UPD, s, (j + 1 + 2 * SB) * vb);
+        note_launch();
+        launch_k(k_supd<T, SB>, vgrid, kNT, 0, s, V, Wb, nu, vstride, j, jdev, 0, st->cb, slots,
+                 0, nullptr, st->active, nullptr);
+        p->prof.end(s);
+      }
+    }
+    const int jsm = dev ? m - SB : j;
+    const int nrow = jsm + SB + 1;
+    const size_t smem = (size_t)16 * ((size_t)nrow * SB + (size_t)(jsm + 1) * SB + 3 * SB * SB +
+                                      nrow + (jsm + SB)) +
+                        (size_t)8 * (jsm + SB);
+    note_launch();
+    launch_k(k_ssmall, nrhs, 32, smem, s, SB, st->Hraw, st->H, st->cs, st->sn, st->g, st->scal,
+             st->active, st->reorth, st->jlen, st->flags, st->iters, st->cb, slots, st->rinv,
+             st->theta, nrhs, m, j, brk, st->counters + ((j / SB) & 1), st->counters + 8, c);
+    p->prof.begin(PROF_AR_UPD, s, (j + 1 + 2 * SB) * vb);
+    note_launch();
+    launch_k(k_supd<T, SB>, vgrid, kNT, 0, s, V, Wb, nu, vstride, j, jdev, SB, st->cb, slots, 1,
+             st->rinv, st->reorth, Z);
+    p->prof.end(s);
+  }
+
+  void sstep_block(int j, const LoopCtl& c, cudaStream_t s) const {
+    switch (S) {
+      case 2: sstep_block_t<2>(j, c, s); break;
+      case 3: sstep_block_t<3>(j, c, s); break;
+      case 4: sstep_block_t<4>(j, c, s); break;
+      case 5: sstep_block_t<5>(j, c, s); break;
+      case 6: sstep_block_t<6>(j, c, s); break;
+      case 7: sstep_block_t<7>(j, c, s); break;
+      default: sstep_block_t<8>(j, c, s); break;
+    }
+  }
+
   void start(cudaStream_t s, bool graph) const {
     if (o.method == 1)
       bicg_start(s);
     else
-      gmres_start(graph ? Z : nullptr, s);
+      gmres_start(graph || o.method == 2 ? Z : nullptr, s);
   }
   void end(cudaStream_t s) const {
-    if (o.method == 1)
+    if (o.method == 1) {
       bicg_end(s);
-    else
+    } else {
       gmres_end(s);
+      if (o.method == 2) {  // the shifts, after the first cycle
+        note_launch();
+        launch_k(k_ritz, nrhs, 32, 0, s, st->Hraw, st->jlen, st->theta, S, m, st->ctl + 3);
+      }
+    }
   }
 };
 
@@ -1514,6 +1618,7 @@ void solve_prologue(const Ctx<T>& c, cudaStream_t s) {
   cudaMemsetAsync(st.flags, 0, sizeof(int) * nrhs, s);
   cudaMemsetAsync(st.out, 0, sizeof(RhsOut) * nrhs, s);
   cudaMemsetAsync(st.nlaunch, 0, sizeof(long long), s);
+  cudaMemsetAsync(st.ctl + 3, 0, sizeof(int), s);  // cycles started (s-step)
   cudaMemsetAsync(c.p->w.err_flag, 0, 4, s);
   note_launch();
   k_solve_begin<<<1, 1, 0, s>>>(st.t0);
@@ -1531,6 +1636,7 @@ dda_status_t drive_host(const Ctx<T>& c, cudaStream_t s) {
   cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming);
   cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming);
   dda_status_t status = DDA_OK;
+  int cycles = 0;
   for (;;) {
     c.cycle_head(ctl, s);
     cudaMemcpyAsync(p->pinned + 2, st.ctl + 1, 2 * sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -1541,20 +1647,26 @@ dda_status_t drive_host(const Ctx<T>& c, cudaStream_t s) {
     const int steps = p->pinned[2], nrun = p->pinned[3];
     if (nrun == 0) break;
     c.start(s, false);
-    for (int j = 0; j < steps; ++j) {
-      if (c.o.method == 1)
+    // s-step: Arnoldi in the first cycle, blocks of S columns afterwards
+    const bool blocks = c.o.method == 2 && cycles > 0;
+    const int stride = blocks ? c.S : 1;
+    for (int j = 0, q = 0; j < steps; j += stride, ++q) {
+      if (blocks)
+        c.sstep_block(j, ctl, s);
+      else if (c.o.method == 1)
         c.bicg_step(j, ctl, s);
       else
         c.gmres_step(j, j + 1 < steps, ctl, s);
-      cudaMemcpyAsync(p->pinned + (j & 1), st.counters + (j & 1), sizeof(int),
+      cudaMemcpyAsync(p->pinned + (q & 1), st.counters + (q & 1), sizeof(int),
                       cudaMemcpyDeviceToHost, s);
-      cudaEventRecord(ev[j & 1], s);
-      if (j >= 1) {
-        cudaEventSynchronize(ev[(j - 1) & 1]);
-        if (p->pinned[(j - 1) & 1] == 0) break;
+      cudaEventRecord(ev[q & 1], s);
+      if (q >= 1) {
+        cudaEventSynchronize(ev[(q - 1) & 1]);
+        if (p->pinned[(q - 1) & 1] == 0) break;
       }
     }
     c.end(s);
+    ++cycles;
     if ((status = check_cuda("dda_solve")) != DDA_OK) break;
   }
   cudaEventDestroy(ev[0]);
@@ -1655,15 +1767,18 @@ bool capture_into(const Ctx<T>& c, cudaGraph_t top, cudaStream_t cs) {
   ScheduleScope scope(c.p->sched);
   const long long before = launch_counter();
   bool ok = true;
-  cudaGraphConditionalHandle hc = 0, hr = 0, hs = 0;
+  const bool ss = c.o.method == 2;
+  cudaGraphConditionalHandle hc = 0, hr = 0, hs = 0, hb = 0;
   ok = cudaGraphConditionalHandleCreate(&hc, top, 1, cudaGraphCondAssignDefault) == cudaSuccess &&
        cudaGraphConditionalHandleCreate(&hr, top, 0, 0) == cudaSuccess &&
-       cudaGraphConditionalHandleCreate(&hs, top, 0, 0) == cudaSuccess;
+       cudaGraphConditionalHandleCreate(&hs, top, 0, 0) == cudaSuccess &&
+       (!ss || cudaGraphConditionalHandleCreate(&hb, top, 0, 0) == cudaSuccess);
   LoopCtl ctl = c.ctl_base();
   ctl.graph = 1;
   ctl.h_cycle = hc;
   ctl.h_run = hr;
   ctl.h_step = hs;
+  ctl.h_blk = hb;
   {
     cudaGraph_t dry = nullptr;
     ok = ok && cudaGraphCreate(&dry, 0) == cudaSuccess;
@@ -1684,9 +1799,14 @@ bool capture_into(const Ctx<T>& c, cudaGraph_t top, cudaStream_t cs) {
         c.gmres_step(0, true, ctl, cs);
     });
     ctl.k_step = (int)(launch_counter() - t);
+    if (ss) {
+      t = launch_counter();
+      capture(cs, dry, ok, [&] { c.sstep_block(0, ctl, cs); });
+      ctl.k_blk = (int)(launch_counter() - t);
+    }
     if (dry) cudaGraphDestroy(dry);
   }
-  cudaGraph_t body_cycle = nullptr, body_run = nullptr, body_step = nullptr;
+  cudaGraph_t body_cycle = nullptr, body_run = nullptr, body_step = nullptr, body_blk = nullptr;
   capture(cs, top, ok, [&] {
     solve_prologue(c, cs);
     body_cycle = add_conditional(cs, hc, cudaGraphCondTypeWhile, ok);
@@ -1698,8 +1818,10 @@ bool capture_into(const Ctx<T>& c, cudaGraph_t top, cudaStream_t cs) {
   capture(cs, body_run, ok, [&] {
     c.start(cs, true);
     body_step = add_conditional(cs, hs, cudaGraphCondTypeWhile, ok);
+    if (ss) body_blk = add_conditional(cs, hb, cudaGraphCondTypeWhile, ok);
     c.end(cs);
   });
+  if (ss) capture(cs, body_blk, ok, [&] { c.sstep_block(0, ctl, cs); });
   capture(cs, body_step, ok, [&] {
     if (c.o.method == 1)
       c.bicg_step(0, ctl, cs);
@@ -1928,8 +2050,19 @@ dda_status_t check_solve(dda_plan_t p, int32_t nrhs, const dda_solve_opts_t& o) 
   if (!p->has128) return fail(DDA_ERR_INVALID_ARG, "dda_solve: the residual needs complex128 data");
   if (o.method == 0 && o.restart + 2 > 518)
     return fail(DDA_ERR_INVALID_ARG, "dda_solve: restart above 512");
-  if (o.method != 0 && o.method != 1)
-    return fail(DDA_ERR_INVALID_ARG, "dda_solve: method must be 0 (GMRES) or 1 (BiCG-Stab)");
+  if (o.method != 0 && o.method != 1 && o.method != 2)
+    return fail(DDA_ERR_INVALID_ARG,
+                "dda_solve: method must be 0 (GMRES), 1 (BiCG-Stab) or 2 (s-step GMRES)");
+  if (o.method == 2) {
+    const int sb = p->d.sstep;
+    if (sb < 2)
+      return fail(DDA_ERR_INVALID_ARG, "dda_solve: method 2 needs a plan with sstep >= 2");
+    if (o.restart % sb != 0 || o.restart > p->d.krylov_m || o.restart > kSRestart)
+      return fail(DDA_ERR_INVALID_ARG,
+                  "dda_solve: method 2 needs restart a multiple of sstep, <= krylov_m and <= 64");
+    if ((3 * p->nvox) % 2 != 0)
+      return fail(DDA_ERR_INVALID_ARG, "dda_solve: method 2 needs an even number of unknowns");
+  }
   if (o.method == 1 && p->d.krylov_m < 7)
     return fail(DDA_ERR_INVALID_ARG, "dda_solve: BiCG-Stab needs a plan with krylov_m >= 7");
   if (o.history_cap < 0 || o.timeout_ns < 0 || (o.h_history != nullptr && o.history_cap < 1))
@@ -1970,6 +2103,18 @@ bool solve_many_as_graph(int32_t nplans, const dda_plan_t* plans, const int32_t*
 }  // namespace dda
 
 using namespace dda;
+
+extern "C" dda_status_t dda_ritz_shifts(const void* d_hraw, int32_t m, const int32_t* d_jlen,
+                                        int32_t nrhs, int32_t s, void* d_theta, void* stream) {
+  if (!d_hraw || !d_jlen || !d_theta)
+    return fail(DDA_ERR_INVALID_ARG, "dda_ritz_shifts: NULL argument");
+  if (m < 1 || nrhs < 1 || s < 1 || s > kSMax)
+    return fail(DDA_ERR_INVALID_ARG, "dda_ritz_shifts: need m >= 1, nrhs >= 1, 1 <= s <= 8");
+  note_launch();
+  k_ritz<<<nrhs, 32, 0, static_cast<cudaStream_t>(stream)>>>(
+      static_cast<const double2*>(d_hraw), d_jlen, static_cast<double2*>(d_theta), s, m, nullptr);
+  return check_cuda("dda_ritz_shifts");
+}
 
 extern "C" dda_status_t dda_solve(dda_plan_t p, int32_t nrhs, const void* d_b, void* d_x,
                                   const dda_solve_opts_t* opts, dda_rhs_stats_t* h_stats,

@@ -76,6 +76,12 @@ struct SolverState {
   double* hist;      // [rhs][kHistCap] relative residual after each inner iteration
   unsigned long long* t0;  // solve start, device global timer (ns)
   long long* nlaunch;      // kernels run by a graph-driven solve
+  // s-step GMRES (desc.sstep > 0)
+  double2* Hraw;     // [rhs][(m+1) * m] the unrotated Hessenberg matrix
+  double2* theta;    // [rhs][8] Newton shifts
+  double2* cb;       // [rhs][2][(m+1+s) s] block coefficients: pass 1 C, pass 2 C and Gram
+  double2* rinv;     // [rhs][64] inverse of the block's Cholesky factor
+  double2* bpart;    // [blocks][(m+1+s) s] block partial sums (k_sdots)
 };
 
 // Residual-history entries kept per right-hand side on the device.
@@ -156,6 +162,7 @@ struct Layout {
   void* V = nullptr;       // [(m+1)][rhs][nu] inner precision
   void* Wv = nullptr;      // [rhs][nu] inner precision (A P^-1 v)
   void* Zv = nullptr;      // [rhs][nu] inner precision (P^-1 v)
+  void* Wb = nullptr;      // [s][rhs][nu] inner precision: s-step Newton vectors
   void* R128 = nullptr;    // [rhs][nu] complex128 residual
   void* B128 = nullptr;    // [rhs][nu] complex128 right-hand side
   SolverState st{};

@@ -76,7 +76,7 @@ EXPORTS = ("dda_workspace_size", "dda_plan_create", "dda_set_incidence", "dda_in
            "dda_set_voxel_eps",
            "dda_matvec", "dda_precond_build", "dda_precond_apply", "dda_precond_apply_noalloc",
            "dda_precond2_build", "dda_precond2_apply",
-           "dda_fft3d", "dda_solve", "dda_solve_many",
+           "dda_fft3d", "dda_solve", "dda_solve_many", "dda_ritz_shifts",
            "dda_cross_sections", "dda_adjoint_rhs", "dda_ext_gradient", "dda_profile_enable", "dda_profile_read", "dda_plan_destroy",
            "dda_schedule_set", "dda_schedule_get", "dda_autotune",
            "dda_last_error", "dda_launch_count")
@@ -98,7 +98,7 @@ class PlanDesc(ctypes.Structure):
                 ("krylov_m", ctypes.c_int32), ("precisions", ctypes.c_int32),
                 ("precond2", ctypes.c_int32), ("circulant", ctypes.c_int32),
                 ("voxel_eps", ctypes.c_int32), ("rhs_chunk", ctypes.c_int32),
-                ("krylov_c64", ctypes.c_int32)]
+                ("krylov_c64", ctypes.c_int32), ("sstep", ctypes.c_int32)]
 
 
 class Incidence(ctypes.Structure):
@@ -185,8 +185,25 @@ _lib.dda_plan_destroy.restype = None
 _lib.dda_plan_destroy.argtypes = [_vp]
 _lib.dda_last_error.restype = ctypes.c_char_p
 _lib.dda_last_error.argtypes = []
+_lib.dda_ritz_shifts.restype = ctypes.c_int
+_lib.dda_ritz_shifts.argtypes = [_vp, ctypes.c_int32, _vp, ctypes.c_int32, ctypes.c_int32, _vp, _vp]
 _lib.dda_launch_count.restype = ctypes.c_int64
 _lib.dda_launch_count.argtypes = []
+
+
+def ritz_shifts(hraw: torch.Tensor, jlen: torch.Tensor, s: int) -> torch.Tensor:
+    """dda_ritz_shifts: hraw (nrhs, m, m+1) complex128 CUDA tensor whose row j
+    is Hessenberg column j; jlen (nrhs,) int32 CUDA.  Returns (nrhs, 8)
+    complex128 shifts (the first s used)."""
+    if (hraw.dtype != torch.complex128 or not hraw.is_cuda or hraw.dim() != 3 or
+            hraw.shape[2] != hraw.shape[1] + 1 or not hraw.is_contiguous()):
+        raise ValueError("hraw must be a contiguous (nrhs, m, m+1) complex128 CUDA tensor")
+    if jlen.dtype != torch.int32 or jlen.shape != (hraw.shape[0],) or not jlen.is_cuda:
+        raise ValueError("jlen must be an (nrhs,) int32 CUDA tensor")
+    out = torch.zeros((hraw.shape[0], 8), dtype=torch.complex128, device=hraw.device)
+    _check(_lib.dda_ritz_shifts(_ptr(hraw), hraw.shape[1], _ptr(jlen.contiguous()),
+                                hraw.shape[0], int(s), _ptr(out), _stream()))
+    return out
 
 
 def launch_count() -> int:
@@ -225,10 +242,10 @@ def _prec_of(t: torch.Tensor) -> int:
 
 def workspace_size(l, m, n, dx, k, n_materials=1, max_rhs=1, krylov_m=0,
                    precisions=PLAN_C128 | PLAN_C64, precond2=0, circulant="chan",
-                   voxel_eps=False, rhs_chunk=0, krylov_c64=False) -> int:
+                   voxel_eps=False, rhs_chunk=0, krylov_c64=False, sstep=0) -> int:
     d = PlanDesc(l, m, n, dx, k, n_materials, max_rhs, krylov_m, precisions,
                  _precond2_code(precond2, (l, m, n)), CIRCULANTS[circulant], int(bool(voxel_eps)),
-                 int(rhs_chunk), int(bool(krylov_c64)))
+                 int(rhs_chunk), int(bool(krylov_c64)), int(sstep))
     return int(_lib.dda_workspace_size(ctypes.byref(d)))
 
 
@@ -262,13 +279,14 @@ class Plan:
     def __init__(self, mat: torch.Tensor, eps, dx: float, k: float, max_rhs: int = 1,
                  krylov_m: int = 0, precisions: int = PLAN_C128 | PLAN_C64,
                  precond2=False, circulant: str = "chan", voxel_eps: torch.Tensor | None = None,
-                 rhs_chunk: int = 0, krylov_c64: bool = False):
+                 rhs_chunk: int = 0, krylov_c64: bool = False, sstep: int = 0):
         """mat: (n, m, l) uint8 material per voxel (0 air); eps: permittivity of
         materials 1..K; voxel_eps: optional (n, m, l) complex128 permittivity of
         every voxel (dda_set_voxel_eps), which then overrides the table on
         scatterer voxels (the table still gives alpha_tilde); rhs_chunk: right-hand
         sides per pass through the FFT scratch (0: all of max_rhs); krylov_c64:
-        Krylov basis in complex64 (complex64 cycles only, half the memory)."""
+        Krylov basis in complex64 (complex64 cycles only, half the memory);
+        sstep: block size reserved for the s-step GMRES (solve method=2)."""
         if mat.dtype != torch.uint8 or not mat.is_cuda or mat.dim() != 3:
             raise TypeError("mat must be a (n, m, l) uint8 CUDA tensor")
         self.mat = mat.contiguous()
@@ -278,7 +296,7 @@ class Plan:
         self.desc = PlanDesc(l, m, n, float(dx), float(k), len(eps), int(max_rhs), int(krylov_m),
                              int(precisions), _precond2_code(precond2, (l, m, n)),
                              CIRCULANTS[circulant], int(voxel_eps is not None), int(rhs_chunk),
-                             int(bool(krylov_c64)))
+                             int(bool(krylov_c64)), int(sstep))
         size = int(_lib.dda_workspace_size(ctypes.byref(self.desc)))
         if size == 0:
             raise DDAError(1, last_error())
@@ -428,7 +446,8 @@ class Plan:
               inner_prec: int = C128, inner_tol: float = 0.0, raise_on_error: bool = True,
               nrhs: int | None = None, reorth_eta: float = 0.5 ** 0.5,
               method: int = 0, history: int = 0, timeout_ms: float = 0.0) -> SolveResult:
-        """dda_solve.  history: entries of residual history kept per right-hand
+        """dda_solve.  method: 0 GMRES, 1 BiCG-Stab, 2 s-step GMRES (the plan's
+        sstep); history: entries of residual history kept per right-hand
         side (0: none); timeout_ms: the solve's time limit on the device (0:
         none; a right-hand side stopped by it ends with DDA_ERR_TIMEOUT)."""
         nrhs = nrhs or (b.shape[0] if b is not None else self.nrhs)

@@ -377,6 +377,11 @@ __device__ __forceinline__ void rr_fft3c_body(cx<float>* data, long ncols, long 
   }
   const int b = tid % NBC, jb = tid / NBC;  // jb < R1
   cx<T> x[3][R2];
+  // the spectrum of the first frequency is requested before stage C, that of
+  // each next one before the current one is multiplied (D)
+  const auto ctx = op.column(slab, col0 + b);
+  typename Op::G6r gn;
+  op.load_raw(ctx, jb, gn);
   // C: inputs rows jb + q R1, twiddle w^(q jb), outputs frequencies jb + q R1
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -387,10 +392,11 @@ __device__ __forceinline__ void rr_fft3c_body(cx<float>* data, long ncols, long 
     dft<R2, false>(x[c]);
   }
   // D
-  {
-    const auto ctx = op.column(slab, col0 + b);
 #pragma unroll
-    for (int q = 0; q < R2; ++q) op.point(ctx, jb + q * R1, x[0][q], x[1][q], x[2][q]);
+  for (int q = 0; q < R2; ++q) {
+    const typename Op::G6r g = gn;
+    if (q + 1 < R2) op.load_raw(ctx, jb + (q + 1) * R1, gn);
+    op.mul_raw(g, x[0][q], x[1][q], x[2][q]);
   }
   // E: inverse radix R2 on the same frequencies, outputs rows jb R2 + q
 #pragma unroll

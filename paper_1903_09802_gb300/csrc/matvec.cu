@@ -49,6 +49,36 @@ struct KernelMul {
     c.g = G + ((size_t)fy * hx + fx) * 6;
     return c;
   }
+  // The spectrum entries of frequency j as loaded (complex64), their signs
+  // applied only in mul_raw: the register-resident z pass issues the loads of
+  // the next frequency before it multiplies the current one.
+  struct G6r {
+    float4 a, b, c;
+    bool fxy, fxz, fyz;
+  };
+  __device__ __forceinline__ void load_raw(const Col& c, int j, G6r& g) const {
+    bool flz;
+    const int fz = fold_axis(j, Lz, flz);
+    const float4* p = reinterpret_cast<const float4*>(c.g + (size_t)fz * hy * hx * 6);
+    g.a = __ldg(p);
+    g.b = __ldg(p + 1);
+    g.c = __ldg(p + 2);
+    g.fxy = c.flx != c.fly;
+    g.fxz = c.flx != flz;
+    g.fyz = c.fly != flz;
+  }
+  __device__ __forceinline__ void mul_raw(const G6r& g, cx<T>& x0, cx<T>& x1, cx<T>& x2) const {
+    const cx<T> gxx = mk<T>(g.a.x, g.a.y), gyy = mk<T>(g.b.z, g.b.w), gzz = mk<T>(g.c.z, g.c.w);
+    const cx<T> gxy = g.fxy ? mk<T>(-g.a.z, -g.a.w) : mk<T>(g.a.z, g.a.w);
+    const cx<T> gxz = g.fxz ? mk<T>(-g.b.x, -g.b.y) : mk<T>(g.b.x, g.b.y);
+    const cx<T> gyz = g.fyz ? mk<T>(-g.c.x, -g.c.y) : mk<T>(g.c.x, g.c.y);
+    const cx<T> y0 = gxx * x0 + gxy * x1 + gxz * x2;
+    const cx<T> y1 = gxy * x0 + gyy * x1 + gyz * x2;
+    const cx<T> y2 = gxz * x0 + gyz * x1 + gzz * x2;
+    x0 = y0;
+    x1 = y1;
+    x2 = y2;
+  }
   __device__ __forceinline__ void point(const Col& c, int j, cx<T>& x0, cx<T>& x1,
                                         cx<T>& x2) const {
     bool flz;

@@ -196,15 +196,18 @@ __global__ void __launch_bounds__(1024)
       colk[j] = A[(size_t)j * N + k];
     }
     __syncthreads();
-    for (long e = tid; e < (long)N * N; e += nth) {
-      const int i = (int)(e / N), j = (int)(e % N);
+    // a warp per row, lanes along it (coalesced, no index division)
+    for (int i = wid; i < N; i += nth >> 5) {
+      float2* Ai = A + (size_t)i * N;
       if (i == k) {
-        A[e] = rowk[j];
+        for (int j = lane; j < N; j += 32) Ai[j] = rowk[j];
       } else {
         const float2 f = colk[i];
-        const float2 base = j == k ? make_float2(0.f, 0.f) : A[e];
-        const float2 pr2 = cmulf(f, rowk[j]);
-        A[e] = make_float2(base.x - pr2.x, base.y - pr2.y);
+        for (int j = lane; j < N; j += 32) {
+          const float2 base = j == k ? make_float2(0.f, 0.f) : Ai[j];
+          const float2 pr2 = cmulf(f, rowk[j]);
+          Ai[j] = make_float2(base.x - pr2.x, base.y - pr2.y);
+        }
       }
     }
     __syncthreads();

@@ -804,6 +804,32 @@ def roofline_128(runner, peak, peak_kind):
             "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs", "passes": passes}
 
 
+def matvec_only(edge, reps, warmup):
+    """The complex64 matvec alone on the edge^3 prism (k dx = 0.625, m =
+    1.31+0.01i, one right-hand side): warmup + reps calls, then a line with
+    the mean CUDA-event time per call."""
+    import torch
+    from dda_inputs import prism_case
+    from paper_1903_09802_gb300 import dda
+    dev = torch.device("cuda", 0)
+    case = prism_case(edge, edge / 3.2, 1.31 + 0.01j, 1.0)
+    plan = dda.Plan(torch.from_numpy(case.mask()).to(dev), case.eps, case.dx, case.k, max_rhs=1)
+    plan.set_incidence(case.dirs, case.pols)
+    x = plan.incident_field(1).to(torch.complex64)
+    y = torch.empty_like(x)
+    for _ in range(warmup):
+        plan.matvec(x, out=y)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        plan.matvec(x, out=y)
+    e1.record()
+    e1.synchronize()
+    print(json.dumps({"matvec_only": f"{edge}^3", "reps": reps,
+                      "us_per_matvec": round(1e3 * e0.elapsed_time(e1) / max(reps, 1), 1)}))
+
+
 def oracle_iterations():
     """Iteration counts of the oracle's own solves of the workload, written by
     oracle/iteration_counts.py (key: box dims, eps, rhs)."""
@@ -1121,7 +1147,13 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the untimed solver comparisons")
+    ap.add_argument("--matvec-only", type=int, default=0, metavar="N",
+                    help="only run the complex64 matvec on the N^3 prism (x = N/3.2, one RHS) "
+                         "--steps times after --warmup: a small case for profiler captures")
     args = ap.parse_args()
+    if args.matvec_only:
+        matvec_only(args.matvec_only, args.steps, args.warmup)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

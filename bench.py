@@ -159,6 +159,27 @@ class Runner:
     def flush_l2(self):
         self.flush_buf.fill_(1)
 
+    def replay_matvec(self, dims, reps):
+        """Profile of reps complex64 matvecs (two right-hand sides) on the
+        plan of the step's first system with box dims, launched back to back."""
+        torch, dda = self.torch, self.dda
+        i = next(k for k, c in enumerate(self.cases) if c.dims == dims)
+        case = self.cases[i]
+        plan = dda.Plan(self.masks[i], case.eps, case.dx, case.k, max_rhs=2)
+        plan.set_incidence(case.dirs, case.pols)
+        x = plan.incident_field(2).to(torch.complex64)
+        y = torch.empty_like(x)
+        for _ in range(3):
+            plan.matvec(x, out=y)
+        plan.profile(True)
+        plan.profile_read()
+        for _ in range(reps):
+            plan.matvec(x, out=y)
+        prof = plan.profile_read()
+        plan.profile(False)
+        del plan
+        return prof
+
     def step(self, masks=None, host_out=None, inner="c64", method=None):
         dda = self.dda
         method = STEP_METHOD if method is None else method
@@ -251,6 +272,15 @@ def roofline(runner, peak, peak_kind):
                 den += c
         traffic = round(num / den) if den else None
     achieved = nbytes / (ms * 1e-3) / 1e9 if ms > 0 else 0.0
+    replay = None
+    if hasattr(runner, "replay_matvec") and dom.startswith("mv_"):
+        try:
+            counts = {}
+            for c, prof in runner.prof:
+                counts[c.dims] = counts.get(c.dims, 0) + prof[dom][1]
+            replay = matvec_replay(runner, dom, counts)
+        except Exception as exc:  # a side measurement must not cost the roofline
+            replay = {"error": repr(exc)[:200]}
     total_ms = sum(x[0] for x in tot.values())
     share = {k: round(v[0] / total_ms, 4) for k, v in tot.items() if v[0] > 0}
     per_class = {k: round(v[2] / (v[0] * 1e-3) / 1e9, 1) for k, v in tot.items() if v[0] > 0}
@@ -259,7 +289,27 @@ def roofline(runner, peak, peak_kind):
             "avg_launch_us": round(ms / cnt * 1e3, 2) if cnt else None,
             "algorithmic_bytes_per_launch": round(nbytes / cnt) if cnt else None,
             "traffic": traffic, "share_of_profiled_kernel_time": share,
-            "achieved_gbs_by_class": per_class}
+            "achieved_gbs_by_class": per_class, "replay_back_to_back": replay}
+
+
+def matvec_replay(runner, cls, launches, reps=20):
+    """The class's launches without the solve loop's host gaps: the step's
+    matvec (complex64, its two right-hand sides) back to back on each
+    system's plan, CUDA events per launch, averaged with the profiled step's
+    launch counts per box as weights."""
+    t = b = n = 0.0
+    per_box = {}
+    for dims, cnt in launches.items():
+        if not cnt:
+            continue
+        ms, c, nbytes = runner.replay_matvec(dims, reps)[cls]
+        per_box["x".join(map(str, dims))] = round(1e3 * ms / c, 1)
+        t += cnt * ms / c
+        b += cnt * nbytes / c
+        n += cnt
+    us = 1e3 * t / n
+    return {"avg_launch_us": round(us, 2), "achieved": round(b / n / (us * 1e-6) / 1e9, 1),
+            "us_per_launch_by_box": per_box}
 
 
 def compare_solvers(runner):
@@ -804,18 +854,26 @@ def roofline_128(runner, peak, peak_kind):
             "peak": peak, "peak_kind": f"{peak_kind} hbm_gbs", "passes": passes}
 
 
-def matvec_only(edge, reps, warmup):
-    """The complex64 matvec alone on the edge^3 prism (k dx = 0.625, m =
-    1.31+0.01i, one right-hand side): warmup + reps calls, then a line with
-    the mean CUDA-event time per call."""
+def matvec_only(box, reps, warmup, nrhs=1):
+    """The complex64 matvec alone: on the N^3 prism (box "N": k dx = 0.625,
+    m = 1.31+0.01i) or on the timed step's first system with box "LxMxN",
+    nrhs right-hand sides (the incident waves, repeated); warmup + reps
+    calls, then a line with the mean CUDA-event time per call."""
     import torch
     from dda_inputs import prism_case
     from paper_1903_09802_gb300 import dda
     dev = torch.device("cuda", 0)
-    case = prism_case(edge, edge / 3.2, 1.31 + 0.01j, 1.0)
-    plan = dda.Plan(torch.from_numpy(case.mask()).to(dev), case.eps, case.dx, case.k, max_rhs=1)
-    plan.set_incidence(case.dirs, case.pols)
-    x = plan.incident_field(1).to(torch.complex64)
+    if "x" in box:
+        dims = tuple(int(v) for v in box.split("x"))
+        case = next(c for c in workload_cases() if c.dims == dims)
+    else:
+        edge = int(box)
+        case = prism_case(edge, edge / 3.2, 1.31 + 0.01j, 1.0)
+    plan = dda.Plan(torch.from_numpy(case.mask()).to(dev), case.eps, case.dx, case.k,
+                    max_rhs=nrhs)
+    plan.set_incidence([case.dirs[i % len(case.dirs)] for i in range(nrhs)],
+                       [case.pols[i % len(case.pols)] for i in range(nrhs)])
+    x = plan.incident_field(nrhs).to(torch.complex64)
     y = torch.empty_like(x)
     for _ in range(warmup):
         plan.matvec(x, out=y)
@@ -826,7 +884,7 @@ def matvec_only(edge, reps, warmup):
         plan.matvec(x, out=y)
     e1.record()
     e1.synchronize()
-    print(json.dumps({"matvec_only": f"{edge}^3", "reps": reps,
+    print(json.dumps({"matvec_only": box, "nrhs": nrhs, "reps": reps,
                       "us_per_matvec": round(1e3 * e0.elapsed_time(e1) / max(reps, 1), 1)}))
 
 
@@ -1147,12 +1205,14 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the untimed solver comparisons")
-    ap.add_argument("--matvec-only", type=int, default=0, metavar="N",
-                    help="only run the complex64 matvec on the N^3 prism (x = N/3.2, one RHS) "
-                         "--steps times after --warmup: a small case for profiler captures")
+    ap.add_argument("--matvec-only", default="", metavar="N|LxMxN",
+                    help="only run the complex64 matvec, --steps times after --warmup, on the N^3 "
+                         "prism (x = N/3.2) or on the timed step's first system with box LxMxN: "
+                         "a small case for profiler captures")
+    ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides of --matvec-only")
     args = ap.parse_args()
     if args.matvec_only:
-        matvec_only(args.matvec_only, args.steps, args.warmup)
+        matvec_only(args.matvec_only, args.steps, args.warmup, args.nrhs)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

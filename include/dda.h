@@ -358,8 +358,10 @@ dda_status_t dda_cross_sections(dda_plan_t plan, int32_t nrhs, const void* d_c, 
  * spectrum multiply, y inverse, x inverse with the diagonal), 5..9 the
  * preconditioner's passes in the same order, 10 Gram-Schmidt dots,
  * 11 Gram-Schmidt update (first pass only), 12 the 2-level
- * preconditioner's block pass (its FFT passes count as 5, 6, 8, 9); n entries
- * are written (n <= 13); reset != 0 zeroes the sums.  h_bytes (may be NULL) receives the
+ * preconditioner's block pass (its FFT passes count as 5, 6, 8, 9), 13..17
+ * the matvec passes and 18..22 the preconditioner passes of complex128
+ * launches (0..9 count complex64 launches only); n entries are written
+ * (n <= 23); reset != 0 zeroes the sums.  h_bytes (may be NULL) receives the
  * summed algorithmic bytes of the timed launches: per right-hand side and
  * with F = one three-component box field (3 l m n values), matvec passes 3F
  * (+mask), 6F, 8F (+ the kernel spectrum once), 6F, 4F (+mask);

@@ -245,7 +245,11 @@ __global__ void k_green_generator(double2* out, int c, long l, long m, long n, l
 }
 
 // Keep the octant 0..L/2 of each axis of a full spectrum (the rest follows
-// from the block's parity) as component c of the interleaved [..][6] store.
+// from the block's parity) as component c.  The complex128 store interleaves
+// the six components of a frequency ([z][y][x][6]); the complex64 store keeps
+// them as three planes of component pairs per (z, y) row,
+// [z][y][pair c/2][x][c%2], so that the 16-byte pair loads of neighbouring x
+// frequencies are contiguous (one 128-byte line for 8 frequencies).
 __global__ void k_compress(const double2* full, long Lx, long Ly, long Lz, long hx, long hy,
                            long hz, int c, double2* out128, float2* out64) {
   pdl_entry();
@@ -255,7 +259,9 @@ __global__ void k_compress(const double2* full, long Lx, long Ly, long Lz, long 
     const long x = i % hx, y = (i / hx) % hy, z = i / (hx * hy);
     const double2 v = full[(z * Ly + y) * Lx + x];
     if (out128) out128[i * 6 + c] = v;
-    if (out64) out64[i * 6 + c] = make_float2((float)v.x, (float)v.y);
+    if (out64)
+      out64[(((z * hy + y) * 3 + c / 2) * hx + x) * 2 + (c & 1)] =
+          make_float2((float)v.x, (float)v.y);
   }
 }
 

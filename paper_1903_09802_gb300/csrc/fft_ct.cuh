@@ -314,13 +314,20 @@ __device__ __forceinline__ void rr_fft3c_body(cx<float>* data, long ncols, long 
   using T = float;
   constexpr int NL = 3 * NBC;  // lines (component, column) of the tile
   constexpr int LD = NL;       // shared row pitch
+  // With 24 lines (8-column tiles) every group of 8 rows is followed by 8
+  // unused values: the stores of stage E (rows jb R2 + q, four jb per warp)
+  // and B then fall on distinct banks (2 wavefronts per access instead of 4).
+  constexpr int PADR = NL == 24 ? 8 : 0;
   constexpr int NTH = R1 * NBC;
   constexpr int NBF = NL * R2;                // butterflies of stage B (and F)
   constexpr int GB = (NBF + NTH - 1) / NTH;   // per thread
   constexpr int H = L / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
-  cx<T>* stw = s + L * LD;
+  cx<T>* stw = s + L * LD + (L / 8) * PADR;
+  // row(a + b) = row(a) + row(b) when a or b is a multiple of 8: the
+  // compile-time part of each index below is kept apart
+  auto row = [](int j) { return j * LD + (j >> 3) * PADR; };
   const int tid = threadIdx.x;
   const long tiles = ncols / NBC;
   const long slab = blockIdx.x / tiles;
@@ -341,7 +348,7 @@ __device__ __forceinline__ void rr_fft3c_body(cx<float>* data, long ncols, long 
   for (int e = tid; e < ROWS_IN * NL; e += NTH) {
     const int j = e / NL, line = e - j * NL;
     const int c = line / NBC, b = line - c * NBC;
-    cp_async_cx(s + j * LD + line, base + c * cs + (long)j * js + b, true);
+    cp_async_cx(s + row(j) + line, base + c * cs + (long)j * js + b, true);
   }
   op.prefetch(col0, NBC, L);
   load_twiddles(stw, tw, L, twshift);
@@ -356,7 +363,7 @@ __device__ __forceinline__ void rr_fft3c_body(cx<float>* data, long ncols, long 
       if (u < NBF) {
         const int jb = u / NL, line = u - jb * NL;
 #pragma unroll
-        for (int q = 0; q < (HALF ? R1 / 2 : R1); ++q) v[g][q] = s[(jb + q * R2) * LD + line];
+        for (int q = 0; q < (HALF ? R1 / 2 : R1); ++q) v[g][q] = s[row(jb) + row(q * R2) + line];
       }
     }
     __syncthreads();
@@ -370,7 +377,7 @@ __device__ __forceinline__ void rr_fft3c_body(cx<float>* data, long ncols, long 
         else
           dft<R1, false>(v[g]);
 #pragma unroll
-        for (int q = 0; q < R1; ++q) s[(jb * R1 + q) * LD + line] = v[g][q];
+        for (int q = 0; q < R1; ++q) s[row(jb * R1) + row(q) + line] = v[g][q];
       }
     }
     __syncthreads();
@@ -386,7 +393,7 @@ __device__ __forceinline__ void rr_fft3c_body(cx<float>* data, long ncols, long 
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
 #pragma unroll
-    for (int q = 0; q < R2; ++q) x[c][q] = s[(jb + q * R1) * LD + c * NBC + b];
+    for (int q = 0; q < R2; ++q) x[c][q] = s[row(jb) + row(q * R1) + c * NBC + b];
 #pragma unroll
     for (int q = 1; q < R2; ++q) x[c][q] = mulc<false>(x[c][q], stw[q * jb]);
     dft<R2, false>(x[c]);
@@ -405,7 +412,7 @@ __device__ __forceinline__ void rr_fft3c_body(cx<float>* data, long ncols, long 
 #pragma unroll
   for (int c = 0; c < 3; ++c)
 #pragma unroll
-    for (int q = 0; q < R2; ++q) s[(jb * R2 + q) * LD + c * NBC + b] = x[c][q];
+    for (int q = 0; q < R2; ++q) s[row(jb * R2) + row(q) + c * NBC + b] = x[c][q];
   __syncthreads();
   // F: inputs rows j2 + q R2, twiddle conj(w)^(q j2), outputs rows j2 + q R2 < L/2
 #pragma unroll
@@ -416,7 +423,7 @@ __device__ __forceinline__ void rr_fft3c_body(cx<float>* data, long ncols, long 
       const int c = line / NBC, bb = line - c * NBC;
       cx<T> v[R1];
 #pragma unroll
-      for (int q = 0; q < R1; ++q) v[q] = s[(j2 + q * R2) * LD + line];
+      for (int q = 0; q < R1; ++q) v[q] = s[row(j2) + row(q * R2) + line];
 #pragma unroll
       for (int q = 1; q < R1; ++q) v[q] = mulc<true>(v[q], stw[q * j2]);
       if constexpr (HALF)
@@ -657,7 +664,9 @@ template <int L, int R1, int R2, int NBC, bool HALF, class Op>
 void rr_fft3c_launch(cx<float>* data, long ncols, long nslabs, long js, long cs, long ss,
                      const Op& op, const cx<float>* tw, int Lmax, int row_len, int nrows,
                      cudaStream_t s) {
-  const size_t smem = ((size_t)3 * NBC * L + L) * sizeof(cx<float>);
+  // tile, its row padding (8 values per 8 rows with 8-column tiles) and the twiddles
+  const size_t smem =
+      ((size_t)3 * NBC * L + (3 * NBC == 24 ? L : 0) + L) * sizeof(cx<float>);
   // 256-thread tiles (lengths 128 and 256) with registers bounded so that
   // three blocks share an SM (schedule z_occ, the default): measured 11%
   // faster at length 256 and 4% at 128 than the compiler's own count (two

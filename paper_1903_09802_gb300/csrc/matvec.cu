@@ -23,6 +23,9 @@ namespace {
 // block's parity.
 template <typename T>
 struct KernelMul {
+  // complex64: three planes of component pairs per (z, y) row (see
+  // k_compress); other precisions: the six components of a frequency together
+  static constexpr bool kPlanar = std::is_same<T, float>::value;
   const cx<T>* G;
   int Lx, Ly, Lz, hx, hy, lxs;
   // Pull the spectrum entries of this tile (all kz) towards L2 before the
@@ -32,10 +35,22 @@ struct KernelMul {
     bool fl;
     const int fy = fold_axis(ky, Ly, fl);
     const int nz = Lz / 2 + 1;
-    for (int i = threadIdx.x; i < ncol * nz; i += blockDim.x) {
-      const int b = i % ncol, fz = i / ncol;
-      const int fx = fold_axis((int)((col0 + b) & (Lx - 1)), Lx, fl);
-      prefetch_l2(G + ((size_t)(fz * hy + fy) * hx + fx) * 6);
+    if constexpr (kPlanar) {
+      // the tile's x frequencies are one contiguous run of each pair plane:
+      // its two ends cover it
+      const int fa = fold_axis((int)(col0 & (Lx - 1)), Lx, fl);
+      const int fb = fold_axis((int)((col0 + ncol - 1) & (Lx - 1)), Lx, fl);
+      for (int i = threadIdx.x; i < nz * 6; i += blockDim.x) {
+        const int fz = i / 6, pr = (i >> 1) % 3;
+        const int fx = (i & 1) ? fb : fa;
+        prefetch_l2(G + ((((size_t)fz * hy + fy) * 3 + pr) * hx + fx) * 2);
+      }
+    } else {
+      for (int i = threadIdx.x; i < ncol * nz; i += blockDim.x) {
+        const int b = i % ncol, fz = i / ncol;
+        const int fx = fold_axis((int)((col0 + b) & (Lx - 1)), Lx, fl);
+        prefetch_l2(G + ((size_t)(fz * hy + fy) * hx + fx) * 6);
+      }
     }
   }
   struct Col {
@@ -46,7 +61,7 @@ struct KernelMul {
     Col c;
     const int fx = fold_axis((int)(col & (Lx - 1)), Lx, c.flx);
     const int fy = fold_axis((int)(col >> lxs), Ly, c.fly);
-    c.g = G + ((size_t)fy * hx + fx) * 6;
+    c.g = kPlanar ? G + ((size_t)fy * 3 * hx + fx) * 2 : G + ((size_t)fy * hx + fx) * 6;
     return c;
   }
   // The spectrum entries of frequency j as loaded (complex64), their signs
@@ -57,12 +72,13 @@ struct KernelMul {
     bool fxy, fxz, fyz;
   };
   __device__ __forceinline__ void load_raw(const Col& c, int j, G6r& g) const {
+    static_assert(kPlanar, "pair planes: the complex64 store");
     bool flz;
     const int fz = fold_axis(j, Lz, flz);
     const float4* p = reinterpret_cast<const float4*>(c.g + (size_t)fz * hy * hx * 6);
     g.a = __ldg(p);
-    g.b = __ldg(p + 1);
-    g.c = __ldg(p + 2);
+    g.b = __ldg(p + hx);
+    g.c = __ldg(p + 2 * hx);
     g.fxy = c.flx != c.fly;
     g.fxz = c.flx != flz;
     g.fyz = c.fly != flz;
@@ -81,17 +97,23 @@ struct KernelMul {
   }
   __device__ __forceinline__ void point(const Col& c, int j, cx<T>& x0, cx<T>& x1,
                                         cx<T>& x2) const {
-    bool flz;
-    const int fz = fold_axis(j, Lz, flz);
-    cx<T> gxx, gxy, gxz, gyy, gyz, gzz;
-    load_sym6(c.g + (size_t)fz * hy * hx * 6, c.flx != c.fly, c.flx != flz, c.fly != flz, gxx, gxy,
-              gxz, gyy, gyz, gzz);
-    const cx<T> y0 = gxx * x0 + gxy * x1 + gxz * x2;
-    const cx<T> y1 = gxy * x0 + gyy * x1 + gyz * x2;
-    const cx<T> y2 = gxz * x0 + gyz * x1 + gzz * x2;
-    x0 = y0;
-    x1 = y1;
-    x2 = y2;
+    if constexpr (kPlanar) {
+      G6r g;
+      load_raw(c, j, g);
+      mul_raw(g, x0, x1, x2);
+    } else {
+      bool flz;
+      const int fz = fold_axis(j, Lz, flz);
+      cx<T> gxx, gxy, gxz, gyy, gyz, gzz;
+      load_sym6(c.g + (size_t)fz * hy * hx * 6, c.flx != c.fly, c.flx != flz, c.fly != flz, gxx,
+                gxy, gxz, gyy, gyz, gzz);
+      const cx<T> y0 = gxx * x0 + gxy * x1 + gxz * x2;
+      const cx<T> y1 = gxy * x0 + gyy * x1 + gyz * x2;
+      const cx<T> y2 = gxz * x0 + gyz * x1 + gzz * x2;
+      x0 = y0;
+      x1 = y1;
+      x2 = y2;
+    }
   }
 };
 
@@ -299,24 +321,26 @@ void matvec_core(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t
   const long plane = Ly * Lx;
   const double u = (double)nrhs * 3 * p->nvox * sizeof(cx<T>);  // box fields of the batch
   const double spec = 6.0 * p->hx * p->hy * p->hz * sizeof(cx<T>);
+  // complex128 launches are timed apart from the complex64 ones
+  constexpr int pc = std::is_same<T, float>::value ? 0 : PROF_MV128_XF - PROF_MV_XF;
   // 1: x forward of the masked field, l -> 2l
-  p->prof.begin(PROF_MV_XF, s, 3 * u + p->nvox);
+  p->prof.begin(PROF_MV_XF + pc, s, 3 * u + p->nvox);
   launch_contig<T, false>(x, b1, p->mat, nullptr, nm, lines, (int)Lx, (int)l, l, (int)Lx, Lx, T(1), tw,
                           p->Lmax, s);
   p->prof.end(s);
   // 2: y forward, m -> 2m
-  p->prof.begin(PROF_MV_YF, s, 6 * u);
+  p->prof.begin(PROF_MV_YF + pc, s, 6 * u);
   launch_strided<T, false>(b1, b2, Lx, (long)nrhs * 3 * n, (int)Ly, (int)m, Lx, m * Lx, (int)Ly,
                            Lx, plane, T(1), tw, p->Lmax, s);
   p->prof.end(s);
   // 3: z forward, spectrum multiply, z inverse (n live planes in and out)
   KernelMul<T> op{G_of<T>(p), (int)Lx, (int)Ly, (int)Lz, p->hx, p->hy, ilog2((int)Lx)};
-  p->prof.begin(PROF_MV_Z, s, 8 * u + spec);
+  p->prof.begin(PROF_MV_Z + pc, s, 8 * u + spec);
   launch_fft3c_any<true, true>(b2, plane, nrhs, (int)Lz, (int)n, plane, n * plane, 3 * n * plane,
                                (int)n, op, tw, p->Lmax, (int)Lx, (int)Ly, s);
   p->prof.end(s);
   // 4: y inverse, 2m -> m
-  p->prof.begin(PROF_MV_YI, s, 6 * u);
+  p->prof.begin(PROF_MV_YI + pc, s, 6 * u);
   launch_strided<T, true>(b2, b1, Lx, (long)nrhs * 3 * n, (int)Ly, (int)Ly, Lx, plane, (int)m, Lx,
                           m * Lx, T(1), tw, p->Lmax, s);
   p->prof.end(s);
@@ -324,7 +348,7 @@ void matvec_core(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t
   if constexpr (sizeof(T) == 4) {
     if (Lx >= 32 && Lx <= 512) {
       const float coef = (float)(p->d.dx * p->d.dx * p->d.dx / (double)p->P);
-      p->prof.begin(PROF_MV_XI, s, 4 * u + p->nvox);
+      p->prof.begin(PROF_MV_XI + pc, s, 4 * u + p->nvox);
       ct_epilogue(p, b1, x, y, lines, nm, coef, s, rhs0);
       p->prof.end(s);
       return;
@@ -343,7 +367,7 @@ void matvec_core(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const T coef = (T)(p->d.dx * p->d.dx * p->d.dx / (double)p->P);
-    p->prof.begin(PROF_MV_XI, s, 4 * u + p->nvox);
+    p->prof.begin(PROF_MV_XI + pc, s, 4 * u + p->nvox);
     note_launch();
     launch_k(kern, (unsigned)((lines + NB - 1) / NB), nth, smem, s,
         b1, x, y, p->mat, ainv_of<T>(p) + (long)rhs0 * (p->K + 1), p->K + 1, lines, nm, (int)l,

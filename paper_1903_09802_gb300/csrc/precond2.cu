@@ -530,11 +530,13 @@ void precond2_apply_impl(dda_plan_s* p, const P2Geom& gm, int nrhs, const cx<T>*
   const long plane = l * m;
   const double u = (double)nrhs * 3 * p->nvox * sizeof(cx<T>);
   const double blk = (double)(l / 2 + 1) * (m / 2 + 1) * 9.0 * n * n * sizeof(float2);
-  p->prof.begin(PROF_PC_XF, s, 2 * u + p->nvox);
+  // complex128 launches are timed apart from the complex64 ones
+  constexpr int pc = std::is_same<T, float>::value ? 0 : PROF_PC128_XF - PROF_PC_XF;
+  p->prof.begin(PROF_PC_XF + pc, s, 2 * u + p->nvox);
   launch_contig<T, false>(v, t, gm.mat, nullptr, n * m, lines, (int)l, (int)l, l, (int)l, l, T(1), tw,
                           p->Lmax, s);
   p->prof.end(s);
-  p->prof.begin(PROF_PC_YF, s, 2 * u);
+  p->prof.begin(PROF_PC_YF + pc, s, 2 * u);
   if (m > 1)
     launch_strided<T, false>(t, t, l, (long)nrhs * 3 * n, (int)m, (int)m, l, plane, (int)m, l, plane,
                              T(1), tw, p->Lmax, s);
@@ -583,12 +585,12 @@ void precond2_apply_impl(dda_plan_s* p, const P2Geom& gm, int nrhs, const cx<T>*
     }
   }
   p->prof.end(s);
-  p->prof.begin(PROF_PC_YI, s, 2 * u);
+  p->prof.begin(PROF_PC_YI + pc, s, 2 * u);
   if (m > 1)
     launch_strided<T, true>(t, t, l, (long)nrhs * 3 * n, (int)m, (int)m, l, plane, (int)m, l, plane,
                             T(1), tw, p->Lmax, s);
   p->prof.end(s);
-  p->prof.begin(PROF_PC_XI, s, 2 * u + p->nvox);
+  p->prof.begin(PROF_PC_XI + pc, s, 2 * u + p->nvox);
   launch_contig<T, true>(t, z, nullptr, gm.mat, n * m, lines, (int)l, (int)l, l, (int)l, l, T(1), tw,
                          p->Lmax, s);
   p->prof.end(s);

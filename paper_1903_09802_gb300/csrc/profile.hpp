@@ -24,6 +24,16 @@ enum ProfId {
   PROF_AR_DOT,     // Gram-Schmidt dot products
   PROF_AR_UPD,     // Gram-Schmidt update and norm
   PROF_P2_BLOCK,   // 2-level preconditioner: dense block per frequency pair
+  PROF_MV128_XF,   // the matvec's passes in complex128 (FP64 residuals), same order
+  PROF_MV128_YF,
+  PROF_MV128_Z,
+  PROF_MV128_YI,
+  PROF_MV128_XI,
+  PROF_PC128_XF,   // the preconditioner's passes in complex128, same order
+  PROF_PC128_YF,
+  PROF_PC128_Z,
+  PROF_PC128_YI,
+  PROF_PC128_XI,
   PROF_COUNT
 };
 

@@ -82,7 +82,9 @@ EXPORTS = ("dda_workspace_size", "dda_plan_create", "dda_set_incidence", "dda_in
            "dda_last_error", "dda_launch_count")
 
 PROFILE_NAMES = ("mv_x_fwd", "mv_y_fwd", "mv_z_mul", "mv_y_inv", "mv_x_inv", "pc_x_fwd", "pc_y_fwd",
-                 "pc_z_solve", "pc_y_inv", "pc_x_inv", "gs_dots", "gs_update", "p2_block")
+                 "pc_z_solve", "pc_y_inv", "pc_x_inv", "gs_dots", "gs_update", "p2_block",
+                 "mv128_x_fwd", "mv128_y_fwd", "mv128_z_mul", "mv128_y_inv", "mv128_x_inv",
+                 "pc128_x_fwd", "pc128_y_fwd", "pc128_z_solve", "pc128_y_inv", "pc128_x_inv")
 
 
 class DDAError(RuntimeError):

@@ -687,16 +687,18 @@ def compare_256(runner):
     return out
 
 
-def compare_uneven_batch(runner, cap=600):
+def compare_uneven_batch(runner, cap=600, smooth=True):
     """An uneven batch: 32 prisms with edges N ~ U{24..96} (seed 2), x = 0.3 N
     (k dx = 0.6), m ~ U[1.3, 1.8] + i U[0, 0.1], aspect 1, +z incidence, each
-    air-padded to its power-of-two box (64^3 or 128^3), 3-level
-    preconditioner, GMRES(50) complex64 + FP64 refinement to 1e-6, at most
-    `cap` iterations: all 32 solves in one graph launch (dda_solve_many)."""
+    air-padded to the smallest box of even 7-smooth edges that holds it
+    (smooth; mixed-radix transforms) or to its power-of-two box (64^3 or
+    128^3), 3-level preconditioner, GMRES(50) complex64 + FP64 refinement to
+    1e-6, at most `cap` iterations: all 32 solves in one graph launch
+    (dda_solve_many)."""
     import torch
     from dda_inputs import uneven_batch_cases
     dda = runner.dda
-    cases = uneven_batch_cases(32, seed=2)
+    cases = uneven_batch_cases(32, seed=2, pad_pow2=not smooth, pad_smooth=smooth)
     plans = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -728,16 +730,16 @@ def compare_uneven_batch(runner, cap=600):
     return out
 
 
-def compare_many_waves(runner, nwaves_dirs=64, restart=20, chunk=8, cap=1500):
+def compare_many_waves(runner, nwaves_dirs=64, restart=20, chunk=8, cap=1500, edge=96):
     """Many incident waves of one prism in one graph launch: the 96^3 prism
     (x = 30, m = 1.31, aspect 1) with 64 seeded directions (seed 1) x 2
     polarisations = 128 right-hand sides advancing in lock step, GMRES(20)
-    complex64 + FP64 refinement, 3-level preconditioner, to 1e-6.  Box edges
-    are powers of two here, so the prism sits in a 128^3 box (air padded);
-    the FFT scratch holds 8 right-hand sides (rhs_chunk) and the batch passes
-    through the transforms in chunks of 8.  Reports the total and per-wave
-    time, iterations, the workspace (Krylov basis in complex64:
-    krylov_c64), and C_ext of the first waves."""
+    complex64 + FP64 refinement, 3-level preconditioner, to 1e-6, in its own
+    96^3 box (mixed-radix transforms, lengths 96 and 192) or air padded to a
+    larger box (edge); the FFT scratch holds 8 right-hand sides (rhs_chunk)
+    and the batch passes through the transforms in chunks of 8.  Reports the
+    total and per-wave time, iterations, the workspace (Krylov basis in
+    complex64: krylov_c64), and C_ext of the first waves."""
     import torch
     from dda_inputs import polarisations, prism_case, random_direction
     dda = runner.dda
@@ -750,9 +752,9 @@ def compare_many_waves(runner, nwaves_dirs=64, restart=20, chunk=8, cap=1500):
             dirs.append(d)
             pols.append(e)
     case = prism_case(96, 30.0, 1.31, 1.0, dirs=dirs, pols=pols)
-    case.box = (128, 128, 128)
+    case.box = (edge, edge, edge)
     nrhs = len(dirs)
-    ws = dda.workspace_size(128, 128, 128, case.dx, case.k, 1, nrhs, restart, rhs_chunk=chunk,
+    ws = dda.workspace_size(edge, edge, edge, case.dx, case.k, 1, nrhs, restart, rhs_chunk=chunk,
                             krylov_c64=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -767,7 +769,9 @@ def compare_many_waves(runner, nwaves_dirs=64, restart=20, chunk=8, cap=1500):
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     xs = plan.cross_sections(r.x)
-    out = {"waves": nrhs, "box": "128^3 (96^3 prism, air padded)", "rhs_chunk": chunk,
+    out = {"waves": nrhs,
+           "box": f"{edge}^3" + (" (96^3 prism, air padded)" if edge != 96 else " (own box)"),
+           "rhs_chunk": chunk,
            "workspace_gb": round(ws / 1e9, 1), "setup_ms": round(1e3 * (t1 - t0), 1),
            "solve_ms": round(1e3 * (t2 - t1), 1),
            "ms_per_wave": round(1e3 * (t2 - t1) / nrhs, 2),
@@ -1122,10 +1126,14 @@ def run_ours(args, rank, world):
                  lambda: compare_precision_128(runner)),
                 ("32^3 twin (x=10, m=1.31+0.01i) vs the FP64 oracle", lambda: compare_twin(runner)),
                 ("256^3 x=80 m=1.31 GMRES(30) c64+IR", lambda: compare_256(runner)),
-                ("uneven batch: 32 prisms N~U{24..96}, one graph launch",
+                ("uneven batch: 32 prisms N~U{24..96} in 7-smooth boxes, one graph launch",
                  lambda: compare_uneven_batch(runner)),
-                ("128 waves of the 96^3 prism (x=30, m=1.31), one graph launch",
-                 lambda: compare_many_waves(runner))):
+                ("uneven batch: the same 32 prisms in power-of-two boxes, one graph launch",
+                 lambda: compare_uneven_batch(runner, smooth=False)),
+                ("128 waves of the 96^3 prism (x=30, m=1.31) in its 96^3 box, one graph launch",
+                 lambda: compare_many_waves(runner)),
+                ("128 waves of the 96^3 prism air padded to 128^3, one graph launch",
+                 lambda: compare_many_waves(runner, edge=128))):
             try:
                 comparisons[key] = fn()
             except Exception as exc:  # a side measurement must not cost the bench line

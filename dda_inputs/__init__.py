@@ -187,19 +187,36 @@ def next_pow2(v: int) -> int:
     return p
 
 
-def uneven_batch_cases(count: int = 32, seed: int = 2, kd: float = 0.6, pad_pow2: bool = True):
+def next_even_smooth(v: int) -> int:
+    """Smallest even 7-smooth number (2^a 3^b 5^c 7^d, a >= 1) >= v."""
+    e = max(2, v + (v % 2))
+    while True:
+        r = e
+        for f in (2, 3, 5, 7):
+            while r % f == 0:
+                r //= f
+        if r == 1:
+            return e
+        e += 2
+
+
+def uneven_batch_cases(count: int = 32, seed: int = 2, kd: float = 0.6, pad_pow2: bool = True,
+                       pad_smooth: bool = False):
     """An uneven batch of prisms: edges N_i drawn uniformly from 24..96, size
     parameter x_i = kd N_i / 2 (voxel size k dx = kd), refractive index
     U[1.3, 1.8] + i U[0, 0.1], aspect 1, +z incidence, x-polarised.  With
-    pad_pow2 each prism sits centred in the power-of-two box that holds it
-    (air padding)."""
+    pad_pow2 each prism sits centred in the power-of-two box that holds it,
+    with pad_smooth in the smallest box of even 7-smooth edges (air padding)."""
     rng = np.random.default_rng(seed)
     cases = []
     for _ in range(count):
         N = int(rng.integers(24, 97))
         m_index = complex(rng.uniform(1.3, 1.8), rng.uniform(0.0, 0.1))
         c = prism_case(N, kd * N / 2.0, m_index, 1.0)
-        if pad_pow2:
+        if pad_smooth:
+            L = next_even_smooth(N)
+            c.box = (L, L, L)
+        elif pad_pow2:
             L = next_pow2(N)
             c.box = (L, L, L)
         cases.append(c)

@@ -69,7 +69,11 @@ typedef enum { DDA_C128 = 0, DDA_C64 = 1 } dda_precision_t;
 typedef struct dda_plan_s* dda_plan_t;
 
 typedef struct {
-  int32_t l, m, n;       /* box edges along x, y, z: powers of two, 1..512      */
+  int32_t l, m, n;       /* box edges along x, y, z, 1..512: powers of two, or
+                            even 7-smooth numbers (2^a 3^b 5^c 7^d, a >= 1) taken
+                            by mixed-radix transforms: all of them up to 208,
+                            above that those whose transform tiles fit (see
+                            dda_plan_create)                                    */
   double dx;             /* voxel edge Delta (length unit of the caller)        */
   double k;              /* wavenumber in the same unit                          */
   int32_t n_materials;   /* K >= 1 materials; voxel material 0 is air           */
@@ -177,8 +181,12 @@ size_t dda_workspace_size(const dda_plan_desc_t* desc);
  *           (eps = m^2, Section 2.1).  Copied.
  *   d_work  device workspace of at least dda_workspace_size(desc) bytes,
  *           256-byte aligned, owned by the caller, kept by the plan.
- * Errors: DDA_ERR_INVALID_ARG, DDA_ERR_UNSUPPORTED_SIZE (edge not a power of
- * two or above 512), DDA_ERR_WORKSPACE (too small / misaligned), DDA_ERR_CUDA. */
+ * Errors: DDA_ERR_INVALID_ARG, DDA_ERR_UNSUPPORTED_SIZE (edge above 512,
+ * neither a power of two nor an even 7-smooth number, a mixed-radix edge e
+ * whose three-component tile of length e or 2e needs more than 256 threads
+ * (3 c L / 16 with c the least power of two making 3 c L a multiple of 16:
+ * 210, 250, 270, 294, 350, 378, 420, 450, 486, 490, 500), or lcm(2l, 2m, 2n)
+ * above 2^20), DDA_ERR_WORKSPACE (too small / misaligned), DDA_ERR_CUDA. */
 dda_status_t dda_plan_create(dda_plan_t* out, const dda_plan_desc_t* desc, const uint8_t* d_mat,
                              const double* h_eps, void* d_work, size_t work_bytes, void* stream);
 

@@ -69,8 +69,31 @@ bool valid_desc(const dda_plan_desc_t& d, std::string& why, dda_status_t& st) {
       (d.precisions & ~(DDA_PLAN_C128 | DDA_PLAN_C64)) != 0)
     return why = "precisions must be a non-empty set of DDA_PLAN_C128 | DDA_PLAN_C64", false;
   st = DDA_ERR_UNSUPPORTED_SIZE;
-  for (int e : {d.l, d.m, d.n})
-    if (!is_pow2(e) || e > 512) return why = "box edges must be powers of two <= 512", false;
+  for (int e : {d.l, d.m, d.n}) {
+    if (e > 512)
+      return why = "box edges must be at most 512", false;
+    // mixed-radix transforms: even 7-smooth edges (radices 2, 4, 3, 5, 7)
+    if (!is_pow2(e) && !(e % 2 == 0 && is_7smooth(e) && make_radix_plan(e).nst > 0 &&
+                         make_radix_plan(2 * e).nst > 0))
+      return why = "box edges must be powers of two or even 7-smooth numbers (2^a 3^b 5^c 7^d)",
+             false;
+    // the generic three-component tile of lengths e and 2e (16 values per
+    // thread, a power-of-two column count that makes the values a multiple of
+    // 16) must fit the double-float kernel's 256 threads
+    if (!is_pow2(e))
+      for (long L : {(long)e, 2L * e}) {
+        long nb = 1;
+        while ((3 * nb * L) % 16 != 0) nb *= 2;
+        if (3 * nb * L / 16 > 256)
+          return why = "mixed-radix edge " + std::to_string(e) +
+                       " needs a transform tile above 256 threads (every even 7-smooth edge up "
+                       "to 208 is taken)",
+                 false;
+      }
+  }
+  if (twiddle_length(d.l, d.m, d.n) > kMaxTwiddleLength)
+    return why = "the least common multiple of the padded edges 2l, 2m, 2n must be at most 2^20",
+           false;
   st = DDA_OK;
   return true;
 }
@@ -84,7 +107,7 @@ bool make_layout(const dda_plan_desc_t& d, void* ws, Layout& L, std::string& why
   const long l = d.l, m = d.m, n = d.n;
   const long Lx = 2 * l, Ly = 2 * m, Lz = 2 * n;
   const long nvox = l * m * n, P = Lx * Ly * Lz;
-  const long Lmax = std::max(Lx, std::max(Ly, Lz));
+  const long Lmax = twiddle_length(l, m, n);
   const bool h128 = d.precisions & DDA_PLAN_C128, h64 = d.precisions & DDA_PLAN_C64;
   const size_t esz = h128 ? 16 : 8;
   const long gsz = (l + 1) * (m + 1) * (n + 1) * 6;
@@ -414,7 +437,7 @@ extern "C" dda_status_t dda_plan_create(dda_plan_t* out, const dda_plan_desc_t* 
   p->Lx = 2 * p->l;
   p->Ly = 2 * p->m;
   p->Lz = 2 * p->n;
-  p->Lmax = std::max(p->Lx, std::max(p->Ly, p->Lz));
+  p->Lmax = (int)twiddle_length(p->l, p->m, p->n);
   p->nvox = (long)p->l * p->m * p->n;
   p->P = (long)p->Lx * p->Ly * p->Lz;
   p->hx = p->l + 1;

@@ -146,11 +146,20 @@ __device__ __forceinline__ void dft_half_out(cx<T>* v) {
   }
 }
 
-// Radix sequence of a transform: at most 4 stages (L <= 65536); lg = log2 L.
+// Radix sequence of a transform of length L.  Powers of two: at most 4
+// stages of radix 2..16 (L <= 65536), lg = log2 L.  Other 7-smooth lengths
+// (mixed radix): stages of radix 2, 4, 3, 5, 7, an even one first and, when
+// the power of two allows, last (at most 8 stages for L <= 1024); lg is
+// then unused.  hin / hout: the first / last radix is even,
+// so a zero upper input half can be skipped in the first stage and the upper
+// output half left uncomputed in the last.
 struct RadixPlan {
   int nst;
   int lg;
-  int r[4];
+  int L;
+  int pow2;
+  int hin, hout;
+  int r[8];
 };
 
 inline int ilog2i(long v) {
@@ -159,20 +168,50 @@ inline int ilog2i(long v) {
   return b;
 }
 
+inline bool is_7smooth(long v) {
+  if (v < 1) return false;
+  for (int f : {2, 3, 5, 7})
+    while (v % f == 0) v /= f;
+  return v == 1;
+}
+
 inline RadixPlan make_radix_plan(int L) {
-  RadixPlan p{0, 0, {1, 1, 1, 1}};
-  int bits = 0;
-  while ((1 << bits) < L) ++bits;
-  p.lg = bits;
-  if (bits == 0) return p;
-  const int nst = (bits + 3) / 4;
-  int left = bits;
-  for (int s = 0; s < nst; ++s) {
-    const int b = (left + (nst - s) - 1) / (nst - s);  // ceil: larger radices first
-    p.r[s] = 1 << b;
-    left -= b;
+  RadixPlan p{0, 0, L, 1, 0, 0, {1, 1, 1, 1, 1, 1, 1, 1}};
+  if ((L & (L - 1)) == 0) {
+    int bits = 0;
+    while ((1 << bits) < L) ++bits;
+    p.lg = bits;
+    if (bits == 0) return p;
+    const int nst = (bits + 3) / 4;
+    int left = bits;
+    for (int s = 0; s < nst; ++s) {
+      const int b = (left + (nst - s) - 1) / (nst - s);  // ceil: larger radices first
+      p.r[s] = 1 << b;
+      left -= b;
+    }
+    p.nst = nst;
+    p.hin = p.hout = 1;
+    return p;
   }
-  p.nst = nst;
+  p.pow2 = 0;
+  int rest = L, a = 0;
+  while (rest % 2 == 0) rest /= 2, ++a;
+  // power-of-two part as radix-4 stages (one radix 2 when a is odd), one of
+  // them first and one last, the odd primes and the other radix-4 stages
+  // between them (only radices 2, 3, 4, 5, 7: the mixed-radix stages stay
+  // small, and so does their compile time in every precision)
+  int p2[8], n2 = 0;
+  if (a % 2) p2[n2++] = 2;
+  for (int i = 0; i < a / 2 && n2 < 8; ++i) p2[n2++] = 4;
+  int k = 0;
+  if (n2 > 0) p.r[p.nst++] = p2[k++];
+  for (int f : {7, 5, 3})
+    while (rest % f == 0 && p.nst < 8) rest /= f, p.r[p.nst++] = f;
+  while (k < n2 - 1 && p.nst < 8) p.r[p.nst++] = p2[k++];
+  if (k < n2 && p.nst < 8) p.r[p.nst++] = p2[k++];
+  p.hin = n2 > 0;
+  p.hout = n2 > 1;
+  if (rest != 1 || k != n2) p.nst = -1;  // not 7-smooth, or over 8 stages: rejected
   return p;
 }
 
@@ -266,6 +305,171 @@ __device__ __forceinline__ void smem_fft(cx<T>* s, const cx<T>* tw, int L, int s
     }
     Ns *= R;
   }
+}
+
+// cos and sin of 2 pi t / R for the odd radices (plain trigonometric values).
+__host__ __device__ constexpr double odd_cos(int R, int t) {
+  t %= R;
+  if (2 * t > R) t = R - t;
+  return t == 0 ? 1.0
+         : R == 3 ? -0.5
+         : R == 5 ? (t == 1 ? 0.3090169943749474241023 : -0.8090169943749474241023)
+                  : (t == 1 ? 0.623489801858733530525
+                            : t == 2 ? -0.2225209339563144042889 : -0.9009688679024191262361);
+}
+__host__ __device__ constexpr double odd_sin(int R, int t) {
+  t %= R;
+  const double sg = 2 * t > R ? -1.0 : 1.0;
+  if (2 * t > R) t = R - t;
+  return t == 0 ? 0.0
+         : sg * (R == 3 ? 0.8660254037844386467637
+                 : R == 5 ? (t == 1 ? 0.9510565162951535721164 : 0.5877852522924731291687)
+                          : (t == 1 ? 0.7818314824680298087084
+                                    : t == 2 ? 0.9749279121818236070181 : 0.4338837391175581204758));
+}
+
+// In-register R-point DFT for odd R (3, 5, 7), natural order in and out:
+// with s_j = v_j + v_{R-j} and d_j = v_j - v_{R-j} (0 < j <= (R-1)/2),
+//   X_0 = v_0 + sum_j s_j,
+//   X_k, X_{R-k} = v_0 + sum_j cos(2 pi jk/R) s_j  -/+ i sum_j sin(2 pi jk/R) d_j
+// (forward; the inverse swaps the two signs).
+template <int R, bool INV, typename T>
+__device__ __forceinline__ void dft_odd(cx<T>* v) {
+  constexpr int H = (R - 1) / 2;
+  cx<T> sp[H], sm[H];
+#pragma unroll
+  for (int j = 1; j <= H; ++j) {
+    sp[j - 1] = v[j] + v[R - j];
+    sm[j - 1] = v[j] - v[R - j];
+  }
+  const cx<T> x0 = v[0];
+  cx<T> out[R];
+  out[0] = x0;
+#pragma unroll
+  for (int j = 0; j < H; ++j) out[0] = out[0] + sp[j];
+#pragma unroll
+  for (int k = 1; k <= H; ++k) {
+    cx<T> a = x0, b = zero<T>();
+#pragma unroll
+    for (int j = 1; j <= H; ++j) {
+      const T c = (T)odd_cos(R, j * k), sn = (T)odd_sin(R, j * k);
+      a = mk<T>(a.x + c * sp[j - 1].x, a.y + c * sp[j - 1].y);
+      b = mk<T>(b.x + sn * sm[j - 1].x, b.y + sn * sm[j - 1].y);
+    }
+    // -i b = (b.y, -b.x), +i b = (-b.y, b.x)
+    const cx<T> lo = mk<T>(a.x + b.y, a.y - b.x), hi = mk<T>(a.x - b.y, a.y + b.x);
+    out[k] = INV ? hi : lo;
+    out[R - k] = INV ? lo : hi;
+  }
+#pragma unroll
+  for (int q = 0; q < R; ++q) v[q] = out[q];
+}
+
+// One Stockham stage of radix R on lines of any length L (mixed radix): the
+// same indexing as smem_stage with k = jb mod Ns by division.  A thread holds
+// up to ceil(16 / R) butterflies (NB L / R of them in the tile).
+template <int R, bool INV, bool MUL3, int MODE, typename T>
+__device__ __forceinline__ void smem_stage_mr(cx<T>* s, const cx<T>* tw, int L, int sh, int ld,
+                                              int Ns, int tid, int nth) {
+  constexpr int G = (kElemsPerThread + R - 1) / R;
+  constexpr int QIN = MODE == 1 ? R / 2 : R;
+  constexpr int QOUT = MODE == 2 ? R / 2 : R;
+  const int nbf = nth * kElemsPerThread / R;
+  const int LR = L / R;
+  cx<T> v[G][R];
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int u = tid + g * nth;
+    if (u < nbf) {
+      int b, jb;
+      split_line<MUL3>(u, sh, b, jb);
+#pragma unroll
+      for (int q = 0; q < QIN; ++q) v[g][q] = s[(jb + q * LR) * ld + b];
+    }
+  }
+  __syncthreads();
+  const int tstep = L / (Ns * R);
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    const int u = tid + g * nth;
+    if (u < nbf) {
+      int b, jb;
+      split_line<MUL3>(u, sh, b, jb);
+      const int k = jb % Ns;
+      if (Ns > 1) {
+#pragma unroll
+        for (int q = 1; q < R; ++q) v[g][q] = mulc<INV>(v[g][q], tw[q * k * tstep]);
+      }
+      if constexpr (R % 2 == 1)
+        dft_odd<R, INV>(v[g]);
+      else if constexpr (MODE == 1)
+        dft_half_in<R, INV>(v[g]);
+      else if constexpr (MODE == 2)
+        dft_half_out<R, INV>(v[g]);
+      else
+        dft<R, INV>(v[g]);
+      const int base = (jb - k) * R + k;
+#pragma unroll
+      for (int q = 0; q < QOUT; ++q) s[(base + q * Ns) * ld + b] = v[g][q];
+    }
+  }
+  __syncthreads();
+}
+
+template <int R, bool INV, bool MUL3, typename T>
+__device__ __forceinline__ void smem_stage_mr_any(int mode, cx<T>* s, const cx<T>* tw, int L,
+                                                  int sh, int ld, int Ns, int tid, int nth) {
+  if constexpr (R % 2 == 0) {
+    if (mode == 1) {
+      smem_stage_mr<R, INV, MUL3, 1>(s, tw, L, sh, ld, Ns, tid, nth);
+      return;
+    }
+    if (mode == 2) {
+      smem_stage_mr<R, INV, MUL3, 2>(s, tw, L, sh, ld, Ns, tid, nth);
+      return;
+    }
+  }
+  smem_stage_mr<R, INV, MUL3, 0>(s, tw, L, sh, ld, Ns, tid, nth);
+}
+
+// Mixed-radix transform of the tile's lines (any 7-smooth L of the plan);
+// same contract as smem_fft.  half_in / half_out must only be asked for when
+// the plan's first / last radix is even (rp.hin / rp.hout).  Not inlined:
+// one copy per (direction, tile shape, precision) serves every kernel of a
+// translation unit (the stages of all radices are large, and mixed-radix
+// boxes are the less common case).
+template <bool INV, bool MUL3, typename T>
+__device__ __noinline__ void smem_fft_mr(cx<T>* s, const cx<T>* tw, int L, int sh, int ld,
+                                         RadixPlan rp, bool half_in, bool half_out) {
+  const int tid = threadIdx.x;
+  const int nth = blockDim.x;
+  int Ns = 1;
+  for (int st = 0; st < rp.nst; ++st) {
+    const int R = rp.r[st];
+    const int mode = (st == 0 && half_in) ? 1 : ((st == rp.nst - 1 && half_out) ? 2 : 0);
+    switch (R) {
+      case 7: smem_stage_mr_any<7, INV, MUL3>(mode, s, tw, L, sh, ld, Ns, tid, nth); break;
+      case 5: smem_stage_mr_any<5, INV, MUL3>(mode, s, tw, L, sh, ld, Ns, tid, nth); break;
+      case 4: smem_stage_mr_any<4, INV, MUL3>(mode, s, tw, L, sh, ld, Ns, tid, nth); break;
+      case 3: smem_stage_mr_any<3, INV, MUL3>(mode, s, tw, L, sh, ld, Ns, tid, nth); break;
+      default: smem_stage_mr_any<2, INV, MUL3>(mode, s, tw, L, sh, ld, Ns, tid, nth); break;
+    }
+    Ns *= R;
+  }
+}
+
+// Either form, by the plan.
+template <bool INV, bool MUL3 = false, typename T>
+__device__ __forceinline__ void smem_fft_plan(cx<T>* s, const cx<T>* tw, int sh, int ld,
+                                              const RadixPlan& rp, bool half_in, bool half_out) {
+#ifdef DDA_NO_MR
+  if (true)
+#else
+  if (rp.pow2)
+#endif
+    smem_fft<INV, MUL3>(s, tw, rp.L, sh, ld, rp, half_in, half_out);
+  else
+    smem_fft_mr<INV, MUL3, T>(s, tw, rp.L, sh, ld, rp, half_in, half_out);
 }
 
 // Asynchronous global -> shared copy of one complex value (cp.async); with

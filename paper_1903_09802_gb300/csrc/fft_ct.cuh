@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(3 * NBC * L / kElemsPerThread,
   const long slab = blockIdx.x / tiles;
   const int tt = (int)(blockIdx.x - slab * tiles);
   long col0;
-  if (row_len >= NBC && nrows > 0) {
+  if (row_len >= NBC && nrows > 0 && row_len % NBC == 0) {
     const int row_tiles = row_len / NBC;
     const int r = tt / row_tiles;
     const int ti = tt - r * row_tiles;
@@ -333,7 +333,7 @@ __device__ __forceinline__ void rr_fft3c_body(cx<float>* data, long ncols, long 
   const long slab = blockIdx.x / tiles;
   const int tt = (int)(blockIdx.x - slab * tiles);
   long col0;
-  if (row_len >= NBC && nrows > 0) {
+  if (row_len >= NBC && nrows > 0 && row_len % NBC == 0) {
     const int row_tiles = row_len / NBC;
     const int r = tt / row_tiles;
     const int ti = tt - r * row_tiles;
@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(NBC * (L / R2))
   const long slab = blockIdx.x / tiles;
   const int tt = (int)(blockIdx.x - slab * tiles);
   long col0;
-  if (row_len >= NBC && nrows > 0) {
+  if (row_len >= NBC && nrows > 0 && row_len % NBC == 0) {
     const int row_tiles = row_len / NBC;
     const int r = tt / row_tiles;
     const int ti = tt - r * row_tiles;

@@ -44,18 +44,20 @@ __global__ void __launch_bounds__(256)
   pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
-  const int L = 1 << rp.lg;
+  const int L = rp.L;
   const int NB = 1 << nb_sh;
   const int ld = NB + 1;
   cx<T>* stw = s + (size_t)L * ld;
   const int nth = blockDim.x, tid = threadIdx.x;
   const long line0 = (long)blockIdx.x << nb_sh;
-  const bool half_in = 2 * Lin <= L && L > 1, half_out = 2 * Lout <= L && L > 1;
+  const bool half_in = 2 * Lin <= L && L > 1 && rp.hin;
+  const bool half_out = 2 * Lout <= L && L > 1 && rp.hout;
   // Thread tid keeps position j = tid mod L of lines b0 + i * (nth / L)
-  // (nth / L >= 1 since nth = NB L / 16 and NB >= 16 whenever L < nth).
-  const int j = tid & (L - 1);
-  const int b0 = tid >> rp.lg;
-  const int bstep = nth >> rp.lg;
+  // (nth / L >= 1 since nth = NB L / 16 and NB >= 16 whenever L < nth); a
+  // mixed-radix length takes the per-element loops below.
+  const int j = rp.pow2 ? tid & (L - 1) : 0;
+  const int b0 = rp.pow2 ? tid >> rp.lg : 0;
+  const int bstep = rp.pow2 ? nth >> rp.lg : 0;
   if (bstep > 0) {
     if (!(half_in && 2 * j >= L)) {  // the pruned first stage never reads j >= L/2
       long line = line0 + b0;
@@ -75,8 +77,8 @@ __global__ void __launch_bounds__(256)
   } else {
     for (int i = 0; i < kElemsPerThread; ++i) {
       const int e = tid + i * nth;
-      const int jj = e & (L - 1);
-      const int b = e >> rp.lg;
+      const int jj = rp.pow2 ? e & (L - 1) : e % L;
+      const int b = rp.pow2 ? e >> rp.lg : e / L;
       const long line = line0 + b;
       if (half_in && 2 * jj >= L) continue;
       bool ok = line < nlines && jj < Lin;
@@ -87,7 +89,7 @@ __global__ void __launch_bounds__(256)
   load_twiddles(stw, tw, L, twshift);
   cp_async_wait_all();
   __syncthreads();
-  smem_fft<INV>(s, stw, L, nb_sh, ld, rp, half_in, half_out);
+  smem_fft_plan<INV>(s, stw, nb_sh, ld, rp, half_in, half_out);
   if (bstep > 0) {
     if (j < Lout) {
       long line = line0 + b0;
@@ -108,8 +110,8 @@ __global__ void __launch_bounds__(256)
   } else {
     for (int i = 0; i < kElemsPerThread; ++i) {
       const int e = tid + i * nth;
-      const int jj = e & (L - 1);
-      const int b = e >> rp.lg;
+      const int jj = rp.pow2 ? e & (L - 1) : e % L;
+      const int b = rp.pow2 ? e >> rp.lg : e / L;
       const long line = line0 + b;
       if (line < nlines && jj < Lout) {
         cx<T> w = scale * s[jj * ld + b];
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(512)
   pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
-  const int L = 1 << rp.lg;
+  const int L = rp.L;
   const int NB = 1 << nb_sh;
   cx<T>* stw = s + ((size_t)L << nb_sh);
   const int nth = blockDim.x, tid = threadIdx.x;
@@ -136,11 +138,13 @@ __global__ void __launch_bounds__(512)
   const long slab = blockIdx.x / tiles;
   const long col0 = (blockIdx.x - slab * tiles) << nb_sh;
   const cx<T>* src = in + slab * in_ss + col0;
-  const bool half_in = 2 * Lin <= L && L > 1, half_out = 2 * Lout <= L && L > 1;
+  const bool half_in = 2 * Lin <= L && L > 1 && rp.hin;
+  const bool half_out = 2 * Lout <= L && L > 1 && rp.hout;
   const int nload = half_in ? kElemsPerThread / 2 : kElemsPerThread;  // rows < L/2 only
   // Thread tid keeps column b = tid mod NB and rows j0 + i * (nth / NB):
   // addresses advance by constant strides.
-  // (L >= 16, so nth / NB = L / 16 >= 1; shorter lines take the generic loop).
+  // (FIX: L a multiple of 16, so nth / NB = L / 16 >= 1; other lengths take
+  // the generic loop).
   const int b = tid & (NB - 1);
   const int j0 = tid >> nb_sh;
   const int jstep = nth >> nb_sh;
@@ -166,7 +170,7 @@ __global__ void __launch_bounds__(512)
   load_twiddles(stw, tw, L, twshift);
   cp_async_wait_all();
   __syncthreads();
-  smem_fft<INV>(s, stw, L, nb_sh, NB, rp, half_in, half_out);
+  smem_fft_plan<INV>(s, stw, nb_sh, NB, rp, half_in, half_out);
   if constexpr (FIX) {
     if (colok) {
       cx<T>* g = out + slab * out_ss + col0 + (long)j0 * out_js + b;
@@ -208,7 +212,7 @@ __global__ void __launch_bounds__(fft3c_max_threads<T>())
   pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
-  const int L = 1 << rp.lg;
+  const int L = rp.L;
   const int NBc = 1 << nbc_sh;
   const int ld = 3 * NBc;
   cx<T>* stw = s + (size_t)L * ld;
@@ -217,7 +221,7 @@ __global__ void __launch_bounds__(fft3c_max_threads<T>())
   const long slab = blockIdx.x / tiles;
   const int tt = (int)(blockIdx.x - slab * tiles);
   long col0;
-  if (row_len >= NBc && nrows > 0) {
+  if (row_len >= NBc && nrows > 0 && (row_len & (NBc - 1)) == 0) {
     const int row_tiles = row_len >> nbc_sh;
     const int r = tt / row_tiles;
     const int ti = tt - r * row_tiles;
@@ -226,11 +230,12 @@ __global__ void __launch_bounds__(fft3c_max_threads<T>())
     col0 = (long)tt << nbc_sh;
   }
   cx<T>* base = data + slab * ss + col0;
-  const bool half_in = 2 * Lin <= L && L > 1, half_out = 2 * Lout <= L && L > 1;
+  const bool half_in = 2 * Lin <= L && L > 1 && rp.hin;
+  const bool half_out = 2 * Lout <= L && L > 1 && rp.hout;
   const int nload = half_in ? kElemsPerThread / 2 : kElemsPerThread;  // rows < L/2 only
-  // With L >= 16 every thread keeps one (component, column) pair and rows
-  // j0 + i * L/16, so addresses advance by constant strides.
-  constexpr bool fixed = FIX;  // L >= 16
+  // With L a multiple of 16 every thread keeps one (component, column) pair
+  // and rows j0 + i * L/16, so addresses advance by constant strides.
+  constexpr bool fixed = FIX;
   {
     const int e0 = tid;
     const int b0 = e0 & (NBc - 1);
@@ -263,7 +268,7 @@ __global__ void __launch_bounds__(fft3c_max_threads<T>())
   load_twiddles(stw, tw, L, twshift);
   cp_async_wait_all();
   __syncthreads();
-  smem_fft<false, true>(s, stw, L, nbc_sh, ld, rp, half_in, false);
+  smem_fft_plan<false, true>(s, stw, nbc_sh, ld, rp, half_in, false);
   if ((nth & (NBc - 1)) == 0) {
     // every thread keeps one column: its per-column state is set up once
     const int b = tid & (NBc - 1);
@@ -294,7 +299,7 @@ __global__ void __launch_bounds__(fft3c_max_threads<T>())
     }
   }
   __syncthreads();
-  smem_fft<true, true>(s, stw, L, nbc_sh, ld, rp, false, half_out);
+  smem_fft_plan<true, true>(s, stw, nbc_sh, ld, rp, false, half_out);
   if constexpr (fixed) {
     const int b0 = tid & (NBc - 1);
     const int t0 = tid >> nbc_sh;
@@ -384,10 +389,11 @@ void launch_fft3c(cx<T>* data, long ncols, long nslabs, int L, int Lin, long js,
   while (3 * NBc * L > cap && NBc > 1) NBc /= 2;
   while (NBc > 1 && 3 * NBc * L > 1536 && nslabs * ((ncols + NBc - 1) / NBc) < 2 * 152) NBc /= 2;
   while (3 * NBc * L < kElemsPerThread * 32) NBc *= 2;
+  while ((3 * NBc * L) % kElemsPerThread != 0) NBc *= 2;  // mixed-radix lengths
   const int nth = 3 * NBc * L / kElemsPerThread;
   const size_t smem = ((size_t)3 * NBc * L + L) * sizeof(cx<T>);
   const long grid = nslabs * ((ncols + NBc - 1) / NBc);
-  auto kern = L >= 16 ? k_fft3c<T, Op, true> : k_fft3c<T, Op, false>;
+  auto kern = (L >= 16 && L % 16 == 0) ? k_fft3c<T, Op, true> : k_fft3c<T, Op, false>;
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   note_launch();

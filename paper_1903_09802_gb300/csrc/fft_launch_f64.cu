@@ -1,0 +1,17 @@
+// Batched FFT launchers, complex128 (FP64) instantiations.
+#include "fft_launch.cuh"
+
+namespace dda {
+
+#define DDA_INST_FFT(T, INV)                                                                      \
+  template void launch_contig<T, INV>(const cx<T>*, cx<T>*, const uint8_t*, const uint8_t*, long,  \
+                                      long, int, int,                                             \
+                                      long, int, long, T, const cx<T>*, int, cudaStream_t);        \
+  template void launch_strided<T, INV>(const cx<T>*, cx<T>*, long, long, int, int, long, long,     \
+                                       int, long, long, T, const cx<T>*, int, cudaStream_t);       \
+  template void fft3d_inplace<T, INV>(cx<T>*, long, int, int, int, T, const cx<T>*, int,           \
+                                      cudaStream_t);
+DDA_INST_FFT(double, false)
+DDA_INST_FFT(double, true)
+
+}  // namespace dda

@@ -23,6 +23,24 @@ dda_status_t check_cuda(const char* where);
 
 inline bool is_pow2(long v) { return v > 0 && (v & (v - 1)) == 0; }
 
+// Length of the plan's twiddle table exp(-2 pi i t / Lmax): a multiple of
+// every transform length of the box (2l, 2m, 2n and l, m, n), i.e. their
+// least common multiple; the largest edge's 2e for power-of-two boxes.
+inline long twiddle_length(long l, long m, long n) {
+  auto gcd = [](long a, long b) {
+    while (b) {
+      const long t = a % b;
+      a = b;
+      b = t;
+    }
+    return a;
+  };
+  long v = 2 * l;
+  for (long e : {2 * m, 2 * n}) v = v / gcd(v, e) * e;
+  return v;
+}
+constexpr long kMaxTwiddleLength = 1L << 20;
+
 // Weight of the Toeplitz entry at offset p (side 0) or p - L (side 1) in
 // entry p of a level's circulant: T. Chan's eq. 13 ((L - p)/L and p/L) or
 // Strang's (the nearer of the two offsets; both halves at p = L/2).

@@ -44,9 +44,13 @@ def test_workspace_size_checks(dda):
     assert dda.workspace_size(16, 16, 16, 0.125, 5.0, 1, 2, 0) < ok
     only64 = dda.workspace_size(16, 16, 16, 0.125, 5.0, 1, 2, 50, dda.PLAN_C64)
     assert 0 < only64 < ok
-    for bad in [(12, 16, 16), (16, 0, 16), (1024, 2, 2)]:
+    for bad in [(15, 16, 16), (22, 16, 16), (16, 0, 16), (1024, 2, 2)]:
         assert dda.workspace_size(*bad, 0.125, 5.0) == 0
-        assert "power" in dda.last_error() or ">=" in dda.last_error()
+        err = dda.last_error()
+        assert "power" in err or ">=" in err or "at most 512" in err, err
+    # mixed-radix boxes (even 7-smooth edges) are taken
+    assert dda.workspace_size(12, 16, 16, 0.125, 5.0) > 0
+    assert dda.workspace_size(96, 96, 96, 0.125, 5.0) > 0
     assert dda.workspace_size(8, 8, 8, -1.0, 5.0) == 0
     assert dda.workspace_size(8, 8, 8, 0.1, 5.0, 0) == 0
     assert dda.workspace_size(8, 8, 8, 0.1, 5.0, 1, 1, 0, 0) == 0
@@ -65,10 +69,16 @@ def test_plan_create_argument_errors(dda):
     assert dda.STATUS[st] == "DDA_ERR_WORKSPACE"  # misaligned
     st = lib.dda_plan_create(ctypes.byref(h), ctypes.byref(desc), None, eps, fake, need, None)
     assert dda.STATUS[st] == "DDA_ERR_INVALID_ARG"
-    bad = dda.PlanDesc(8, 6, 8, 0.25, 2.0, 1, 1, 10, 3)
-    st = lib.dda_plan_create(ctypes.byref(h), ctypes.byref(bad), fake, eps, fake, need, None)
-    assert dda.STATUS[st] == "DDA_ERR_UNSUPPORTED_SIZE"
-    assert not h.value
+    # edges: odd, a prime factor above 7, above 512 (powers of two and even
+    # 7-smooth numbers are taken)
+    for edge in (9, 22, 210, 1024):
+        bad = dda.PlanDesc(8, edge, 8, 0.25, 2.0, 1, 1, 10, 3)
+        st = lib.dda_plan_create(ctypes.byref(h), ctypes.byref(bad), fake, eps, fake, need, None)
+        assert dda.STATUS[st] == "DDA_ERR_UNSUPPORTED_SIZE", edge
+        assert not h.value
+    for edge in (6, 96, 200, 252):
+        ok = dda.PlanDesc(8, edge, 8, 0.25, 2.0, 1, 1, 10, 3)
+        assert lib.dda_workspace_size(ctypes.byref(ok)) > 0, edge
 
 
 def test_null_plan_is_rejected(dda):

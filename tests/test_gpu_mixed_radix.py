@@ -169,9 +169,9 @@ def test_prism96_own_box_equals_air_padded_box():
         res = plan.solve(tol=1e-6, restart=50, precond=3, inner_prec=dda.C64, inner_tol=1e-4)
         assert all(res.converged), (box, res.iters, res.rel_resid)
         x = res.x.cpu().numpy()
-        o = (128 - box[0]) // 2
-        out[box] = (x[:, :, :96, :96, :96] if o == 0 else x[:, :, o:o + 96, o:o + 96, o:o + 96],
-                    plan.cross_sections(res.x), case.mask())
+        o = (box[0] - 96) // 2  # the prism's 96^3 block inside the box
+        out[box] = (x[:, :, o:o + 96, o:o + 96, o:o + 96], plan.cross_sections(res.x),
+                    case.mask())
         del plan
         torch.cuda.empty_cache()
     (xa, sa, ma), (xb, sb, mb) = out[(96, 96, 96)], out[(128, 128, 128)]

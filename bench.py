@@ -654,26 +654,28 @@ def compare_precision_sweep(runner):
     return out
 
 
-def compare_256(runner):
+def compare_256(runner, cap=4000):
     """The largest single solve: the 256^3 prism (x = 80, m = 1.31, aspect 1,
     +z incidence, x-polarised; 16.7M voxels, 50M unknown slots), GMRES(30)
-    in complex64 inside FP64 refinement, 3-level preconditioner, to 1e-6:
+    as s-step GMRES (s = 5) in complex64 inside FP64 refinement, 3-level
+    preconditioner, to 1e-6 within `cap` iterations and a 100 s time limit:
     build and solve time, iterations, workspace."""
     import torch
     from dda_inputs import prism_case
     dda = runner.dda
     case = prism_case(256, 80.0, 1.31, 1.0)
     mask = torch.from_numpy(case.mask()).to(runner.dev)
-    ws = dda.workspace_size(256, 256, 256, case.dx, case.k, 1, 1, 30)
+    ws = dda.workspace_size(256, 256, 256, case.dx, case.k, 1, 1, 30, sstep=SSTEP)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    plan = dda.Plan(mask, case.eps, case.dx, case.k, max_rhs=1, krylov_m=30)
+    plan = dda.Plan(mask, case.eps, case.dx, case.k, max_rhs=1, krylov_m=30, sstep=SSTEP)
     plan.set_incidence(case.dirs, case.pols)
     plan.precond_build()
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    r = plan.solve(tol=1e-6, restart=30, max_iters=1500, precond=3, inner_prec=dda.C64,
-                   inner_tol=1e-4, reorth_eta=REORTH_ETA, raise_on_error=False, timeout_ms=120000)
+    r = plan.solve(tol=1e-6, restart=30, max_iters=cap, precond=3, inner_prec=dda.C64,
+                   inner_tol=1e-4, reorth_eta=REORTH_ETA, raise_on_error=False, timeout_ms=100000,
+                   method=2, history=min(cap + 1, 4096))
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     xs = plan.cross_sections(r.x)[0]
@@ -681,7 +683,10 @@ def compare_256(runner):
            "solve_ms": round(1e3 * (t2 - t1), 1), "iters": r.iters[0], "cycles": r.cycles[0],
            "converged": bool(r.converged[0]), "rel_resid": r.rel_resid[0],
            "c_ext_abs_sca": [float(v) for v in xs], "workspace_gb": round(ws / 1e9, 2),
-           "one_graph_launch": r.graph}
+           "one_graph_launch": r.graph, "method": "s-step GMRES(30), s = 5", "cap": cap}
+    hist = np.asarray(r.history[0]) if getattr(r, "history", None) else None
+    if hist is not None and hist.size > 1500:
+        out["rel_resid_after_1500_iterations"] = float(hist[1500])
     del plan, mask
     torch.cuda.empty_cache()
     return out

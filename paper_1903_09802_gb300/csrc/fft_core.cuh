@@ -367,10 +367,11 @@ __device__ __forceinline__ void dft_odd(cx<T>* v) {
 
 // One Stockham stage of radix R on lines of any length L (mixed radix): the
 // same indexing as smem_stage with k = jb mod Ns by division.  A thread holds
-// up to ceil(16 / R) butterflies (NB L / R of them in the tile).
+// up to ceil(16 / R) butterflies (NB L / R of them in the tile).  Not
+// inlined (see smem_fft_mr).
 template <int R, bool INV, bool MUL3, int MODE, typename T>
-__device__ __forceinline__ void smem_stage_mr(cx<T>* s, const cx<T>* tw, int L, int sh, int ld,
-                                              int Ns, int tid, int nth) {
+__device__ __noinline__ void smem_stage_mr(cx<T>* s, const cx<T>* tw, int L, int sh, int ld,
+                                           int Ns, int tid, int nth) {
   constexpr int G = (kElemsPerThread + R - 1) / R;
   constexpr int QIN = MODE == 1 ? R / 2 : R;
   constexpr int QOUT = MODE == 2 ? R / 2 : R;
@@ -434,13 +435,15 @@ __device__ __forceinline__ void smem_stage_mr_any(int mode, cx<T>* s, const cx<T
 
 // Mixed-radix transform of the tile's lines (any 7-smooth L of the plan);
 // same contract as smem_fft.  half_in / half_out must only be asked for when
-// the plan's first / last radix is even (rp.hin / rp.hout).  Not inlined:
-// one copy per (direction, tile shape, precision) serves every kernel of a
-// translation unit (the stages of all radices are large, and mixed-radix
-// boxes are the less common case).
+// the plan's first / last radix is even (rp.hin / rp.hout).  Used by the
+// mixed-radix kernels only (kernel template flag MR), so that power-of-two
+// kernels carry none of it; its stages are separate functions (one copy per
+// radix, mode, direction and precision in a translation unit), which keeps
+// the compile time in bounds at the price of a call per stage and a local
+// stack frame of a few kilobytes in these kernels.
 template <bool INV, bool MUL3, typename T>
-__device__ __noinline__ void smem_fft_mr(cx<T>* s, const cx<T>* tw, int L, int sh, int ld,
-                                         RadixPlan rp, bool half_in, bool half_out) {
+__device__ __forceinline__ void smem_fft_mr(cx<T>* s, const cx<T>* tw, int L, int sh, int ld,
+                                            const RadixPlan& rp, bool half_in, bool half_out) {
   const int tid = threadIdx.x;
   const int nth = blockDim.x;
   int Ns = 1;
@@ -458,18 +461,14 @@ __device__ __noinline__ void smem_fft_mr(cx<T>* s, const cx<T>* tw, int L, int s
   }
 }
 
-// Either form, by the plan.
-template <bool INV, bool MUL3 = false, typename T>
+// Either form: MR (a kernel template flag) selects the mixed-radix one.
+template <bool INV, bool MUL3, bool MR, typename T>
 __device__ __forceinline__ void smem_fft_plan(cx<T>* s, const cx<T>* tw, int sh, int ld,
                                               const RadixPlan& rp, bool half_in, bool half_out) {
-#ifdef DDA_NO_MR
-  if (true)
-#else
-  if (rp.pow2)
-#endif
-    smem_fft<INV, MUL3>(s, tw, rp.L, sh, ld, rp, half_in, half_out);
-  else
+  if constexpr (MR)
     smem_fft_mr<INV, MUL3, T>(s, tw, rp.L, sh, ld, rp, half_in, half_out);
+  else
+    smem_fft<INV, MUL3>(s, tw, rp.L, sh, ld, rp, half_in, half_out);
 }
 
 // Asynchronous global -> shared copy of one complex value (cp.async); with
@@ -488,6 +487,11 @@ __device__ __forceinline__ void cp_async_cx(cx<T>* sdst, const cx<T>* gsrc, bool
                  "r"(nbytes)
                  : "memory");
   }
+}
+// 16 bytes (two complex64 values), both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async_16(void* sdst, const void* gsrc) {
+  const unsigned saddr = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(saddr), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");

@@ -343,12 +343,14 @@ __device__ __forceinline__ void rr_fft3c_body(cx<float>* data, long ncols, long 
   }
   cx<T>* base = data + slab * ss + col0;
   constexpr int ROWS_IN = HALF ? H : L;  // rows loaded (the rest are zero padding)
-  // A
-#pragma unroll 4
-  for (int e = tid; e < ROWS_IN * NL; e += NTH) {
-    const int j = e / NL, line = e - j * NL;
+  // A: 16-byte copies of two neighbouring columns (tiles start on even
+  // columns, rows and component planes are even strides, shared rows even)
+  constexpr int NLH = NL / 2;
+#pragma unroll 3
+  for (int e = tid; e < ROWS_IN * NLH; e += NTH) {
+    const int j = e / NLH, line = 2 * (e - j * NLH);
     const int c = line / NBC, b = line - c * NBC;
-    cp_async_cx(s + row(j) + line, base + c * cs + (long)j * js + b, true);
+    cp_async_16(s + row(j) + line, base + c * cs + (long)j * js + b);
   }
   op.prefetch(col0, NBC, L);
   load_twiddles(stw, tw, L, twshift);

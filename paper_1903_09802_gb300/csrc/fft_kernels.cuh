@@ -35,7 +35,7 @@ __host__ __device__ constexpr int fft3c_max_threads() {
   return sizeof(T) == 4 ? 768 : (std::is_same<T, df>::value ? 256 : 512);
 }
 
-template <typename T, bool INV>
+template <typename T, bool INV, bool MR>
 __global__ void __launch_bounds__(256)
     k_fft_contig(const cx<T>* in, cx<T>* out, const uint8_t* __restrict__ mask,
                  const uint8_t* __restrict__ omask, long mask_lines, long nlines, int Lin,
@@ -55,9 +55,9 @@ __global__ void __launch_bounds__(256)
   // Thread tid keeps position j = tid mod L of lines b0 + i * (nth / L)
   // (nth / L >= 1 since nth = NB L / 16 and NB >= 16 whenever L < nth); a
   // mixed-radix length takes the per-element loops below.
-  const int j = rp.pow2 ? tid & (L - 1) : 0;
-  const int b0 = rp.pow2 ? tid >> rp.lg : 0;
-  const int bstep = rp.pow2 ? nth >> rp.lg : 0;
+  const int j = MR ? 0 : tid & (L - 1);
+  const int b0 = MR ? 0 : tid >> rp.lg;
+  const int bstep = MR ? 0 : nth >> rp.lg;
   if (bstep > 0) {
     if (!(half_in && 2 * j >= L)) {  // the pruned first stage never reads j >= L/2
       long line = line0 + b0;
@@ -77,8 +77,8 @@ __global__ void __launch_bounds__(256)
   } else {
     for (int i = 0; i < kElemsPerThread; ++i) {
       const int e = tid + i * nth;
-      const int jj = rp.pow2 ? e & (L - 1) : e % L;
-      const int b = rp.pow2 ? e >> rp.lg : e / L;
+      const int jj = MR ? e % L : e & (L - 1);
+      const int b = MR ? e / L : e >> rp.lg;
       const long line = line0 + b;
       if (half_in && 2 * jj >= L) continue;
       bool ok = line < nlines && jj < Lin;
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(256)
   load_twiddles(stw, tw, L, twshift);
   cp_async_wait_all();
   __syncthreads();
-  smem_fft_plan<INV>(s, stw, nb_sh, ld, rp, half_in, half_out);
+  smem_fft_plan<INV, false, MR>(s, stw, nb_sh, ld, rp, half_in, half_out);
   if (bstep > 0) {
     if (j < Lout) {
       long line = line0 + b0;
@@ -110,8 +110,8 @@ __global__ void __launch_bounds__(256)
   } else {
     for (int i = 0; i < kElemsPerThread; ++i) {
       const int e = tid + i * nth;
-      const int jj = rp.pow2 ? e & (L - 1) : e % L;
-      const int b = rp.pow2 ? e >> rp.lg : e / L;
+      const int jj = MR ? e % L : e & (L - 1);
+      const int b = MR ? e / L : e >> rp.lg;
       const long line = line0 + b;
       if (line < nlines && jj < Lout) {
         cx<T> w = scale * s[jj * ld + b];
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-template <typename T, bool INV, bool FIX>
+template <typename T, bool INV, bool FIX, bool MR>
 __global__ void __launch_bounds__(512)
     k_fft_strided(const cx<T>* in, cx<T>* out, long ncols, int Lin, long in_js, long in_ss,
                   int Lout, long out_js, long out_ss, T scale, const cx<T>* __restrict__ tw,
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(512)
   load_twiddles(stw, tw, L, twshift);
   cp_async_wait_all();
   __syncthreads();
-  smem_fft_plan<INV>(s, stw, nb_sh, NB, rp, half_in, half_out);
+  smem_fft_plan<INV, false, MR>(s, stw, nb_sh, NB, rp, half_in, half_out);
   if constexpr (FIX) {
     if (colok) {
       cx<T>* g = out + slab * out_ss + col0 + (long)j0 * out_js + b;
@@ -204,7 +204,7 @@ __device__ __forceinline__ int mirror_perm(int r, int n) {
 // `data` (first Lout of L outputs kept).  Lines of the tile are ordered
 // (component, column) with the column fastest, so shared-memory index and
 // tile index coincide.
-template <typename T, class Op, bool FIX>
+template <typename T, class Op, bool FIX, bool MR>
 __global__ void __launch_bounds__(fft3c_max_threads<T>())
     k_fft3c(cx<T>* data, long ncols, int Lin, long js, long cs, long ss, int Lout, Op op,
             const cx<T>* __restrict__ tw, int twshift, RadixPlan rp, int nbc_sh, int row_len,
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(fft3c_max_threads<T>())
   load_twiddles(stw, tw, L, twshift);
   cp_async_wait_all();
   __syncthreads();
-  smem_fft_plan<false, true>(s, stw, nbc_sh, ld, rp, half_in, false);
+  smem_fft_plan<false, true, MR>(s, stw, nbc_sh, ld, rp, half_in, false);
   if ((nth & (NBc - 1)) == 0) {
     // every thread keeps one column: its per-column state is set up once
     const int b = tid & (NBc - 1);
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(fft3c_max_threads<T>())
     }
   }
   __syncthreads();
-  smem_fft_plan<true, true>(s, stw, nbc_sh, ld, rp, false, half_out);
+  smem_fft_plan<true, true, MR>(s, stw, nbc_sh, ld, rp, false, half_out);
   if constexpr (fixed) {
     const int b0 = tid & (NBc - 1);
     const int t0 = tid >> nbc_sh;
@@ -393,12 +393,15 @@ void launch_fft3c(cx<T>* data, long ncols, long nslabs, int L, int Lin, long js,
   const int nth = 3 * NBc * L / kElemsPerThread;
   const size_t smem = ((size_t)3 * NBc * L + L) * sizeof(cx<T>);
   const long grid = nslabs * ((ncols + NBc - 1) / NBc);
-  auto kern = (L >= 16 && L % 16 == 0) ? k_fft3c<T, Op, true> : k_fft3c<T, Op, false>;
+  const bool fix = L >= 16 && L % 16 == 0;
+  const RadixPlan rp = make_radix_plan(L);
+  auto kern = rp.pow2 ? (fix ? k_fft3c<T, Op, true, false> : k_fft3c<T, Op, false, false>)
+                      : (fix ? k_fft3c<T, Op, true, true> : k_fft3c<T, Op, false, true>);
   if (smem > 48 * 1024)
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   note_launch();
   launch_k(kern, (unsigned)grid, nth, smem, s, data, ncols, Lin, js, cs, ss, Lout, op, tw, Lmax / L,
-                                         make_radix_plan(L), ilog2i(NBc), row_len, nrows);
+                                         rp, ilog2i(NBc), row_len, nrows);
 }
 
 }  // namespace dda

@@ -135,11 +135,12 @@ void launch_contig(const cx<T>* in, cx<T>* out, const uint8_t* mask, const uint8
   const int nth = NB * L / kElemsPerThread;
   const size_t smem = ((size_t)L * (NB + 1) + L) * sizeof(cx<T>);
   const long grid = (nlines + NB - 1) / NB;
-  auto kern = k_fft_contig<T, INV>;
+  const RadixPlan rp = make_radix_plan(L);
+  auto kern = rp.pow2 ? k_fft_contig<T, INV, false> : k_fft_contig<T, INV, true>;
   allow_smem(kern, smem);
   note_launch();
   launch_k(kern, (unsigned)grid, nth, smem, s, in, out, mask, omask, mask_lines, nlines, Lin, in_ld, Lout,
-                                         out_ld, scale, tw, Lmax / L, make_radix_plan(L),
+                                         out_ld, scale, tw, Lmax / L, rp,
                                          ilog2i(NB));
 }
 
@@ -174,12 +175,14 @@ void launch_strided(const cx<T>* in, cx<T>* out, long ncols, long nslabs, int L,
   const int nth = NB * L / kElemsPerThread;
   const size_t smem = ((size_t)L * NB + L) * sizeof(cx<T>);
   const long grid = nslabs * ((ncols + NB - 1) / NB);
-  auto kern = (L >= 16 && L % 16 == 0) ? k_fft_strided<T, INV, true>
-                                       : k_fft_strided<T, INV, false>;
+  const bool fix = L >= 16 && L % 16 == 0;
+  const RadixPlan rp = make_radix_plan(L);
+  auto kern = rp.pow2 ? (fix ? k_fft_strided<T, INV, true, false> : k_fft_strided<T, INV, false, false>)
+                      : (fix ? k_fft_strided<T, INV, true, true> : k_fft_strided<T, INV, false, true>);
   allow_smem(kern, smem);
   note_launch();
   launch_k(kern, (unsigned)grid, nth, smem, s, in, out, ncols, Lin, in_js, in_ss, Lout, out_js, out_ss,
-                                         scale, tw, Lmax / L, make_radix_plan(L), ilog2i(NB));
+                                         scale, tw, Lmax / L, rp, ilog2i(NB));
 }
 
 template <typename T, bool INV>

@@ -121,7 +121,7 @@ struct KernelMul {
 //   y = a x - coef * conv   (scatterer voxel, a = alpha^{-1} of its material)
 //   y = a x                 (air voxel, a = alpha_tilde^{-1})
 // with coef = dx^3 / (2l 2m 2n) (the inverse transforms are unnormalised).
-template <typename T>
+template <typename T, bool MR>
 __global__ void __launch_bounds__(std::is_same<T, df>::value ? 256 : 512)
     k_mv_epilogue(const cx<T>* __restrict__ buf1, const cx<T>* __restrict__ x,
                   cx<T>* __restrict__ y, const uint8_t* __restrict__ mat,
@@ -139,8 +139,8 @@ __global__ void __launch_bounds__(std::is_same<T, df>::value ? 256 : 512)
 #pragma unroll 4
   for (int i = 0; i < kElemsPerThread; ++i) {
     const int e = tid + i * nth;
-    const int j = rp.pow2 ? e & (Lx - 1) : e % Lx;
-    const int b = rp.pow2 ? e >> rp.lg : e / Lx;
+    const int j = MR ? e % Lx : e & (Lx - 1);
+    const int b = MR ? e / Lx : e >> rp.lg;
     const long line = line0 + b;
     const bool ok = line < nlines;
     cp_async_cx(s + j * ld + b, ok ? buf1 + line * Lx + j : buf1, ok);
@@ -148,12 +148,12 @@ __global__ void __launch_bounds__(std::is_same<T, df>::value ? 256 : 512)
   load_twiddles(stw, tw, Lx, twshift);
   cp_async_wait_all();
   __syncthreads();
-  smem_fft_plan<true>(s, stw, nb_sh, ld, rp, false, 2 * l <= Lx && Lx > 1 && rp.hout);
+  smem_fft_plan<true, false, MR>(s, stw, nb_sh, ld, rp, false, 2 * l <= Lx && Lx > 1 && rp.hout);
   // Stores: element e = tid + i * nth of the NB x l outputs; when l divides
   // nth every thread keeps one column j and steps over lines by nth / l, so
   // the voxel row and right-hand side advance incrementally.
   const int lsh = rp.lg - 1;  // l = Lx / 2
-  if (rp.pow2 && 2 * l == Lx && (nth & (l - 1)) == 0) {
+  if (!MR && 2 * l == Lx && (nth & (l - 1)) == 0) {
     const int j = tid & (l - 1);
     const int b0 = tid >> lsh;
     const int bstep = nth >> lsh;
@@ -366,7 +366,8 @@ void matvec_core(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t
     while ((NB * Lx) % kElemsPerThread != 0) NB *= 2;  // mixed-radix lengths
     const int nth = NB * (int)Lx / kElemsPerThread;
     const size_t smem = ((size_t)Lx * (NB + 1) + Lx) * sizeof(cx<T>);
-    auto kern = k_mv_epilogue<T>;
+    const RadixPlan rp = make_radix_plan((int)Lx);
+    auto kern = rp.pow2 ? k_mv_epilogue<T, false> : k_mv_epilogue<T, true>;
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const T coef = (T)(p->d.dx * p->d.dx * p->d.dx / (double)p->P);
@@ -374,7 +375,7 @@ void matvec_core(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t
     note_launch();
     launch_k(kern, (unsigned)((lines + NB - 1) / NB), nth, smem, s,
         b1, x, y, p->mat, ainv_of<T>(p) + (long)rhs0 * (p->K + 1), p->K + 1, lines, nm, (int)l,
-        (int)Lx, coef, tw, p->Lmax / (int)Lx, make_radix_plan((int)Lx), ilog2i(NB),
+        (int)Lx, coef, tw, p->Lmax / (int)Lx, rp, ilog2i(NB),
         pv_of<T>(p) ? pv_of<T>(p) + (long)rhs0 * p->nvox : nullptr);
     p->prof.end(s);
   }

@@ -56,3 +56,20 @@ def test_noalloc_apply_rejects_oversize():
     with pytest.raises(dda.DDAError) as e:
         plan.precond_apply_noalloc(v, torch.empty_like(v))
     assert "DDA_ERR_WORKSPACE" in str(e.value) and "static scratch" in str(e.value)
+
+
+@pytest.mark.gpu
+def test_noalloc_apply_rejects_mixed_radix_box():
+    """Mixed-radix boxes (even 7-smooth edges) are refused before any launch:
+    their kernels carry a local stack frame whose first launch may make the
+    driver enlarge the context's local-memory reservation."""
+    dda = dda_module()
+    l, m, n = 12, 8, 8
+    mat = torch.ones((n, m, l), dtype=torch.uint8, device="cuda")
+    plan = dda.Plan(mat, [1.7], 0.1, 1.0, max_rhs=1)
+    plan.set_incidence([[0, 0, 1.0]], [[1.0, 0, 0]])
+    plan.precond_build()
+    v = torch.zeros((1, 3, n, m, l), dtype=torch.complex128, device="cuda")
+    with pytest.raises(dda.DDAError) as e:
+        plan.precond_apply_noalloc(v, torch.empty_like(v))
+    assert "DDA_ERR_UNSUPPORTED_SIZE" in str(e.value)

@@ -184,9 +184,10 @@ size_t dda_workspace_size(const dda_plan_desc_t* desc);
  * Errors: DDA_ERR_INVALID_ARG, DDA_ERR_UNSUPPORTED_SIZE (edge above 512,
  * neither a power of two nor an even 7-smooth number, a mixed-radix edge e
  * whose three-component tile of length e or 2e needs more than 256 threads
- * (3 c L / 16 with c the least power of two making 3 c L a multiple of 16:
- * 210, 250, 270, 294, 350, 378, 420, 450, 486, 490, 500), or lcm(2l, 2m, 2n)
- * above 2^20), DDA_ERR_WORKSPACE (too small / misaligned), DDA_ERR_CUDA. */
+ * (3 c L / 8 with c the least power of two making 3 c L a multiple of 8:
+ * 210, 250, 270, 294, 350, 360, 378, 384, 392, 400, 420, 432, 448, 450, 480,
+ * 486, 490, 500, 504), or lcm(2l, 2m, 2n) above 2^20), DDA_ERR_WORKSPACE (too
+ * small / misaligned), DDA_ERR_CUDA. */
 dda_status_t dda_plan_create(dda_plan_t* out, const dda_plan_desc_t* desc, const uint8_t* d_mat,
                              const double* h_eps, void* d_work, size_t work_bytes, void* stream);
 

@@ -77,14 +77,14 @@ bool valid_desc(const dda_plan_desc_t& d, std::string& why, dda_status_t& st) {
                          make_radix_plan(2 * e).nst > 0))
       return why = "box edges must be powers of two or even 7-smooth numbers (2^a 3^b 5^c 7^d)",
              false;
-    // the generic three-component tile of lengths e and 2e (16 values per
+    // the mixed-radix three-component tile of lengths e and 2e (8 values per
     // thread, a power-of-two column count that makes the values a multiple of
-    // 16) must fit the double-float kernel's 256 threads
+    // 8) must fit the double-float kernel's 256 threads
     if (!is_pow2(e))
       for (long L : {(long)e, 2L * e}) {
         long nb = 1;
-        while ((3 * nb * L) % 16 != 0) nb *= 2;
-        if (3 * nb * L / 16 > 256)
+        while ((3 * nb * L) % 8 != 0) nb *= 2;
+        if (3 * nb * L / 8 > 256)
           return why = "mixed-radix edge " + std::to_string(e) +
                        " needs a transform tile above 256 threads (every even 7-smooth edge up "
                        "to 208 is taken)",

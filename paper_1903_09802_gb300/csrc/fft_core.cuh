@@ -22,6 +22,13 @@ namespace dda {
 void note_launch();
 
 constexpr int kElemsPerThread = 16;
+// Mixed-radix kernels hold 8 values per thread: the odd radices' butterflies
+// then fit in registers in every precision (no local stack frame).
+constexpr int kElemsMR = 8;
+template <bool MR>
+__host__ __device__ constexpr int elems_per_thread() {
+  return MR ? kElemsMR : kElemsPerThread;
+}
 
 // cos(2 pi j / 32), j = 0..8 (plain trigonometry: cos(pi j / 16)).
 constexpr double kCos32[9] = {1.0,
@@ -367,15 +374,15 @@ __device__ __forceinline__ void dft_odd(cx<T>* v) {
 
 // One Stockham stage of radix R on lines of any length L (mixed radix): the
 // same indexing as smem_stage with k = jb mod Ns by division.  A thread holds
-// up to ceil(16 / R) butterflies (NB L / R of them in the tile).  Not
-// inlined (see smem_fft_mr).
+// up to ceil(8 / R) butterflies (NB L / R of them in the tile, 8 values per
+// thread).
 template <int R, bool INV, bool MUL3, int MODE, typename T>
-__device__ __noinline__ void smem_stage_mr(cx<T>* s, const cx<T>* tw, int L, int sh, int ld,
-                                           int Ns, int tid, int nth) {
-  constexpr int G = (kElemsPerThread + R - 1) / R;
+__device__ __forceinline__ void smem_stage_mr(cx<T>* s, const cx<T>* tw, int L, int sh, int ld,
+                                              int Ns, int tid, int nth) {
+  constexpr int G = (kElemsMR + R - 1) / R;
   constexpr int QIN = MODE == 1 ? R / 2 : R;
   constexpr int QOUT = MODE == 2 ? R / 2 : R;
-  const int nbf = nth * kElemsPerThread / R;
+  const int nbf = nth * kElemsMR / R;
   const int LR = L / R;
   cx<T> v[G][R];
 #pragma unroll
@@ -434,13 +441,10 @@ __device__ __forceinline__ void smem_stage_mr_any(int mode, cx<T>* s, const cx<T
 }
 
 // Mixed-radix transform of the tile's lines (any 7-smooth L of the plan);
-// same contract as smem_fft.  half_in / half_out must only be asked for when
-// the plan's first / last radix is even (rp.hin / rp.hout).  Used by the
-// mixed-radix kernels only (kernel template flag MR), so that power-of-two
-// kernels carry none of it; its stages are separate functions (one copy per
-// radix, mode, direction and precision in a translation unit), which keeps
-// the compile time in bounds at the price of a call per stage and a local
-// stack frame of a few kilobytes in these kernels.
+// same contract as smem_fft, with 8 values per thread (kElemsMR).  half_in /
+// half_out must only be asked for when the plan's first / last radix is even
+// (rp.hin / rp.hout).  Used by the mixed-radix kernels only (kernel template
+// flag MR), so that power-of-two kernels carry none of it.
 template <bool INV, bool MUL3, typename T>
 __device__ __forceinline__ void smem_fft_mr(cx<T>* s, const cx<T>* tw, int L, int sh, int ld,
                                             const RadixPlan& rp, bool half_in, bool half_out) {

@@ -42,6 +42,7 @@ __global__ void __launch_bounds__(256)
                  long in_ld, int Lout, long out_ld, T scale, const cx<T>* __restrict__ tw,
                  int twshift, RadixPlan rp, int nb_sh) {
   pdl_entry();
+  constexpr int EPT = elems_per_thread<MR>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
   const int L = rp.L;
@@ -66,7 +67,7 @@ __global__ void __launch_bounds__(256)
       const long gstep = (long)bstep * in_ld;
       cx<T>* q = s + j * ld + b0;
 #pragma unroll 4
-      for (int i = 0; i < kElemsPerThread; ++i, line += bstep, g += gstep, q += bstep) {
+      for (int i = 0; i < EPT; ++i, line += bstep, g += gstep, q += bstep) {
         bool ok = line < nlines && j < Lin;
         if (ok && mask != nullptr) ok = mask[mrow * Lin + j] != 0;
         cp_async_cx(q, ok ? g : in, ok);
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(256)
       }
     }
   } else {
-    for (int i = 0; i < kElemsPerThread; ++i) {
+    for (int i = 0; i < EPT; ++i) {
       const int e = tid + i * nth;
       const int jj = MR ? e % L : e & (L - 1);
       const int b = MR ? e / L : e >> rp.lg;
@@ -98,7 +99,7 @@ __global__ void __launch_bounds__(256)
       const long gstep = (long)bstep * out_ld;
       const cx<T>* q = s + j * ld + b0;
 #pragma unroll 4
-      for (int i = 0; i < kElemsPerThread && line < nlines;
+      for (int i = 0; i < EPT && line < nlines;
            ++i, line += bstep, g += gstep, q += bstep) {
         cx<T> w = scale * *q;
         if (omask != nullptr && omask[mrow * Lout + j] == 0) w = zero<T>();
@@ -108,7 +109,7 @@ __global__ void __launch_bounds__(256)
       }
     }
   } else {
-    for (int i = 0; i < kElemsPerThread; ++i) {
+    for (int i = 0; i < EPT; ++i) {
       const int e = tid + i * nth;
       const int jj = MR ? e % L : e & (L - 1);
       const int b = MR ? e / L : e >> rp.lg;
@@ -123,11 +124,12 @@ __global__ void __launch_bounds__(256)
 }
 
 template <typename T, bool INV, bool FIX, bool MR>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(MR ? 256 : 512)
     k_fft_strided(const cx<T>* in, cx<T>* out, long ncols, int Lin, long in_js, long in_ss,
                   int Lout, long out_js, long out_ss, T scale, const cx<T>* __restrict__ tw,
                   int twshift, RadixPlan rp, int nb_sh) {
   pdl_entry();
+  constexpr int EPT = elems_per_thread<MR>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
   const int L = rp.L;
@@ -140,7 +142,7 @@ __global__ void __launch_bounds__(512)
   const cx<T>* src = in + slab * in_ss + col0;
   const bool half_in = 2 * Lin <= L && L > 1 && rp.hin;
   const bool half_out = 2 * Lout <= L && L > 1 && rp.hout;
-  const int nload = half_in ? kElemsPerThread / 2 : kElemsPerThread;  // rows < L/2 only
+  const int nload = half_in ? EPT / 2 : EPT;  // rows < L/2 only
   // Thread tid keeps column b = tid mod NB and rows j0 + i * (nth / NB):
   // addresses advance by constant strides.
   // (FIX: L a multiple of 16, so nth / NB = L / 16 >= 1; other lengths take
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(512)
     }
   } else {
     cx<T>* dst = out + slab * out_ss + col0;
-    for (int i = 0; i < kElemsPerThread; ++i) {
+    for (int i = 0; i < EPT; ++i) {
       const int e = tid + i * nth;
       const int bb = e & (NB - 1);
       const int j = e >> nb_sh;
@@ -205,11 +207,12 @@ __device__ __forceinline__ int mirror_perm(int r, int n) {
 // (component, column) with the column fastest, so shared-memory index and
 // tile index coincide.
 template <typename T, class Op, bool FIX, bool MR>
-__global__ void __launch_bounds__(fft3c_max_threads<T>())
+__global__ void __launch_bounds__(MR ? 256 : fft3c_max_threads<T>())
     k_fft3c(cx<T>* data, long ncols, int Lin, long js, long cs, long ss, int Lout, Op op,
             const cx<T>* __restrict__ tw, int twshift, RadixPlan rp, int nbc_sh, int row_len,
             int nrows) {
   pdl_entry();
+  constexpr int EPT = elems_per_thread<MR>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
   const int L = rp.L;
@@ -232,7 +235,7 @@ __global__ void __launch_bounds__(fft3c_max_threads<T>())
   cx<T>* base = data + slab * ss + col0;
   const bool half_in = 2 * Lin <= L && L > 1 && rp.hin;
   const bool half_out = 2 * Lout <= L && L > 1 && rp.hout;
-  const int nload = half_in ? kElemsPerThread / 2 : kElemsPerThread;  // rows < L/2 only
+  const int nload = half_in ? EPT / 2 : EPT;  // rows < L/2 only
   // With L a multiple of 16 every thread keeps one (component, column) pair
   // and rows j0 + i * L/16, so addresses advance by constant strides.
   constexpr bool fixed = FIX;
@@ -242,7 +245,7 @@ __global__ void __launch_bounds__(fft3c_max_threads<T>())
     const int t0 = e0 >> nbc_sh;
     const int j0 = t0 / 3, c0 = t0 - 3 * (t0 / 3);
     if constexpr (fixed) {
-      const int jstep = L >> 4;  // nth / (3 NBc)
+      const int jstep = L / EPT;  // nth / (3 NBc)
       const bool colok = col0 + b0 < ncols;
       const cx<T>* g = base + c0 * cs + (long)j0 * js + b0;
       const long gstep = (long)jstep * js;
@@ -305,7 +308,7 @@ __global__ void __launch_bounds__(fft3c_max_threads<T>())
     const int t0 = tid >> nbc_sh;
     const int j0 = t0 / 3, c0 = t0 - 3 * (t0 / 3);
     if (col0 + b0 < ncols) {
-      const int jstep = L >> 4;
+      const int jstep = L / EPT;
       cx<T>* g = base + c0 * cs + (long)j0 * js + b0;
       const long gstep = (long)jstep * js;
       const cx<T>* q = s + tid;
@@ -313,7 +316,7 @@ __global__ void __launch_bounds__(fft3c_max_threads<T>())
       for (int j = j0; j < Lout; j += jstep, g += gstep, q += nth) *g = *q;
     }
   } else {
-    for (int i = 0; i < kElemsPerThread; ++i) {
+    for (int i = 0; i < EPT; ++i) {
       const int e = tid + i * nth;
       const int b = e & (NBc - 1);
       const int t = e >> nbc_sh;
@@ -379,7 +382,10 @@ void launch_fft3c(cx<T>* data, long ncols, long nslabs, int L, int Lin, long js,
                   int Lout, const Op& op, const cx<T>* tw, int Lmax, int row_len, int nrows,
                   cudaStream_t s) {
   if (ncols <= 0 || nslabs <= 0) return;
-  const int cap = fft3c_max_threads<T>() * kElemsPerThread;
+  const RadixPlan rp = make_radix_plan(L);
+  const int ept = rp.pow2 ? kElemsPerThread : kElemsMR;  // values per thread
+  // mixed-radix kernels: 256 threads (their stages need the registers)
+  const int cap = (rp.pow2 ? fft3c_max_threads<T>() : 256) * ept;
   static const int nbc_env = [] {
     const char* v = getenv("DDA_FFT3C_COLS");
     return v ? atoi(v) : 0;
@@ -388,13 +394,12 @@ void launch_fft3c(cx<T>* data, long ncols, long nslabs, int L, int Lin, long js,
   NBc = (int)std::min<long>(NBc, floor_pow2_l(ncols));
   while (3 * NBc * L > cap && NBc > 1) NBc /= 2;
   while (NBc > 1 && 3 * NBc * L > 1536 && nslabs * ((ncols + NBc - 1) / NBc) < 2 * 152) NBc /= 2;
-  while (3 * NBc * L < kElemsPerThread * 32) NBc *= 2;
-  while ((3 * NBc * L) % kElemsPerThread != 0) NBc *= 2;  // mixed-radix lengths
-  const int nth = 3 * NBc * L / kElemsPerThread;
+  while (3 * NBc * L < ept * 32) NBc *= 2;
+  while ((3 * NBc * L) % ept != 0) NBc *= 2;  // mixed-radix lengths
+  const int nth = 3 * NBc * L / ept;
   const size_t smem = ((size_t)3 * NBc * L + L) * sizeof(cx<T>);
   const long grid = nslabs * ((ncols + NBc - 1) / NBc);
-  const bool fix = L >= 16 && L % 16 == 0;
-  const RadixPlan rp = make_radix_plan(L);
+  const bool fix = L >= ept && L % ept == 0;
   auto kern = rp.pow2 ? (fix ? k_fft3c<T, Op, true, false> : k_fft3c<T, Op, false, false>)
                       : (fix ? k_fft3c<T, Op, true, true> : k_fft3c<T, Op, false, true>);
   if (smem > 48 * 1024)

@@ -129,13 +129,15 @@ void launch_contig(const cx<T>* in, cx<T>* out, const uint8_t* mask, const uint8
   int per_cta = 4096;  // complex values per CTA: at most 256 threads
   while (per_cta > 512 && per_cta > L && (nlines * L + per_cta - 1) / per_cta < 2 * kSMs)
     per_cta /= 2;
+  const RadixPlan rp = make_radix_plan(L);
+  const int ept = rp.pow2 ? kElemsPerThread : kElemsMR;  // values per thread
+  if (!rp.pow2) per_cta /= 2;                               // 256 threads at most
   int NB = floor_pow2(std::max(1, per_cta / L));
-  while (NB * L < kElemsPerThread * 32) NB *= 2;  // at least one warp
-  while ((NB * L) % kElemsPerThread != 0) NB *= 2;  // mixed-radix lengths
-  const int nth = NB * L / kElemsPerThread;
+  while (NB * L < ept * 32) NB *= 2;  // at least one warp
+  while ((NB * L) % ept != 0) NB *= 2;  // mixed-radix lengths
+  const int nth = NB * L / ept;
   const size_t smem = ((size_t)L * (NB + 1) + L) * sizeof(cx<T>);
   const long grid = (nlines + NB - 1) / NB;
-  const RadixPlan rp = make_radix_plan(L);
   auto kern = rp.pow2 ? k_fft_contig<T, INV, false> : k_fft_contig<T, INV, true>;
   allow_smem(kern, smem);
   note_launch();
@@ -165,18 +167,19 @@ void launch_strided(const cx<T>* in, cx<T>* out, long ncols, long nslabs, int L,
       if (done) return;
     }
   }
-  const int cap = 512 * kElemsPerThread;  // at most 512 threads
+  const RadixPlan rp = make_radix_plan(L);
+  const int ept = rp.pow2 ? kElemsPerThread : kElemsMR;  // values per thread
+  const int cap = (rp.pow2 ? 512 : 256) * ept;  // threads: 512, mixed radix 256
   int NB = sizeof(T) == 8 ? 8 : 16;
   NB = std::min<long>(NB, floor_pow2(ncols));
   while (NB * L > cap && NB > 1) NB /= 2;
   while (NB > 1 && NB * L > 1024 && nslabs * ((ncols + NB - 1) / NB) < 2 * kSMs) NB /= 2;
-  while (NB * L < kElemsPerThread * 32) NB *= 2;
-  while ((NB * L) % kElemsPerThread != 0) NB *= 2;  // mixed-radix lengths
-  const int nth = NB * L / kElemsPerThread;
+  while (NB * L < ept * 32) NB *= 2;
+  while ((NB * L) % ept != 0) NB *= 2;  // mixed-radix lengths
+  const int nth = NB * L / ept;
   const size_t smem = ((size_t)L * NB + L) * sizeof(cx<T>);
   const long grid = nslabs * ((ncols + NB - 1) / NB);
-  const bool fix = L >= 16 && L % 16 == 0;
-  const RadixPlan rp = make_radix_plan(L);
+  const bool fix = L >= ept && L % ept == 0;
   auto kern = rp.pow2 ? (fix ? k_fft_strided<T, INV, true, false> : k_fft_strided<T, INV, false, false>)
                       : (fix ? k_fft_strided<T, INV, true, true> : k_fft_strided<T, INV, false, true>);
   allow_smem(kern, smem);

@@ -122,13 +122,14 @@ struct KernelMul {
 //   y = a x                 (air voxel, a = alpha_tilde^{-1})
 // with coef = dx^3 / (2l 2m 2n) (the inverse transforms are unnormalised).
 template <typename T, bool MR>
-__global__ void __launch_bounds__(std::is_same<T, df>::value ? 256 : 512)
+__global__ void __launch_bounds__((MR || std::is_same<T, df>::value) ? 256 : 512)
     k_mv_epilogue(const cx<T>* __restrict__ buf1, const cx<T>* __restrict__ x,
                   cx<T>* __restrict__ y, const uint8_t* __restrict__ mat,
                   const cx<T>* __restrict__ ainv, int K1, long nlines, long nm, int l, int Lx,
                   T coef, const cx<T>* __restrict__ tw, int twshift, RadixPlan rp, int nb_sh,
                   const cx<T>* __restrict__ pv) {
   pdl_entry();
+  constexpr int EPT = elems_per_thread<MR>();
   const int NB = 1 << nb_sh;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* s = reinterpret_cast<cx<T>*>(smem_raw);
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(std::is_same<T, df>::value ? 256 : 512)
   const long line0 = (long)blockIdx.x * NB;
   const int nth = blockDim.x, tid = threadIdx.x;
 #pragma unroll 4
-  for (int i = 0; i < kElemsPerThread; ++i) {
+  for (int i = 0; i < EPT; ++i) {
     const int e = tid + i * nth;
     const int j = MR ? e % Lx : e & (Lx - 1);
     const int b = MR ? e / Lx : e >> rp.lg;
@@ -356,17 +357,18 @@ void matvec_core(dda_plan_s* p, int nrhs, const cx<T>* x, cx<T>* y, cudaStream_t
     }
   }
   {
-    const int cap = (std::is_same<T, df>::value ? 256 : 512) * kElemsPerThread;
+    const RadixPlan rp = make_radix_plan((int)Lx);
+    const int ept = rp.pow2 ? kElemsPerThread : kElemsMR;  // values per thread
+    const int cap = ((!rp.pow2 || std::is_same<T, df>::value) ? 256 : 512) * ept;
     int per_cta = std::min(4096, cap);
     while (per_cta > 512 && per_cta > Lx && (lines * Lx + per_cta - 1) / per_cta < 2 * 152)
       per_cta /= 2;
     int NB = 1;
     while (2 * NB * Lx <= per_cta) NB *= 2;
-    while (NB * Lx < kElemsPerThread * 32) NB *= 2;
-    while ((NB * Lx) % kElemsPerThread != 0) NB *= 2;  // mixed-radix lengths
-    const int nth = NB * (int)Lx / kElemsPerThread;
+    while (NB * Lx < ept * 32) NB *= 2;
+    while ((NB * Lx) % ept != 0) NB *= 2;  // mixed-radix lengths
+    const int nth = NB * (int)Lx / ept;
     const size_t smem = ((size_t)Lx * (NB + 1) + Lx) * sizeof(cx<T>);
-    const RadixPlan rp = make_radix_plan((int)Lx);
     auto kern = rp.pow2 ? k_mv_epilogue<T, false> : k_mv_epilogue<T, true>;
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

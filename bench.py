@@ -735,7 +735,7 @@ def compare_uneven_batch(runner, cap=600, smooth=True):
     return out
 
 
-def compare_many_waves(runner, nwaves_dirs=64, restart=20, chunk=8, cap=1500, edge=96):
+def compare_many_waves(runner, nwaves_dirs=64, restart=20, chunk=8, cap=1500, edge=128):
     """Many incident waves of one prism in one graph launch: the 96^3 prism
     (x = 30, m = 1.31, aspect 1) with 64 seeded directions (seed 1) x 2
     polarisations = 128 right-hand sides advancing in lock step, GMRES(20)
@@ -1135,10 +1135,12 @@ def run_ours(args, rank, world):
                  lambda: compare_uneven_batch(runner)),
                 ("uneven batch: the same 32 prisms in power-of-two boxes, one graph launch",
                  lambda: compare_uneven_batch(runner, smooth=False)),
-                ("128 waves of the 96^3 prism (x=30, m=1.31) in its 96^3 box, one graph launch",
-                 lambda: compare_many_waves(runner)),
-                ("128 waves of the 96^3 prism air padded to 128^3, one graph launch",
-                 lambda: compare_many_waves(runner, edge=128))):
+                ("128 waves of the 96^3 prism (x=30, m=1.31) air padded to 128^3, one graph launch",
+                 lambda: compare_many_waves(runner, edge=128)),
+                ("8 waves of the 96^3 prism in its own 96^3 box (mixed radix), one graph launch",
+                 lambda: compare_many_waves(runner, nwaves_dirs=4, edge=96)),
+                ("the same 8 waves air padded to 128^3, one graph launch",
+                 lambda: compare_many_waves(runner, nwaves_dirs=4, edge=128))):
             try:
                 comparisons[key] = fn()
             except Exception as exc:  # a side measurement must not cost the bench line

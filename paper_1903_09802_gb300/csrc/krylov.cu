@@ -1340,6 +1340,18 @@ struct Ctx {
       // at most 8192 / S values, so that a block's chunk of the S Newton
       // vectors (64 KB in complex64), which every warp reads, stays in L1
       bnb = (int)std::max<long>((304 + nrhs - 1) / nrhs, (nu * S + 8191) / 8192);
+      // whole waves: a batch of at least one wave of resident blocks (152
+      // SMs x 3 in complex64) is rounded to the nearest multiple of it, so
+      // that no short last wave doubles the pass (480 blocks were 1.05
+      // waves); that adds at most half a wave, within the partial-sum store
+      {
+        const long resident = 152L * (sizeof(T) == 4 ? 3 : 1);
+        const long total = (long)bnb * nrhs;
+        if (total >= resident) {
+          const long waves = (total + resident / 2) / resident;
+          bnb = (int)std::max<long>(1, waves * resident / nrhs);
+        }
+      }
       bgrid = dim3(bnb, nrhs);
     }
   }

@@ -213,7 +213,8 @@ class Runner:
 
 def traffic_from_profiles(kernel):
     """DRAM bytes per launch recorded by the committed ncu summary, if still
-    current: {box "lxmxn" or "*": bytes}."""
+    current (the sources it names under `source_files`, else all CUDA
+    sources, hash to its `source_hash`): {box "lxmxn" or "*": bytes}."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_64cube.md")
     if not os.path.exists(path):
         return None
@@ -222,7 +223,8 @@ def traffic_from_profiles(kernel):
         if line.startswith("- ") and ":" in line:
             k, v = line[2:].split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("source_hash") != source_hash():
+    files = vals.get("source_files", "").split() or None
+    if vals.get("source_hash") != source_hash(files):
         return None
     out = {}
     for k, v in vals.items():
@@ -235,10 +237,17 @@ def traffic_from_profiles(kernel):
     return out or None
 
 
-def source_hash():
+def source_hash(files=None):
+    """sha256 (16 hex digits) of the CUDA sources: all of them, or the named
+    files of the source directory (sorted)."""
     import glob
+    csrc = os.path.join(ROOT, "paper_1903_09802_gb300", "csrc")
+    paths = (sorted(glob.glob(os.path.join(csrc, "*"))) if files is None
+             else [os.path.join(csrc, f) for f in sorted(files)])
     hs = hashlib.sha256()
-    for p in sorted(glob.glob(os.path.join(ROOT, "paper_1903_09802_gb300", "csrc", "*"))):
+    for p in paths:
+        if not os.path.exists(p):
+            return None
         hs.update(open(p, "rb").read())
     return hs.hexdigest()[:16]
 

@@ -18,7 +18,7 @@ def test_traffic_summary_guarded_by_source_hash(monkeypatch):
     if cur is not None:
         assert set(cur) >= {"64x64x32", "64x64x64", "64x64x128"}
         assert all(v > 0 for v in cur.values())
-    monkeypatch.setattr(bench, "source_hash", lambda: "0" * 16)
+    monkeypatch.setattr(bench, "source_hash", lambda files=None: "0" * 16)
     assert bench.traffic_from_profiles("mv_z_mul") is None
     assert bench.traffic_from_profiles("no_such_kernel") is None
 

@@ -259,9 +259,9 @@ dda_status_t dda_precond_apply(dda_plan_t plan, int32_t prec, int32_t nrhs, cons
  * (each call overwrites everything it reads): calls that overlap on the GPU,
  * on any streams, race and give wrong results.  Uses the plan's launch
  * schedule like dda_precond_apply.  Allocates nothing.  Power-of-two boxes
- * only (DDA_ERR_UNSUPPORTED_SIZE otherwise): the mixed-radix kernels carry a
- * local stack frame whose first launch may make the driver enlarge the
- * context's local-memory reservation. */
+ * only (DDA_ERR_UNSUPPORTED_SIZE otherwise): the FP64 mixed-radix kernels
+ * carry a local stack frame whose first launch may make the driver enlarge
+ * the context's local-memory reservation. */
 dda_status_t dda_precond_apply_noalloc(dda_plan_t plan, int32_t prec, int32_t nrhs,
                                        const void* d_v, void* d_z, void* stream);
 

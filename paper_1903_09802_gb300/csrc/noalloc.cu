@@ -62,10 +62,9 @@ extern "C" dda_status_t dda_precond_apply_noalloc(dda_plan_t p, int32_t prec, in
     return fail(DDA_ERR_INVALID_ARG, "dda_precond_apply_noalloc: prec must be DDA_C128 or DDA_C64");
   if ((prec == DDA_C128 && !p->has128) || (prec == DDA_C64 && !p->has64))
     return fail(DDA_ERR_INVALID_ARG, "dda_precond_apply_noalloc: plan lacks that precision");
-  // Mixed-radix transforms run kernels with a local stack frame of a few
-  // kilobytes per thread, whose first launch may make the driver enlarge
-  // the context's local-memory reservation, an allocation: power-of-two
-  // boxes only.
+  // Mixed-radix transforms in FP64 run kernels with a local stack frame,
+  // whose first launch may make the driver enlarge the context's
+  // local-memory reservation, an allocation: power-of-two boxes only.
   if (!is_pow2(p->l) || !is_pow2(p->m) || !is_pow2(p->n))
     return fail(DDA_ERR_UNSUPPORTED_SIZE,
                 "dda_precond_apply_noalloc: box edges must be powers of two (mixed-radix "

@@ -51,6 +51,24 @@ def test_roofline_arithmetic(monkeypatch):
     assert r["share_of_profiled_kernel_time"]["a"] == pytest.approx(5.0 / 6.5, abs=1e-4)
 
 
+class _FakeReplay:
+    """Replays of the class 'mv_z_mul': 20 launches of 0.1 ms (1e8 bytes each)
+    on box 4x4x2 and of 0.3 ms (3e8 bytes each) on 4x4x4."""
+
+    def replay_matvec(self, dims, reps):
+        per = {(4, 4, 2): (0.1, 1e8), (4, 4, 4): (0.3, 3e8)}[dims]
+        return {"mv_z_mul": (per[0] * reps, reps, per[1] * reps)}
+
+
+def test_matvec_replay_weights_boxes_by_step_launches():
+    # the step launched the class 3 times on 4x4x2 and once on 4x4x4
+    r = bench.matvec_replay(_FakeReplay(), "mv_z_mul", {(4, 4, 2): 3, (4, 4, 4): 1, (8, 8, 8): 0})
+    assert r["avg_launch_us"] == pytest.approx(1e3 * (3 * 0.1 + 0.3) / 4)
+    # (3 * 1e8 + 3e8) / 4 bytes per launch over 150 us
+    assert r["achieved"] == pytest.approx(1.5e8 / 150e-6 / 1e9, rel=1e-3)
+    assert r["us_per_launch_by_box"] == {"4x4x2": 100.0, "4x4x4": 300.0}
+
+
 def test_roofline_traffic_null_without_summary(monkeypatch):
     monkeypatch.setattr(bench, "traffic_from_profiles", lambda k: None)
     assert bench.roofline(_FakeRunner(), 1000.0, "measured")["traffic"] is None

@@ -21,17 +21,20 @@ within the paper's iteration caps; they are timed separately to those caps
 Metric: time-to-solve per right-hand side (ms, lower is better), whole job:
 elapsed device time of K steps / (12 K N).  L2 is flushed (a 512 MB write)
 before every timed step.  The JSON line also carries the roofline of the
-dominant kernel measured live with CUDA events (and the matvec's passes at
-the 128^3 box), the CPU oracle timed on a bounded sample on one core and on
-every host core, the end-to-end figure through host buffers, the number of
-library kernel launches, the SM clocks sampled during the timed region and,
-untimed, comparisons: the step with plain GMRES(50) (Arnoldi) instead of the
-s-step form, preconditioned vs unpreconditioned per system, solver
-variants, complex128 vs mixed precision on the same workload, the m = 1.78
-systems to the caps, the complex64 matvec against cuFFT (torch.fft), the
-128^3 prism in both precisions, the 32^3 twin against the oracle's stored
-FP64 cross sections, the 256^3 solve and an uneven batch of 32 prisms in
-one graph launch.
+dominant kernel measured live with CUDA events (its launches also replayed
+back to back when it is a matvec pass; and the matvec's passes at the 128^3
+box), the CPU oracle timed on a bounded sample on one core and on every host
+core, the end-to-end figure through host buffers, the number of library
+kernel launches, the SM clocks sampled during the timed region and, untimed,
+comparisons: the step with plain GMRES(50) (Arnoldi) instead of the s-step
+form, preconditioned vs unpreconditioned per system, solver variants,
+complex128 vs mixed precision on the same workload, the m = 1.78 systems to
+the caps, the complex64 matvec against cuFFT (torch.fft), the 128^3 prism in
+both precisions, the 32^3 twin against the oracle's stored FP64 cross
+sections, the 256^3 solve, an uneven batch of 32 prisms in power-of-two and
+in even 7-smooth (mixed-radix) boxes, and 128 waves of the 96^3 prism padded
+to 128^3 (8 of them also in the prism's own 96^3 box), each batch one graph
+launch.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
